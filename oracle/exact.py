@@ -1,0 +1,125 @@
+"""Exact (unregularised) OT values used to pin the oracle and to measure true optimality gaps.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  The paper measures errors against an exact
+network-simplex solution (Sec. 5); here the exact optimum comes from textbook special cases and
+from the HiGHS LP solver (a library routine):
+
+* brute force over permutations (uniform marginals, n <= 8; by Birkhoff-von Neumann an optimal
+  plan is a permutation matrix scaled by 1/n);
+* the monotone (north-west corner) coupling of sorted supports for 1-D problems with a convex
+  cost of x - y, optimal for any n;
+* the full transportation LP (n <= ~300);
+* column generation for large n: the LP restricted to a candidate arc set, priced against all
+  n^2 reduced costs C_ij - f_i - g_j; it stops only when no arc prices out, so the returned dual
+  (f, g) is feasible to the pricing tolerance and certifies the value.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+from scipy.optimize import linprog
+from scipy.sparse import coo_matrix
+
+
+def brute_force_uniform(C: np.ndarray) -> float:
+    """min over permutations sigma of (1/n) sum_i C[i, sigma(i)]."""
+    n = C.shape[0]
+    best = np.inf
+    for perm in itertools.permutations(range(n)):
+        best = min(best, float(C[np.arange(n), list(perm)].sum()))
+    return best / n
+
+
+def monotone_1d(x: np.ndarray, y: np.ndarray, r: np.ndarray, c: np.ndarray, cost) -> float:
+    """OT between sum r_i delta_{x_i} and sum c_j delta_{y_j} on the real line for a convex
+    cost(x - y): the north-west corner coupling of the sorted supports."""
+    ix, iy = np.argsort(x, kind="stable"), np.argsort(y, kind="stable")
+    xs, rs, ys, cs = x[ix], r[ix].astype(np.float64).copy(), y[iy], c[iy].astype(np.float64).copy()
+    i = j = 0
+    total = 0.0
+    while i < len(xs) and j < len(ys):
+        m = min(rs[i], cs[j])
+        total += m * cost(xs[i] - ys[j])
+        rs[i] -= m
+        cs[j] -= m
+        if rs[i] <= cs[j]:
+            i += 1
+        else:
+            j += 1
+    return total
+
+
+def _lp(Cflat, rows, cols, n, r, c):
+    m = len(Cflat)
+    A = coo_matrix((np.ones(2 * m), (np.concatenate([rows, n + cols]),
+                                     np.concatenate([np.arange(m), np.arange(m)]))),
+                   shape=(2 * n, m)).tocsr()
+    b = np.concatenate([r, c])
+    res = linprog(Cflat, A_eq=A, b_eq=b, bounds=(0, None), method="highs",
+                  options={"primal_feasibility_tolerance": 1e-10, "dual_feasibility_tolerance": 1e-10})
+    if res.status != 0:
+        raise RuntimeError(f"HiGHS failed: {res.message}")
+    duals = res.eqlin.marginals
+    return res.fun, duals[:n], duals[n:], res.x
+
+
+def exact_ot_lp(C: np.ndarray, r: np.ndarray, c: np.ndarray) -> float:
+    """Full transportation LP over all n^2 arcs."""
+    n = C.shape[0]
+    rows, cols = np.divmod(np.arange(n * n), n)
+    val, _, _, _ = _lp(np.asarray(C, np.float64).reshape(-1), rows, cols, n,
+                       np.asarray(r, np.float64), np.asarray(c, np.float64))
+    return float(val)
+
+
+def _northwest(r, c):
+    """Arcs of the north-west corner rule: a feasible basis of the transportation polytope."""
+    r, c = r.copy(), c.copy()
+    i = j = 0
+    arcs = []
+    n = len(r)
+    while i < n and j < n:
+        arcs.append((i, j))
+        m = min(r[i], c[j])
+        r[i] -= m
+        c[j] -= m
+        if r[i] <= c[j] and i < n - 1:
+            i += 1
+        else:
+            j += 1
+    return arcs
+
+
+def exact_ot_colgen(C: np.ndarray, r: np.ndarray, c: np.ndarray, k_init: int = 8,
+                    tol: float = 1e-11, max_rounds: int = 200, add_per_row: int = 8):
+    """Exact OT by column generation.  Returns (value, f, g, rounds).
+    Candidate arcs start as the k_init cheapest arcs of every row and column plus a north-west
+    corner basis (so the restricted LP is feasible); each round adds, per row, the add_per_row
+    most negative reduced-cost arcs until none is below -tol."""
+    C = np.asarray(C, np.float64)
+    r = np.asarray(r, np.float64)
+    c = np.asarray(c, np.float64)
+    n = C.shape[0]
+    cand = set()
+    part_r = np.argpartition(C, k_init, axis=1)[:, :k_init]
+    for i in range(n):
+        cand.update((i, int(j)) for j in part_r[i])
+    part_c = np.argpartition(C, k_init, axis=0)[:k_init, :]
+    for j in range(n):
+        cand.update((int(i), j) for i in part_c[:, j])
+    cand.update(_northwest(r, c))
+    for rnd in range(max_rounds):
+        arr = np.array(sorted(cand), dtype=np.int64)
+        val, f, g, _ = _lp(C[arr[:, 0], arr[:, 1]], arr[:, 0], arr[:, 1], n, r, c)
+        red = C - f[:, None] - g[None, :]
+        neg = red < -tol
+        if not neg.any():
+            return float(val), f, g, rnd + 1
+        k = min(add_per_row, n - 1)
+        idx = np.argpartition(red, k, axis=1)[:, :k]
+        for i in np.nonzero(neg.any(axis=1))[0]:
+            for j in idx[i]:
+                if red[i, j] < -tol:
+                    cand.add((int(i), int(j)))
+    raise RuntimeError("column generation did not converge")
