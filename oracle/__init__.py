@@ -181,7 +181,7 @@ def solve(C, r, c, eps_target: float | None = None, gamma_f: float | None = None
     r, c = _f64(r), _f64(c)
     prm = params(**kw)
     if gamma_f is None:
-        H = min(entropy(r), entropy(c))
+        H = max(min(entropy(r), entropy(c)), 1e-12)
         gamma_f = gamma_f_for_eps(H, eps_target, prm.gamma_i, prm.q, prm.p)
     u, v, rc, st, log = mdot(C, r, c, gamma_f=gamma_f, **kw)
     cost, _ = round_plan(C, u, v, gamma_f, r, c)

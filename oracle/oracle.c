@@ -311,7 +311,9 @@ int or_sinkhorn(int n, const double* C, double gamma, const double* r, const dou
 int or_mdot(int n, const double* C, const double* r, const double* c, const or_params* prm,
             double* u, double* v, or_stats* st, double* stage_log, int max_log)
 {
-    const double H = fmin(or_entropy(n, r), or_entropy(n, c));      /* H_min(r, c) */
+    /* H_min(r, c); reading: floored at 1e-12 so that a point-mass marginal (H_min = 0) still gets
+     * a positive smoothing weight (Alg. 1 line 4) instead of log 0 */
+    const double H = fmax(fmin(or_entropy(n, r), or_entropy(n, c)), 1e-12);
     double* rt = (double*)malloc(sizeof(double) * (size_t)n);
     double* ct = (double*)malloc(sizeof(double) * (size_t)n);
     double* u_prev = (double*)malloc(sizeof(double) * (size_t)n);
@@ -336,7 +338,9 @@ int or_mdot(int n, const double* C, const double* r, const double* c, const or_p
             memcpy(u_prev, u, sizeof(double) * (size_t)n);
             memcpy(v_prev, v, sizeof(double) * (size_t)n);
         }
-        double tol = eps_d / 2.0;                                   /* line 6 */
+        /* line 6; reading: a tolerance below 1e-13 cannot be resolved by fp64 sums of the
+         * marginals and would never be met, so it is floored there */
+        double tol = fmax(eps_d / 2.0, 1e-13);
         if (gamma == prm->gamma_f && prm->final_tol > 0.0) tol = prm->final_tol;
         int rc;
         if (prm->projector == 1)

@@ -362,3 +362,18 @@ def test_entropy_and_gamma_f_mapping():
     k = math.log(g / 16.0) / math.log(q)
     assert g >= target * (1 - 1e-12) and g / q < target
     assert abs(k - round(k)) < 1e-9
+
+
+def test_point_mass_marginal_has_a_single_feasible_plan():
+    """r = e_i0 (H_min = 0): U(r, c) = {e_i0 c^T}, so the rounded cost is sum_j c_j C_i0j."""
+    n, i0 = 7, 3
+    rng = np.random.default_rng(23)
+    C = rng.uniform(0, 1, (n, n))
+    r = np.zeros(n); r[i0] = 1.0
+    c = rng.uniform(0.2, 1, n); c /= c.sum()
+    res = O.solve(C, r, c, gamma_f=2.0 ** 10)
+    assert abs(res.cost - float(c @ C[i0])) < 1e-12
+    assert res.lb <= res.cost + 1e-12
+    one = np.ones(1)
+    res1 = O.solve(np.array([[0.3]]), one, one, gamma_f=2.0 ** 10)
+    assert abs(res1.cost - 0.3) < 1e-15
