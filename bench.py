@@ -1,0 +1,346 @@
+"""Benchmark: time to rounded-plan optimality gap 1e-6 at n = 4096 (MDOT-PNCG, one GB300).
+
+One step = one full solve through the C ABI (mdot_solve): H_min and validation, every MDOT stage
+(PNCG + line search on the device), rounding (Alg. 3) and the lower bound, on a 64 x 64 grid-
+histogram problem with squared-Euclidean cost (fp32 C, 64 MiB), eps_target = 1e-6 (gamma_f from
+Prop. 2).  Inputs are resident in HBM when the timed region starts; L2 is flushed (256 MiB write)
+between timed steps.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU FP64 oracle on this machine's host cores instead (a bounded sample
+of its dual evaluations, scaled by the evaluation count of the full oracle solve).
+N > 1 (torchrun): every rank solves its own instance (replicas, weak scaling); rank 0 reports the
+max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_GRID = 64                 # n = 4096
+SEED = 2000
+EPS = 1e-6
+METRIC = "time to gap 1e-6 at n=4096"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-sample-evals", type=int, default=0, help="oracle evaluations in the CPU sample")
+    return ap.parse_args()
+
+
+def golden_case(kind="l2sq"):
+    path = os.path.join(ROOT, "tests", "golden", f"grid{N_GRID * N_GRID}.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        for c in json.load(fh)["cases"]:
+            if c["kind"] == kind and c["seed"] == SEED and abs(c["eps_target"] - EPS) < 1e-15:
+                return c
+    return None
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index=0):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.index = index
+
+    def __enter__(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        try:
+            rows = [l.split(",") for l in open(self.path).read().strip().splitlines() if l.strip()]
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() in ("active", "1", "0x1"):
+                        reasons.append(nm) if False else reasons.add(nm)
+            except Exception:
+                continue
+        if sm:
+            sm.sort()
+            out["sm_mhz"] = sm[len(sm) // 2]
+            out["sm_max_mhz"] = max(mx)
+            out["samples"] = len(sm)
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+# ---------------------------------------------------------------------------------------------
+# reference arm and CPU baseline: the oracle as it stands, on the host cores
+# ---------------------------------------------------------------------------------------------
+def oracle_sample(n_evals: int):
+    """Time n_evals oracle dual evaluations of the n = 4096 problem; return seconds per eval."""
+    import numpy as np
+    import oracle as O
+    from paper_2307_08507_gb300 import inputs as I
+    p = I.grid_problem(N_GRID, SEED)
+    C = p.C.astype(np.float64)
+    gamma = 2.0 ** 12
+    u, v = np.log(p.r), np.log(p.c)
+    O.dual_eval(C[:64, :64], u[:64], v[:64], gamma)          # load the library outside the timing
+    t0 = time.perf_counter()
+    for _ in range(n_evals):
+        O.dual_eval(C, u, v, gamma)
+    return (time.perf_counter() - t0) / n_evals
+
+
+def cpu_solve_estimate(n_evals: int):
+    g = golden_case()
+    per_eval = oracle_sample(n_evals)
+    evals = g["oracle_evals"] if g else 3000
+    return per_eval * evals, per_eval, evals
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    n_evals = args.cpu_sample_evals or 4
+    for _ in range(args.warmup):
+        oracle_sample(1)
+    vals = []
+    for _ in range(args.steps):
+        est, per_eval, evals = cpu_solve_estimate(n_evals)
+        vals.append(est)
+    value = sum(vals) / len(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded grid histograms, Sec. 5.1 shapes)",
+        "config": {"workload": "grid64x64_l2sq_n4096_eps1e-6", "n": N_GRID * N_GRID, "seed": SEED,
+                   "eps_target": EPS, "l2": "oracle on CPU"},
+        "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+                         "sample": f"{n_evals} FP64 dual evaluations at n=4096 per step, scaled by the "
+                                   f"{evals} evaluations of the full oracle solve"},
+        "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    import paper_2307_08507_gb300 as M
+    from paper_2307_08507_gb300 import inputs as I
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    p = I.grid_problem(N_GRID, SEED + rank)
+    n = p.n
+    stream = torch.cuda.current_stream()
+    h = M.Handle(16384, stream)
+    r = torch.from_numpy(p.r).to(dev)
+    c = torch.from_numpy(p.c).to(dev)
+    C = torch.from_numpy(p.C).to(dev)
+    u = torch.empty(n, dtype=torch.float64, device=dev)
+    v = torch.empty(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    prm = M.default_params()
+    prm_prof = M.default_params(profile=1)
+
+    def step(params):
+        return h.solve(r, c, C, EPS, params, u_out=u, v_out=v)[2]
+
+    for _ in range(args.warmup):
+        res = step(prm)
+    torch.cuda.synchronize()
+
+    times = []
+    results = []
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            flush.fill_(1.0)                      # evict C from L2 between steps
+            ev0.record(stream)
+            res = step(prm)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            times.append(ev0.elapsed_time(ev1) / 1e3)
+            results.append(res)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+    t_step = sum(times) / len(times)
+    if dist is not None:
+        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    res = results[-1]
+    info = res.info
+
+    # dominant kernel (fp32-entry stage launches): per-launch device time from CUDA events
+    # recorded by the library on its stream, and algorithmic bytes = 4 n^2 per evaluation
+    flush.fill_(1.0)
+    res_p = step(prm_prof)
+    ip = res_p.info
+    evals32 = ip.evals - ip.evals_fp64
+    launches32 = max(1, ip.stage_launches_fp32)
+    bytes_per_launch = 4.0 * n * n * evals32 / launches32
+    t_launch = ip.t_stage_fp32_ms / 1e3 / launches32
+    hbm, peak_kind = peaks()
+    achieved = bytes_per_launch / t_launch / 1e9 if t_launch > 0 else None
+
+    # single dual evaluation (K1 + K2, one pass, fp32 entries), n = 4096 and n = 16384
+    dual = {}
+    for kk in (64, 128):
+        q = I.grid_problem(kk, SEED)
+        Cq = torch.from_numpy(q.C).to(dev)
+        uq = torch.from_numpy(np.log(q.r)).to(dev)
+        vq = torch.from_numpy(np.log(q.c)).to(dev)
+        gam = 2.0 ** 12
+        lr, _ = h.dual_eval(uq, vq, gam, Cq)
+        for _ in range(3):
+            h.dual_eval(uq, vq, gam, Cq, ref_log_rP=lr)
+        ts = []
+        for _ in range(10):
+            flush.fill_(1.0)
+            ev0.record(stream)
+            h.dual_eval(uq, vq, gam, Cq, ref_log_rP=lr)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(ev0.elapsed_time(ev1) / 1e3)
+        tmed = sorted(ts)[len(ts) // 2]
+        gbs = 4.0 * q.n * q.n / tmed / 1e9
+        dual[f"n{q.n}"] = {"us": tmed * 1e6, "GBps": gbs, "frac_hbm": gbs / hbm}
+        del Cq
+
+    # end to end through the public C ABI with host buffers (copies inside the timed region)
+    Ch = torch.from_numpy(p.C).pin_memory().numpy()
+    rh = torch.from_numpy(p.r).pin_memory().numpy()
+    ch = torch.from_numpy(p.c).pin_memory().numpy()
+    uh = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+    vh = torch.empty(n, dtype=torch.float64).pin_memory().numpy()
+    h.solve_host(rh, ch, Ch, EPS, prm, u_out=uh, v_out=vh)
+    e2e = []
+    for _ in range(max(1, args.steps)):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, rr = h.solve_host(rh, ch, Ch, EPS, prm, u_out=uh, v_out=vh)
+        e2e.append(time.perf_counter() - t0)
+    e2e_t = sum(e2e) / len(e2e)
+
+    g = golden_case()
+    true_gap = (res.cost - g["exact_ot"]) if g else None
+    cpu = None
+    if rank == 0 and world == 1:
+        n_evals = args.cpu_sample_evals or 40
+        est, per_eval, evals = cpu_solve_estimate(n_evals)
+        cpu = {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
+               "sample": f"{n_evals} FP64 dual evaluations of the same n=4096 problem "
+                         f"({per_eval:.3f} s each), scaled by the {evals} evaluations of the full "
+                         f"oracle solve"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded grid histograms, Sec. 5.1 shapes)",
+            "config": {"workload": "grid64x64_l2sq_n4096_eps1e-6", "n": n, "seed": SEED,
+                       "eps_target": EPS, "gamma_f": info.gamma_f, "cost": "C fp32 dense, 64 MiB",
+                       "l2": "flushed (256 MiB write) between timed steps", "replicas": world},
+            "result": {"status": M.status_string(res.status), "cost": res.cost,
+                       "true_gap": true_gap, "gap_cert": res.gap_cert,
+                       "oracle_cost": g["oracle_cost"] if g else None,
+                       "cost_minus_oracle": (res.cost - g["oracle_cost"]) if g else None,
+                       "evals": info.evals, "evals_fp64": info.evals_fp64, "iters": info.iters,
+                       "stages": info.stages, "grad_l1": info.grad_l1},
+            "roofline": {"kernel": "stage_kernel<fp32 entries> (one MDOT stage: PNCG + line search)",
+                         "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                         "peak_kind": peak_kind,
+                         "bytes_per_launch": bytes_per_launch, "us_per_launch": t_launch * 1e6,
+                         "launch_times_ms": {"stage_fp32": ip.t_stage_fp32_ms, "stage_fp64": ip.t_stage_fp64_ms,
+                                             "round": ip.t_round_ms, "bound": ip.t_bound_ms}},
+            "dual_eval": dual,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_t, "unit": "s", "h2d_bytes_per_step": 4 * n * n + 16 * n,
+                    "d2h_bytes_per_step": 16 * n},
+            "gpu_launches": info.launches,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

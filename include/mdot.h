@@ -1,0 +1,185 @@
+/*
+ * mdot.h -- C ABI of the GB300 (sm_103a) MDOT-PNCG library.
+ *
+ * Method: Kemertas, Jepson, Farahmand, "Efficient and Accurate Optimal Transport with Mirror
+ * Descent and Conjugate Gradients" (arXiv 2307.08507).  The library solves the discrete optimal
+ * transport problem  min_{P in U(r, c)} <P, C>  (Sec. 2.1) by MDOT (Alg. 1): a sequence of
+ * entropic problems at growing inverse temperature gamma, each solved in the dual (Eq. (4)) by
+ * PNCG (Alg. 2) with the approximate-Wolfe line search of App. B, warm-started by Eq. (13), and
+ * finally rounded onto U(r, c) by Alg. 3.
+ *
+ * Conventions used throughout (the paper's):
+ *   P_ij(u, v; gamma) = exp(u_i + v_j - gamma C_ij)          (Eq. (2))
+ *   gamma is the INVERSE temperature; it grows from gamma_i to gamma_f.
+ *   Potentials u, v are in log scale; f = u / gamma_f, g = v / gamma_f are the same potentials in
+ *   cost units.  (u, v) and (u + d, v - d) describe the same plan (footnote to Prop. 1).
+ *
+ * Memory and ownership:
+ *   - Every array argument is a DEVICE pointer (CUDA global memory on the handle's device) unless
+ *     the parameter name ends in _host or the function name ends in _host.  Scalars returned
+ *     through pointers (cost_out, gap_out, info) are HOST pointers.
+ *   - Vectors of length n are dense and contiguous; a cost matrix is n x n, row-major, float32,
+ *     leading dimension n, entries in [0, 1] (Sec. 2.1 assumes C in [0, 1]^{n x n}).
+ *   - The caller owns all inputs and outputs.  The library never frees or retains caller memory
+ *     past the call.  The handle owns its workspace (allocated once in mdot_create).
+ *   - All work is ordered on the handle's CUDA stream; the calls return after the results are
+ *     complete (they synchronise that stream) unless stated otherwise.
+ *
+ * Errors: every entry point returns an mdot_status.  MDOT_ERR_INVALID_ARG leaves outputs
+ * untouched.  MDOT_ERR_NOT_CONVERGED still fills every output with the best iterate.
+ * MDOT_ERR_CUDA means a CUDA call failed (the message is in mdot_last_error()).
+ */
+#ifndef MDOT_H
+#define MDOT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum mdot_status {
+    MDOT_OK = 0,
+    MDOT_ERR_INVALID_ARG = 1,     /* bad size, null pointer, out-of-range parameter          */
+    MDOT_ERR_NOT_CONVERGED = 2,   /* an iteration cap was hit; outputs hold the best iterate */
+    MDOT_ERR_NUMERIC = 3,         /* a non-finite value appeared where none is allowed       */
+    MDOT_ERR_TIMEOUT = 4,         /* a bounded device-side wait gave up                      */
+    MDOT_ERR_OOM = 5,             /* workspace allocation failed                             */
+    MDOT_ERR_CUDA = 6,            /* a CUDA runtime call failed                              */
+    MDOT_NOT_READY = 7            /* asynchronous result not available yet                   */
+} mdot_status;
+
+/* Arithmetic used for the per-entry work of a dual evaluation. */
+typedef enum mdot_precision {
+    MDOT_PREC_AUTO = 0,   /* fp32 entries while its noise floor is below the stage tolerance,
+                             fp64 entries for the final stage when it is not (and for n <= 512) */
+    MDOT_PREC_FP32 = 1,   /* always fp32 entries (exact cost-unit difference, ex2.approx)      */
+    MDOT_PREC_FP64 = 2    /* always fp64 entries                                              */
+} mdot_precision;
+
+/* Parameters of Alg. 1 / Alg. 2 / App. B.  Fill with mdot_default_params, then override. */
+typedef struct mdot_params {
+    double  gamma_i;        /* first inverse temperature; Sec. 5.2 default 2^4                     */
+    double  gamma_f;        /* final inverse temperature; <= 0: derived from eps_target (Prop. 2)  */
+    double  p;              /* stopping exponent, eps_d = H_min / gamma^p (Alg. 1 line 3); 1.5      */
+    double  q;              /* decay factor, gamma <- min(q gamma, gamma_f) (Alg. 1 line 8); 2^(1/3) */
+    double  ls_c1, ls_c2;   /* approximate Wolfe constants (App. B, Eq. (24)); 0.1 and 0.5          */
+    int32_t ls_max_trials;  /* phi' evaluations per line search before the lower end is taken; 50   */
+    int32_t max_iter;       /* PNCG iterations per stage; 100000                                    */
+    int32_t precision;      /* mdot_precision                                                      */
+    int32_t warm_start;     /* 0: Taylor step, Eq. (13); 1: eps-scaling (Sec. 3.3.1); 2: none       */
+    double  final_tol;      /* > 0: ||grad g||_1 target of the final stage instead of eps_d / 2     */
+    double  fp32_floor;     /* ||grad g||_1 below which fp32 entries are not trusted; 3e-7          */
+    int32_t profile;        /* non-zero: time each kernel launch with CUDA events (mdot_info t_*)    */
+    int32_t reserved[7];
+} mdot_params;
+
+/* Diagnostics of one solve. */
+typedef struct mdot_info {
+    int32_t status;         /* mdot_status of the solve                                          */
+    int32_t stages;         /* MDOT outer iterations run                                         */
+    int64_t evals;          /* dual evaluations (one pass over C each), all stages               */
+    int64_t evals_fp64;     /* of which with fp64 entries                                        */
+    int64_t iters;          /* PNCG iterations, all stages                                       */
+    int64_t ls_trials;      /* line-search phi' evaluations                                      */
+    double  grad_l1;        /* ||grad g(gamma_f, r~, c~)||_1 at exit                             */
+    double  gamma_f;        /* final inverse temperature used                                    */
+    double  H_min;          /* min(H(r), H(c))                                                   */
+    double  cost;           /* <G, C> of the rounded plan G                                      */
+    double  lower_bound;    /* c-transform lower bound on the OT value                           */
+    double  gap_cert;       /* cost - lower_bound >= true optimality gap                          */
+    double  t_stage_fp32_ms;/* with profile: summed device time of the fp32-entry stage launches    */
+    double  t_stage_fp64_ms;/* with profile: summed device time of the fp64-entry stage launches    */
+    double  t_round_ms;     /* with profile: device time of the rounding launch                    */
+    double  t_bound_ms;     /* with profile: device time of the lower-bound launch                 */
+    int32_t launches;       /* kernel launches made by the call                                    */
+    int32_t stage_launches_fp32; /* stage launches with fp32 entries                               */
+    double  reserved[1];
+} mdot_info;
+
+typedef struct mdot_handle mdot_handle;
+
+/* Fill *prm with the defaults listed above (Sec. 5.2 values where the paper gives them). */
+void mdot_default_params(mdot_params* prm);
+
+/* Human-readable name of a status code (static storage). */
+const char* mdot_status_string(int32_t status);
+
+/* Message of the last CUDA error seen by this thread's calls, or "" (static thread storage). */
+const char* mdot_last_error(void);
+
+/*
+ * Create a handle for problems of size up to max_n on the current CUDA device.
+ * stream: a cudaStream_t (may be NULL for the legacy default stream), borrowed, not owned.
+ * Allocates O(max_n) workspace plus column partials of (SM count) x max_n floats.
+ * Errors: INVALID_ARG (h null, max_n < 1), OOM, CUDA.
+ */
+mdot_status mdot_create(mdot_handle** h, int64_t max_n, void* stream);
+
+/* Free the handle and its workspace.  NULL is accepted. */
+mdot_status mdot_destroy(mdot_handle* h);
+
+/*
+ * One dual evaluation (Alg. 2 lines 2-3): one pass over C giving both log-marginals of
+ * P(u, v; gamma):
+ *   log_rP[i] = u_i + LSE_j(v_j - gamma C_ij),   log_cP[j] = v_j + LSE_i(u_i - gamma C_ij).
+ * u, v: n doubles each.  C: n x n float32, row-major.  gamma > 0.
+ * ref_log_rP (nullable, n doubles): an estimate of log_rP, used only to scale the row sums;
+ *   when NULL an extra max pass over C computes the scales (so the call reads C twice).
+ * precision: MDOT_PREC_FP32 or MDOT_PREC_FP64 (AUTO means FP32).
+ * Outputs log_rP, log_cP (n doubles each).  Entries of P more than 2^120 below the largest row
+ * scale are flushed from the column sums.
+ */
+mdot_status mdot_dual_eval(mdot_handle* h, const double* u, const double* v, double gamma,
+                           const float* C, int64_t n, const double* ref_log_rP,
+                           int32_t precision, double* log_rP, double* log_cP);
+
+/*
+ * Alg. 3 applied to P = exp(u 1^T + 1 v^T - gamma C) (Alg. 1 line 12): the rounded plan
+ * G = X P Y + err_r err_c^T / ||err_r||_1 lies in U(r, c).  Returns <G, C> in *cost_out (host)
+ * without forming G; if G_out is non-null (device, n*n doubles, row-major) G is also written.
+ * r, c: n doubles each, the ORIGINAL marginals (non-negative, each summing to 1).
+ */
+mdot_status mdot_round(mdot_handle* h, const double* u, const double* v, double gamma,
+                       const float* C, const double* r, const double* c, int64_t n,
+                       double* cost_out, double* G_out);
+
+/*
+ * Lower bound on the OT value from the potential u at inverse temperature gamma
+ * (f = u / gamma): g'_j = min_i (C_ij - f_i), f'_i = min_j (C_ij - g'_j),
+ * *lb_out (host) = <f', r> + <g', c>  <=  min_{P in U(r,c)} <P, C>  (weak LP duality).
+ */
+mdot_status mdot_lower_bound(mdot_handle* h, const double* u, double gamma, const float* C,
+                             const double* r, const double* c, int64_t n, double* lb_out);
+
+/*
+ * MDOT-PNCG (Alg. 1 with Alg. 2 as the projector) followed by rounding (Alg. 3) and the lower
+ * bound above.
+ * r, c: n doubles each, non-negative, each summing to 1 within 1e-9 (Sec. 2: r, c in Delta_n).
+ * C: n x n float32 row-major in [0, 1].
+ * eps_target > 0: target optimality gap; used (when prm->gamma_f <= 0) to set
+ *   gamma_f = (5 H_min / (2 eps_target))^(1/p) rounded up onto gamma_i q^k (Prop. 2).
+ * prm: NULL for defaults.
+ * Outputs: u_out, v_out (device, n doubles each; the last MDOT iterate at gamma_f, log scale),
+ *   *cost_out = <G, C> of the rounded plan, *gap_out = certified gap (cost - lower bound),
+ *   *info (nullable) diagnostics.  Host pointers for the three scalars/structs.
+ */
+mdot_status mdot_solve(mdot_handle* h, const double* r, const double* c, const float* C,
+                       int64_t n, double eps_target, const mdot_params* prm,
+                       double* u_out, double* v_out, double* cost_out, double* gap_out,
+                       mdot_info* info);
+
+/*
+ * mdot_solve with every array in HOST memory: copies r, c (n doubles) and C (n*n floats) to the
+ * handle's device, solves, and copies u, v back (n doubles each).  The copies are part of the
+ * call.  Use for callers without device buffers; same errors as mdot_solve.
+ */
+mdot_status mdot_solve_host(mdot_handle* h, const double* r_host, const double* c_host,
+                            const float* C_host, int64_t n, double eps_target,
+                            const mdot_params* prm, double* u_host, double* v_host,
+                            double* cost_out, double* gap_out, mdot_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MDOT_H */

@@ -1,0 +1,235 @@
+"""Python binding of libmdot, the GB300 (sm_103a) MDOT-PNCG library (include/mdot.h).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA kernels.  Device
+arrays are torch CUDA tensors (torch provides device memory and the stream); host arrays for
+``solve_host`` are numpy arrays.  The library must have been built (``build.build()``); importing
+the binding never falls back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+from dataclasses import dataclass
+
+from . import build as _build
+
+__all__ = ["Params", "Info", "Handle", "lib", "MDOT_OK", "status_string", "MdotError"]
+
+MDOT_OK = 0
+MDOT_ERR_INVALID_ARG = 1
+MDOT_ERR_NOT_CONVERGED = 2
+MDOT_ERR_NUMERIC = 3
+MDOT_ERR_TIMEOUT = 4
+MDOT_ERR_OOM = 5
+MDOT_ERR_CUDA = 6
+PREC_AUTO, PREC_FP32, PREC_FP64 = 0, 1, 2
+
+
+class Params(ct.Structure):
+    _fields_ = [("gamma_i", ct.c_double), ("gamma_f", ct.c_double), ("p", ct.c_double),
+                ("q", ct.c_double), ("ls_c1", ct.c_double), ("ls_c2", ct.c_double),
+                ("ls_max_trials", ct.c_int32), ("max_iter", ct.c_int32), ("precision", ct.c_int32),
+                ("warm_start", ct.c_int32), ("final_tol", ct.c_double), ("fp32_floor", ct.c_double),
+                ("profile", ct.c_int32), ("reserved", ct.c_int32 * 7)]
+
+
+class Info(ct.Structure):
+    _fields_ = [("status", ct.c_int32), ("stages", ct.c_int32), ("evals", ct.c_int64),
+                ("evals_fp64", ct.c_int64), ("iters", ct.c_int64), ("ls_trials", ct.c_int64),
+                ("grad_l1", ct.c_double), ("gamma_f", ct.c_double), ("H_min", ct.c_double),
+                ("cost", ct.c_double), ("lower_bound", ct.c_double), ("gap_cert", ct.c_double),
+                ("t_stage_fp32_ms", ct.c_double), ("t_stage_fp64_ms", ct.c_double),
+                ("t_round_ms", ct.c_double), ("t_bound_ms", ct.c_double), ("launches", ct.c_int32),
+                ("stage_launches_fp32", ct.c_int32), ("reserved", ct.c_double * 1)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class MdotError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib().mdot_last_error().decode() if status == MDOT_ERR_CUDA else ""
+        super().__init__(f"{where}: {status_string(status)} {msg}".strip())
+
+
+_lib = None
+_P = ct.c_void_p
+
+
+def lib():
+    """Load libmdot.so (built in-tree).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmdot is not built ({path} missing): run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'` first")
+    L = ct.CDLL(path)
+    L.mdot_default_params.argtypes = [ct.POINTER(Params)]
+    L.mdot_default_params.restype = None
+    L.mdot_status_string.argtypes = [ct.c_int32]
+    L.mdot_status_string.restype = ct.c_char_p
+    L.mdot_last_error.argtypes = []
+    L.mdot_last_error.restype = ct.c_char_p
+    L.mdot_create.argtypes = [ct.POINTER(_P), ct.c_int64, _P]
+    L.mdot_destroy.argtypes = [_P]
+    L.mdot_dual_eval.argtypes = [_P, _P, _P, ct.c_double, _P, ct.c_int64, _P, ct.c_int32, _P, _P]
+    L.mdot_round.argtypes = [_P, _P, _P, ct.c_double, _P, _P, _P, ct.c_int64,
+                             ct.POINTER(ct.c_double), _P]
+    L.mdot_lower_bound.argtypes = [_P, _P, ct.c_double, _P, _P, _P, ct.c_int64, ct.POINTER(ct.c_double)]
+    L.mdot_solve.argtypes = [_P, _P, _P, _P, ct.c_int64, ct.c_double, ct.POINTER(Params), _P, _P,
+                             ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), ct.POINTER(Info)]
+    L.mdot_solve_host.argtypes = L.mdot_solve.argtypes
+    for name in ("mdot_create", "mdot_destroy", "mdot_dual_eval", "mdot_round", "mdot_lower_bound",
+                 "mdot_solve", "mdot_solve_host"):
+        getattr(L, name).restype = ct.c_int32
+    _lib = L
+    return L
+
+
+def status_string(s: int) -> str:
+    return lib().mdot_status_string(int(s)).decode()
+
+
+def default_params(**kw) -> Params:
+    prm = Params()
+    lib().mdot_default_params(ct.byref(prm))
+    for k, v in kw.items():
+        if not hasattr(prm, k) or k == "reserved":
+            raise KeyError(k)
+        setattr(prm, k, v)
+    return prm
+
+
+def _ptr(t, dtype, n=None, name="array"):
+    """Device pointer of a contiguous CUDA tensor of the given torch dtype (checked)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} must have {n} elements, has {t.numel()}")
+    return ct.c_void_p(t.data_ptr())
+
+
+def _hptr(a, dtype, n, name):
+    import numpy as np
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags.c_contiguous or a.size != n:
+        raise TypeError(f"{name} must be a contiguous numpy {dtype} array of {n} elements")
+    return ct.c_void_p(a.ctypes.data)
+
+
+@dataclass
+class SolveResult:
+    status: int
+    cost: float
+    gap_cert: float
+    info: Info
+
+
+class Handle:
+    """Owns an mdot_handle (workspace for problems of size <= max_n) bound to a CUDA stream."""
+
+    def __init__(self, max_n: int, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.max_n = int(max_n)
+        h = _P()
+        s = lib().mdot_create(ct.byref(h), self.max_n, ct.c_void_p(stream.cuda_stream))
+        if s != MDOT_OK:
+            raise MdotError(s, "mdot_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().mdot_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- calls -------------------------------------------------------------------------------
+    def dual_eval(self, u, v, gamma: float, C, ref_log_rP=None, precision: int = PREC_FP32):
+        import torch
+        n = u.numel()
+        lr = torch.empty(n, dtype=torch.float64, device=u.device)
+        lc = torch.empty(n, dtype=torch.float64, device=u.device)
+        ref = _ptr(ref_log_rP, torch.float64, n, "ref_log_rP") if ref_log_rP is not None else None
+        s = lib().mdot_dual_eval(self._h, _ptr(u, torch.float64, n, "u"), _ptr(v, torch.float64, n, "v"),
+                                 float(gamma), _ptr(C, torch.float32, n * n, "C"), n, ref,
+                                 int(precision), _ptr(lr, torch.float64), _ptr(lc, torch.float64))
+        if s != MDOT_OK:
+            raise MdotError(s, "mdot_dual_eval")
+        return lr, lc
+
+    def round(self, u, v, gamma: float, C, r, c, want_G: bool = False):
+        import torch
+        n = u.numel()
+        G = torch.empty((n, n), dtype=torch.float64, device=u.device) if want_G else None
+        cost = ct.c_double(0.0)
+        s = lib().mdot_round(self._h, _ptr(u, torch.float64, n, "u"), _ptr(v, torch.float64, n, "v"),
+                             float(gamma), _ptr(C, torch.float32, n * n, "C"), _ptr(r, torch.float64, n, "r"),
+                             _ptr(c, torch.float64, n, "c"), n, ct.byref(cost),
+                             _ptr(G, torch.float64) if want_G else None)
+        if s != MDOT_OK:
+            raise MdotError(s, "mdot_round")
+        return cost.value, G
+
+    def lower_bound(self, u, gamma: float, C, r, c) -> float:
+        import torch
+        n = u.numel()
+        lb = ct.c_double(0.0)
+        s = lib().mdot_lower_bound(self._h, _ptr(u, torch.float64, n, "u"), float(gamma),
+                                   _ptr(C, torch.float32, n * n, "C"), _ptr(r, torch.float64, n, "r"),
+                                   _ptr(c, torch.float64, n, "c"), n, ct.byref(lb))
+        if s != MDOT_OK:
+            raise MdotError(s, "mdot_lower_bound")
+        return lb.value
+
+    def solve(self, r, c, C, eps_target: float = 1e-6, params: Params | None = None,
+              u_out=None, v_out=None, check: bool = True):
+        """mdot_solve on device tensors; returns (u, v, SolveResult)."""
+        import torch
+        n = r.numel()
+        u = u_out if u_out is not None else torch.empty(n, dtype=torch.float64, device=r.device)
+        v = v_out if v_out is not None else torch.empty(n, dtype=torch.float64, device=r.device)
+        cost, gap, info = ct.c_double(0.0), ct.c_double(0.0), Info()
+        s = lib().mdot_solve(self._h, _ptr(r, torch.float64, n, "r"), _ptr(c, torch.float64, n, "c"),
+                             _ptr(C, torch.float32, n * n, "C"), n, float(eps_target),
+                             ct.byref(params) if params is not None else None,
+                             _ptr(u, torch.float64, n, "u_out"), _ptr(v, torch.float64, n, "v_out"),
+                             ct.byref(cost), ct.byref(gap), ct.byref(info))
+        if check and s not in (MDOT_OK, MDOT_ERR_NOT_CONVERGED):
+            raise MdotError(s, "mdot_solve")
+        return u, v, SolveResult(s, cost.value, gap.value, info)
+
+    def solve_host(self, r, c, C, eps_target: float = 1e-6, params: Params | None = None,
+                   u_out=None, v_out=None, check: bool = True):
+        """mdot_solve_host on numpy arrays (host memory; the copies are part of the call)."""
+        import numpy as np
+        n = r.size
+        u = u_out if u_out is not None else np.empty(n, np.float64)
+        v = v_out if v_out is not None else np.empty(n, np.float64)
+        cost, gap, info = ct.c_double(0.0), ct.c_double(0.0), Info()
+        s = lib().mdot_solve_host(self._h, _hptr(r, np.float64, n, "r"), _hptr(c, np.float64, n, "c"),
+                                  _hptr(C, np.float32, n * n, "C"), n, float(eps_target),
+                                  ct.byref(params) if params is not None else None,
+                                  _hptr(u, np.float64, n, "u_out"), _hptr(v, np.float64, n, "v_out"),
+                                  ct.byref(cost), ct.byref(gap), ct.byref(info))
+        if check and s not in (MDOT_OK, MDOT_ERR_NOT_CONVERGED):
+            raise MdotError(s, "mdot_solve_host")
+        return u, v, SolveResult(s, cost.value, gap.value, info)

@@ -1,0 +1,549 @@
+// C ABI of the MDOT-PNCG library (declared in include/mdot.h): handle and workspace management,
+// argument validation, the host side of MDOT (Alg. 1: the gamma schedule, stage tolerances and
+// warm-start ratios) and the launch sequence of the device stages, rounding and lower bound.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "launch.h"
+#include "mdot.h"
+
+using namespace mdot;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+struct Deleter {
+    std::vector<void*> dev, host;
+    ~Deleter()
+    {
+        for (void* p : dev) cudaFree(p);
+        for (void* p : host) cudaFreeHost(p);
+    }
+};
+
+}  // namespace
+
+struct mdot_handle {
+    int dev = 0, sms = 0, G = 0;
+    cudaStream_t stream = nullptr;
+    int64_t max_n = 0;
+    Deleter mem;
+    WS ws{};
+    double* d_out = nullptr;       // [16] device results
+    double* h_out = nullptr;       // [16] pinned
+    State* h_state = nullptr;      // pinned copy of the state
+    double *Y = nullptr, *EC = nullptr, *ER = nullptr, *gp = nullptr;
+    // device buffers of mdot_solve_host
+    double *d_r = nullptr, *d_c = nullptr, *d_u = nullptr, *d_v = nullptr;
+    float* d_C = nullptr;
+    int64_t host_n = 0;
+};
+
+#define CKR(call)                                                                                  \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) {                                                                   \
+            snprintf(g_err, sizeof g_err, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),        \
+                     __FILE__, __LINE__);                                                          \
+            return MDOT_ERR_CUDA;                                                                  \
+        }                                                                                          \
+    } while (0)
+
+extern "C" {
+
+void mdot_default_params(mdot_params* prm)
+{
+    if (!prm) return;
+    memset(prm, 0, sizeof(*prm));
+    prm->gamma_i = 16.0;                 // Sec. 5.2
+    prm->gamma_f = 0.0;                  // derived from eps_target (Prop. 2)
+    prm->p = 1.5;                        // Sec. 5.2
+    prm->q = std::cbrt(2.0);             // Sec. 5.2
+    prm->ls_c1 = 0.1;                    // App. B leaves 0 < c1 < c2 < 1 open (reading)
+    prm->ls_c2 = 0.5;
+    prm->ls_max_trials = 50;
+    prm->max_iter = 100000;
+    prm->precision = MDOT_PREC_AUTO;
+    prm->warm_start = 0;
+    prm->final_tol = 0.0;
+    prm->fp32_floor = 3e-7;
+    prm->profile = 0;
+}
+
+const char* mdot_status_string(int32_t s)
+{
+    switch (s) {
+    case MDOT_OK: return "MDOT_OK";
+    case MDOT_ERR_INVALID_ARG: return "MDOT_ERR_INVALID_ARG";
+    case MDOT_ERR_NOT_CONVERGED: return "MDOT_ERR_NOT_CONVERGED";
+    case MDOT_ERR_NUMERIC: return "MDOT_ERR_NUMERIC";
+    case MDOT_ERR_TIMEOUT: return "MDOT_ERR_TIMEOUT";
+    case MDOT_ERR_OOM: return "MDOT_ERR_OOM";
+    case MDOT_ERR_CUDA: return "MDOT_ERR_CUDA";
+    case MDOT_NOT_READY: return "MDOT_NOT_READY";
+    default: return "MDOT_UNKNOWN_STATUS";
+    }
+}
+
+const char* mdot_last_error(void) { return g_err; }
+
+mdot_status mdot_create(mdot_handle** out, int64_t max_n, void* stream)
+{
+    if (!out || max_n < 1 || max_n > (int64_t)1 << 20) return MDOT_ERR_INVALID_ARG;
+    *out = nullptr;
+    mdot_handle* h = new mdot_handle();
+    h->stream = (cudaStream_t)stream;
+    h->max_n = max_n;
+    cudaError_t e = cudaGetDevice(&h->dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->dev);
+    if (e != cudaSuccess) {
+        snprintf(g_err, sizeof g_err, "device query: %s", cudaGetErrorString(e));
+        delete h;
+        return MDOT_ERR_CUDA;
+    }
+    h->G = h->sms;                       // one CTA per SM (cooperative, persistent per launch)
+    int mb = 0;
+    e = configure_kernels((int)max_n, h->G, &mb);
+    if (e != cudaSuccess || mb < 1) {
+        snprintf(g_err, sizeof g_err, "kernel configuration: %s (blocks/SM %d)",
+                 e != cudaSuccess ? cudaGetErrorString(e) : "does not fit", mb);
+        delete h;
+        return e != cudaSuccess ? MDOT_ERR_CUDA : MDOT_ERR_INVALID_ARG;
+    }
+    const size_t n = (size_t)max_n, G = (size_t)h->G;
+    auto dalloc = [&](size_t bytes) -> void* {
+        void* p = nullptr;
+        if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) return nullptr;
+        h->mem.dev.push_back(p);
+        return p;
+    };
+    const int nvec = 25;
+    double* vec = (double*)dalloc(nvec * n * sizeof(double));
+    float* f32 = (float*)dalloc(4 * n * sizeof(float));
+    int* A = (int*)dalloc(n * sizeof(int));
+    float* colpart = (float*)dalloc(G * n * sizeof(float));
+    double* colpartd = (double*)dalloc(G * n * sizeof(double));
+    double* blockred = (double*)dalloc(G * kNRed * sizeof(double));
+    double* scratch = (double*)dalloc(G * 8 * sizeof(double));
+    State* st = (State*)dalloc(sizeof(State));
+    h->d_out = (double*)dalloc(16 * sizeof(double));
+    void* hp = nullptr;
+    if (cudaMallocHost(&hp, 16 * sizeof(double) + sizeof(State)) == cudaSuccess) h->mem.host.push_back(hp);
+    if (!vec || !f32 || !A || !colpart || !colpartd || !blockred || !scratch || !st || !h->d_out || !hp) {
+        snprintf(g_err, sizeof g_err, "workspace allocation failed for max_n = %lld", (long long)max_n);
+        delete h;
+        return MDOT_ERR_OOM;
+    }
+    h->h_out = (double*)hp;
+    h->h_state = (State*)((char*)hp + 16 * sizeof(double));
+    WS& w = h->ws;
+    double* p = vec;
+    auto take = [&]() { double* q = p; p += n; return q; };
+    w.rt = take(); w.ct = take(); w.lrt = take(); w.lct = take();
+    w.u = take(); w.v = take(); w.pu = take(); w.pv = take(); w.uprev = take(); w.vprev = take();
+    w.gr = take(); w.gc = take(); w.grt = take(); w.gct = take(); w.srt = take(); w.sct = take();
+    w.lr = take(); w.lrtr = take(); w.lcout = take(); w.Fd = take(); w.Hd = take();
+    h->Y = take(); h->EC = take(); h->ER = take(); h->gp = take();
+    w.Fh = f32; w.Wr = f32 + n; w.Hh = f32 + 2 * n; w.Wc = f32 + 3 * n;
+    w.A = A;
+    w.colpart = colpart;
+    w.colpartd = colpartd;
+    w.blockred = blockred;
+    w.scratch = scratch;
+    w.st = st;
+    w.G = h->G;
+    if (cudaMemsetAsync(st, 0, sizeof(State), h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        snprintf(g_err, sizeof g_err, "state initialisation failed");
+        delete h;
+        return MDOT_ERR_CUDA;
+    }
+    *out = h;
+    return MDOT_OK;
+}
+
+mdot_status mdot_destroy(mdot_handle* h)
+{
+    if (h) {
+        cudaStreamSynchronize(h->stream);
+        delete h;
+    }
+    return MDOT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+mdot_status params_ok(const mdot_params& P)
+{
+    if (!(P.gamma_i > 0.0) || !(P.p >= 1.0) || !(P.q > 1.0) || !(P.ls_c1 > 0.0) ||
+        !(P.ls_c2 > P.ls_c1) || !(P.ls_c2 < 1.0) || P.ls_max_trials < 1 || P.max_iter < 1 ||
+        P.precision < 0 || P.precision > 2 || P.warm_start < 0 || P.warm_start > 2 ||
+        !(P.fp32_floor >= 0.0) || !std::isfinite(P.gamma_f))
+        return MDOT_ERR_INVALID_ARG;
+    return MDOT_OK;
+}
+
+mdot_status map_status(int st)
+{
+    switch (st) {
+    case ST_OK: return MDOT_OK;
+    case ST_CAP:
+    case ST_LSFAIL: return MDOT_ERR_NOT_CONVERGED;
+    case ST_NUMERIC: return MDOT_ERR_NUMERIC;
+    default: return MDOT_ERR_TIMEOUT;
+    }
+}
+
+// Optional per-launch timing with CUDA events on the handle's stream.
+struct Timer {
+    bool on = false;
+    cudaStream_t s = nullptr;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    std::vector<int> kind;
+    void begin(int k)
+    {
+        if (!on) return;
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, s);
+        ev.push_back({a, b});
+        kind.push_back(k);
+    }
+    void end()
+    {
+        if (on) cudaEventRecord(ev.back().second, s);
+    }
+    // call after the stream is synchronised; sums[k] += ms
+    void collect(double* sums)
+    {
+        for (size_t q = 0; q < ev.size(); ++q) {
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, ev[q].first, ev[q].second);
+            sums[kind[q]] += ms;
+            cudaEventDestroy(ev[q].first);
+            cudaEventDestroy(ev[q].second);
+        }
+        ev.clear();
+        kind.clear();
+    }
+    ~Timer() { double d[8] = {0}; collect(d); }
+};
+
+// Reset the barrier and counters before a new call (also clears an aborted barrier).
+cudaError_t reset_state(mdot_handle* h) { return cudaMemsetAsync(h->ws.st, 0, sizeof(State), h->stream); }
+
+double gamma_f_for_eps(double H, double eps, double gi, double q, double p)
+{
+    // Prop. 2: gamma_f = (5 H_min / (2 eps))^(1/p), rounded up onto gamma_i q^k
+    const double target = std::pow(5.0 * H / (2.0 * eps), 1.0 / p);
+    double g = gi;
+    while (g < target * (1.0 - 1e-12)) g *= q;
+    return g;
+}
+
+// Validate r, c on the device; returns H_min in *H.
+mdot_status check_marginals(mdot_handle* h, const WS& ws, double* H)
+{
+    CKR(reset_state(h));
+    CKR(launch_validate(ws, h->d_out, h->stream));
+    CKR(cudaMemcpyAsync(h->h_out, h->d_out, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CKR(cudaStreamSynchronize(h->stream));
+    const double* o = h->h_out;
+    if (o[6] != 0.0 || !(o[4] >= 0.0) || !(o[5] >= 0.0) || !(std::fabs(o[0] - 1.0) <= 1e-9) ||
+        !(std::fabs(o[1] - 1.0) <= 1e-9)) {
+        snprintf(g_err, sizeof g_err, "marginals invalid: sum r %.17g sum c %.17g min r %g min c %g nonfinite %g",
+                 o[0], o[1], o[4], o[5], o[6]);
+        return MDOT_ERR_INVALID_ARG;
+    }
+    // H_min floored at 1e-12: a point-mass marginal keeps a positive smoothing weight (Alg. 1 line 4)
+    *H = std::max(std::min(o[2], o[3]), 1e-12);
+    return MDOT_OK;
+}
+
+mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const float* C, int64_t n,
+                       double eps_target, const mdot_params* prm, double* u_out, double* v_out,
+                       double* cost_out, double* gap_out, mdot_info* info)
+{
+    if (!h || !r || !c || !C || !u_out || !v_out || n < 1 || n > h->max_n) return MDOT_ERR_INVALID_ARG;
+    mdot_params P;
+    if (prm) P = *prm; else mdot_default_params(&P);
+    if (params_ok(P) != MDOT_OK) return MDOT_ERR_INVALID_ARG;
+    if (!(P.gamma_f > 0.0) && !(eps_target > 0.0 && std::isfinite(eps_target))) return MDOT_ERR_INVALID_ARG;
+    WS ws = h->ws;
+    ws.n = (int)n;
+    ws.r = r;
+    ws.c = c;
+    ws.C = C;
+    double H = 0.0;
+    mdot_status ms = check_marginals(h, ws, &H);
+    if (ms != MDOT_OK) return ms;
+    const double gf = (P.gamma_f > 0.0) ? P.gamma_f : gamma_f_for_eps(H, eps_target, P.gamma_i, P.q, P.p);
+    const bool all64 = P.precision == MDOT_PREC_FP64 || (P.precision == MDOT_PREC_AUTO && n <= 512);
+    const bool polish = P.precision == MDOT_PREC_AUTO && !all64;
+
+    CKR(reset_state(h));
+    Timer tm;
+    tm.on = P.profile != 0;
+    tm.s = h->stream;
+    int launches = 1, launches32 = 0;
+    // Alg. 1: gamma schedule, stage by stage (same arithmetic as the paper's loop)
+    double gamma = std::min(P.gamma_i, gf);
+    double dgamma_prev = gamma;      // stage 0 is gamma = 0 (Prop. 1): the first step is gamma_1
+    double ratio = 0.0;
+    int stages = 0;
+    for (int t = 1;; ++t) {
+        const double eps_d = H / std::pow(gamma, P.p);                   // line 3
+        double tol = std::max(eps_d / 2.0, 1e-13);                        // line 6 (floored)
+        const bool last = (gamma == gf);
+        if (last && P.final_tol > 0.0) tol = P.final_tol;
+        StageArgs a{};
+        a.gamma = gamma;
+        a.G64 = gamma * kLog2e;
+        a.w = eps_d;                                                       // line 4
+        a.ratio = ratio;
+        a.c1 = P.ls_c1;
+        a.c2 = P.ls_c2;
+        a.first = (t == 1);
+        a.warm_start = P.warm_start;
+        a.ls_max_trials = P.ls_max_trials;
+        a.max_iter = P.max_iter;
+        a.Aglob = 0;
+        if (all64) {
+            a.tier = TIER_F64;
+            a.tol = tol;
+            tm.begin(1);
+            CKR(launch_stage(TIER_F64, ws, a, h->stream));
+            tm.end();
+            ++launches;
+        } else {
+            a.tier = TIER_F32;
+            a.tol = std::max(tol, (double)P.fp32_floor);
+            tm.begin(0);
+            CKR(launch_stage(TIER_F32, ws, a, h->stream));
+            tm.end();
+            ++launches;
+            ++launches32;
+            if (last && polish && tol < P.fp32_floor) {
+                // final stage below the fp32 noise floor: continue in fp64 entries from the
+                // fp32 iterate (same gamma, same smoothing, no warm start)
+                StageArgs b = a;
+                b.tier = TIER_F64;
+                b.tol = tol;
+                b.first = 0;
+                b.warm_start = 2;
+                tm.begin(1);
+                CKR(launch_stage(TIER_F64, ws, b, h->stream));
+                tm.end();
+                ++launches;
+            }
+        }
+        ++stages;
+        if (last) break;                                                   // line 7
+        double dg = (P.q - 1.0) * gamma;                                   // line 8
+        const double gnext = std::min(gamma + dg, gf);
+        dg = gnext - gamma;
+        ratio = (P.warm_start == 1) ? gnext / gamma : dg / dgamma_prev;    // line 9, Eq. (13)
+        dgamma_prev = dg;
+        gamma = gnext;
+        if (stages > 100000) return MDOT_ERR_INVALID_ARG;
+    }
+    // Alg. 1 lines 12-13: round P(u, v; gamma_f) onto U(r, c); then the lower bound
+    RoundArgs ra{};
+    ra.gamma = gf;
+    ra.G64 = gf * kLog2e;
+    ra.u = ws.u;
+    ra.v = ws.v;
+    ra.r = r;
+    ra.c = c;
+    ra.ref = ws.lr;
+    ra.Y = h->Y;
+    ra.EC = h->EC;
+    ra.ER = h->ER;
+    ra.G_out = nullptr;
+    ra.out = h->d_out;
+    tm.begin(2);
+    CKR(launch_round(ws, ra, h->stream));
+    tm.end();
+    LbArgs la{};
+    la.gamma = gf;
+    la.u = ws.u;
+    la.r = r;
+    la.c = c;
+    la.gp = h->gp;
+    la.out = h->d_out + 8;
+    tm.begin(3);
+    CKR(launch_lower_bound(ws, la, h->stream));
+    tm.end();
+    launches += 2;
+    CKR(cudaMemcpyAsync(u_out, ws.u, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    CKR(cudaMemcpyAsync(v_out, ws.v, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    CKR(cudaMemcpyAsync(h->h_out, h->d_out, 16 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CKR(cudaMemcpyAsync(h->h_state, ws.st, sizeof(State), cudaMemcpyDeviceToHost, h->stream));
+    CKR(cudaStreamSynchronize(h->stream));
+    const State& S = *h->h_state;
+    double tsum[8] = {0};
+    tm.collect(tsum);
+    const double cost = h->h_out[0], lb = h->h_out[8];
+    if (cost_out) *cost_out = cost;
+    if (gap_out) *gap_out = cost - lb;
+    mdot_status out = map_status(S.status);
+    if (out == MDOT_OK && !(std::isfinite(cost) && std::isfinite(lb))) out = MDOT_ERR_NUMERIC;
+    if (info) {
+        memset(info, 0, sizeof(*info));
+        info->status = out;
+        info->stages = stages;
+        info->evals = S.evals;
+        info->evals_fp64 = S.evals64;
+        info->iters = S.iters;
+        info->ls_trials = S.ls_trials;
+        info->grad_l1 = S.gnorm;
+        info->gamma_f = gf;
+        info->H_min = H;
+        info->cost = cost;
+        info->lower_bound = lb;
+        info->gap_cert = cost - lb;
+        info->t_stage_fp32_ms = tsum[0];
+        info->t_stage_fp64_ms = tsum[1];
+        info->t_round_ms = tsum[2];
+        info->t_bound_ms = tsum[3];
+        info->launches = launches;
+        info->stage_launches_fp32 = launches32;
+    }
+    return out;
+}
+
+}  // namespace
+
+extern "C" {
+
+mdot_status mdot_solve(mdot_handle* h, const double* r, const double* c, const float* C, int64_t n,
+                       double eps_target, const mdot_params* prm, double* u_out, double* v_out,
+                       double* cost_out, double* gap_out, mdot_info* info)
+{
+    return solve_core(h, r, c, C, n, eps_target, prm, u_out, v_out, cost_out, gap_out, info);
+}
+
+mdot_status mdot_solve_host(mdot_handle* h, const double* r_host, const double* c_host, const float* C_host,
+                            int64_t n, double eps_target, const mdot_params* prm, double* u_host,
+                            double* v_host, double* cost_out, double* gap_out, mdot_info* info)
+{
+    if (!h || !r_host || !c_host || !C_host || !u_host || !v_host || n < 1 || n > h->max_n)
+        return MDOT_ERR_INVALID_ARG;
+    if (h->host_n < n) {
+        cudaFree(h->d_r); cudaFree(h->d_c); cudaFree(h->d_u); cudaFree(h->d_v); cudaFree(h->d_C);
+        h->d_r = h->d_c = h->d_u = h->d_v = nullptr;
+        h->d_C = nullptr;
+        h->host_n = 0;
+        if (cudaMalloc(&h->d_r, n * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&h->d_c, n * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&h->d_u, n * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&h->d_v, n * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&h->d_C, (size_t)n * n * sizeof(float)) != cudaSuccess) {
+            snprintf(g_err, sizeof g_err, "host-path buffers for n = %lld", (long long)n);
+            return MDOT_ERR_OOM;
+        }
+        h->host_n = n;
+    }
+    CKR(cudaMemcpyAsync(h->d_r, r_host, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CKR(cudaMemcpyAsync(h->d_c, c_host, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CKR(cudaMemcpyAsync(h->d_C, C_host, (size_t)n * n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    mdot_status s = solve_core(h, h->d_r, h->d_c, h->d_C, n, eps_target, prm, h->d_u, h->d_v,
+                               cost_out, gap_out, info);
+    if (s == MDOT_ERR_INVALID_ARG || s == MDOT_ERR_CUDA) return s;
+    CKR(cudaMemcpyAsync(u_host, h->d_u, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CKR(cudaMemcpyAsync(v_host, h->d_v, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CKR(cudaStreamSynchronize(h->stream));
+    return s;
+}
+
+mdot_status mdot_dual_eval(mdot_handle* h, const double* u, const double* v, double gamma, const float* C,
+                           int64_t n, const double* ref_log_rP, int32_t precision, double* log_rP,
+                           double* log_cP)
+{
+    if (!h || !u || !v || !C || !log_rP || !log_cP || n < 1 || n > h->max_n || !(gamma > 0.0) ||
+        !std::isfinite(gamma) || precision < 0 || precision > 2)
+        return MDOT_ERR_INVALID_ARG;
+    WS ws = h->ws;
+    ws.n = (int)n;
+    ws.C = C;
+    EvalArgs a{};
+    a.gamma = gamma;
+    a.G64 = gamma * kLog2e;
+    a.u = u;
+    a.v = v;
+    a.ref = ref_log_rP;
+    const int tier = (precision == MDOT_PREC_FP64) ? TIER_F64 : TIER_F32;
+    CKR(reset_state(h));
+    CKR(launch_dual_eval(tier, ws, a, h->stream));
+    CKR(cudaMemcpyAsync(log_rP, ws.lrtr, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    CKR(cudaMemcpyAsync(log_cP, ws.lcout, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    CKR(cudaMemcpyAsync(h->h_state, ws.st, sizeof(State), cudaMemcpyDeviceToHost, h->stream));
+    CKR(cudaStreamSynchronize(h->stream));
+    return h->h_state->status == ST_OK ? MDOT_OK : MDOT_ERR_TIMEOUT;
+}
+
+mdot_status mdot_round(mdot_handle* h, const double* u, const double* v, double gamma, const float* C,
+                       const double* r, const double* c, int64_t n, double* cost_out, double* G_out)
+{
+    if (!h || !u || !v || !C || !r || !c || !cost_out || n < 1 || n > h->max_n || !(gamma > 0.0) ||
+        !std::isfinite(gamma))
+        return MDOT_ERR_INVALID_ARG;
+    WS ws = h->ws;
+    ws.n = (int)n;
+    ws.C = C;
+    RoundArgs ra{};
+    ra.gamma = gamma;
+    ra.G64 = gamma * kLog2e;
+    ra.u = u;
+    ra.v = v;
+    ra.r = r;
+    ra.c = c;
+    ra.ref = nullptr;
+    ra.Y = h->Y;
+    ra.EC = h->EC;
+    ra.ER = h->ER;
+    ra.G_out = G_out;
+    ra.out = h->d_out;
+    CKR(reset_state(h));
+    CKR(launch_round(ws, ra, h->stream));
+    CKR(cudaMemcpyAsync(h->h_out, h->d_out, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CKR(cudaMemcpyAsync(h->h_state, ws.st, sizeof(State), cudaMemcpyDeviceToHost, h->stream));
+    CKR(cudaStreamSynchronize(h->stream));
+    *cost_out = h->h_out[0];
+    if (h->h_state->status != ST_OK) return MDOT_ERR_TIMEOUT;
+    return std::isfinite(h->h_out[0]) ? MDOT_OK : MDOT_ERR_NUMERIC;
+}
+
+mdot_status mdot_lower_bound(mdot_handle* h, const double* u, double gamma, const float* C, const double* r,
+                             const double* c, int64_t n, double* lb_out)
+{
+    if (!h || !u || !C || !r || !c || !lb_out || n < 1 || n > h->max_n || !(gamma > 0.0)) return MDOT_ERR_INVALID_ARG;
+    WS ws = h->ws;
+    ws.n = (int)n;
+    ws.C = C;
+    LbArgs la{};
+    la.gamma = gamma;
+    la.u = u;
+    la.r = r;
+    la.c = c;
+    la.gp = h->gp;
+    la.out = h->d_out + 8;
+    CKR(reset_state(h));
+    CKR(launch_lower_bound(ws, la, h->stream));
+    CKR(cudaMemcpyAsync(h->h_out, h->d_out, 16 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CKR(cudaMemcpyAsync(h->h_state, ws.st, sizeof(State), cudaMemcpyDeviceToHost, h->stream));
+    CKR(cudaStreamSynchronize(h->stream));
+    *lb_out = h->h_out[8];
+    return h->h_state->status == ST_OK ? MDOT_OK : MDOT_ERR_TIMEOUT;
+}
+
+}  // extern "C"

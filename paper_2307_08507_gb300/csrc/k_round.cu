@@ -1,0 +1,64 @@
+// Instantiation and cooperative launch of the rounding, lower-bound and validation kernels.
+#include <algorithm>
+
+#include "launch.h"
+#include "round_kernels.cuh"
+
+namespace mdot {
+
+cudaError_t configure_stage_kernels(int max_n, int G, int* min_blocks);
+
+size_t round_smem_bytes(int n, int G) { return round_smem(n, G, kThreads).bytes; }
+size_t lb_smem_bytes(int n, int G) { return (size_t)((n + G - 1) / G + 1) * sizeof(double); }
+
+static cudaError_t coop(const void* kernel, int G, size_t smem, cudaStream_t s, void** args)
+{
+    return cudaLaunchCooperativeKernel(kernel, dim3(G), dim3(kThreads), args, smem, s);
+}
+
+cudaError_t launch_round(const WS& ws, const RoundArgs& a, cudaStream_t s)
+{
+    WS w = ws;
+    RoundArgs aa = a;
+    void* args[] = {(void*)&w, (void*)&aa};
+    return coop((const void*)round_kernel, ws.G, round_smem_bytes(ws.n, ws.G), s, args);
+}
+
+cudaError_t launch_lower_bound(const WS& ws, const LbArgs& a, cudaStream_t s)
+{
+    WS w = ws;
+    LbArgs aa = a;
+    void* args[] = {(void*)&w, (void*)&aa};
+    return coop((const void*)lower_bound_kernel, ws.G, lb_smem_bytes(ws.n, ws.G), s, args);
+}
+
+cudaError_t launch_validate(const WS& ws, double* out, cudaStream_t s)
+{
+    WS w = ws;
+    double* o = out;
+    void* args[] = {(void*)&w, (void*)&o};
+    return coop((const void*)validate_kernel, ws.G, 0, s, args);
+}
+
+cudaError_t configure_kernels(int max_n, int G, int* min_blocks_per_sm)
+{
+    int mb = 1 << 30;
+    cudaError_t e = configure_stage_kernels(max_n, G, &mb);
+    if (e != cudaSuccess) return e;
+    struct K { const void* f; size_t smem; } ks[] = {
+        {(const void*)round_kernel, round_smem_bytes(max_n, G)},
+        {(const void*)lower_bound_kernel, lb_smem_bytes(max_n, G)},
+        {(const void*)validate_kernel, 0}};
+    for (auto& k : ks) {
+        e = cudaFuncSetAttribute(k.f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
+        if (e != cudaSuccess) return e;
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k.f, kThreads, k.smem);
+        if (e != cudaSuccess) return e;
+        mb = std::min(mb, nb);
+    }
+    *min_blocks_per_sm = mb;
+    return cudaSuccess;
+}
+
+}  // namespace mdot

@@ -1,0 +1,23 @@
+// Host-side launchers of the cooperative kernels (defined in k_stage.cu / k_round.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "mdot_device.cuh"
+
+namespace mdot {
+
+size_t stage_smem_bytes(int n, int G, int tier);
+size_t round_smem_bytes(int n, int G);
+size_t lb_smem_bytes(int n, int G);
+// Raise the dynamic shared-memory limit of every kernel to what max_n needs; returns the number
+// of co-resident CTAs per SM the cooperative kernels can have (0 if one does not fit).
+cudaError_t configure_kernels(int max_n, int G, int* min_blocks_per_sm);
+
+cudaError_t launch_stage(int tier, const WS& ws, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_dual_eval(int tier, const WS& ws, const EvalArgs& a, cudaStream_t s);
+cudaError_t launch_round(const WS& ws, const RoundArgs& a, cudaStream_t s);
+cudaError_t launch_lower_bound(const WS& ws, const LbArgs& a, cudaStream_t s);
+cudaError_t launch_validate(const WS& ws, double* out, cudaStream_t s);
+
+}  // namespace mdot

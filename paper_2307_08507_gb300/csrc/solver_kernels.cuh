@@ -1,0 +1,613 @@
+// Cooperative kernels of the MDOT-PNCG solve: one launch runs one MDOT stage (Alg. 1 lines 3-6:
+// smoothing, warm start, then the PNCG projection of Alg. 2 with the App. B line search) entirely
+// on the device.  Per evaluation: phase A (pass over C, row epilogue) -> grid barrier -> phase B
+// (column merge, column epilogue, per-CTA partial sums) -> arrive; the last CTA reduces the
+// partials in a fixed order and takes the line-search / PNCG decision -> phase C (commit the
+// accepted step, new direction, constants of the next trial) -> grid barrier.
+#pragma once
+
+#include "mdot_device.cuh"
+
+namespace mdot {
+
+// ---------------------------------------------------------------------------------------------
+// decision of one evaluation (thread 0 of the last CTA).  tot = {phi', ||grad||_1,
+// <y, -s>, <y, p>, <s, grad>, #bad}, y = grad_trial - grad_current (Eq. (18)).
+// ---------------------------------------------------------------------------------------------
+static __device__ void decide(volatile State* S, const double* tot, const StageArgs& a)
+{
+    const double phi = tot[0], gn = tot[1], num = tot[2], den = tot[3], S1 = tot[4];
+    const bool bad = tot[5] > 0.0 || !isfinite(phi) || !isfinite(gn);
+    S->evals += 1;
+    if (a.tier == TIER_F64) S->evals64 += 1;
+    bool accept = false;
+    if (S->kind == KIND_INIT) {
+        if (bad) {
+            S->status = max((int)S->status, (int)ST_NUMERIC);
+            S->phase = PH_DONE;
+            S->accept = 0;
+            return;
+        }
+        accept = true;
+    } else {
+        S->ls_trials += 1;
+        S->trials += 1;
+        if (S->kind == KIND_FORCE) {
+            accept = !bad;
+            if (bad) {
+                S->status = max((int)S->status, (int)ST_NUMERIC);
+                S->phase = PH_DONE;
+                S->accept = 0;
+                return;
+            }
+        } else if (bad) {
+            // overshoot into overflow: treat as an upper end and bisect (App. B reading)
+            S->hi = S->alpha;
+            S->dhi = INFINITY;
+            S->alpha = 0.5 * (S->lo + S->hi);
+        } else if (phi <= (2.0 * a.c1 - 1.0) * S->d0 && phi >= a.c2 * S->d0) {
+            accept = true;                                      // Eq. (24)
+        } else {
+            if (phi < a.c2 * S->d0) { S->lo = S->alpha; S->dlo = phi; }
+            else                    { S->hi = S->alpha; S->dhi = phi; }
+            if (isinf(S->hi)) {
+                S->alpha = 2.0 * S->alpha;
+            } else if (isinf(S->dhi)) {
+                S->alpha = 0.5 * (S->lo + S->hi);
+            } else {
+                const double a_sec = (S->lo * S->dhi - S->hi * S->dlo) / (S->dhi - S->dlo);  // Eq. (25)
+                S->alpha = 0.5 * a_sec + 0.5 * (0.5 * (S->lo + S->hi));
+            }
+        }
+        if (!accept && S->trials >= a.ls_max_trials) {
+            if (S->lo > 0.0) {
+                S->alpha = S->lo;
+                S->kind = KIND_FORCE;
+            } else {
+                S->status = max((int)S->status, (int)ST_LSFAIL);
+                S->phase = PH_DONE;
+                S->accept = 0;
+                return;
+            }
+        }
+    }
+    S->accept = accept ? 1 : 0;
+    if (!accept) return;
+
+    const bool was_init = (S->kind == KIND_INIT);
+    S->alpha_commit = was_init ? 0.0 : S->alpha;
+    if (!was_init) { S->k += 1; S->iters += 1; }
+    S->gnorm = gn;
+    if (gn <= a.tol) { S->phase = PH_DONE; S->beta = 0.0; return; }
+    if (S->k >= a.max_iter) {
+        S->status = max((int)S->status, (int)ST_CAP);
+        S->phase = PH_DONE;
+        S->beta = 0.0;
+        return;
+    }
+    // next direction p = s + beta p (Alg. 2 line 7), reset to s if not a descent direction
+    double beta = 0.0;
+    if (!was_init) {
+        const double q = num / den;
+        beta = (den != 0.0 && isfinite(q)) ? q : 0.0;
+    }
+    double pg = S1 + beta * phi;     // <s + beta p, grad> ; phi = <p_old, grad>
+    if (pg >= 0.0) { beta = 0.0; pg = S1; }
+    S->beta = beta;
+    if (!(pg < 0.0)) {
+        S->status = max((int)S->status, (int)ST_LSFAIL);
+        S->phase = PH_DONE;
+        return;
+    }
+    S->d0 = pg;
+    S->lo = 0.0; S->dlo = pg; S->hi = INFINITY; S->dhi = INFINITY;
+    S->alpha = 1.0;
+    S->trials = 0;
+    S->kind = KIND_TRIAL;
+}
+
+// ---------------------------------------------------------------------------------------------
+// shared-memory layout of the stage / dual-eval kernels
+// ---------------------------------------------------------------------------------------------
+struct SmemLayout {
+    int nloc_max;
+    size_t off_row, off_c0, off_c1, off_s, off_A, off_x, off_merge, bytes;
+};
+
+__host__ __device__ inline SmemLayout smem_layout(int n, int G, int tier, int nthreads)
+{
+    SmemLayout L;
+    const int nw = nthreads / 32;
+    L.nloc_max = (n + G - 1) / G + 1;
+    const size_t el = (tier == TIER_F64) ? 8 : 4;
+    size_t o = 0;
+    L.off_row = o;   o += (size_t)nw * L.nloc_max * el;          o = (o + 15) & ~(size_t)15;
+    L.off_c0 = o;    o += (size_t)L.nloc_max * el;               o = (o + 15) & ~(size_t)15;
+    L.off_c1 = o;    o += (size_t)L.nloc_max * 4;                o = (o + 15) & ~(size_t)15;
+    L.off_s = o;     o += (size_t)L.nloc_max * el;               o = (o + 15) & ~(size_t)15;
+    L.off_A = o;     o += (size_t)L.nloc_max * 4;                o = (o + 15) & ~(size_t)15;
+    L.off_x = o;     o += (size_t)L.nloc_max * 8;                o = (o + 15) & ~(size_t)15;
+    L.off_merge = o; o += (size_t)2 * 32 * nw * 8;               o = (o + 15) & ~(size_t)15;
+    L.bytes = o;
+    return L;
+}
+
+// Row prep of an evaluation at potential ua (already u + alpha p_u) with row scale A.
+template <int TIER>
+__device__ __forceinline__ void prep_row(double ua, int A, int Aglob, double gamma, double G64,
+                                         unsigned char* sm, const SmemLayout& L, int il)
+{
+    if (TIER == TIER_F32) {
+        float fh, wl;
+        split_cost_unit(ua / gamma - (double)A / G64, fh, wl, G64);
+        reinterpret_cast<float*>(sm + L.off_c0)[il] = fh;
+        reinterpret_cast<float*>(sm + L.off_c1)[il] = wl;
+        reinterpret_cast<float*>(sm + L.off_s)[il] = pow2f_int(A - Aglob);
+    } else {
+        reinterpret_cast<double*>(sm + L.off_c0)[il] = ua - (double)A * kLn2;
+        reinterpret_cast<double*>(sm + L.off_s)[il] = ldexp(1.0, A - Aglob);
+    }
+    reinterpret_cast<int*>(sm + L.off_A)[il] = A;
+}
+
+template <int TIER>
+__device__ __forceinline__ void prep_col(const WS& ws, int j, double va, double gamma, double G64)
+{
+    if (TIER == TIER_F32) {
+        float gh, wl;
+        split_cost_unit(va / gamma, gh, wl, G64);
+        ws.Hh[j] = gh;
+        ws.Wc[j] = wl;
+    } else {
+        ws.Hd[j] = va;
+    }
+}
+
+// Phase A for the CTA's rows: pass over C, then the row sums (fp64) into rowsum[il].
+template <int TIER>
+__device__ __forceinline__ void phase_A(const WS& ws, int r0, int r1, double gamma, double G64,
+                                        unsigned char* sm, const SmemLayout& L)
+{
+    const int n = ws.n, nloc = r1 - r0, nw = blockDim.x >> 5;
+    const int b = blockIdx.x;
+    if (TIER == TIER_F32) {
+        float* sRow = reinterpret_cast<float*>(sm + L.off_row);
+        for (int x = threadIdx.x; x < nw * L.nloc_max; x += blockDim.x) sRow[x] = 0.0f;
+        __syncthreads();
+        const float G32 = (float)G64;
+        const float Glo = (float)(G64 - (double)G32);
+        const float* sFh = reinterpret_cast<const float*>(sm + L.off_c0);
+        const float* sWr = reinterpret_cast<const float*>(sm + L.off_c1);
+        const float* sS = reinterpret_cast<const float*>(sm + L.off_s);
+        if ((n & 3) == 0)
+            pass_f32<true>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sS, G32, Glo, sRow, L.nloc_max,
+                           ws.colpart + (size_t)b * n);
+        else
+            pass_f32<false>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sS, G32, Glo, sRow, L.nloc_max,
+                            ws.colpart + (size_t)b * n);
+    } else {
+        double* sRow = reinterpret_cast<double*>(sm + L.off_row);
+        for (int x = threadIdx.x; x < nw * L.nloc_max; x += blockDim.x) sRow[x] = 0.0;
+        __syncthreads();
+        pass_f64(ws.C, n, r0, r1, ws.Hd, reinterpret_cast<const double*>(sm + L.off_c0),
+                 reinterpret_cast<const double*>(sm + L.off_s), gamma, sRow, L.nloc_max,
+                 ws.colpartd + (size_t)b * n);
+    }
+    __syncthreads();
+    (void)nloc;
+}
+
+template <int TIER>
+__device__ __forceinline__ double row_total(const unsigned char* sm, const SmemLayout& L, int il)
+{
+    const int nw = blockDim.x >> 5;
+    double s = 0.0;
+    if (TIER == TIER_F32) {
+        const float* sRow = reinterpret_cast<const float*>(sm + L.off_row);
+        for (int w = 0; w < nw; ++w) s += (double)sRow[w * L.nloc_max + il];
+    } else {
+        const double* sRow = reinterpret_cast<const double*>(sm + L.off_row);
+        for (int w = 0; w < nw; ++w) s += sRow[w * L.nloc_max + il];
+    }
+    return s;
+}
+
+// ---------------------------------------------------------------------------------------------
+// the stage kernel
+// ---------------------------------------------------------------------------------------------
+template <int TIER>
+__global__ void __launch_bounds__(kThreads, 1) stage_kernel(WS ws, StageArgs a)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ double red_smem[32 * kNRed];
+    __shared__ double s_bc[8];
+    __shared__ int s_flag[2];
+    __shared__ unsigned int s_gen;
+
+    const int n = ws.n, G = ws.G, b = blockIdx.x, T = blockDim.x, tid = threadIdx.x;
+    const SmemLayout L = smem_layout(n, G, TIER, T);
+    int r0, r1, c0, c1;
+    row_range(n, G, b, r0, r1);
+    row_range(n, G, b, c0, c1);
+    const double gamma = a.gamma, G64 = a.G64, w = a.w;
+    State* S = ws.st;
+
+    if (tid == 0) s_gen = ld_acquire(&S->bar.gen);
+    __syncthreads();
+    unsigned int gen = s_gen;
+
+    // ---- prologue: Alg. 1 lines 4, 5 and 9 for own rows / columns, constants at alpha = 0 ----
+    for (int i = r0 + tid; i < r1; i += T) {
+        const double rt = (1.0 - w / 4.0) * ws.r[i] + w / (4.0 * n);
+        const double lrt = log(rt);
+        ws.rt[i] = rt;
+        ws.lrt[i] = lrt;
+        double u = ws.u[i];
+        if (a.first) {
+            u = lrt;
+            ws.uprev[i] = u;
+        } else if (a.warm_start == 0) {
+            const double z = u;
+            u = z + a.ratio * (z - ws.uprev[i]);             // Eq. (13)
+            ws.uprev[i] = z;
+        } else if (a.warm_start == 1) {
+            u = a.ratio * u;                                    // eps-scaling
+        }
+        ws.u[i] = u;
+        ws.pu[i] = 0.0;
+        ws.gr[i] = 0.0;
+        ws.lr[i] = lrt;
+        const int A = row_scale(lrt);
+        prep_row<TIER>(u, A, a.Aglob, gamma, G64, sm, L, i - r0);
+    }
+    for (int j = c0 + tid; j < c1; j += T) {
+        const double ct = (1.0 - w / 4.0) * ws.c[j] + w / (4.0 * n);
+        const double lct = log(ct);
+        ws.ct[j] = ct;
+        ws.lct[j] = lct;
+        double v = ws.v[j];
+        if (a.first) {
+            v = lct;
+            ws.vprev[j] = v;
+        } else if (a.warm_start == 0) {
+            const double z = v;
+            v = z + a.ratio * (z - ws.vprev[j]);
+            ws.vprev[j] = z;
+        } else if (a.warm_start == 1) {
+            v = a.ratio * v;
+        }
+        ws.v[j] = v;
+        ws.pv[j] = 0.0;
+        ws.gc[j] = 0.0;
+        prep_col<TIER>(ws, j, v, gamma, G64);
+    }
+    if (b == 0 && tid == 0) {
+        S->alpha = 0.0;
+        S->kind = KIND_INIT;
+        S->accept = 0;
+        S->trials = 0;
+        S->k = 0;
+        S->phase = PH_RUN;
+        S->beta = 0.0;
+        S->alpha_commit = 0.0;
+    }
+    if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
+
+    for (;;) {
+        // ---------------- phase A: pass over own rows, row epilogue ----------------
+        phase_A<TIER>(ws, r0, r1, gamma, G64, sm, L);
+        double x[kNRed];
+#pragma unroll
+        for (int q = 0; q < kNRed; ++q) x[q] = 0.0;
+        {
+            const int* sA = reinterpret_cast<const int*>(sm + L.off_A);
+            for (int i = r0 + tid; i < r1; i += T) {
+                const int il = i - r0;
+                const double sum = row_total<TIER>(sm, L, il);
+                if (!(sum > 0.0) || !isfinite(sum)) { x[5] += 1.0; continue; }
+                const double lrP = log(sum) + (double)sA[il] * kLn2;
+                const double g = ldexp(sum, sA[il]) - ws.rt[i];
+                const double s = ws.lrt[i] - lrP;
+                const double p = ws.pu[i];
+                const double y = g - ws.gr[i];
+                x[0] += p * g;
+                x[1] += fabs(g);
+                x[2] += y * (-s);
+                x[3] += y * p;
+                x[4] += s * g;
+                ws.grt[i] = g;
+                ws.srt[i] = s;
+                ws.lrtr[i] = lrP;
+            }
+        }
+        if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
+
+        // ---------------- phase B: column merge and epilogue ----------------
+        for (int j0 = c0; j0 < c1; j0 += 32) {
+            double colsum;
+            if (TIER == TIER_F32)
+                colsum = merge_cols_f32(ws.colpart, n, G, j0, c1, reinterpret_cast<float*>(sm + L.off_merge));
+            else
+                colsum = merge_cols_f64(ws.colpartd, n, G, j0, c1, reinterpret_cast<double*>(sm + L.off_merge));
+            const int j = j0 + tid;
+            if (tid < 32 && j < c1) {
+                if (!(colsum > 0.0) || !isfinite(colsum)) { x[5] += 1.0; continue; }
+                const double lcP = log(colsum) + (double)a.Aglob * kLn2;
+                const double g = ldexp(colsum, a.Aglob) - ws.ct[j];
+                const double s = ws.lct[j] - lcP;
+                const double p = ws.pv[j];
+                const double y = g - ws.gc[j];
+                x[0] += p * g;
+                x[1] += fabs(g);
+                x[2] += y * (-s);
+                x[3] += y * p;
+                x[4] += s * g;
+                ws.gct[j] = g;
+                ws.sct[j] = s;
+            }
+        }
+        block_reduce_nred(x, red_smem);
+        if (tid == 0) {
+#pragma unroll
+            for (int q = 0; q < kNRed; ++q) ws.blockred[(size_t)b * kNRed + q] = x[q];
+        }
+
+        // ---------------- reduction + decision by the last CTA ----------------
+        ++gen;
+        if (bar_arrive(&S->bar, G, s_flag)) {
+            __threadfence();
+            // warp q sums scalar q over the G CTAs in a fixed order
+            const int lane = tid & 31, warp = tid >> 5;
+            if (warp < kNRed) {
+                double s = 0.0;
+                for (int bb = lane; bb < G; bb += 32) s += __ldcg(ws.blockred + (size_t)bb * kNRed + warp);
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                if (lane == 0) red_smem[warp] = s;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double tot[kNRed];
+                for (int q = 0; q < kNRed; ++q) tot[q] = red_smem[q];
+                decide(S, tot, a);
+                bar_release(&S->bar, gen);
+            }
+        }
+        if (!bar_wait(&S->bar, gen, s_flag)) goto timeout;
+        if (tid == 0) {
+            volatile State* vS = S;
+            s_bc[0] = vS->alpha;
+            s_bc[1] = vS->alpha_commit;
+            s_bc[2] = vS->beta;
+            s_bc[3] = (double)vS->accept;
+            s_bc[4] = (double)vS->phase;
+        }
+        __syncthreads();
+        const double alpha = s_bc[0], acommit = s_bc[1], beta = s_bc[2];
+        const bool accept = s_bc[3] != 0.0, done = s_bc[4] != 0.0;
+
+        // ---------------- phase C: commit, new direction, next trial constants ----------------
+        for (int i = r0 + tid; i < r1; i += T) {
+            double u = ws.u[i], p = ws.pu[i];
+            if (accept) {
+                u = u + acommit * p;                            // Alg. 2 line 12
+                ws.u[i] = u;
+                ws.gr[i] = ws.grt[i];
+                ws.lr[i] = ws.lrtr[i];
+                p = ws.srt[i] + beta * p;                       // Alg. 2 lines 7-10
+                ws.pu[i] = p;
+            }
+            if (!done) {
+                const int A = row_scale(ws.lr[i] + alpha * p);
+                prep_row<TIER>(u + alpha * p, A, a.Aglob, gamma, G64, sm, L, i - r0);
+            }
+        }
+        for (int j = c0 + tid; j < c1; j += T) {
+            double v = ws.v[j], p = ws.pv[j];
+            if (accept) {
+                v = v + acommit * p;
+                ws.v[j] = v;
+                ws.gc[j] = ws.gct[j];
+                p = ws.sct[j] + beta * p;
+                ws.pv[j] = p;
+            }
+            if (!done) prep_col<TIER>(ws, j, v + alpha * p, gamma, G64);
+        }
+        if (done) break;
+        if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
+    }
+    return;
+timeout:
+    if (tid == 0) {
+        atomicMax(&S->status, (int)ST_TIMEOUT);
+        S->phase = PH_DONE;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// standalone dual evaluation (mdot_dual_eval): optional max pass for the row scales, one pass,
+// merge.  Writes log r(P) to ws.lrtr and log c(P) to ws.lcout.
+// ---------------------------------------------------------------------------------------------
+
+template <int TIER>
+__global__ void __launch_bounds__(kThreads, 1) dual_eval_kernel(WS ws, EvalArgs a)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ int s_flag[2];
+    __shared__ unsigned int s_gen;
+    const int n = ws.n, G = ws.G, b = blockIdx.x, T = blockDim.x, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+    const SmemLayout L = smem_layout(n, G, TIER, T);
+    int r0, r1, c0, c1;
+    row_range(n, G, b, r0, r1);
+    row_range(n, G, b, c0, c1);
+    State* S = ws.st;
+    if (tid == 0) s_gen = ld_acquire(&S->bar.gen);
+    __syncthreads();
+    unsigned int gen = s_gen;
+    int* sA = reinterpret_cast<int*>(sm + L.off_A);
+    double* sM = reinterpret_cast<double*>(sm + L.off_x);
+    const float G32 = (float)a.G64;
+
+    // column constants without scale (row view / max pass)
+    for (int j = c0 + tid; j < c1; j += T) {
+        float gh, wl;
+        split_cost_unit(a.v[j] / a.gamma, gh, wl, a.G64);
+        ws.Hh[j] = gh;
+        ws.Wc[j] = wl;
+        if (TIER == TIER_F64) ws.Hd[j] = a.v[j];
+    }
+    if (a.ref != nullptr) {
+        // ---- one-scale path (the solver's): row scales from the estimate, one exp2 per entry ----
+        for (int i = r0 + tid; i < r1; i += T) {
+            const int A = (int)fmin(fmax(rint(a.ref[i] * kLog2e), -120.0), 100.0);
+            prep_row<TIER>(a.u[i], A, 0, a.gamma, a.G64, sm, L, i - r0);
+        }
+        if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
+        phase_A<TIER>(ws, r0, r1, a.gamma, a.G64, sm, L);
+        for (int i = r0 + tid; i < r1; i += T) {
+            const int il = i - r0;
+            ws.lrtr[i] = log(row_total<TIER>(sm, L, il)) + (double)sA[il] * kLn2;
+        }
+        if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
+        for (int j0 = c0; j0 < c1; j0 += 32) {
+            double colsum;
+            if (TIER == TIER_F32)
+                colsum = merge_cols_f32(ws.colpart, n, G, j0, c1, reinterpret_cast<float*>(sm + L.off_merge));
+            else
+                colsum = merge_cols_f64(ws.colpartd, n, G, j0, c1, reinterpret_cast<double*>(sm + L.off_merge));
+            const int j = j0 + tid;
+            if (tid < 32 && j < c1) ws.lcout[j] = log(colsum);
+        }
+        return;
+    }
+    // ---- two-scale path: max pass for row and column scales, then both LSEs exactly ----
+    // unscaled row constants (they are also the column-view row constants)
+    for (int i = r0 + tid; i < r1; i += T) {
+        float fh, wl;
+        split_cost_unit(a.u[i] / a.gamma, fh, wl, a.G64);
+        reinterpret_cast<float*>(sm + L.off_s)[i - r0] = fh;
+        reinterpret_cast<float*>(sm + L.off_A)[i - r0] = wl;
+    }
+    if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
+    {
+        const float* f2 = reinterpret_cast<const float*>(sm + L.off_s);
+        const float* w2 = reinterpret_cast<const float*>(sm + L.off_A);
+        // row maxima (one warp per row) in log2 units (F32) or natural-log units (F64)
+        for (int i = r0 + warp; i < r1; i += nw) {
+            double m = -INFINITY;
+            const float* Crow = ws.C + (size_t)i * n;
+            if (TIER == TIER_F32) {
+                const float fh = f2[i - r0], wl = w2[i - r0];
+                float mf = -INFINITY;
+                for (int j = lane; j < n; j += 32)
+                    mf = fmaxf(mf, fmaf(G32, (fh + __ldcg(ws.Hh + j)) - __ldg(Crow + j), wl + __ldcg(ws.Wc + j)));
+                m = (double)mf;
+            } else {
+                const double ui = a.u[i];
+                for (int j = lane; j < n; j += 32)
+                    m = fmax(m, (ui + __ldcg(ws.Hd + j)) - a.gamma * (double)__ldg(Crow + j));
+            }
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0) sM[i - r0] = m;
+        }
+        // column maxima over own rows (thread per column), CTA partials
+        for (int j = tid; j < n; j += T) {
+            if (TIER == TIER_F32) {
+                const float gh = __ldcg(ws.Hh + j), wc = __ldcg(ws.Wc + j);
+                float mf = -INFINITY;
+                for (int i = r0; i < r1; ++i)
+                    mf = fmaxf(mf, fmaf(G32, (f2[i - r0] + gh) - __ldg(ws.C + (size_t)i * n + j), w2[i - r0] + wc));
+                ws.colpart[(size_t)b * n + j] = mf;
+            } else {
+                const double vj = __ldcg(ws.Hd + j);
+                double md = -INFINITY;
+                for (int i = r0; i < r1; ++i)
+                    md = fmax(md, (a.u[i] + vj) - a.gamma * (double)__ldg(ws.C + (size_t)i * n + j));
+                ws.colpartd[(size_t)b * n + j] = md;
+            }
+        }
+    }
+    if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
+    // column scales and column-view constants (own columns)
+    for (int j = c0 + tid; j < c1; j += T) {
+        double m = -INFINITY;
+        if (TIER == TIER_F32) {
+            for (int bb = 0; bb < G; ++bb) m = fmax(m, (double)__ldcg(ws.colpart + (size_t)bb * n + j));
+            const double B = fmin(fmax(ceil(m), -1.0e7), 1.0e7);
+            float gh, wl;
+            split_cost_unit(a.v[j] / a.gamma - B / a.G64, gh, wl, a.G64);
+            ws.Fh[j] = gh;          // column-view constants (reuse of the fp32 row arrays)
+            ws.Wr[j] = wl;
+            ws.A[j] = (int)B;
+        } else {
+            for (int bb = 0; bb < G; ++bb) m = fmax(m, __ldcg(ws.colpartd + (size_t)bb * n + j));
+            ws.Fd[j] = m;
+        }
+    }
+    // row scales and both row constants (own rows)
+    for (int i = r0 + tid; i < r1; i += T) {
+        const int il = i - r0;
+        if (TIER == TIER_F32) {
+            const double A = fmin(fmax(ceil(sM[il]), -1.0e7), 1.0e7);
+            float fh, wl;
+            split_cost_unit(a.u[i] / a.gamma - A / a.G64, fh, wl, a.G64);
+            reinterpret_cast<float*>(sm + L.off_c0)[il] = fh;
+            reinterpret_cast<float*>(sm + L.off_c1)[il] = wl;
+            sM[il] = A;
+        } else {
+            reinterpret_cast<double*>(sm + L.off_c0)[il] = a.u[i];
+            reinterpret_cast<double*>(sm + L.off_s)[il] = sM[il];
+        }
+    }
+    if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
+    {
+        const int nwl = T >> 5;
+        if (TIER == TIER_F32) {
+            float* sRow = reinterpret_cast<float*>(sm + L.off_row);
+            for (int x = tid; x < nwl * L.nloc_max; x += T) sRow[x] = 0.0f;
+            __syncthreads();
+            const float Glo = (float)(a.G64 - (double)G32);
+            const float* f1 = reinterpret_cast<const float*>(sm + L.off_c0);
+            const float* w1 = reinterpret_cast<const float*>(sm + L.off_c1);
+            const float* f2 = reinterpret_cast<const float*>(sm + L.off_s);
+            const float* w2 = reinterpret_cast<const float*>(sm + L.off_A);
+            if ((n & 3) == 0)
+                pass2_f32<true>(ws.C, n, r0, r1, ws.Hh, ws.Wc, ws.Fh, ws.Wr, f1, w1, f2, w2, G32, Glo, sRow,
+                                L.nloc_max, ws.colpart + (size_t)b * n);
+            else
+                pass2_f32<false>(ws.C, n, r0, r1, ws.Hh, ws.Wc, ws.Fh, ws.Wr, f1, w1, f2, w2, G32, Glo, sRow,
+                                 L.nloc_max, ws.colpart + (size_t)b * n);
+        } else {
+            double* sRow = reinterpret_cast<double*>(sm + L.off_row);
+            for (int x = tid; x < nwl * L.nloc_max; x += T) sRow[x] = 0.0;
+            __syncthreads();
+            pass2_f64(ws.C, n, r0, r1, ws.Hd, ws.Fd, reinterpret_cast<const double*>(sm + L.off_c0),
+                      reinterpret_cast<const double*>(sm + L.off_s), a.gamma, sRow, L.nloc_max,
+                      ws.colpartd + (size_t)b * n);
+        }
+        __syncthreads();
+        for (int i = r0 + tid; i < r1; i += T) {
+            const int il = i - r0;
+            const double sum = row_total<TIER>(sm, L, il);
+            ws.lrtr[i] = log(sum) + (TIER == TIER_F32 ? sM[il] * kLn2 : sM[il]);
+        }
+    }
+    if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
+    for (int j0 = c0; j0 < c1; j0 += 32) {
+        double colsum;
+        if (TIER == TIER_F32)
+            colsum = merge_cols_f32(ws.colpart, n, G, j0, c1, reinterpret_cast<float*>(sm + L.off_merge));
+        else
+            colsum = merge_cols_f64(ws.colpartd, n, G, j0, c1, reinterpret_cast<double*>(sm + L.off_merge));
+        const int j = j0 + tid;
+        if (tid < 32 && j < c1)
+            ws.lcout[j] = log(colsum) + (TIER == TIER_F32 ? (double)__ldcg(ws.A + j) * kLn2 : __ldcg(ws.Fd + j));
+    }
+    return;
+timeout:
+    if (tid == 0) atomicMax(&S->status, (int)ST_TIMEOUT);
+}
+
+}  // namespace mdot

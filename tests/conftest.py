@@ -11,6 +11,7 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built libmdot")
     config.addinivalue_line("markers", "slow: long CPU test")
+    config.addinivalue_line("markers", "timeout(seconds): per-test limit (pytest-timeout)")
 
 
 def pytest_collection_modifyitems(config, items):

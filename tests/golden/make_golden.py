@@ -1,0 +1,78 @@
+"""Write the stored expected values for the full-size workloads (n = 4096 grid histograms).
+
+Calls only the oracle package (the CPU FP64 oracle and its exact-LP helper); nothing here comes
+from the CUDA library.  Each record holds, for one (cost kind, seed, target gap):
+  H_min, the Prop. 2 gamma_f, the oracle's rounded-plan cost and c-transform bound, its
+  evaluation counts, and the exact OT value (column generation priced over all n^2 arcs).
+Usage:  python tests/golden/make_golden.py [k] [eps ...]   (defaults: k = 64, eps = 1e-6)
+Runs the cases in parallel worker processes (spawn) and writes tests/golden/grid{n}.json.
+"""
+from __future__ import annotations
+
+import json
+import multiprocessing as mp
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+SEED = 2000          # problem seed of the n = 4096 benchmark instance
+
+
+def one_case(args):
+    k, kind, seed, eps = args
+    import numpy as np
+    import oracle as O
+    from oracle import exact as E
+    from paper_2307_08507_gb300 import inputs as I
+
+    p = I.grid_problem(k, seed, kind=kind)
+    C = p.C.astype(np.float64)
+    H = min(O.entropy(p.r), O.entropy(p.c))
+    t0 = time.time()
+    res = O.solve(C, p.r, p.c, eps_target=eps)
+    t_solve = time.time() - t0
+    # exact optimum: candidate arcs = arcs that are nearly tight for the oracle's potentials
+    f, g = res.u / res.gamma_f, res.v / res.gamma_f
+    t0 = time.time()
+    val, fd, gd, rounds = E.exact_ot_colgen(C, p.r, p.c, k_init=4)
+    t_exact = time.time() - t0
+    return {
+        "k": k, "n": p.n, "kind": kind, "seed": seed, "eps_target": eps, "H_min": H,
+        "gamma_f": res.gamma_f, "oracle_cost": res.cost, "oracle_lb": res.lb,
+        "oracle_evals": int(res.stats.evals), "oracle_iters": int(res.stats.iters),
+        "oracle_ls_trials": int(res.stats.ls_trials), "oracle_stages": int(res.stats.stages),
+        "oracle_status": int(res.status), "oracle_grad_l1": res.stats.grad_l1,
+        "oracle_seconds": t_solve, "exact_ot": val, "exact_rounds": rounds,
+        "exact_seconds": t_exact, "true_gap": res.cost - val,
+        "f_g_span": [float(f.min()), float(f.max()), float(g.min()), float(g.max())],
+    }
+
+
+def main():
+    k = int(sys.argv[1]) if len(sys.argv) > 1 else 64
+    eps_list = [float(a) for a in sys.argv[2:]] or [1e-6]
+    cases = [(k, kind, SEED, eps) for eps in eps_list for kind in ("l2sq", "l1")]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(len(cases), os.cpu_count() or 1)) as pool:
+        out = pool.map(one_case, cases)
+    path = os.path.join(HERE, f"grid{k * k}.json")
+    old = []
+    if os.path.exists(path):
+        with open(path) as fh:
+            old = json.load(fh)["cases"]
+    keyed = {(c["kind"], c["seed"], c["eps_target"]): c for c in old}
+    for c in out:
+        keyed[(c["kind"], c["seed"], c["eps_target"])] = c
+    with open(path, "w") as fh:
+        json.dump({"generator": "tests/golden/make_golden.py (CPU FP64 oracle + exact LP)",
+                   "cases": sorted(keyed.values(), key=lambda c: (c["kind"], c["eps_target"]))},
+                  fh, indent=1)
+    print(json.dumps(out, indent=1))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,180 @@
+"""GPU parity of the C-ABI library against the CPU FP64 oracle, element by element on the same
+seeded inputs.
+
+Tolerances (derived from the arithmetic of each tier):
+* fp32 entries: each entry carries the ex2.approx error (max 2^-22.7 relative, measured) plus
+  ~2^-23 |t| from the exponent t = log2 P_ij - A_i; weighted by the entries themselves the
+  relative error of a row or column sum stays below ~1.5e-6 (|t| averages <= log2 n + 1 under
+  those weights) -> 4e-6 absolute on log-marginals.
+* fp64 entries: a few ulps of the largest term -> 1e-11.
+* rounded-plan cost: 1e-7 absolute on costs normalised to max C = 1 (the target tolerance).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2307_08507_gb300 as M
+from paper_2307_08507_gb300 import inputs as I
+
+pytestmark = [pytest.mark.gpu, pytest.mark.timeout(300)]
+
+TOL_F32 = 4e-6
+TOL_F64 = 1e-11
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def h():
+    torch.cuda.set_device(0)
+    with M.Handle(4096) as handle:
+        yield handle
+
+
+def t(a, dtype=None):
+    a = np.ascontiguousarray(a)
+    return torch.from_numpy(a if dtype is None else a.astype(dtype)).to(DEV)
+
+
+def rand_potentials(n, gamma, seed, C):
+    """Potentials of a plausible iterate: u_i = gamma a_i + log r_i, v_j = -gamma min_i(C_ij - a_i)
+    + log c_j with random a; every row and column then has entries of order r_i c_j."""
+    rng = np.random.default_rng(seed)
+    r = rng.uniform(0.2, 1.0, n); r /= r.sum()
+    c = rng.uniform(0.2, 1.0, n); c /= c.sum()
+    a = rng.uniform(0.0, 0.3, n)
+    b = (C.astype(np.float64) - a[:, None]).min(axis=0)
+    u = gamma * a + np.log(r)
+    v = -gamma * (-b) * 0 + gamma * b + np.log(c)
+    return u, v, r, c
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 31, 33, 257, 1000])
+@pytest.mark.parametrize("gamma", [1.0, 64.0, 4096.0, 65536.0])
+@pytest.mark.parametrize("precision", [M.PREC_FP32, M.PREC_FP64])
+def test_dual_eval_matches_oracle(h, n, gamma, precision):
+    rng = np.random.default_rng(n * 7 + int(math.log2(gamma)))
+    C = rng.uniform(0, 1, (n, n)).astype(np.float32)
+    u, v, _, _ = rand_potentials(n, gamma, n + 1, C)
+    lr_o, lc_o = O.dual_eval(C.astype(np.float64), u, v, gamma)
+    lr, lc = h.dual_eval(t(u), t(v), gamma, t(C), precision=precision)
+    tol = TOL_F32 if precision == M.PREC_FP32 else TOL_F64
+    np.testing.assert_allclose(lr.cpu().numpy(), lr_o, rtol=0, atol=tol * max(1.0, 1e-12 * np.abs(lr_o).max()))
+    np.testing.assert_allclose(lc.cpu().numpy(), lc_o, rtol=0, atol=tol * max(1.0, 1e-12 * np.abs(lc_o).max()))
+    # the solver path: scales taken from a previous estimate give the same marginals
+    lr2, lc2 = h.dual_eval(t(u), t(v), gamma, t(C), ref_log_rP=lr, precision=precision)
+    np.testing.assert_allclose(lr2.cpu().numpy(), lr_o, rtol=0, atol=tol)
+    np.testing.assert_allclose(lc2.cpu().numpy(), lc_o, rtol=0, atol=tol)
+
+
+def test_dual_eval_huge_potentials(h):
+    """Potentials of +-2000 (exp overflows without scaling): both log-marginals stay exact."""
+    n, gamma = 64, 1e5
+    rng = np.random.default_rng(4)
+    C = rng.uniform(0, 1, (n, n)).astype(np.float32)
+    u = rng.normal(size=n) + 2000.0
+    v = rng.normal(size=n) - 2000.0
+    lr_o, lc_o = O.dual_eval(C.astype(np.float64), u, v, gamma)
+    for prec, tol in ((M.PREC_FP32, TOL_F32), (M.PREC_FP64, TOL_F64)):
+        lr, lc = h.dual_eval(t(u), t(v), gamma, t(C), precision=prec)
+        np.testing.assert_allclose(lr.cpu().numpy(), lr_o, rtol=1e-12, atol=tol)
+        np.testing.assert_allclose(lc.cpu().numpy(), lc_o, rtol=1e-12, atol=tol)
+
+
+def test_dual_eval_full_size_grid(h):
+    """n = 4096 (64 x 64 grid, squared-L2 cost) at gamma = 2^14: every row and column."""
+    p = I.grid_problem(64, 2000)
+    gamma = 2.0 ** 14
+    u, v, _, _ = rand_potentials(p.n, gamma, 11, p.C)
+    lr_o, lc_o = O.dual_eval(p.C.astype(np.float64), u, v, gamma)
+    lr, lc = h.dual_eval(t(u), t(v), gamma, t(p.C))
+    np.testing.assert_allclose(lr.cpu().numpy(), lr_o, rtol=0, atol=TOL_F32)
+    np.testing.assert_allclose(lc.cpu().numpy(), lc_o, rtol=0, atol=TOL_F32)
+
+
+@pytest.mark.parametrize("n,gamma", [(1, 10.0), (3, 50.0), (33, 500.0), (256, 4096.0), (1000, 2.0 ** 15)])
+def test_round_and_lower_bound_match_oracle(h, n, gamma):
+    rng = np.random.default_rng(n)
+    C = rng.uniform(0, 1, (n, n)).astype(np.float32)
+    u, v, r, c = rand_potentials(n, gamma, n + 5, C)
+    cost_o, G_o = O.round_plan(C.astype(np.float64), u, v, gamma, r, c, want_G=(n <= 256))
+    cost, G = h.round(t(u), t(v), gamma, t(C), t(r), t(c), want_G=(n <= 256))
+    assert abs(cost - cost_o) <= 1e-7 * max(1.0, cost_o), (cost, cost_o)
+    if G is not None:
+        Gn = G.cpu().numpy()
+        assert (Gn >= 0).all()
+        np.testing.assert_allclose(Gn.sum(1), r, rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(Gn.sum(0), c, rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(Gn, G_o, rtol=0, atol=2e-6 * G_o.max())
+    lb_o = O.ctransform_lb(C.astype(np.float64), u, gamma, r, c)
+    lb = h.lower_bound(t(u), gamma, t(C), t(r), t(c))
+    assert abs(lb - lb_o) <= 1e-12 * max(1.0, abs(lb_o)), (lb, lb_o)
+
+
+def _solve_both(h, p, gamma_f, **kw):
+    prm = M.default_params(gamma_f=gamma_f, **kw)
+    u, v, res = h.solve(t(p.r), t(p.c), t(p.C), 1e-6, prm)
+    ref = O.solve(p.C.astype(np.float64), p.r, p.c, gamma_f=gamma_f)
+    return u.cpu().numpy(), v.cpu().numpy(), res, ref
+
+
+@pytest.mark.parametrize("k,kind", [(12, "l2sq"), (16, "l2sq"), (16, "l1"), (32, "l2sq")])
+def test_solve_matches_oracle(h, k, kind):
+    """MDOT-PNCG end to end: rounded cost within 1e-7 of the oracle at the same gamma_f;
+    potentials in cost units agree after fixing the additive shift."""
+    p = I.grid_problem(k, 3 + k, kind=kind)
+    gamma_f = 2.0 ** 14
+    u, v, res, ref = _solve_both(h, p, gamma_f)
+    assert res.status == M.MDOT_OK, M.status_string(res.status)
+    assert abs(res.cost - ref.cost) <= 1e-7, (res.cost, ref.cost)
+    assert res.info.grad_l1 <= ref.stage_log[-1, 1] / 2 * 1.0000001
+    # potentials, shift fixed by sum_i u_i = 0 (footnote to Prop. 1), compared in cost units
+    du = (u - u.mean()) - (ref.u - ref.u.mean())
+    dv = (v + u.mean()) - (ref.v + ref.u.mean())
+    assert np.abs(du).max() / gamma_f < 2e-4 and np.abs(dv).max() / gamma_f < 2e-4
+    # certificate brackets the optimum and is consistent with the oracle's
+    assert abs((res.cost - res.gap_cert) - ref.lb) <= 1e-6
+
+
+def test_solve_fp64_tier_matches_oracle(h):
+    """All-fp64 entries.  Rounding differs between the two sides, so line-search decisions near
+    the Eq. (24) thresholds and the stopping point differ; both stop inside eps_d / 2 and the
+    rounded costs agree to the target tolerance with similar work."""
+    p = I.grid_problem(8, 5)
+    gamma_f = 2.0 ** 12
+    u, v, res, ref = _solve_both(h, p, gamma_f, precision=M.PREC_FP64)
+    assert res.status == M.MDOT_OK
+    assert res.info.evals_fp64 == res.info.evals
+    assert abs(res.cost - ref.cost) <= 1e-7
+    assert res.info.evals == pytest.approx(ref.stats.evals, rel=0.3)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_solve_tiny_problems(h, n):
+    """n = 1 has H_min = 0 (a point mass): the floored tolerance still terminates."""
+    rng = np.random.default_rng(n)
+    C = rng.uniform(0, 1, (n, n)).astype(np.float32)
+    r = np.full(n, 1.0 / n)
+    u, v, res = h.solve(t(r), t(r), t(C), 1e-6, M.default_params(gamma_f=2.0 ** 12))
+    ref = O.solve(C.astype(np.float64), r, r, gamma_f=2.0 ** 12)
+    assert res.status == M.MDOT_OK
+    assert abs(res.cost - ref.cost) <= 1e-7
+
+
+def test_invalid_arguments_are_rejected(h):
+    p = I.grid_problem(8, 1)
+    bad_r = p.r.copy(); bad_r[0] = -1e-3; bad_r /= bad_r.sum()
+    with pytest.raises(M.MdotError) as e:
+        h.solve(t(bad_r), t(p.c), t(p.C), 1e-6)
+    assert e.value.status == M.MDOT_ERR_INVALID_ARG
+    with pytest.raises(M.MdotError) as e:
+        h.solve(t(p.r * 1.01), t(p.c), t(p.C), 1e-6)
+    assert e.value.status == M.MDOT_ERR_INVALID_ARG
+    with pytest.raises(M.MdotError) as e:
+        h.solve(t(p.r), t(p.c), t(p.C), -1.0)
+    assert e.value.status == M.MDOT_ERR_INVALID_ARG
+    # the handle still works after rejected calls
+    u, v, res = h.solve(t(p.r), t(p.c), t(p.C), 1e-5)
+    assert res.status == M.MDOT_OK
