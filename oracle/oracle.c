@@ -338,9 +338,11 @@ int or_mdot(int n, const double* C, const double* r, const double* c, const or_p
             memcpy(u_prev, u, sizeof(double) * (size_t)n);
             memcpy(v_prev, v, sizeof(double) * (size_t)n);
         }
-        /* line 6; reading: a tolerance below 1e-13 cannot be resolved by fp64 sums of the
-         * marginals and would never be met, so it is floored there */
-        double tol = fmax(eps_d / 2.0, 1e-13);
+        /* line 6; reading: the fp64 exponent u_i + v_j - gamma C_ij cancels terms of size ~gamma,
+         * so the marginals carry ~2e-16 gamma relative noise; a tolerance below
+         * 1e-13 + 1e-15 gamma could never be met and is floored there (far below eps_d / 2 for
+         * any gamma used in practice) */
+        double tol = fmax(eps_d / 2.0, 1e-13 + 1e-15 * gamma);
         if (gamma == prm->gamma_f && prm->final_tol > 0.0) tol = prm->final_tol;
         int rc;
         if (prm->projector == 1)
