@@ -302,7 +302,8 @@ mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const f
     int stages = 0;
     for (int t = 1;; ++t) {
         const double eps_d = H / std::pow(gamma, P.p);                   // line 3
-        double tol = std::max(eps_d / 2.0, 1e-13);                        // line 6 (floored)
+        // line 6, floored at the fp64 resolution of the marginals (~2e-16 gamma relative noise)
+        double tol = std::max(eps_d / 2.0, 1e-13 + 1e-15 * gamma);
         const bool last = (gamma == gf);
         if (last && P.final_tol > 0.0) tol = P.final_tol;
         StageArgs a{};

@@ -279,10 +279,13 @@ __device__ __forceinline__ void split_cost_unit(double x, float& hi, float& lo, 
     lo = (float)(G64 * (x - h));
 }
 
+// Row scale A_i = round(log2 of the predicted row sum).  Not clamped to the fp32 exponent range:
+// the row sum is formed relative to 2^{A_i} for any A_i; only the column weight 2^{A_i - Aglob}
+// flushes to 0 below 2^-126 (see pow2f_int).
 __device__ __forceinline__ int row_scale(double log_r_pred)
 {
     double a = rint(log_r_pred * kLog2e);
-    a = fmin(fmax(a, -120.0), 100.0);
+    a = fmin(fmax(a, -1.0e6), 1.0e6);
     return (int)a;
 }
 

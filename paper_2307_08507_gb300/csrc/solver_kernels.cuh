@@ -307,7 +307,9 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(WS ws, StageArgs a)
                 if (!(sum > 0.0) || !isfinite(sum)) { x[5] += 1.0; continue; }
                 const double lrP = log(sum) + (double)sA[il] * kLn2;
                 const double g = ldexp(sum, sA[il]) - ws.rt[i];
-                const double s = ws.lrt[i] - lrP;
+                // Eq. (17): s = log r~ - log r(P) = -log1p(g / r~); this form keeps the sign of s
+                // opposite to g down to the last bit, so <s, grad> < 0 (Sec. 4) holds numerically
+                const double s = -log1p(g / ws.rt[i]);
                 const double p = ws.pu[i];
                 const double y = g - ws.gr[i];
                 x[0] += p * g;
@@ -332,9 +334,8 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(WS ws, StageArgs a)
             const int j = j0 + tid;
             if (tid < 32 && j < c1) {
                 if (!(colsum > 0.0) || !isfinite(colsum)) { x[5] += 1.0; continue; }
-                const double lcP = log(colsum) + (double)a.Aglob * kLn2;
                 const double g = ldexp(colsum, a.Aglob) - ws.ct[j];
-                const double s = ws.lct[j] - lcP;
+                const double s = -log1p(g / ws.ct[j]);                  // Eq. (17)
                 const double p = ws.pv[j];
                 const double y = g - ws.gc[j];
                 x[0] += p * g;
@@ -458,26 +459,53 @@ __global__ void __launch_bounds__(kThreads, 1) dual_eval_kernel(WS ws, EvalArgs 
         if (TIER == TIER_F64) ws.Hd[j] = a.v[j];
     }
     if (a.ref != nullptr) {
-        // ---- one-scale path (the solver's): row scales from the estimate, one exp2 per entry ----
-        for (int i = r0 + tid; i < r1; i += T) {
-            const int A = (int)fmin(fmax(rint(a.ref[i] * kLog2e), -120.0), 100.0);
-            prep_row<TIER>(a.u[i], A, 0, a.gamma, a.G64, sm, L, i - r0);
+        // ---- one-scale path (the solver's): row scales from the estimate, one exp2 per entry;
+        // column weights relative to the largest row scale Aglob (grid max) ----
+        {
+            int am = -2000000;
+            for (int i = r0 + tid; i < r1; i += T) {
+                const int A = row_scale(a.ref[i]);
+                sA[i - r0] = A;
+                am = max(am, A);
+            }
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) am = max(am, __shfl_xor_sync(0xffffffffu, am, o));
+            __shared__ int s_am[32];
+            if (lane == 0) s_am[warp] = am;
+            __syncthreads();
+            if (tid == 0) {
+                for (int w = 1; w < nw; ++w) am = max(am, s_am[w]);
+                reinterpret_cast<volatile int*>(ws.scratch)[b] = max(am, s_am[0]);
+            }
         }
         if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
-        phase_A<TIER>(ws, r0, r1, a.gamma, a.G64, sm, L);
-        for (int i = r0 + tid; i < r1; i += T) {
-            const int il = i - r0;
-            ws.lrtr[i] = log(row_total<TIER>(sm, L, il)) + (double)sA[il] * kLn2;
-        }
-        if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
-        for (int j0 = c0; j0 < c1; j0 += 32) {
-            double colsum;
-            if (TIER == TIER_F32)
-                colsum = merge_cols_f32(ws.colpart, n, G, j0, c1, reinterpret_cast<float*>(sm + L.off_merge));
-            else
-                colsum = merge_cols_f64(ws.colpartd, n, G, j0, c1, reinterpret_cast<double*>(sm + L.off_merge));
-            const int j = j0 + tid;
-            if (tid < 32 && j < c1) ws.lcout[j] = log(colsum);
+        {
+            __shared__ int s_ag;
+            if (tid == 0) {
+                int m = -2000000;
+                for (int bb = 0; bb < G; ++bb) m = max(m, reinterpret_cast<const volatile int*>(ws.scratch)[bb]);
+                s_ag = m;
+            }
+            __syncthreads();
+            const int Aglob = s_ag;
+            for (int i = r0 + tid; i < r1; i += T)
+                prep_row<TIER>(a.u[i], sA[i - r0], Aglob, a.gamma, a.G64, sm, L, i - r0);
+            __syncthreads();
+            phase_A<TIER>(ws, r0, r1, a.gamma, a.G64, sm, L);
+            for (int i = r0 + tid; i < r1; i += T) {
+                const int il = i - r0;
+                ws.lrtr[i] = log(row_total<TIER>(sm, L, il)) + (double)sA[il] * kLn2;
+            }
+            if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
+            for (int j0 = c0; j0 < c1; j0 += 32) {
+                double colsum;
+                if (TIER == TIER_F32)
+                    colsum = merge_cols_f32(ws.colpart, n, G, j0, c1, reinterpret_cast<float*>(sm + L.off_merge));
+                else
+                    colsum = merge_cols_f64(ws.colpartd, n, G, j0, c1, reinterpret_cast<double*>(sm + L.off_merge));
+                const int j = j0 + tid;
+                if (tid < 32 && j < c1) ws.lcout[j] = log(colsum) + (double)Aglob * kLn2;
+            }
         }
         return;
     }
