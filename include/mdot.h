@@ -179,6 +179,37 @@ mdot_status mdot_solve_host(mdot_handle* h, const double* r_host, const double* 
                             const mdot_params* prm, double* u_host, double* v_host,
                             double* cost_out, double* gap_out, mdot_info* info);
 
+
+/* ------------------------------------------------------------------------------------------ */
+/* Dual evaluation without any allocation.                                                     */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Largest n accepted by mdot_dual_eval_noalloc. */
+#define MDOT_NOALLOC_MAX_N 4096
+
+/*
+ * mdot_dual_eval without a handle and without allocating device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc, e.g. plugins
+ * whose host framework owns every device allocation, or pipelines that must not allocate once
+ * they are running.  Its scratch (column partials, per-row/column constants, the grid barrier)
+ * is a fixed static device array of about 2.6 MiB, compiled into the library: every GPU on which
+ * the library is loaded holds it until the process exits.
+ *
+ * Semantics are those of mdot_dual_eval with precision MDOT_PREC_FP32; outputs are written
+ * straight into log_rP and log_cP (device, n doubles each).  n must not exceed
+ * MDOT_NOALLOC_MAX_N (larger n returns MDOT_ERR_INVALID_ARG).  stream: a cudaStream_t or NULL.
+ * The call calls no cudaMalloc/cudaFree; it synchronises `stream` before returning.
+ *
+ * Set-up: the first call on a device looks up the device address of the static scratch with
+ * cudaGetSymbolAddress (with that device current); make that first call before any stream
+ * capture.  All calls share the one scratch array and leave it holding their values; the call
+ * clears what must start at zero.  Calls that overlap on the GPU (other streams, other host
+ * threads) race on the scratch: serialise them.
+ */
+mdot_status mdot_dual_eval_noalloc(const double* u, const double* v, double gamma, const float* C,
+                                   int64_t n, const double* ref_log_rP, double* log_rP,
+                                   double* log_cP, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -233,3 +233,27 @@ class Handle:
         if check and s not in (MDOT_OK, MDOT_ERR_NOT_CONVERGED):
             raise MdotError(s, "mdot_solve_host")
         return u, v, SolveResult(s, cost.value, gap.value, info)
+
+
+NOALLOC_MAX_N = 4096
+
+
+def dual_eval_noalloc(u, v, gamma: float, C, log_rP, log_cP, ref_log_rP=None, stream=None) -> int:
+    """mdot_dual_eval_noalloc: fp32-entry dual evaluation that allocates no device memory (its
+    scratch is a static device array inside the library).  For callers that cannot allocate;
+    u, v, C, log_rP, log_cP are caller-owned CUDA tensors.  Returns the mdot_status."""
+    import torch
+    L = lib()
+    if not hasattr(L, "_noalloc_typed"):
+        L.mdot_dual_eval_noalloc.argtypes = [_P, _P, ct.c_double, _P, ct.c_int64, _P, _P, _P, _P]
+        L.mdot_dual_eval_noalloc.restype = ct.c_int32
+        L._noalloc_typed = True
+    n = u.numel()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    ref = _ptr(ref_log_rP, torch.float64, n, "ref_log_rP") if ref_log_rP is not None else None
+    return L.mdot_dual_eval_noalloc(_ptr(u, torch.float64, n, "u"), _ptr(v, torch.float64, n, "v"),
+                                    float(gamma), _ptr(C, torch.float32, n * n, "C"), n, ref,
+                                    _ptr(log_rP, torch.float64, n, "log_rP"),
+                                    _ptr(log_cP, torch.float64, n, "log_cP"),
+                                    ct.c_void_p(stream.cuda_stream))
