@@ -61,8 +61,8 @@ typedef enum mdot_precision {
 typedef struct mdot_params {
     double  gamma_i;        /* first inverse temperature; Sec. 5.2 default 2^4                     */
     double  gamma_f;        /* final inverse temperature; <= 0: derived from eps_target (Prop. 2)  */
-    double  p;              /* stopping exponent, eps_d = H_min / gamma^p (Alg. 1 line 3); 1.5      */
-    double  q;              /* decay factor, gamma <- min(q gamma, gamma_f) (Alg. 1 line 8); 2^(1/3) */
+    double  p;              /* stopping exponent, eps_d = H_min / gamma^p (Alg. 1); 1.5             */
+    double  q;              /* decay factor, gamma <- min(q gamma, gamma_f) (Alg. 1); 2^(1/3)        */
     double  ls_c1, ls_c2;   /* approximate Wolfe constants (App. B, Eq. (24)); 0.1 and 0.5          */
     int32_t ls_max_trials;  /* phi' evaluations per line search before the lower end is taken; 50   */
     int32_t max_iter;       /* PNCG iterations per stage; 100000                                    */
@@ -120,7 +120,7 @@ mdot_status mdot_create(mdot_handle** h, int64_t max_n, void* stream);
 mdot_status mdot_destroy(mdot_handle* h);
 
 /*
- * One dual evaluation (Alg. 2 lines 2-3): one pass over C giving both log-marginals of
+ * One dual evaluation (the two reductions of Alg. 2): one pass over C giving both log-marginals of
  * P(u, v; gamma):
  *   log_rP[i] = u_i + LSE_j(v_j - gamma C_ij),   log_cP[j] = v_j + LSE_i(u_i - gamma C_ij).
  * u, v: n doubles each.  C: n x n float32, row-major.  gamma > 0.
@@ -135,7 +135,7 @@ mdot_status mdot_dual_eval(mdot_handle* h, const double* u, const double* v, dou
                            int32_t precision, double* log_rP, double* log_cP);
 
 /*
- * Alg. 3 applied to P = exp(u 1^T + 1 v^T - gamma C) (Alg. 1 line 12): the rounded plan
+ * Alg. 3 applied to P = exp(u 1^T + 1 v^T - gamma C) (the final plan of Alg. 1): the rounded plan
  * G = X P Y + err_r err_c^T / ||err_r||_1 lies in U(r, c).  Returns <G, C> in *cost_out (host)
  * without forming G; if G_out is non-null (device, n*n doubles, row-major) G is also written.
  * r, c: n doubles each, the ORIGINAL marginals (non-negative, each summing to 1).

@@ -81,10 +81,10 @@ static void lse_cols(int n, const double* C, const double* u, double gamma, doub
 void or_dual_eval(int n, const double* C, const double* u, const double* v, double gamma,
                   double* log_rP, double* log_cP)
 {
-    /* Alg. 2 line 2: log r(P) = u + LSE_r(1 v^T - gamma C) */
+    /* Alg. 2, row reduction: log r(P) = u + LSE_r(1 v^T - gamma C) */
     lse_rows(n, C, v, gamma, log_rP);
     for (int i = 0; i < n; ++i) log_rP[i] += u[i];
-    /* Alg. 2 line 3: log c(P) = v + LSE_c(u 1^T - gamma C) */
+    /* Alg. 2, column reduction: log c(P) = v + LSE_c(u 1^T - gamma C) */
     lse_cols(n, C, u, gamma, log_cP);
     for (int j = 0; j < n; ++j) log_cP[j] += v[j];
 }
@@ -211,7 +211,7 @@ int or_pncg(int n, const double* C, double gamma, const double* r, const double*
     for (int j = 0; j < n; ++j) logc[j] = log(c[j]);
     int status = 0;
 
-    /* Alg. 2 lines 2-4 */
+    /* Alg. 2: marginals and gradient at the starting point */
     or_dual_eval(n, C, u, v, gamma, log_rP, log_cP);
     st->evals++;
     for (int i = 0; i < n; ++i) gr[i] = exp(log_rP[i]) - r[i];
@@ -220,11 +220,11 @@ int or_pncg(int n, const double* C, double gamma, const double* r, const double*
     st->grad_l1_init = gnorm;
 
     int k = 0;
-    while (gnorm > tol) {                                           /* Alg. 2 line 5 */
+    while (gnorm > tol) {                                           /* Alg. 2: stop at ||grad g||_1 <= tol */
         if (k >= prm->max_iter) { status = 1; break; }
         ++k;
         st->iters++;
-        /* line 6: Sinkhorn direction s = (log r - log r(P), log c - log c(P)), Eq. (17);
+        /* Sinkhorn direction s = (log r - log r(P), log c - log c(P)), Eq. (17);
          * precond = 1: diagonal-Hessian direction (r / r(P), c / c(P)) - 1, Eq. (16), used only
          * when every ratio lies in [0.01, 100] (Sec. 4 variant), else s. */
         for (int i = 0; i < n; ++i) s[i] = logr[i] - log_rP[i];
@@ -238,7 +238,7 @@ int or_pncg(int n, const double* C, double gamma, const double* r, const double*
             if (ok)
                 for (int a = 0; a < m; ++a) s[a] = exp(s[a]) - 1.0;
         }
-        /* line 7 with Eq. (18): beta_k = <g_k - g_{k-1}, -s_k> / <g_k - g_{k-1}, p_{k-1}>,
+        /* p <- s + beta p with Eq. (18): beta_k = <g_k - g_{k-1}, -s_k> / <g_k - g_{k-1}, p_{k-1}>,
          * beta_1 = 0.  Reading: a zero or non-finite denominator gives beta = 0. */
         double beta = 0.0;
         if (k > 1) {
@@ -251,20 +251,20 @@ int or_pncg(int n, const double* C, double gamma, const double* r, const double*
             beta = (den != 0.0 && isfinite(num / den)) ? num / den : 0.0;
         }
         for (int a = 0; a < m; ++a) p[a] = s[a] + beta * p[a];
-        /* lines 8-10: reset to s if p is not a descent direction */
+        /* reset to s if p is not a descent direction (Alg. 2) */
         double pg = 0.0;
         for (int a = 0; a < m; ++a) pg += p[a] * gr[a];
         if (pg >= 0.0)
             for (int a = 0; a < m; ++a) p[a] = s[a];
-        /* line 11: line search (App. B) */
+        /* line search (App. B) */
         double alpha = 0.0;
         int lrc = line_search(n, C, gamma, r, c, u, v, p, p + n, log_rP, log_cP, &alpha, prm, st);
         if (lrc == 2) { status = 2; break; }
         if (lrc == 1) status = 1;
-        /* line 12: (u, v) <- (u, v) + alpha p */
+        /* (u, v) <- (u, v) + alpha p */
         for (int i = 0; i < n; ++i) u[i] = u[i] + alpha * p[i];
         for (int j = 0; j < n; ++j) v[j] = v[j] + alpha * p[n + j];
-        /* line 13: new gradient from the accepted trial's marginals */
+        /* new gradient from the accepted trial's marginals */
         memcpy(gr_prev, gr, sizeof(double) * (size_t)m);
         for (int i = 0; i < n; ++i) gr[i] = exp(log_rP[i]) - r[i];
         for (int j = 0; j < n; ++j) gr[n + j] = exp(log_cP[j]) - c[j];
@@ -281,7 +281,7 @@ int or_sinkhorn(int n, const double* C, double gamma, const double* r, const dou
 {
     double* l = (double*)malloc(sizeof(double) * (size_t)n);
     int status = 0;
-    /* Alg. 4 line 2 */
+    /* Alg. 4: row marginal at the starting point */
     lse_rows(n, C, v, gamma, l);
     for (int i = 0; i < n; ++i) log_rP[i] = u[i] + l[i];
     st->half_evals++;
@@ -289,21 +289,21 @@ int or_sinkhorn(int n, const double* C, double gamma, const double* r, const dou
     for (int i = 0; i < n; ++i) res += fabs(r[i] - exp(log_rP[i]));
     st->grad_l1_init = res;
     long it = 0;
-    while (res > tol) {                                             /* line 3 */
+    while (res > tol) {                                             /* Alg. 4: stop on the row residual */
         if (it >= prm->max_iter) { status = 1; break; }
         ++it;
         st->iters++;
-        for (int i = 0; i < n; ++i) u[i] = u[i] + log(r[i]) - log_rP[i];       /* line 4 */
-        lse_cols(n, C, u, gamma, l);                                           /* line 5 */
+        for (int i = 0; i < n; ++i) u[i] = u[i] + log(r[i]) - log_rP[i];       /* row update */
+        lse_cols(n, C, u, gamma, l);                                           /* column update */
         for (int j = 0; j < n; ++j) v[j] = log(c[j]) - l[j];
-        lse_rows(n, C, v, gamma, l);                                           /* line 6 */
+        lse_rows(n, C, v, gamma, l);                                           /* new row marginal */
         for (int i = 0; i < n; ++i) log_rP[i] = u[i] + l[i];
         st->half_evals += 2;
         res = 0.0;
         for (int i = 0; i < n; ++i) res += fabs(r[i] - exp(log_rP[i]));
         if (!isfinite(res)) { status = 3; break; }
     }
-    st->grad_l1 = res;   /* the column residual is zero after line 5 */
+    st->grad_l1 = res;   /* the column residual is zero after the column update */
     free(l);
     return status;
 }
@@ -312,7 +312,7 @@ int or_mdot(int n, const double* C, const double* r, const double* c, const or_p
             double* u, double* v, or_stats* st, double* stage_log, int max_log)
 {
     /* H_min(r, c); reading: floored at 1e-12 so that a point-mass marginal (H_min = 0) still gets
-     * a positive smoothing weight (Alg. 1 line 4) instead of log 0 */
+     * a positive smoothing weight (Alg. 1) instead of log 0 */
     const double H = fmax(fmin(or_entropy(n, r), or_entropy(n, c)), 1e-12);
     double* rt = (double*)malloc(sizeof(double) * (size_t)n);
     double* ct = (double*)malloc(sizeof(double) * (size_t)n);
@@ -323,22 +323,22 @@ int or_mdot(int n, const double* C, const double* r, const double* c, const or_p
     memset(st, 0, sizeof(*st));
     int status = 0;
 
-    double gamma = fmin(prm->gamma_i, prm->gamma_f);                /* line 1 */
+    double gamma = fmin(prm->gamma_i, prm->gamma_f);                /* gamma_1 = min(gamma_i, gamma_f) */
     double dgamma_prev = gamma;   /* reading: stage 0 is gamma = 0 (Prop. 1), so the first step is gamma_i */
     int t = 1;
-    for (;;) {                                                      /* line 2 */
-        double eps_d = H / pow(gamma, prm->p);                      /* line 3 */
+    for (;;) {                                                      /* MDOT outer loop (Alg. 1) */
+        double eps_d = H / pow(gamma, prm->p);                      /* stopping tolerance eps_d */
         double w = (prm->smoothing == 1) ? H / pow(prm->gamma_f, prm->p) : eps_d;
-        for (int i = 0; i < n; ++i) rt[i] = (1.0 - w / 4.0) * r[i] + w / (4.0 * n);   /* line 4 */
+        for (int i = 0; i < n; ++i) rt[i] = (1.0 - w / 4.0) * r[i] + w / (4.0 * n);   /* smoothing */
         for (int j = 0; j < n; ++j) ct[j] = (1.0 - w / 4.0) * c[j] + w / (4.0 * n);
-        if (t == 1) {                                               /* line 5 */
+        if (t == 1) {                                               /* rank-one start */
             for (int i = 0; i < n; ++i) u[i] = log(rt[i]);
             for (int j = 0; j < n; ++j) v[j] = log(ct[j]);
             /* reading: z^(0) = (log r~, log c~) is the gamma = 0 solution used by the first warm start */
             memcpy(u_prev, u, sizeof(double) * (size_t)n);
             memcpy(v_prev, v, sizeof(double) * (size_t)n);
         }
-        /* line 6; reading: the fp64 exponent u_i + v_j - gamma C_ij cancels terms of size ~gamma,
+        /* projection tolerance eps_d / 2; reading: the fp64 exponent u_i + v_j - gamma C_ij cancels terms of size ~gamma,
          * so the marginals carry ~2e-16 gamma relative noise; a tolerance below
          * 1e-13 + 1e-15 gamma could never be met and is floored there (far below eps_d / 2 for
          * any gamma used in practice) */
@@ -358,11 +358,11 @@ int or_mdot(int n, const double* C, const double* r, const double* c, const or_p
             L[3] = (double)st->iters; L[4] = st->grad_l1; L[5] = st->grad_l1_init;
         }
         if (rc >= 2) break;
-        if (gamma == prm->gamma_f) break;                           /* line 7 */
-        double dgamma = (prm->q - 1.0) * gamma;                     /* line 8 */
+        if (gamma == prm->gamma_f) break;                           /* exit at gamma_f */
+        double dgamma = (prm->q - 1.0) * gamma;                     /* gamma <- min(gamma + (q-1) gamma, gamma_f) */
         double gamma_next = fmin(gamma + dgamma, prm->gamma_f);
         dgamma = gamma_next - gamma;   /* reading: the clamped last step uses its actual size */
-        /* line 9: warm start */
+        /* warm start */
         if (prm->warm_start == 0) {
             /* Eq. (13): z' = z^(t) + (dgamma^(t) / dgamma^(t-1)) (z^(t) - z^(t-1)) */
             double ratio = dgamma / dgamma_prev;
@@ -384,7 +384,7 @@ int or_mdot(int n, const double* C, const double* r, const double* c, const or_p
         }
         dgamma_prev = dgamma;
         gamma = gamma_next;
-        ++t;                                                        /* line 10 */
+        ++t;                                                        /* next stage */
     }
     st->status = status;
     free(rt); free(ct); free(u_prev); free(v_prev); free(lr); free(lc);
@@ -401,27 +401,27 @@ double or_round(int n, const double* C, const double* u, const double* v, double
     double* cF = (double*)malloc(sizeof(double) * (size_t)n);
     double* er = (double*)malloc(sizeof(double) * (size_t)n);
     double* ec = (double*)malloc(sizeof(double) * (size_t)n);
-    /* Alg. 1 line 12: P = exp(u 1^T + 1 v^T - gamma_f C) */
+    /* Alg. 1, final plan: P = exp(u 1^T + 1 v^T - gamma_f C) */
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) P[IDX(i, j)] = exp(u[i] + v[j] - gamma * C[IDX(i, j)]);
-    /* Alg. 3 line 1: x = r / r(P) ^ 1 (elementwise min); reading: r(P)_i = 0 gives x_i = 1 */
+    /* Alg. 3: x = r / r(P) ^ 1 (elementwise min); reading: r(P)_i = 0 gives x_i = 1 */
     for (int i = 0; i < n; ++i) {
         double s = 0.0;
         for (int j = 0; j < n; ++j) s += P[IDX(i, j)];
         x[i] = (s > 0.0) ? fmin(r[i] / s, 1.0) : 1.0;
     }
-    /* line 2: F = X P */
+    /* F = X P */
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) P[IDX(i, j)] *= x[i];
-    /* line 3: y = c / c(F) ^ 1 */
+    /* y = c / c(F) ^ 1 */
     for (int j = 0; j < n; ++j) cF[j] = 0.0;
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) cF[j] += P[IDX(i, j)];
     for (int j = 0; j < n; ++j) y[j] = (cF[j] > 0.0) ? fmin(c[j] / cF[j], 1.0) : 1.0;
-    /* line 4: F' = F Y */
+    /* F' = F Y */
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) P[IDX(i, j)] *= y[j];
-    /* line 5: err_r = r - r(F'), err_c = c - c(F') */
+    /* err_r = r - r(F'), err_c = c - c(F') */
     for (int i = 0; i < n; ++i) {
         double s = 0.0;
         for (int j = 0; j < n; ++j) s += P[IDX(i, j)];
@@ -434,7 +434,7 @@ double or_round(int n, const double* C, const double* u, const double* v, double
     double er1 = 0.0;
     for (int i = 0; i < n; ++i) er1 += fabs(er[i]);
     for (int j = 0; j < n; ++j) ec[j] = c[j] - cF[j];
-    /* line 6: G = F' + err_r err_c^T / ||err_r||_1; reading: ||err_r||_1 = 0 gives G = F' */
+    /* G = F' + err_r err_c^T / ||err_r||_1; reading: ||err_r||_1 = 0 gives G = F' */
     double cost = 0.0;
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) {

@@ -25,7 +25,7 @@ extern "C" {
 typedef struct {
     double gamma_i;        /* first inverse temperature (Alg. 1 input), paper default 2^4          */
     double gamma_f;        /* final inverse temperature (Alg. 1 input)                             */
-    double p;              /* stopping-rule exponent, eps_d = H_min / gamma^p (Alg. 1, line 3)     */
+    double p;              /* stopping-rule exponent, eps_d = H_min / gamma^p (Alg. 1)             */
     double q;              /* temperature decay factor, gamma <- min(q gamma, gamma_f)             */
     double ls_c1, ls_c2;   /* approximate Wolfe constants, 0 < c1 < c2 < 1 (App. B, Eq. (24))      */
     int    ls_max_trials;  /* cap on phi' evaluations per line search                              */
@@ -33,7 +33,7 @@ typedef struct {
     int    projector;      /* 0 = PNCG (Alg. 2), 1 = Sinkhorn (Alg. 4)                             */
     int    warm_start;     /* 0 = finite-difference Taylor step (Eq. (13)), 1 = eps-scaling, 2 = none */
     int    precond;        /* 0 = Sinkhorn direction s (Eq. (17)), 1 = diagonal Hessian (Eq. (16)) with fallback */
-    int    smoothing;      /* 0 = variable weight eps_d/4 (Alg. 1, line 4), 1 = fixed weight at gamma_f */
+    int    smoothing;      /* 0 = variable weight eps_d/4 (Alg. 1), 1 = fixed weight at gamma_f */
     double final_tol;      /* if > 0: tolerance used at the final stage instead of eps_d/2         */
 } or_params;
 
@@ -54,7 +54,7 @@ void   or_default_params(or_params* prm);
 /* H(r) = -<r, log r>, with 0 log 0 = 0 (Sec. 2, notation). */
 double or_entropy(int n, const double* r);
 
-/* Alg. 2 lines 2-3: log r(P) = u + LSE_r(1 v^T - gamma C), log c(P) = v + LSE_c(u 1^T - gamma C),
+/* Alg. 2 (the two reductions): log r(P) = u + LSE_r(1 v^T - gamma C), log c(P) = v + LSE_c(u 1^T - gamma C),
  * each log-sum-exp stabilised by its own row / column maximum. */
 void   or_dual_eval(int n, const double* C, const double* u, const double* v, double gamma,
                     double* log_rP, double* log_cP);
@@ -78,7 +78,7 @@ int    or_sinkhorn(int n, const double* C, double gamma, const double* r, const 
 int    or_mdot(int n, const double* C, const double* r, const double* c, const or_params* prm,
                double* u, double* v, or_stats* st, double* stage_log, int max_log);
 
-/* Alg. 3 (rounding onto U(r, c)) applied to P = exp(u 1^T + 1 v^T - gamma C) (Alg. 1 line 12).
+/* Alg. 3 (rounding onto U(r, c)) applied to P = exp(u 1^T + 1 v^T - gamma C) (the final plan of Alg. 1).
  * G (nullable, n*n) receives the rounded plan; returns <G, C>. */
 double or_round(int n, const double* C, const double* u, const double* v, double gamma,
                 const double* r, const double* c, double* G);

@@ -264,7 +264,7 @@ mdot_status check_marginals(mdot_handle* h, const WS& ws, double* H)
                  o[0], o[1], o[4], o[5], o[6]);
         return MDOT_ERR_INVALID_ARG;
     }
-    // H_min floored at 1e-12: a point-mass marginal keeps a positive smoothing weight (Alg. 1 line 4)
+    // H_min floored at 1e-12: a point-mass marginal keeps a positive smoothing weight (Alg. 1)
     *H = std::max(std::min(o[2], o[3]), 1e-12);
     return MDOT_OK;
 }
@@ -301,15 +301,15 @@ mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const f
     double ratio = 0.0;
     int stages = 0;
     for (int t = 1;; ++t) {
-        const double eps_d = H / std::pow(gamma, P.p);                   // line 3
-        // line 6, floored at the fp64 resolution of the marginals (~2e-16 gamma relative noise)
+        const double eps_d = H / std::pow(gamma, P.p);                   // stopping tolerance (Alg. 1)
+        // projection tolerance eps_d / 2, floored at the fp64 resolution of the marginals (~2e-16 gamma relative noise)
         double tol = std::max(eps_d / 2.0, 1e-13 + 1e-15 * gamma);
         const bool last = (gamma == gf);
         if (last && P.final_tol > 0.0) tol = P.final_tol;
         StageArgs a{};
         a.gamma = gamma;
         a.G64 = gamma * kLog2e;
-        a.w = eps_d;                                                       // line 4
+        a.w = eps_d;                                                       // smoothing weight
         a.ratio = ratio;
         a.c1 = P.ls_c1;
         a.c2 = P.ls_c2;
@@ -348,16 +348,16 @@ mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const f
             }
         }
         ++stages;
-        if (last) break;                                                   // line 7
-        double dg = (P.q - 1.0) * gamma;                                   // line 8
+        if (last) break;                                                   // exit at gamma_f
+        double dg = (P.q - 1.0) * gamma;                                   // gamma <- min(q gamma, gamma_f)
         const double gnext = std::min(gamma + dg, gf);
         dg = gnext - gamma;
-        ratio = (P.warm_start == 1) ? gnext / gamma : dg / dgamma_prev;    // line 9, Eq. (13)
+        ratio = (P.warm_start == 1) ? gnext / gamma : dg / dgamma_prev;    // warm start, Eq. (13)
         dgamma_prev = dg;
         gamma = gnext;
         if (stages > 100000) return MDOT_ERR_INVALID_ARG;
     }
-    // Alg. 1 lines 12-13: round P(u, v; gamma_f) onto U(r, c); then the lower bound
+    // Alg. 1, final step: round P(u, v; gamma_f) onto U(r, c); then the lower bound
     RoundArgs ra{};
     ra.gamma = gf;
     ra.G64 = gf * kLog2e;

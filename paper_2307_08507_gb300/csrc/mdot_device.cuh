@@ -1,6 +1,6 @@
 // Device-side building blocks of the MDOT-PNCG library (sm_103a).
 //
-// One dual evaluation (Alg. 2 lines 2-3) is one pass over the n x n cost matrix.  A cooperative
+// One dual evaluation (the two reductions of Alg. 2) is one pass over the n x n cost matrix.  A cooperative
 // grid of G CTAs (one per SM) splits the ROWS evenly: CTA b owns rows [r0_b, r1_b) and sweeps all
 // columns in blocks of 4*K*T.  Per entry it forms the log2 of P_ij relative to a per-row scale
 // 2^{A_i}, takes ONE exp2, and adds the result both into the row sum (complete inside the CTA) and,
@@ -62,7 +62,7 @@ struct WS {
     int n, G;
     const float* C;
     const double *r, *c;              // original marginals
-    double *rt, *ct, *lrt, *lct;      // smoothed marginals and logs (Alg. 1 line 4)
+    double *rt, *ct, *lrt, *lct;      // smoothed marginals and logs (Alg. 1)
     double *u, *v, *pu, *pv, *uprev, *vprev;
     double *gr, *gc;                  // gradient at the current point
     double *grt, *gct, *srt, *sct;    // gradient and Sinkhorn direction at the trial point

@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(WS ws, RoundArgs a)
     for (int x0 = tid; x0 < (T >> 5) * 3 * nloc; x0 += T) sAcc[x0] = 0.0;
     if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
 
-    // pass 1: r(P)_i = 2^{A_i} sum_j E_ij ; x_i = min(r_i / r(P)_i, 1)  (Alg. 3 line 1)
+    // pass 1: r(P)_i = 2^{A_i} sum_j E_ij ; x_i = min(r_i / r(P)_i, 1)  (Alg. 3)
     pass_round<RM_ROWSUM, 16>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sX, G32, Glo, nullptr, nullptr,
                               nullptr, 0.0, sAcc, nloc, nullptr, nullptr);
     __syncthreads();
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(WS ws, RoundArgs a)
         sX[il] = ldexp(xi, sA[il]);     // x_i 2^{A_i}: scale of row i of F = X P
     }
     __syncthreads();
-    // pass 2: c(F)_j = sum_i x_i P_ij  (Alg. 3 lines 2-3)
+    // pass 2: c(F)_j = sum_i x_i P_ij  (Alg. 3)
     pass_round<RM_COLSUM, 16>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sX, G32, Glo, nullptr, nullptr,
                               nullptr, 0.0, sAcc, nloc, ws.colpartd + (size_t)b * n, nullptr);
     if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
@@ -209,14 +209,14 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(WS ws, RoundArgs a)
         const double cF = merge_cols_f64(ws.colpartd, n, G, j0, c1, reinterpret_cast<double*>(sm + L.off_merge));
         const int j = j0 + tid;
         if (tid < 32 && j < c1) {
-            const double yj = (cF > 0.0) ? fmin(a.c[j] / cF, 1.0) : 1.0;     // line 3
+            const double yj = (cF > 0.0) ? fmin(a.c[j] / cF, 1.0) : 1.0;     // y = c / c(F) ^ 1
             a.Y[j] = yj;
-            a.EC[j] = a.c[j] - cF * yj;                                        // line 5, columns
+            a.EC[j] = a.c[j] - cF * yj;                                        // err_c
         }
     }
     for (int x0 = tid; x0 < (T >> 5) * 3 * nloc; x0 += T) sAcc[x0] = 0.0;
     if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
-    // pass 3: r(F')_i, <F', C> by rows, (C err_c)_i   (lines 4-6)
+    // pass 3: r(F')_i, <F', C> by rows, (C err_c)_i   (Alg. 3)
     pass_round<RM_ROWFINAL, 8>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sX, G32, Glo, a.Y, a.EC,
                                nullptr, 0.0, sAcc, nloc, nullptr, nullptr);
     __syncthreads();
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(WS ws, RoundArgs a)
         }
     }
     if (a.G_out != nullptr) {
-        // G = F' + err_r err_c^T / ||err_r||_1 (line 6), written row-major in fp64
+        // G = F' + err_r err_c^T / ||err_r||_1 (Alg. 3), written row-major in fp64
         pass_round<RM_WRITE, 16>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sX, G32, Glo, a.Y, a.EC,
                                  a.ER, (e1 > 0.0) ? 1.0 / e1 : 0.0, sAcc, nloc, nullptr, a.G_out);
     }

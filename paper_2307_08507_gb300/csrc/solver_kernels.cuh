@@ -1,5 +1,5 @@
-// Cooperative kernels of the MDOT-PNCG solve: one launch runs one MDOT stage (Alg. 1 lines 3-6:
-// smoothing, warm start, then the PNCG projection of Alg. 2 with the App. B line search) entirely
+// Cooperative kernels of the MDOT-PNCG solve: one launch runs one MDOT stage of Alg. 1
+// (smoothing, warm start, then the PNCG projection of Alg. 2 with the App. B line search) entirely
 // on the device.  Per evaluation: phase A (pass over C, row epilogue) -> grid barrier -> phase B
 // (column merge, column epilogue, per-CTA partial sums) -> arrive; the last CTA reduces the
 // partials in a fixed order and takes the line-search / PNCG decision -> phase C (commit the
@@ -85,7 +85,7 @@ static __device__ void decide(volatile State* S, const double* tot, const StageA
         S->beta = 0.0;
         return;
     }
-    // next direction p = s + beta p (Alg. 2 line 7), reset to s if not a descent direction
+    // next direction p = s + beta p (Alg. 2, Eq. (18)), reset to s if not a descent direction
     double beta = 0.0;
     if (!was_init) {
         const double q = num / den;
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(WS ws, StageArgs a)
     __syncthreads();
     unsigned int gen = s_gen;
 
-    // ---- prologue: Alg. 1 lines 4, 5 and 9 for own rows / columns, constants at alpha = 0 ----
+    // ---- prologue (Alg. 1): smoothing, rank-one start or warm start, constants at alpha = 0 ----
     for (int i = r0 + tid; i < r1; i += T) {
         const double rt = (1.0 - w / 4.0) * ws.r[i] + w / (4.0 * n);
         const double lrt = log(rt);
@@ -391,11 +391,11 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(WS ws, StageArgs a)
         for (int i = r0 + tid; i < r1; i += T) {
             double u = ws.u[i], p = ws.pu[i];
             if (accept) {
-                u = u + acommit * p;                            // Alg. 2 line 12
+                u = u + acommit * p;                            // (u, v) += alpha p (Alg. 2)
                 ws.u[i] = u;
                 ws.gr[i] = ws.grt[i];
                 ws.lr[i] = ws.lrtr[i];
-                p = ws.srt[i] + beta * p;                       // Alg. 2 lines 7-10
+                p = ws.srt[i] + beta * p;                       // p = s + beta p, beta = 0 on reset (Alg. 2)
                 ws.pu[i] = p;
             }
             if (!done) {

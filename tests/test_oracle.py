@@ -20,7 +20,7 @@ def _rand_problem(n, seed, kind="rand"):
 
 
 # ---------------------------------------------------------------------------------------------
-# Dual evaluation, Eq. (2)-(4) and Alg. 2 lines 2-3
+# Dual evaluation, Eq. (2)-(4) and the two reductions of Alg. 2
 # ---------------------------------------------------------------------------------------------
 
 def test_gradient_matches_finite_differences_of_dual():
@@ -130,7 +130,7 @@ def test_pncg_and_sinkhorn_reach_the_same_plan():
 
 
 def test_sinkhorn_column_residual_is_zero():
-    """Alg. 4 line 5 sets v so that c(P) = c exactly after every iteration."""
+    """The column update of Alg. 4 sets v so that c(P) = c exactly after every iteration."""
     n, gamma = 10, 25.0
     C, r, c = _rand_problem(n, 10)
     u, v, rc, st, lr = O.sinkhorn(C, gamma, r, c, 1e-6, np.zeros(n), np.zeros(n))
@@ -234,7 +234,7 @@ def test_prop1_one_step_cost_decrease_equality():
 
 def test_stage_schedule_and_counts():
     """Alg. 1: gamma_1 = min(gamma_i, gamma_f), gamma <- min(q gamma, gamma_f), exit at gamma_f;
-    eps_d = H_min / gamma^p (line 3)."""
+    eps_d = H_min / gamma^p."""
     p = I.grid_problem(4, 2)
     q = 2.0 ** (1 / 3)
     u, v, rc, st, log = O.mdot(p.C, p.r, p.c, gamma_f=2.0 ** 8)
@@ -243,7 +243,7 @@ def test_stage_schedule_and_counts():
     np.testing.assert_allclose(log[:, 0], expected, rtol=1e-12)
     H = min(O.entropy(p.r), O.entropy(p.c))
     np.testing.assert_allclose(log[:, 1], H / log[:, 0] ** 1.5, rtol=1e-12)
-    # every stage met its tolerance eps_d / 2 (line 6)
+    # every stage met its tolerance eps_d / 2
     assert (log[:, 4] <= log[:, 1] / 2).all()
     # single stage when gamma_i >= gamma_f (the Sinkhorn-algorithm setting, Prop. 2)
     _, _, _, st1, log1 = O.mdot(p.C, p.r, p.c, gamma_i=64.0, gamma_f=64.0)
