@@ -39,6 +39,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample-evals", type=int, default=0, help="oracle evaluations in the CPU sample")
+    ap.add_argument("--case", default="solve", choices=["solve", "dual_eval", "stage"],
+                    help="dual_eval / stage: run only that kernel (for profiler captures)")
+    ap.add_argument("--grid", type=int, default=64, help="k of the k x k grid for --case runs")
+    ap.add_argument("--reps", type=int, default=3)
     return ap.parse_args()
 
 
@@ -332,8 +336,39 @@ def run_ours(args, rank, world):
         dist.destroy_process_group()
 
 
+def run_case(args):
+    """Small fixed workloads for profiler captures: the one-pass dual evaluation (fp32 entries,
+    row scales given) or one full solve of a k x k grid problem."""
+    import numpy as np
+    import torch
+    import paper_2307_08507_gb300 as M
+    from paper_2307_08507_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    p = I.grid_problem(args.grid, SEED)
+    h = M.Handle(p.n)
+    C = torch.from_numpy(p.C).to(dev)
+    if args.case == "dual_eval":
+        u = torch.from_numpy(np.log(p.r)).to(dev)
+        v = torch.from_numpy(np.log(p.c)).to(dev)
+        lr, _ = h.dual_eval(u, v, 2.0 ** 12, C)
+        for _ in range(args.reps):
+            h.dual_eval(u, v, 2.0 ** 12, C, ref_log_rP=lr)
+    else:
+        r = torch.from_numpy(p.r).to(dev)
+        c = torch.from_numpy(p.c).to(dev)
+        for _ in range(args.reps):
+            h.solve(r, c, C, EPS)
+    torch.cuda.synchronize()
+    h.close()
+    print(f"case {args.case} n={p.n} reps={args.reps} done")
+
+
 def main():
     args = parse()
+    if args.case != "solve":
+        run_case(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":

@@ -49,12 +49,16 @@ typedef enum mdot_status {
     MDOT_NOT_READY = 7            /* asynchronous result not available yet                   */
 } mdot_status;
 
-/* Arithmetic used for the per-entry work of a dual evaluation. */
+/* Arithmetic used for the per-entry work of a dual evaluation (the O(n) work, the line-search test,
+ * rounding sums and the bound are fp64 in every mode). */
 typedef enum mdot_precision {
     MDOT_PREC_AUTO = 0,   /* fp32 entries while its noise floor is below the stage tolerance,
                              fp64 entries for the final stage when it is not (and for n <= 512) */
     MDOT_PREC_FP32 = 1,   /* always fp32 entries (exact cost-unit difference, ex2.approx)      */
-    MDOT_PREC_FP64 = 2    /* always fp64 entries                                              */
+    MDOT_PREC_FP64 = 2,   /* always fp64 entries                                              */
+    MDOT_PREC_FP32A = 3   /* fp32 entries with a double-float exponent and a polynomial exp2
+                             (about 1 ulp, unbiased); AUTO uses it once a stage's tolerance is
+                             below 2e-6                                                         */
 } mdot_precision;
 
 /* Parameters of Alg. 1 / Alg. 2 / App. B.  Fill with mdot_default_params, then override. */
@@ -69,7 +73,7 @@ typedef struct mdot_params {
     int32_t precision;      /* mdot_precision                                                      */
     int32_t warm_start;     /* 0: Taylor step, Eq. (13); 1: eps-scaling (Sec. 3.3.1); 2: none       */
     double  final_tol;      /* > 0: ||grad g||_1 target of the final stage instead of eps_d / 2     */
-    double  fp32_floor;     /* ||grad g||_1 below which fp32 entries are not trusted; 3e-7          */
+    double  fp32_floor;     /* ||grad g||_1 below which fp32 entries are not trusted; 5e-8          */
     int32_t profile;        /* non-zero: time each kernel launch with CUDA events (mdot_info t_*)    */
     int32_t reserved[7];
 } mdot_params;
@@ -94,7 +98,9 @@ typedef struct mdot_info {
     double  t_bound_ms;     /* with profile: device time of the lower-bound launch                 */
     int32_t launches;       /* kernel launches made by the call                                    */
     int32_t stage_launches_fp32; /* stage launches with fp32 entries                               */
-    double  reserved[1];
+    int32_t stalls;         /* stages ended because ||grad g||_1 stopped improving (no 1 % gain in
+                               40 accepted iterations: tolerance below the arithmetic's floor)   */
+    int32_t reserved_i;
 } mdot_info;
 
 typedef struct mdot_handle mdot_handle;

@@ -22,7 +22,7 @@ MDOT_ERR_NUMERIC = 3
 MDOT_ERR_TIMEOUT = 4
 MDOT_ERR_OOM = 5
 MDOT_ERR_CUDA = 6
-PREC_AUTO, PREC_FP32, PREC_FP64 = 0, 1, 2
+PREC_AUTO, PREC_FP32, PREC_FP64, PREC_FP32A = 0, 1, 2, 3
 
 
 class Params(ct.Structure):
@@ -40,10 +40,10 @@ class Info(ct.Structure):
                 ("cost", ct.c_double), ("lower_bound", ct.c_double), ("gap_cert", ct.c_double),
                 ("t_stage_fp32_ms", ct.c_double), ("t_stage_fp64_ms", ct.c_double),
                 ("t_round_ms", ct.c_double), ("t_bound_ms", ct.c_double), ("launches", ct.c_int32),
-                ("stage_launches_fp32", ct.c_int32), ("reserved", ct.c_double * 1)]
+                ("stage_launches_fp32", ct.c_int32), ("stalls", ct.c_int32), ("reserved_i", ct.c_int32)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
 
 
 class MdotError(RuntimeError):

@@ -72,7 +72,7 @@ void mdot_default_params(mdot_params* prm)
     prm->precision = MDOT_PREC_AUTO;
     prm->warm_start = 0;
     prm->final_tol = 0.0;
-    prm->fp32_floor = 3e-7;
+    prm->fp32_floor = 5e-8;
     prm->profile = 0;
 }
 
@@ -185,7 +185,7 @@ mdot_status params_ok(const mdot_params& P)
 {
     if (!(P.gamma_i > 0.0) || !(P.p >= 1.0) || !(P.q > 1.0) || !(P.ls_c1 > 0.0) ||
         !(P.ls_c2 > P.ls_c1) || !(P.ls_c2 < 1.0) || P.ls_max_trials < 1 || P.max_iter < 1 ||
-        P.precision < 0 || P.precision > 2 || P.warm_start < 0 || P.warm_start > 2 ||
+        P.precision < 0 || P.precision > 3 || P.warm_start < 0 || P.warm_start > 2 ||
         !(P.fp32_floor >= 0.0) || !std::isfinite(P.gamma_f))
         return MDOT_ERR_INVALID_ARG;
     return MDOT_OK;
@@ -287,9 +287,13 @@ mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const f
     mdot_status ms = check_marginals(h, ws, &H);
     if (ms != MDOT_OK) return ms;
     const double gf = (P.gamma_f > 0.0) ? P.gamma_f : gamma_f_for_eps(H, eps_target, P.gamma_i, P.q, P.p);
+    // precision tiers: fp64 entries for small n; otherwise fp32 entries with ex2.approx while the
+    // stage tolerance is loose, the accurate fp32 tier (double-float exponent, polynomial exp2)
+    // once it is below kAccSwitch, and an fp64 polish of the last stage if even that tolerance is
+    // below the accurate tier's noise floor (fp32_floor)
+    constexpr double kAccSwitch = 2e-6;
     const bool all64 = P.precision == MDOT_PREC_FP64 || (P.precision == MDOT_PREC_AUTO && n <= 512);
     const bool polish = P.precision == MDOT_PREC_AUTO && !all64;
-
     CKR(reset_state(h));
     Timer tm;
     tm.on = P.profile != 0;
@@ -326,10 +330,12 @@ mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const f
             tm.end();
             ++launches;
         } else {
-            a.tier = TIER_F32;
+            int tier = TIER_F32;
+            if (P.precision == MDOT_PREC_FP32A || (P.precision == MDOT_PREC_AUTO && tol < kAccSwitch)) tier = TIER_F32A;
+            a.tier = tier;
             a.tol = std::max(tol, (double)P.fp32_floor);
             tm.begin(0);
-            CKR(launch_stage(TIER_F32, ws, a, h->stream));
+            CKR(launch_stage(tier, ws, a, h->stream));
             tm.end();
             ++launches;
             ++launches32;
@@ -417,6 +423,7 @@ mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const f
         info->t_round_ms = tsum[2];
         info->t_bound_ms = tsum[3];
         info->launches = launches;
+        info->stalls = S.stalls;
         info->stage_launches_fp32 = launches32;
     }
     return out;
@@ -471,7 +478,7 @@ mdot_status mdot_dual_eval(mdot_handle* h, const double* u, const double* v, dou
                            double* log_cP)
 {
     if (!h || !u || !v || !C || !log_rP || !log_cP || n < 1 || n > h->max_n || !(gamma > 0.0) ||
-        !std::isfinite(gamma) || precision < 0 || precision > 2)
+        !std::isfinite(gamma) || precision < 0 || precision > 3)
         return MDOT_ERR_INVALID_ARG;
     WS ws = h->ws;
     ws.n = (int)n;
@@ -482,7 +489,7 @@ mdot_status mdot_dual_eval(mdot_handle* h, const double* u, const double* v, dou
     a.u = u;
     a.v = v;
     a.ref = ref_log_rP;
-    const int tier = (precision == MDOT_PREC_FP64) ? TIER_F64 : TIER_F32;
+    const int tier = (precision == MDOT_PREC_FP64) ? TIER_F64 : (precision == MDOT_PREC_FP32A) ? TIER_F32A : TIER_F32;
     CKR(reset_state(h));
     CKR(launch_dual_eval(tier, ws, a, h->stream));
     CKR(cudaMemcpyAsync(log_rP, ws.lrtr, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));

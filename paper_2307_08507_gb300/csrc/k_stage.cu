@@ -5,12 +5,12 @@
 
 namespace mdot {
 
-size_t stage_smem_bytes(int n, int G, int tier) { return smem_layout(n, G, tier, kThreads).bytes; }
+size_t stage_smem_bytes(int n, int G, int tier) { return smem_layout(n, G, tier, kStageThreads).bytes; }
 
 template <typename K>
 static cudaError_t coop(K kernel, int G, size_t smem, cudaStream_t s, void** args)
 {
-    return cudaLaunchCooperativeKernel((const void*)kernel, dim3(G), dim3(kThreads), args, smem, s);
+    return cudaLaunchCooperativeKernel((const void*)kernel, dim3(G), dim3(kStageThreads), args, smem, s);
 }
 
 cudaError_t launch_stage(int tier, const WS& ws, const StageArgs& a, cudaStream_t s)
@@ -19,8 +19,9 @@ cudaError_t launch_stage(int tier, const WS& ws, const StageArgs& a, cudaStream_
     StageArgs aa = a;
     void* args[] = {(void*)&w, (void*)&aa};
     const size_t smem = stage_smem_bytes(ws.n, ws.G, tier);
-    return tier == TIER_F64 ? coop(stage_kernel<TIER_F64>, ws.G, smem, s, args)
-                            : coop(stage_kernel<TIER_F32>, ws.G, smem, s, args);
+    if (tier == TIER_F64) return coop(stage_kernel<TIER_F64>, ws.G, smem, s, args);
+    if (tier == TIER_F32A) return coop(stage_kernel<TIER_F32A>, ws.G, smem, s, args);
+    return coop(stage_kernel<TIER_F32>, ws.G, smem, s, args);
 }
 
 cudaError_t launch_dual_eval(int tier, const WS& ws, const EvalArgs& a, cudaStream_t s)
@@ -29,21 +30,24 @@ cudaError_t launch_dual_eval(int tier, const WS& ws, const EvalArgs& a, cudaStre
     EvalArgs aa = a;
     void* args[] = {(void*)&w, (void*)&aa};
     const size_t smem = stage_smem_bytes(ws.n, ws.G, tier);
-    return tier == TIER_F64 ? coop(dual_eval_kernel<TIER_F64>, ws.G, smem, s, args)
-                            : coop(dual_eval_kernel<TIER_F32>, ws.G, smem, s, args);
+    if (tier == TIER_F64) return coop(dual_eval_kernel<TIER_F64>, ws.G, smem, s, args);
+    if (tier == TIER_F32A) return coop(dual_eval_kernel<TIER_F32A>, ws.G, smem, s, args);
+    return coop(dual_eval_kernel<TIER_F32>, ws.G, smem, s, args);
 }
 
 cudaError_t configure_stage_kernels(int max_n, int G, int* min_blocks)
 {
     struct K { const void* f; int tier; } ks[] = {
         {(const void*)stage_kernel<TIER_F32>, TIER_F32}, {(const void*)stage_kernel<TIER_F64>, TIER_F64},
-        {(const void*)dual_eval_kernel<TIER_F32>, TIER_F32}, {(const void*)dual_eval_kernel<TIER_F64>, TIER_F64}};
+        {(const void*)stage_kernel<TIER_F32A>, TIER_F32A},
+        {(const void*)dual_eval_kernel<TIER_F32>, TIER_F32}, {(const void*)dual_eval_kernel<TIER_F64>, TIER_F64},
+        {(const void*)dual_eval_kernel<TIER_F32A>, TIER_F32A}};
     for (auto& k : ks) {
         const size_t smem = stage_smem_bytes(max_n, G, k.tier);
         cudaError_t e = cudaFuncSetAttribute(k.f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k.f, kThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k.f, kStageThreads, smem);
         if (e != cudaSuccess) return e;
         *min_blocks = std::min(*min_blocks, nb);
     }

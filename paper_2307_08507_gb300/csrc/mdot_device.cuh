@@ -25,10 +25,13 @@ constexpr double kLog2e = 1.4426950408889634074;
 constexpr double kLn2 = 0.69314718055994530942;
 constexpr double kQuant = 2097152.0;          // 2^21: quantum of the exact part of f, g
 constexpr int kNRed = 6;                       // scalars reduced per evaluation
+constexpr int kStallIters = 400;               // accepted iterations without 1 % progress end a stage
+                                               // (||grad g||_1 is not monotone along PNCG: a last-resort guard)
 constexpr int kThreads = 256;                  // CTA size of the cooperative kernels
 constexpr int kK = 4;                          // float4 column groups per thread per sweep
+constexpr int kRG = 4;                         // rows per group in the passes (keeps the loop body small)
 
-enum Tier { TIER_F32 = 0, TIER_F64 = 1 };
+enum Tier { TIER_F32 = 0, TIER_F64 = 1, TIER_F32A = 2 };   // F32A: fp32 with an accurate exponent and exp2
 enum EvalKind { KIND_INIT = 0, KIND_TRIAL = 1, KIND_FORCE = 2 };
 enum Phase { PH_RUN = 0, PH_DONE = 1 };
 enum SolveStatus { ST_OK = 0, ST_CAP = 1, ST_LSFAIL = 2, ST_NUMERIC = 3, ST_TIMEOUT = 4 };
@@ -53,7 +56,9 @@ struct State {
     int k;                 // PNCG iterations in this stage
     int phase;             // Phase
     int status;            // SolveStatus (sticky, worst wins)
-    int pad0, pad1;
+    int since_best;        // accepted iterations since ||grad g||_1 last improved by 1 %
+    int stalls;            // stages ended by the stall rule (cumulative)
+    double best_gnorm;     // smallest ||grad g||_1 seen in this stage
     long long evals, evals64, iters, ls_trials;
     GridBar bar;
 };
@@ -121,6 +126,42 @@ __device__ __forceinline__ float ex2f(float x)
     return y;
 }
 
+// 2^(th + tl) for th <= 127 (tl a small correction), relative error ~1.3 ulp and unbiased (unlike
+// ex2.approx, whose error on this GPU averages -5e-8): th = k + f with k = rint(th); 2^(f + tl)
+// by a degree-6 minimax polynomial for 2^x on [-1/2, 1/2] (Remez fit made for this library,
+// relative error 1.9e-9 before fp32 rounding); 2^k applied to the exponent bits.  Results below
+// 2^-125 are returned as 0.
+__device__ __forceinline__ float exp2_acc(float th, float tl)
+{
+    th = fminf(th, 127.0f);
+    const bool under = th < -125.0f;
+    th = fmaxf(th, -125.0f);
+    const float kf = rintf(th);
+    const float x = (th - kf) + tl;
+    float p = 1.53458124e-4f;
+    p = fmaf(p, x, 1.33999309e-3f);
+    p = fmaf(p, x, 9.61848907e-3f);
+    p = fmaf(p, x, 5.55032864e-2f);
+    p = fmaf(p, x, 2.40226462e-1f);
+    p = fmaf(p, x, 6.93147182e-1f);
+    p = fmaf(p, x, 1.0f);
+    const float r = __int_as_float(__float_as_int(p) + ((int)kf << 23));
+    return under ? 0.0f : r;
+}
+
+// log2 P_ij - A_i for the accurate tier as an unevaluated sum th + tl: the product G32 * d and
+// its exact error, the row + column remainders, their TwoSum error and the small G - G32 term.
+__device__ __forceinline__ float exponent_acc(float d, float G32, float Glo, float W, float& tl)
+{
+    const float p = G32 * d;
+    const float pe = fmaf(G32, d, -p);
+    const float th = p + W;
+    const float bb = th - p;
+    const float e = (p - (th - bb)) + (W - bb);
+    tl = e + fmaf(Glo, d, pe);
+    return th;
+}
+
 __device__ __forceinline__ float4 ldg4(const float* p)
 {
     return __ldg(reinterpret_cast<const float4*>(p));
@@ -163,7 +204,7 @@ __device__ __forceinline__ void kahan_add(float& s, float& comp, float x)
 }
 
 // Reduce N values held by every lane across the 32 lanes of a warp; afterwards lane l holds in
-// v[0] the warp total of value (l mod N).  N = 32, 16 or 8.  Fixed shuffle tree: deterministic.
+// v[0] the warp total of value (l mod N).  N a power of two <= 32.  Fixed shuffle tree: deterministic.
 template <int N, typename T>
 __device__ __forceinline__ void butterfly(T (&v)[N], int lane)
 {
@@ -185,6 +226,7 @@ __device__ __forceinline__ void butterfly(T (&v)[N], int lane)
 }
 
 // Block-wide sum of kNRed doubles; result valid in thread 0.  red_smem: >= 32 * kNRed doubles.
+// Fixed reduction tree (deterministic); the last step runs on kNRed lanes in parallel.
 __device__ __forceinline__ void block_reduce_nred(double (&x)[kNRed], double* red_smem)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -197,12 +239,15 @@ __device__ __forceinline__ void block_reduce_nred(double (&x)[kNRed], double* re
 #pragma unroll
         for (int q = 0; q < kNRed; ++q) red_smem[warp * kNRed + q] = x[q];
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (warp == 0) {
+        double s = 0.0;
+        if (lane < kNRed)
+            for (int w = 0; w < nw; ++w) s += red_smem[w * kNRed + lane];
+        // move lane q's total into x[q] of thread 0
 #pragma unroll
         for (int q = 0; q < kNRed; ++q) {
-            double s = 0.0;
-            for (int w = 0; w < nw; ++w) s += red_smem[w * kNRed + q];
-            x[q] = s;
+            const double t = __shfl_sync(0xffffffffu, s, q);
+            if (lane == 0) x[q] = t;
         }
     }
     __syncthreads();
@@ -293,7 +338,7 @@ __device__ __forceinline__ int row_scale(double log_r_pred)
 // Phase A: one pass over the rows [r0, r1) of C.  Row sums go to sRow[warp][local row]
 // (accumulated, fp32 or fp64), column partials to colpart_b[j].
 // ---------------------------------------------------------------------------------------------
-template <bool VEC4>
+template <bool VEC4, bool ACC>
 __device__ __forceinline__ void pass_f32(const float* __restrict__ C, int n, int r0, int r1,
                                          const float* Hh, const float* Wc,
                                          const float* sFh, const float* sWr, const float* sS,
@@ -319,10 +364,10 @@ __device__ __forceinline__ void pass_f32(const float* __restrict__ C, int n, int
                 ca[k][e] = 0.0f;
             }
         }
-        for (int rg = r0; rg < r1; rg += 32) {
-            float rp[32];
+        for (int rg = r0; rg < r1; rg += kRG) {
+            float rp[kRG];
 #pragma unroll
-            for (int ii = 0; ii < 32; ++ii) {
+            for (int ii = 0; ii < kRG; ++ii) {
                 rp[ii] = 0.0f;
                 const int i = rg + ii;
                 if (i < r1) {
@@ -345,17 +390,23 @@ __device__ __forceinline__ void pass_f32(const float* __restrict__ C, int n, int
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             const float d = (fh + hh[k][e]) - cv[e];
-                            const float t = fmaf(Glo, d, fmaf(G32, d, wr + wc[k][e]));
-                            const float E = ex2f(t);
+                            float E;
+                            if (ACC) {
+                                float tl;
+                                const float th = exponent_acc(d, G32, Glo, wr + wc[k][e], tl);
+                                E = exp2_acc(th, tl);
+                            } else {
+                                E = ex2f(fmaf(Glo, d, fmaf(G32, d, wr + wc[k][e])));
+                            }
                             rp[ii] += E;
                             ca[k][e] = fmaf(E, s, ca[k][e]);
                         }
                     }
                 }
             }
-            butterfly<32>(rp, lane);
+            butterfly<kRG>(rp, lane);
             const int il = rg + lane;
-            if (il < r1) sRow[warp * nloc + (il - r0)] += rp[0];
+            if (lane < kRG && il < r1) sRow[warp * nloc + (il - r0)] += rp[0];
         }
 #pragma unroll
         for (int k = 0; k < kK; ++k)
@@ -385,10 +436,10 @@ __device__ __forceinline__ void pass_f64(const float* __restrict__ C, int n, int
                 ca[k][e] = 0.0;
             }
         }
-        for (int rg = r0; rg < r1; rg += 16) {
-            double rp[16];
+        for (int rg = r0; rg < r1; rg += kRG) {
+            double rp[kRG];
 #pragma unroll
-            for (int ii = 0; ii < 16; ++ii) {
+            for (int ii = 0; ii < kRG; ++ii) {
                 rp[ii] = 0.0;
                 const int i = rg + ii;
                 if (i < r1) {
@@ -407,9 +458,9 @@ __device__ __forceinline__ void pass_f64(const float* __restrict__ C, int n, int
                     }
                 }
             }
-            butterfly<16>(rp, lane);
-            const int il = rg + (lane & 15);
-            if (lane < 16 && il < r1) sRow[warp * nloc + (il - r0)] += rp[0];
+            butterfly<kRG>(rp, lane);
+            const int il = rg + lane;
+            if (lane < kRG && il < r1) sRow[warp * nloc + (il - r0)] += rp[0];
         }
 #pragma unroll
         for (int k = 0; k < kK; ++k)
@@ -419,11 +470,202 @@ __device__ __forceinline__ void pass_f64(const float* __restrict__ C, int n, int
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// TMA-fed pass (fp32 entries): one producer warp streams row segments C[i, cb : cb + 4096) into a
+// ring of kStages shared-memory slots with cp.async.bulk (completion counted on a per-slot "full"
+// mbarrier); the 8 consumer warps read each slot with 128-bit shared loads and release it on a
+// per-slot "empty" mbarrier.  Every wait is bounded; a wait that gives up sets *abort and the
+// pass drains what it issued (bounded as well) before returning.
+// ---------------------------------------------------------------------------------------------
+constexpr int kConsumerThreads = 256;
+constexpr int kStageThreads = kConsumerThreads + 32;    // + one producer warp
+constexpr int kStages = 12;                            // ring slots at most (fewer if smem is short)
+constexpr size_t kSmemLimit = 227 * 1024;
+constexpr int kSegFloats = 4 * kK * kConsumerThreads;   // 4096 floats = 16 KiB per slot
+constexpr unsigned int kWaitSpins = 1u << 24;           // bounded mbarrier wait (with backoff)
+
+__device__ __forceinline__ unsigned int smem_u32(const void* p)
+{
+    return (unsigned int)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned int count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned int bytes)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}"
+                 ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned int parity)
+{
+    unsigned int ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned int parity)
+{
+    for (unsigned int it = 0; it < kWaitSpins; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (it > 32) __nanosleep(32);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_1d(void* dst_smem, const void* src_gmem, unsigned int bytes,
+                                            unsigned long long* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst_smem)), "l"(src_gmem), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
+// Requires n % 4 == 0 and C 16-byte aligned.  ring: kStages * kSegFloats floats (16-byte aligned);
+// bars: 2 * kStages mbarriers (full, empty).  Block = kStageThreads threads.
+template <bool ACC>
+__device__ __forceinline__ void pass_f32_tma(const float* __restrict__ C, int n, int r0, int r1,
+                                             const float* Hh, const float* Wc, const float* sFh,
+                                             const float* sWr, const float* sS, float G32, float Glo,
+                                             float* sRow, int nloc, float* colpart_b, float* ring,
+                                             int nst, unsigned long long* bars, int* s_issued,
+                                             unsigned int* abort)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nrows = r1 - r0;
+    const int ncb = (n + kSegFloats - 1) / kSegFloats;
+    const int items = nrows * ncb;
+    unsigned long long* full = bars;
+    unsigned long long* empty = bars + kStages;
+    if (tid == 0) {
+        for (int s = 0; s < nst; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kConsumerThreads / 32);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (warp == kConsumerThreads / 32) {
+        // ------------------------------ producer warp ------------------------------
+        if (lane == 0) {
+            bool ok = true;
+            int q = 0, s = 0, ph = 0, cbi = 0, il = 0;       // slot, parity of its current use, item
+            for (; q < items && ok; ++q) {
+                if (q >= nst) ok = mbar_wait(&empty[s], ph ^ 1);
+                if (!ok) break;
+                const int i = r0 + il;
+                const int cb = cbi * kSegFloats;
+                const unsigned int bytes = (unsigned int)(min(kSegFloats, n - cb) * 4);
+                mbar_arrive_expect_tx(&full[s], bytes);
+                tma_load_1d(ring + (size_t)s * kSegFloats, C + (size_t)i * n + cb, bytes, &full[s]);
+                if (++s == nst) { s = 0; ph ^= 1; }
+                if (++il == nrows) { il = 0; ++cbi; }
+            }
+            *s_issued = q;
+            if (!ok) atomicExch(abort, 1u);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------ consumer warps ------------------------------
+        int q = 0, sl = 0, ph = 0;
+        bool ok = true;
+        for (int cbi = 0; cbi < ncb; ++cbi) {
+            const int cb = cbi * kSegFloats;
+            float hh[kK][4], wc[kK][4], ca[kK][4];
+            int jk[kK];
+#pragma unroll
+            for (int k = 0; k < kK; ++k) {
+                jk[k] = cb + 4 * (tid + k * kConsumerThreads);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int j = jk[k] + e;
+                    const bool okj = j < n;
+                    hh[k][e] = okj ? __ldcg(Hh + j) : 0.0f;
+                    wc[k][e] = okj ? __ldcg(Wc + j) : -INFINITY;
+                    ca[k][e] = 0.0f;
+                }
+            }
+            for (int rg = r0; rg < r1; rg += kRG) {
+                float rp[kRG];
+#pragma unroll
+                for (int ii = 0; ii < kRG; ++ii) {
+                    rp[ii] = 0.0f;
+                    const int i = rg + ii;
+                    if (i < r1) {
+                        const int s = sl;
+                        if (ok) ok = mbar_wait(&full[s], ph);
+                        const float fh = sFh[i - r0], wr = sWr[i - r0], sc = sS[i - r0];
+                        const float4* seg = reinterpret_cast<const float4*>(ring + (size_t)s * kSegFloats);
+#pragma unroll
+                        for (int k = 0; k < kK; ++k) {
+                            float cv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                            if (ok && jk[k] < n) {
+                                const float4 t4 = seg[tid + k * kConsumerThreads];
+                                cv[0] = t4.x; cv[1] = t4.y; cv[2] = t4.z; cv[3] = t4.w;
+                            }
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const float d = (fh + hh[k][e]) - cv[e];
+                                float E;
+                                if (ACC) {
+                                    float tl;
+                                    const float th = exponent_acc(d, G32, Glo, wr + wc[k][e], tl);
+                                    E = exp2_acc(th, tl);
+                                } else {
+                                    E = ex2f(fmaf(Glo, d, fmaf(G32, d, wr + wc[k][e])));
+                                }
+                                rp[ii] += E;
+                                ca[k][e] = fmaf(E, sc, ca[k][e]);
+                            }
+                        }
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&empty[s]);
+                        ++q;
+                        if (++sl == nst) { sl = 0; ph ^= 1; }
+                    }
+                }
+                butterfly<kRG>(rp, lane);
+                const int il = rg + lane;
+                if (lane < kRG && il < r1) sRow[warp * nloc + (il - r0)] += rp[0];
+            }
+#pragma unroll
+            for (int k = 0; k < kK; ++k)
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (jk[k] + e < n) colpart_b[jk[k] + e] = ca[k][e];
+        }
+        if (!ok && lane == 0) atomicExch(abort, 1u);
+    }
+    __syncthreads();
+    if (tid == 0 && *reinterpret_cast<volatile unsigned int*>(abort)) {
+        // a wait gave up: let every copy that may still be in flight land (bounded) before the
+        // shared memory is reused or the CTA exits
+        const int issued = *s_issued;
+        for (int q = max(0, issued - nst); q < issued; ++q) mbar_wait(&full[q % nst], (q / nst) & 1);
+    }
+    __syncthreads();
+}
+
 // Two-scale pass of the generic dual evaluation: the row sum of row i uses exponents relative to
 // the row scale A_i (folded into the row constants sFh/sWr), the column sum of column j uses
 // exponents relative to the column scale B_j (folded into the column constants Hh2/Wc2), so both
 // log-sum-exps stay exact for potentials of any spread.  Two exp2 per entry.
-template <bool VEC4>
+template <bool VEC4, bool ACC>
 __device__ __forceinline__ void pass2_f32(const float* __restrict__ C, int n, int r0, int r1,
                                           const float* Hh, const float* Wc, const float* Hh2,
                                           const float* Wc2, const float* sFh, const float* sWr,
@@ -450,10 +692,10 @@ __device__ __forceinline__ void pass2_f32(const float* __restrict__ C, int n, in
                 ca[k][e] = 0.0f;
             }
         }
-        for (int rg = r0; rg < r1; rg += 32) {
-            float rp[32];
+        for (int rg = r0; rg < r1; rg += kRG) {
+            float rp[kRG];
 #pragma unroll
-            for (int ii = 0; ii < 32; ++ii) {
+            for (int ii = 0; ii < kRG; ++ii) {
                 rp[ii] = 0.0f;
                 const int i = rg + ii;
                 if (i < r1) {
@@ -476,16 +718,24 @@ __device__ __forceinline__ void pass2_f32(const float* __restrict__ C, int n, in
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             const float d = (fh + hh[k][e]) - cv[e];
-                            rp[ii] += ex2f(fmaf(Glo, d, fmaf(G32, d, wr + wc[k][e])));
                             const float d2 = (fh2 + hh2[k][e]) - cv[e];
-                            ca[k][e] += ex2f(fmaf(Glo, d2, fmaf(G32, d2, wr2 + wc2[k][e])));
+                            if (ACC) {
+                                float tl, tl2;
+                                const float th = exponent_acc(d, G32, Glo, wr + wc[k][e], tl);
+                                const float th2 = exponent_acc(d2, G32, Glo, wr2 + wc2[k][e], tl2);
+                                rp[ii] += exp2_acc(th, tl);
+                                ca[k][e] += exp2_acc(th2, tl2);
+                            } else {
+                                rp[ii] += ex2f(fmaf(Glo, d, fmaf(G32, d, wr + wc[k][e])));
+                                ca[k][e] += ex2f(fmaf(Glo, d2, fmaf(G32, d2, wr2 + wc2[k][e])));
+                            }
                         }
                     }
                 }
             }
-            butterfly<32>(rp, lane);
+            butterfly<kRG>(rp, lane);
             const int il = rg + lane;
-            if (il < r1) sRow[warp * nloc + (il - r0)] += rp[0];
+            if (lane < kRG && il < r1) sRow[warp * nloc + (il - r0)] += rp[0];
         }
 #pragma unroll
         for (int k = 0; k < K2; ++k)
@@ -517,10 +767,10 @@ __device__ __forceinline__ void pass2_f64(const float* __restrict__ C, int n, in
                 ca[k][e] = 0.0;
             }
         }
-        for (int rg = r0; rg < r1; rg += 16) {
-            double rp[16];
+        for (int rg = r0; rg < r1; rg += kRG) {
+            double rp[kRG];
 #pragma unroll
-            for (int ii = 0; ii < 16; ++ii) {
+            for (int ii = 0; ii < kRG; ++ii) {
                 rp[ii] = 0.0;
                 const int i = rg + ii;
                 if (i < r1) {
@@ -539,9 +789,9 @@ __device__ __forceinline__ void pass2_f64(const float* __restrict__ C, int n, in
                     }
                 }
             }
-            butterfly<16>(rp, lane);
-            const int il = rg + (lane & 15);
-            if (lane < 16 && il < r1) sRow[warp * nloc + (il - r0)] += rp[0];
+            butterfly<kRG>(rp, lane);
+            const int il = rg + lane;
+            if (lane < kRG && il < r1) sRow[warp * nloc + (il - r0)] += rp[0];
         }
 #pragma unroll
         for (int k = 0; k < K2; ++k)
@@ -553,15 +803,24 @@ __device__ __forceinline__ void pass2_f64(const float* __restrict__ C, int n, in
 
 // Sum of the G column partials of column j (fp32 partials, Kahan per warp, warps combined in
 // fp64).  Called by all threads of the CTA for the 32 columns [j0, j0 + 32); the result for
-// column j0 + lane is returned in warp 0.  sm: >= 2 * 32 * nwarps floats.
+// column j0 + lane is returned in warp 0.  Each warp issues all of its partial loads before
+// summing them (independent loads in flight instead of a dependent chain).  sm: >= 2 * 32 * nwarps
+// floats.  Requires G <= 24 * nwarps.
 __device__ __forceinline__ double merge_cols_f32(const float* colpart, int n, int G,
                                                  int j0, int j1, float* sm)
 {
+    constexpr int kMaxPer = 24;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int j = j0 + lane;
+    float vals[kMaxPer];
+#pragma unroll
+    for (int k = 0; k < kMaxPer; ++k) {
+        const int b = warp + k * nw;
+        vals[k] = (j < j1 && b < G) ? __ldcg(colpart + (size_t)b * n + j) : 0.0f;
+    }
     float s = 0.0f, comp = 0.0f;
-    if (j < j1)
-        for (int b = warp; b < G; b += nw) kahan_add(s, comp, __ldcg(colpart + (size_t)b * n + j));
+#pragma unroll
+    for (int k = 0; k < kMaxPer; ++k) kahan_add(s, comp, vals[k]);
     sm[warp * 32 + lane] = s;
     sm[(nw + warp) * 32 + lane] = -comp;
     __syncthreads();
@@ -575,11 +834,18 @@ __device__ __forceinline__ double merge_cols_f32(const float* colpart, int n, in
 __device__ __forceinline__ double merge_cols_f64(const double* colpart, int n, int G,
                                                  int j0, int j1, double* sm)
 {
+    constexpr int kMaxPer = 24;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int j = j0 + lane;
+    double vals[kMaxPer];
+#pragma unroll
+    for (int k = 0; k < kMaxPer; ++k) {
+        const int b = warp + k * nw;
+        vals[k] = (j < j1 && b < G) ? __ldcg(colpart + (size_t)b * n + j) : 0.0;
+    }
     double s = 0.0;
-    if (j < j1)
-        for (int b = warp; b < G; b += nw) s += __ldcg(colpart + (size_t)b * n + j);
+#pragma unroll
+    for (int k = 0; k < kMaxPer; ++k) s += vals[k];
     sm[warp * 32 + lane] = s;
     __syncthreads();
     double tot = 0.0;

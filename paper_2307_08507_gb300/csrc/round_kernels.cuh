@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(WS ws, RoundArgs a)
     if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
 
     // pass 1: r(P)_i = 2^{A_i} sum_j E_ij ; x_i = min(r_i / r(P)_i, 1)  (Alg. 3)
-    pass_round<RM_ROWSUM, 16>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sX, G32, Glo, nullptr, nullptr,
+    pass_round<RM_ROWSUM, 4>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sX, G32, Glo, nullptr, nullptr,
                               nullptr, 0.0, sAcc, nloc, nullptr, nullptr);
     __syncthreads();
     for (int i = r0 + tid; i < r1; i += T) {
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(WS ws, RoundArgs a)
     }
     __syncthreads();
     // pass 2: c(F)_j = sum_i x_i P_ij  (Alg. 3)
-    pass_round<RM_COLSUM, 16>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sX, G32, Glo, nullptr, nullptr,
+    pass_round<RM_COLSUM, 4>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sX, G32, Glo, nullptr, nullptr,
                               nullptr, 0.0, sAcc, nloc, ws.colpartd + (size_t)b * n, nullptr);
     if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
     for (int j0 = c0; j0 < c1; j0 += 32) {
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(WS ws, RoundArgs a)
     for (int x0 = tid; x0 < (T >> 5) * 3 * nloc; x0 += T) sAcc[x0] = 0.0;
     if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
     // pass 3: r(F')_i, <F', C> by rows, (C err_c)_i   (Alg. 3)
-    pass_round<RM_ROWFINAL, 8>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sX, G32, Glo, a.Y, a.EC,
+    pass_round<RM_ROWFINAL, 4>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sX, G32, Glo, a.Y, a.EC,
                                nullptr, 0.0, sAcc, nloc, nullptr, nullptr);
     __syncthreads();
 #pragma unroll
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(WS ws, RoundArgs a)
     }
     if (a.G_out != nullptr) {
         // G = F' + err_r err_c^T / ||err_r||_1 (Alg. 3), written row-major in fp64
-        pass_round<RM_WRITE, 16>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sX, G32, Glo, a.Y, a.EC,
+        pass_round<RM_WRITE, 4>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sX, G32, Glo, a.Y, a.EC,
                                  a.ER, (e1 > 0.0) ? 1.0 / e1 : 0.0, sAcc, nloc, nullptr, a.G_out);
     }
     return;

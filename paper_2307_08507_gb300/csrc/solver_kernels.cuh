@@ -6,6 +6,8 @@
 // accepted step, new direction, constants of the next trial) -> grid barrier.
 #pragma once
 
+#include <cstddef>
+
 #include "mdot_device.cuh"
 
 namespace mdot {
@@ -14,7 +16,7 @@ namespace mdot {
 // decision of one evaluation (thread 0 of the last CTA).  tot = {phi', ||grad||_1,
 // <y, -s>, <y, p>, <s, grad>, #bad}, y = grad_trial - grad_current (Eq. (18)).
 // ---------------------------------------------------------------------------------------------
-static __device__ void decide(volatile State* S, const double* tot, const StageArgs& a)
+static __device__ void decide(State* S, const double* tot, const StageArgs& a)
 {
     const double phi = tot[0], gn = tot[1], num = tot[2], den = tot[3], S1 = tot[4];
     const bool bad = tot[5] > 0.0 || !isfinite(phi) || !isfinite(gn);
@@ -79,6 +81,17 @@ static __device__ void decide(volatile State* S, const double* tot, const StageA
     if (!was_init) { S->k += 1; S->iters += 1; }
     S->gnorm = gn;
     if (gn <= a.tol) { S->phase = PH_DONE; S->beta = 0.0; return; }
+    // stall rule: a stage whose tolerance lies below the noise floor of its arithmetic stops after
+    // kStallIters accepted iterations without 1 % progress (the next stage or tier continues)
+    if (was_init || gn < 0.99 * S->best_gnorm) {
+        S->best_gnorm = gn;
+        S->since_best = 0;
+    } else if (++S->since_best >= kStallIters) {
+        S->stalls += 1;
+        S->phase = PH_DONE;
+        S->beta = 0.0;
+        return;
+    }
     if (S->k >= a.max_iter) {
         S->status = max((int)S->status, (int)ST_CAP);
         S->phase = PH_DONE;
@@ -111,8 +124,14 @@ static __device__ void decide(volatile State* S, const double* tot, const StageA
 // ---------------------------------------------------------------------------------------------
 struct SmemLayout {
     int nloc_max;
-    size_t off_row, off_c0, off_c1, off_s, off_A, off_x, off_merge, bytes;
+    size_t off_row, off_c0, off_c1, off_s, off_A, off_x, off_merge, off_ring, off_bars, off_misc,
+        off_rstate, off_cstate, bytes;
+    int stages;        // TMA ring slots (fp32 entries)
 };
+
+// per-row / per-column state of the CTA's own rows and columns, kept in shared memory for a stage
+enum RowState { RS_U = 0, RS_P, RS_G, RS_T, RS_LT, RS_L, RS_GT, RS_ST, RS_LTR, RS_COUNT };
+enum ColState { CS_V = 0, CS_P, CS_G, CS_T, CS_GT, CS_ST, CS_COUNT };
 
 __host__ __device__ inline SmemLayout smem_layout(int n, int G, int tier, int nthreads)
 {
@@ -128,6 +147,17 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int G, int tier, int nt
     L.off_A = o;     o += (size_t)L.nloc_max * 4;                o = (o + 15) & ~(size_t)15;
     L.off_x = o;     o += (size_t)L.nloc_max * 8;                o = (o + 15) & ~(size_t)15;
     L.off_merge = o; o += (size_t)2 * 32 * nw * 8;               o = (o + 15) & ~(size_t)15;
+    L.off_rstate = o; o += (size_t)RS_COUNT * L.nloc_max * 8;   o = (o + 15) & ~(size_t)15;
+    L.off_cstate = o; o += (size_t)CS_COUNT * L.nloc_max * 8;   o = (o + 15) & ~(size_t)15;
+    L.off_misc = o;  o += 16;
+    L.off_bars = o;  o += (tier != TIER_F64) ? (size_t)2 * kStages * 8 : 0;   o = (o + 127) & ~(size_t)127;
+    L.off_ring = o;
+    L.stages = 0;
+    if (tier != TIER_F64) {
+        const size_t room = (o < kSmemLimit) ? (kSmemLimit - o) / ((size_t)kSegFloats * 4) : 0;
+        L.stages = (int)(room < (size_t)kStages ? room : (size_t)kStages);
+        o += (size_t)L.stages * kSegFloats * 4;
+    }
     L.bytes = o;
     return L;
 }
@@ -137,9 +167,11 @@ template <int TIER>
 __device__ __forceinline__ void prep_row(double ua, int A, int Aglob, double gamma, double G64,
                                          unsigned char* sm, const SmemLayout& L, int il)
 {
-    if (TIER == TIER_F32) {
+    if (TIER != TIER_F64) {
         float fh, wl;
-        split_cost_unit(ua / gamma - (double)A / G64, fh, wl, G64);
+        // (u - A ln2) / gamma, with the division replaced by a product with 1/gamma (exact to
+        // fp64 rounding; fp64 division is slow on this GPU)
+        split_cost_unit((ua - (double)A * kLn2) * (1.0 / gamma), fh, wl, G64);
         reinterpret_cast<float*>(sm + L.off_c0)[il] = fh;
         reinterpret_cast<float*>(sm + L.off_c1)[il] = wl;
         reinterpret_cast<float*>(sm + L.off_s)[il] = pow2f_int(A - Aglob);
@@ -153,9 +185,9 @@ __device__ __forceinline__ void prep_row(double ua, int A, int Aglob, double gam
 template <int TIER>
 __device__ __forceinline__ void prep_col(const WS& ws, int j, double va, double gamma, double G64)
 {
-    if (TIER == TIER_F32) {
+    if (TIER != TIER_F64) {
         float gh, wl;
-        split_cost_unit(va / gamma, gh, wl, G64);
+        split_cost_unit(va * (1.0 / gamma), gh, wl, G64);
         ws.Hh[j] = gh;
         ws.Wc[j] = wl;
     } else {
@@ -170,7 +202,7 @@ __device__ __forceinline__ void phase_A(const WS& ws, int r0, int r1, double gam
 {
     const int n = ws.n, nloc = r1 - r0, nw = blockDim.x >> 5;
     const int b = blockIdx.x;
-    if (TIER == TIER_F32) {
+    if (TIER != TIER_F64) {
         float* sRow = reinterpret_cast<float*>(sm + L.off_row);
         for (int x = threadIdx.x; x < nw * L.nloc_max; x += blockDim.x) sRow[x] = 0.0f;
         __syncthreads();
@@ -179,11 +211,17 @@ __device__ __forceinline__ void phase_A(const WS& ws, int r0, int r1, double gam
         const float* sFh = reinterpret_cast<const float*>(sm + L.off_c0);
         const float* sWr = reinterpret_cast<const float*>(sm + L.off_c1);
         const float* sS = reinterpret_cast<const float*>(sm + L.off_s);
-        if ((n & 3) == 0)
-            pass_f32<true>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sS, G32, Glo, sRow, L.nloc_max,
+        if ((n & 3) == 0 && (reinterpret_cast<uintptr_t>(ws.C) & 15) == 0 && blockDim.x == kStageThreads &&
+            L.stages >= 2)
+            pass_f32_tma<TIER == TIER_F32A>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sS, G32, Glo, sRow, L.nloc_max,
+                         ws.colpart + (size_t)b * n, reinterpret_cast<float*>(sm + L.off_ring), L.stages,
+                         reinterpret_cast<unsigned long long*>(sm + L.off_bars),
+                         reinterpret_cast<int*>(sm + L.off_misc), &ws.st->bar.abort);
+        else if ((n & 3) == 0)
+            pass_f32<true, TIER == TIER_F32A>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sS, G32, Glo, sRow, L.nloc_max,
                            ws.colpart + (size_t)b * n);
         else
-            pass_f32<false>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sS, G32, Glo, sRow, L.nloc_max,
+            pass_f32<false, TIER == TIER_F32A>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sS, G32, Glo, sRow, L.nloc_max,
                             ws.colpart + (size_t)b * n);
     } else {
         double* sRow = reinterpret_cast<double*>(sm + L.off_row);
@@ -202,7 +240,7 @@ __device__ __forceinline__ double row_total(const unsigned char* sm, const SmemL
 {
     const int nw = blockDim.x >> 5;
     double s = 0.0;
-    if (TIER == TIER_F32) {
+    if (TIER != TIER_F64) {
         const float* sRow = reinterpret_cast<const float*>(sm + L.off_row);
         for (int w = 0; w < nw; ++w) s += (double)sRow[w * L.nloc_max + il];
     } else {
@@ -215,8 +253,11 @@ __device__ __forceinline__ double row_total(const unsigned char* sm, const SmemL
 // ---------------------------------------------------------------------------------------------
 // the stage kernel
 // ---------------------------------------------------------------------------------------------
+// words of State before the grid barrier (the part the decision reads and writes)
+constexpr int kStateWords = (int)(offsetof(State, bar) / 8);
+
 template <int TIER>
-__global__ void __launch_bounds__(kThreads, 1) stage_kernel(WS ws, StageArgs a)
+__global__ void __launch_bounds__(kStageThreads, 1) stage_kernel(WS ws, StageArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ double red_smem[32 * kNRed];
@@ -229,6 +270,9 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(WS ws, StageArgs a)
     int r0, r1, c0, c1;
     row_range(n, G, b, r0, r1);
     row_range(n, G, b, c0, c1);
+    const int NL = L.nloc_max;
+    double* R = reinterpret_cast<double*>(sm + L.off_rstate);     // R[k * NL + local row]
+    double* Q = reinterpret_cast<double*>(sm + L.off_cstate);     // Q[k * NL + local column]
     const double gamma = a.gamma, G64 = a.G64, w = a.w;
     State* S = ws.st;
 
@@ -238,10 +282,9 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(WS ws, StageArgs a)
 
     // ---- prologue (Alg. 1): smoothing, rank-one start or warm start, constants at alpha = 0 ----
     for (int i = r0 + tid; i < r1; i += T) {
+        const int il = i - r0;
         const double rt = (1.0 - w / 4.0) * ws.r[i] + w / (4.0 * n);
         const double lrt = log(rt);
-        ws.rt[i] = rt;
-        ws.lrt[i] = lrt;
         double u = ws.u[i];
         if (a.first) {
             u = lrt;
@@ -253,21 +296,20 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(WS ws, StageArgs a)
         } else if (a.warm_start == 1) {
             u = a.ratio * u;                                    // eps-scaling
         }
-        ws.u[i] = u;
-        ws.pu[i] = 0.0;
-        ws.gr[i] = 0.0;
-        ws.lr[i] = lrt;
-        const int A = row_scale(lrt);
-        prep_row<TIER>(u, A, a.Aglob, gamma, G64, sm, L, i - r0);
+        R[RS_U * NL + il] = u;
+        R[RS_P * NL + il] = 0.0;
+        R[RS_G * NL + il] = 0.0;
+        R[RS_T * NL + il] = rt;
+        R[RS_LT * NL + il] = lrt;
+        R[RS_L * NL + il] = lrt;
+        prep_row<TIER>(u, row_scale(lrt), a.Aglob, gamma, G64, sm, L, il);
     }
     for (int j = c0 + tid; j < c1; j += T) {
+        const int jl = j - c0;
         const double ct = (1.0 - w / 4.0) * ws.c[j] + w / (4.0 * n);
-        const double lct = log(ct);
-        ws.ct[j] = ct;
-        ws.lct[j] = lct;
         double v = ws.v[j];
         if (a.first) {
-            v = lct;
+            v = log(ct);
             ws.vprev[j] = v;
         } else if (a.warm_start == 0) {
             const double z = v;
@@ -276,9 +318,10 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(WS ws, StageArgs a)
         } else if (a.warm_start == 1) {
             v = a.ratio * v;
         }
-        ws.v[j] = v;
-        ws.pv[j] = 0.0;
-        ws.gc[j] = 0.0;
+        Q[CS_V * NL + jl] = v;
+        Q[CS_P * NL + jl] = 0.0;
+        Q[CS_G * NL + jl] = 0.0;
+        Q[CS_T * NL + jl] = ct;
         prep_col<TIER>(ws, j, v, gamma, G64);
     }
     if (b == 0 && tid == 0) {
@@ -291,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(WS ws, StageArgs a)
         S->beta = 0.0;
         S->alpha_commit = 0.0;
     }
-    if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
+    if (!grid_sync(&S->bar, G, gen, s_flag)) goto finish;
 
     for (;;) {
         // ---------------- phase A: pass over own rows, row epilogue ----------------
@@ -305,46 +348,50 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(WS ws, StageArgs a)
                 const int il = i - r0;
                 const double sum = row_total<TIER>(sm, L, il);
                 if (!(sum > 0.0) || !isfinite(sum)) { x[5] += 1.0; continue; }
-                const double lrP = log(sum) + (double)sA[il] * kLn2;
-                const double g = ldexp(sum, sA[il]) - ws.rt[i];
+                const double rt = R[RS_T * NL + il];
+                const double g = ldexp(sum, sA[il]) - rt;
                 // Eq. (17): s = log r~ - log r(P) = -log1p(g / r~); this form keeps the sign of s
-                // opposite to g down to the last bit, so <s, grad> < 0 (Sec. 4) holds numerically
-                const double s = -log1p(g / ws.rt[i]);
-                const double p = ws.pu[i];
-                const double y = g - ws.gr[i];
+                // opposite to g, so <s, grad> < 0 (Sec. 4) holds numerically.  s is a search
+                // direction: fp32 accuracy suffices (fp64 transcendentals cost ~16 cycles per warp
+                // instruction on this GPU); the gradient g and every dot product stay fp64.
+                const double s = -(double)log1pf((float)g / (float)rt);
+                const double p = R[RS_P * NL + il];
+                const double y = g - R[RS_G * NL + il];
                 x[0] += p * g;
                 x[1] += fabs(g);
                 x[2] += y * (-s);
                 x[3] += y * p;
                 x[4] += s * g;
-                ws.grt[i] = g;
-                ws.srt[i] = s;
-                ws.lrtr[i] = lrP;
+                R[RS_GT * NL + il] = g;
+                R[RS_ST * NL + il] = s;
+                R[RS_LTR * NL + il] = ((double)__log2f((float)sum) + (double)sA[il]) * kLn2;   // scale only
             }
         }
-        if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
+        if (!grid_sync(&S->bar, G, gen, s_flag)) goto finish;
 
         // ---------------- phase B: column merge and epilogue ----------------
         for (int j0 = c0; j0 < c1; j0 += 32) {
             double colsum;
-            if (TIER == TIER_F32)
+            if (TIER != TIER_F64)
                 colsum = merge_cols_f32(ws.colpart, n, G, j0, c1, reinterpret_cast<float*>(sm + L.off_merge));
             else
                 colsum = merge_cols_f64(ws.colpartd, n, G, j0, c1, reinterpret_cast<double*>(sm + L.off_merge));
             const int j = j0 + tid;
             if (tid < 32 && j < c1) {
                 if (!(colsum > 0.0) || !isfinite(colsum)) { x[5] += 1.0; continue; }
-                const double g = ldexp(colsum, a.Aglob) - ws.ct[j];
-                const double s = -log1p(g / ws.ct[j]);                  // Eq. (17)
-                const double p = ws.pv[j];
-                const double y = g - ws.gc[j];
+                const int jl = j - c0;
+                const double ct = Q[CS_T * NL + jl];
+                const double g = ldexp(colsum, a.Aglob) - ct;
+                const double s = -(double)log1pf((float)g / (float)ct);   // Eq. (17), see rows
+                const double p = Q[CS_P * NL + jl];
+                const double y = g - Q[CS_G * NL + jl];
                 x[0] += p * g;
                 x[1] += fabs(g);
                 x[2] += y * (-s);
                 x[3] += y * p;
                 x[4] += s * g;
-                ws.gct[j] = g;
-                ws.sct[j] = s;
+                Q[CS_GT * NL + jl] = g;
+                Q[CS_ST * NL + jl] = s;
             }
         }
         block_reduce_nred(x, red_smem);
@@ -357,31 +404,49 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(WS ws, StageArgs a)
         ++gen;
         if (bar_arrive(&S->bar, G, s_flag)) {
             __threadfence();
-            // warp q sums scalar q over the G CTAs in a fixed order
+            // warp q sums scalar q over the G CTAs in a fixed order; all loads issued first
             const int lane = tid & 31, warp = tid >> 5;
             if (warp < kNRed) {
-                double s = 0.0;
-                for (int bb = lane; bb < G; bb += 32) s += __ldcg(ws.blockred + (size_t)bb * kNRed + warp);
+                double v8[8];
 #pragma unroll
-                for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                if (lane == 0) red_smem[warp] = s;
+                for (int k = 0; k < 8; ++k) {
+                    const int bb = lane + 32 * k;
+                    v8[k] = (bb < G) ? __ldcg(ws.blockred + (size_t)bb * kNRed + warp) : 0.0;
+                }
+                double sacc = 0.0;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) sacc += v8[k];
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+                if (lane == 0) red_smem[warp] = sacc;
             }
             __syncthreads();
             if (tid == 0) {
                 double tot[kNRed];
                 for (int q = 0; q < kNRed; ++q) tot[q] = red_smem[q];
-                decide(S, tot, a);
+                // decide on a local copy: one pipelined load and one store of the state words
+                State loc;
+                unsigned long long* lw = reinterpret_cast<unsigned long long*>(&loc);
+                const volatile unsigned long long* sw = reinterpret_cast<const volatile unsigned long long*>(S);
+#pragma unroll
+                for (int k = 0; k < kStateWords; ++k) lw[k] = sw[k];
+                decide(&loc, tot, a);
+                volatile unsigned long long* dw = reinterpret_cast<volatile unsigned long long*>(S);
+#pragma unroll
+                for (int k = 0; k < kStateWords; ++k) dw[k] = lw[k];
                 bar_release(&S->bar, gen);
             }
         }
-        if (!bar_wait(&S->bar, gen, s_flag)) goto timeout;
+        if (!bar_wait(&S->bar, gen, s_flag)) goto finish;
         if (tid == 0) {
-            volatile State* vS = S;
-            s_bc[0] = vS->alpha;
-            s_bc[1] = vS->alpha_commit;
-            s_bc[2] = vS->beta;
-            s_bc[3] = (double)vS->accept;
-            s_bc[4] = (double)vS->phase;
+            const volatile State* vS = S;
+            const double d0 = vS->alpha, d1 = vS->alpha_commit, d2 = vS->beta;
+            const int i3 = vS->accept, i4 = vS->phase;
+            s_bc[0] = d0;
+            s_bc[1] = d1;
+            s_bc[2] = d2;
+            s_bc[3] = (double)i3;
+            s_bc[4] = (double)i4;
         }
         __syncthreads();
         const double alpha = s_bc[0], acommit = s_bc[1], beta = s_bc[2];
@@ -389,37 +454,43 @@ __global__ void __launch_bounds__(kThreads, 1) stage_kernel(WS ws, StageArgs a)
 
         // ---------------- phase C: commit, new direction, next trial constants ----------------
         for (int i = r0 + tid; i < r1; i += T) {
-            double u = ws.u[i], p = ws.pu[i];
+            const int il = i - r0;
+            double u = R[RS_U * NL + il], p = R[RS_P * NL + il];
             if (accept) {
                 u = u + acommit * p;                            // (u, v) += alpha p (Alg. 2)
-                ws.u[i] = u;
-                ws.gr[i] = ws.grt[i];
-                ws.lr[i] = ws.lrtr[i];
-                p = ws.srt[i] + beta * p;                       // p = s + beta p, beta = 0 on reset (Alg. 2)
-                ws.pu[i] = p;
+                R[RS_U * NL + il] = u;
+                R[RS_G * NL + il] = R[RS_GT * NL + il];
+                R[RS_L * NL + il] = R[RS_LTR * NL + il];
+                p = R[RS_ST * NL + il] + beta * p;              // p = s + beta p, beta = 0 on reset (Alg. 2)
+                R[RS_P * NL + il] = p;
             }
-            if (!done) {
-                const int A = row_scale(ws.lr[i] + alpha * p);
-                prep_row<TIER>(u + alpha * p, A, a.Aglob, gamma, G64, sm, L, i - r0);
-            }
+            if (!done) prep_row<TIER>(u + alpha * p, row_scale(R[RS_L * NL + il] + alpha * p), a.Aglob,
+                                      gamma, G64, sm, L, il);
         }
         for (int j = c0 + tid; j < c1; j += T) {
-            double v = ws.v[j], p = ws.pv[j];
+            const int jl = j - c0;
+            double v = Q[CS_V * NL + jl], p = Q[CS_P * NL + jl];
             if (accept) {
                 v = v + acommit * p;
-                ws.v[j] = v;
-                ws.gc[j] = ws.gct[j];
-                p = ws.sct[j] + beta * p;
-                ws.pv[j] = p;
+                Q[CS_V * NL + jl] = v;
+                Q[CS_G * NL + jl] = Q[CS_GT * NL + jl];
+                p = Q[CS_ST * NL + jl] + beta * p;
+                Q[CS_P * NL + jl] = p;
             }
             if (!done) prep_col<TIER>(ws, j, v + alpha * p, gamma, G64);
         }
         if (done) break;
-        if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
+        if (!grid_sync(&S->bar, G, gen, s_flag)) goto finish;
     }
-    return;
-timeout:
-    if (tid == 0) {
+finish:
+    // the stage's iterate (also on a timeout: the best iterate so far) goes back to global memory
+    __syncthreads();
+    for (int i = r0 + tid; i < r1; i += T) {
+        ws.u[i] = R[RS_U * NL + i - r0];
+        ws.lr[i] = R[RS_L * NL + i - r0];
+    }
+    for (int j = c0 + tid; j < c1; j += T) ws.v[j] = Q[CS_V * NL + j - c0];
+    if (tid == 0 && *reinterpret_cast<volatile unsigned int*>(&S->bar.abort)) {
         atomicMax(&S->status, (int)ST_TIMEOUT);
         S->phase = PH_DONE;
     }
@@ -431,7 +502,7 @@ timeout:
 // ---------------------------------------------------------------------------------------------
 
 template <int TIER>
-__global__ void __launch_bounds__(kThreads, 1) dual_eval_kernel(WS ws, EvalArgs a)
+__global__ void __launch_bounds__(kStageThreads, 1) dual_eval_kernel(WS ws, EvalArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ int s_flag[2];
@@ -499,7 +570,7 @@ __global__ void __launch_bounds__(kThreads, 1) dual_eval_kernel(WS ws, EvalArgs 
             if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
             for (int j0 = c0; j0 < c1; j0 += 32) {
                 double colsum;
-                if (TIER == TIER_F32)
+                if (TIER != TIER_F64)
                     colsum = merge_cols_f32(ws.colpart, n, G, j0, c1, reinterpret_cast<float*>(sm + L.off_merge));
                 else
                     colsum = merge_cols_f64(ws.colpartd, n, G, j0, c1, reinterpret_cast<double*>(sm + L.off_merge));
@@ -525,7 +596,7 @@ __global__ void __launch_bounds__(kThreads, 1) dual_eval_kernel(WS ws, EvalArgs 
         for (int i = r0 + warp; i < r1; i += nw) {
             double m = -INFINITY;
             const float* Crow = ws.C + (size_t)i * n;
-            if (TIER == TIER_F32) {
+            if (TIER != TIER_F64) {
                 const float fh = f2[i - r0], wl = w2[i - r0];
                 float mf = -INFINITY;
                 for (int j = lane; j < n; j += 32)
@@ -542,7 +613,7 @@ __global__ void __launch_bounds__(kThreads, 1) dual_eval_kernel(WS ws, EvalArgs 
         }
         // column maxima over own rows (thread per column), CTA partials
         for (int j = tid; j < n; j += T) {
-            if (TIER == TIER_F32) {
+            if (TIER != TIER_F64) {
                 const float gh = __ldcg(ws.Hh + j), wc = __ldcg(ws.Wc + j);
                 float mf = -INFINITY;
                 for (int i = r0; i < r1; ++i)
@@ -561,7 +632,7 @@ __global__ void __launch_bounds__(kThreads, 1) dual_eval_kernel(WS ws, EvalArgs 
     // column scales and column-view constants (own columns)
     for (int j = c0 + tid; j < c1; j += T) {
         double m = -INFINITY;
-        if (TIER == TIER_F32) {
+        if (TIER != TIER_F64) {
             for (int bb = 0; bb < G; ++bb) m = fmax(m, (double)__ldcg(ws.colpart + (size_t)bb * n + j));
             const double B = fmin(fmax(ceil(m), -1.0e7), 1.0e7);
             float gh, wl;
@@ -577,7 +648,7 @@ __global__ void __launch_bounds__(kThreads, 1) dual_eval_kernel(WS ws, EvalArgs 
     // row scales and both row constants (own rows)
     for (int i = r0 + tid; i < r1; i += T) {
         const int il = i - r0;
-        if (TIER == TIER_F32) {
+        if (TIER != TIER_F64) {
             const double A = fmin(fmax(ceil(sM[il]), -1.0e7), 1.0e7);
             float fh, wl;
             split_cost_unit(a.u[i] / a.gamma - A / a.G64, fh, wl, a.G64);
@@ -592,7 +663,7 @@ __global__ void __launch_bounds__(kThreads, 1) dual_eval_kernel(WS ws, EvalArgs 
     if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
     {
         const int nwl = T >> 5;
-        if (TIER == TIER_F32) {
+        if (TIER != TIER_F64) {
             float* sRow = reinterpret_cast<float*>(sm + L.off_row);
             for (int x = tid; x < nwl * L.nloc_max; x += T) sRow[x] = 0.0f;
             __syncthreads();
@@ -602,10 +673,10 @@ __global__ void __launch_bounds__(kThreads, 1) dual_eval_kernel(WS ws, EvalArgs 
             const float* f2 = reinterpret_cast<const float*>(sm + L.off_s);
             const float* w2 = reinterpret_cast<const float*>(sm + L.off_A);
             if ((n & 3) == 0)
-                pass2_f32<true>(ws.C, n, r0, r1, ws.Hh, ws.Wc, ws.Fh, ws.Wr, f1, w1, f2, w2, G32, Glo, sRow,
+                pass2_f32<true, TIER == TIER_F32A>(ws.C, n, r0, r1, ws.Hh, ws.Wc, ws.Fh, ws.Wr, f1, w1, f2, w2, G32, Glo, sRow,
                                 L.nloc_max, ws.colpart + (size_t)b * n);
             else
-                pass2_f32<false>(ws.C, n, r0, r1, ws.Hh, ws.Wc, ws.Fh, ws.Wr, f1, w1, f2, w2, G32, Glo, sRow,
+                pass2_f32<false, TIER == TIER_F32A>(ws.C, n, r0, r1, ws.Hh, ws.Wc, ws.Fh, ws.Wr, f1, w1, f2, w2, G32, Glo, sRow,
                                  L.nloc_max, ws.colpart + (size_t)b * n);
         } else {
             double* sRow = reinterpret_cast<double*>(sm + L.off_row);
@@ -619,19 +690,19 @@ __global__ void __launch_bounds__(kThreads, 1) dual_eval_kernel(WS ws, EvalArgs 
         for (int i = r0 + tid; i < r1; i += T) {
             const int il = i - r0;
             const double sum = row_total<TIER>(sm, L, il);
-            ws.lrtr[i] = log(sum) + (TIER == TIER_F32 ? sM[il] * kLn2 : sM[il]);
+            ws.lrtr[i] = log(sum) + (TIER != TIER_F64 ? sM[il] * kLn2 : sM[il]);
         }
     }
     if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
     for (int j0 = c0; j0 < c1; j0 += 32) {
         double colsum;
-        if (TIER == TIER_F32)
+        if (TIER != TIER_F64)
             colsum = merge_cols_f32(ws.colpart, n, G, j0, c1, reinterpret_cast<float*>(sm + L.off_merge));
         else
             colsum = merge_cols_f64(ws.colpartd, n, G, j0, c1, reinterpret_cast<double*>(sm + L.off_merge));
         const int j = j0 + tid;
         if (tid < 32 && j < c1)
-            ws.lcout[j] = log(colsum) + (TIER == TIER_F32 ? (double)__ldcg(ws.A + j) * kLn2 : __ldcg(ws.Fd + j));
+            ws.lcout[j] = log(colsum) + (TIER != TIER_F64 ? (double)__ldcg(ws.A + j) * kLn2 : __ldcg(ws.Fd + j));
     }
     return;
 timeout:

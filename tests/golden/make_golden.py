@@ -5,7 +5,9 @@ from the CUDA library.  Each record holds, for one (cost kind, seed, target gap)
   H_min, the Prop. 2 gamma_f, the oracle's rounded-plan cost and c-transform bound, its
   evaluation counts, and the exact OT value (column generation priced over all n^2 arcs).
 Usage:  python tests/golden/make_golden.py [k] [eps ...]   (defaults: k = 64, eps = 1e-6)
-Runs the cases in parallel worker processes (spawn) and writes tests/golden/grid{n}.json.
+        python tests/golden/make_golden.py --exact-only [k]   (only the exact OT values)
+Runs the cases in parallel worker processes (spawn) and merges each finished case into
+tests/golden/grid{n}.json (or exact{n}.json) as soon as it completes.
 """
 from __future__ import annotations
 
@@ -52,26 +54,50 @@ def one_case(args):
     }
 
 
-def main():
-    k = int(sys.argv[1]) if len(sys.argv) > 1 else 64
-    eps_list = [float(a) for a in sys.argv[2:]] or [1e-6]
-    cases = [(k, kind, SEED, eps) for eps in eps_list for kind in ("l2sq", "l1")]
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(min(len(cases), os.cpu_count() or 1)) as pool:
-        out = pool.map(one_case, cases)
-    path = os.path.join(HERE, f"grid{k * k}.json")
+def exact_case(args):
+    k, kind, seed = args
+    import numpy as np
+    from oracle import exact as E
+    from paper_2307_08507_gb300 import inputs as I
+    p = I.grid_problem(k, seed, kind=kind)
+    t0 = time.time()
+    val, f, g, rounds = E.exact_ot_colgen(p.C.astype(np.float64), p.r, p.c, k_init=4)
+    return {"k": k, "n": p.n, "kind": kind, "seed": seed, "exact_ot": val, "exact_rounds": rounds,
+            "exact_seconds": time.time() - t0}
+
+
+def _merge(path, record, key):
     old = []
     if os.path.exists(path):
         with open(path) as fh:
             old = json.load(fh)["cases"]
-    keyed = {(c["kind"], c["seed"], c["eps_target"]): c for c in old}
-    for c in out:
-        keyed[(c["kind"], c["seed"], c["eps_target"])] = c
+    keyed = {key(c): c for c in old}
+    keyed[key(record)] = record
     with open(path, "w") as fh:
         json.dump({"generator": "tests/golden/make_golden.py (CPU FP64 oracle + exact LP)",
-                   "cases": sorted(keyed.values(), key=lambda c: (c["kind"], c["eps_target"]))},
+                   "cases": sorted(keyed.values(), key=lambda c: tuple(str(x) for x in key(c)))},
                   fh, indent=1)
-    print(json.dumps(out, indent=1))
+
+
+def main():
+    ctx = mp.get_context("spawn")
+    if len(sys.argv) > 1 and sys.argv[1] == "--exact-only":
+        k = int(sys.argv[2]) if len(sys.argv) > 2 else 64
+        cases = [(k, kind, SEED) for kind in ("l2sq", "l1")]
+        path = os.path.join(HERE, f"exact{k * k}.json")
+        with ctx.Pool(len(cases)) as pool:
+            for rec in pool.imap_unordered(exact_case, cases):
+                _merge(path, rec, lambda c: (c["kind"], c["seed"]))
+                print(json.dumps(rec), flush=True)
+        return
+    k = int(sys.argv[1]) if len(sys.argv) > 1 else 64
+    eps_list = [float(a) for a in sys.argv[2:]] or [1e-6]
+    cases = [(k, kind, SEED, eps) for eps in eps_list for kind in ("l2sq", "l1")]
+    path = os.path.join(HERE, f"grid{k * k}.json")
+    with ctx.Pool(min(len(cases), os.cpu_count() or 1)) as pool:
+        for rec in pool.imap_unordered(one_case, cases):
+            _merge(path, rec, lambda c: (c["kind"], c["seed"], c["eps_target"]))
+            print(json.dumps(rec), flush=True)
 
 
 if __name__ == "__main__":

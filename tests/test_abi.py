@@ -41,3 +41,30 @@ def test_oracle_is_not_linked_into_the_product():
                 text = open(os.path.join(dirpath, fn)).read()
                 assert "import oracle" not in text and "from oracle" not in text, fn
                 assert "oracle.h" not in text, fn
+
+
+def test_struct_layouts_match_the_binding(tmp_path):
+    """mdot_params / mdot_info: size and every field offset agree between include/mdot.h (compiled
+    with gcc) and the ctypes binding."""
+    import shutil
+    import subprocess
+    import paper_2307_08507_gb300 as M
+    if shutil.which("gcc") is None:
+        import pytest
+        pytest.skip("gcc not available")
+    lines = []
+    for struct, cls in (("mdot_params", M.Params), ("mdot_info", M.Info)):
+        lines.append(f'printf("{struct} size %zu\\n", sizeof({struct}));')
+        for name, _ in cls._fields_:
+            lines.append(f'printf("{struct} {name} %zu\\n", offsetof({struct}, {name}));')
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"mdot.h\"\nint main(void){\n"
+                   + "\n".join(lines) + "\nreturn 0;}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", f"-I{os.path.join(ROOT, 'include')}", str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for struct, cls in (("mdot_params", M.Params), ("mdot_info", M.Info)):
+        assert got[(struct, "size")] == ctypes.sizeof(cls), struct
+        for name, _ in cls._fields_:
+            assert got[(struct, name)] == getattr(cls, name).offset, (struct, name)

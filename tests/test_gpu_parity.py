@@ -22,6 +22,7 @@ from paper_2307_08507_gb300 import inputs as I
 pytestmark = [pytest.mark.gpu, pytest.mark.timeout(300)]
 
 TOL_F32 = 4e-6
+TOL_F32A = 1e-6     # accurate fp32 tier: ~1.3 ulp per entry, unbiased, exponent in double-float
 TOL_F64 = 1e-11
 DEV = "cuda:0"
 
@@ -53,14 +54,14 @@ def rand_potentials(n, gamma, seed, C):
 
 @pytest.mark.parametrize("n", [1, 2, 3, 31, 33, 257, 1000])
 @pytest.mark.parametrize("gamma", [1.0, 64.0, 4096.0, 65536.0])
-@pytest.mark.parametrize("precision", [M.PREC_FP32, M.PREC_FP64])
+@pytest.mark.parametrize("precision", [M.PREC_FP32, M.PREC_FP64, M.PREC_FP32A])
 def test_dual_eval_matches_oracle(h, n, gamma, precision):
     rng = np.random.default_rng(n * 7 + int(math.log2(gamma)))
     C = rng.uniform(0, 1, (n, n)).astype(np.float32)
     u, v, _, _ = rand_potentials(n, gamma, n + 1, C)
     lr_o, lc_o = O.dual_eval(C.astype(np.float64), u, v, gamma)
     lr, lc = h.dual_eval(t(u), t(v), gamma, t(C), precision=precision)
-    tol = TOL_F32 if precision == M.PREC_FP32 else TOL_F64
+    tol = {M.PREC_FP32: TOL_F32, M.PREC_FP32A: TOL_F32A, M.PREC_FP64: TOL_F64}[precision]
     np.testing.assert_allclose(lr.cpu().numpy(), lr_o, rtol=0, atol=tol * max(1.0, 1e-12 * np.abs(lr_o).max()))
     np.testing.assert_allclose(lc.cpu().numpy(), lc_o, rtol=0, atol=tol * max(1.0, 1e-12 * np.abs(lc_o).max()))
     # the solver path: scales taken from a previous estimate give the same marginals
@@ -81,6 +82,24 @@ def test_dual_eval_huge_potentials(h):
         lr, lc = h.dual_eval(t(u), t(v), gamma, t(C), precision=prec)
         np.testing.assert_allclose(lr.cpu().numpy(), lr_o, rtol=1e-12, atol=tol)
         np.testing.assert_allclose(lc.cpu().numpy(), lc_o, rtol=1e-12, atol=tol)
+
+
+def test_accurate_tier_removes_the_ex2_bias(h):
+    """ex2.approx errs low by ~5e-8 on average, which biases every marginal; the accurate tier's
+    polynomial exp2 is unbiased: its mean signed log-marginal error against the oracle is far
+    smaller (n = 4096 grid at gamma = 2^16, every row and column)."""
+    p = I.grid_problem(64, 2000)
+    gamma = 2.0 ** 16
+    u, v, _, _ = rand_potentials(p.n, gamma, 13, p.C)
+    lr_o, lc_o = O.dual_eval(p.C.astype(np.float64), u, v, gamma)
+    err = {}
+    for prec in (M.PREC_FP32, M.PREC_FP32A):
+        lr, lc = h.dual_eval(t(u), t(v), gamma, t(p.C), precision=prec)
+        d = np.concatenate([lr.cpu().numpy() - lr_o, lc.cpu().numpy() - lc_o])
+        err[prec] = (d.mean(), np.abs(d).max())
+    assert abs(err[M.PREC_FP32A][0]) < 1e-8, err
+    assert err[M.PREC_FP32A][1] < TOL_F32A, err
+    assert abs(err[M.PREC_FP32A][0]) < abs(err[M.PREC_FP32][0]), err
 
 
 def test_dual_eval_full_size_grid(h):
