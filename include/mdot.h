@@ -61,6 +61,17 @@ typedef enum mdot_precision {
                              below 2e-6                                                         */
 } mdot_precision;
 
+/* Source of the cost matrix for the *_points entry points: C_ij regenerated inside every pass
+ * from coordinates x_i, y_j (n x 3 fp32 each, row-major; 2-D data uses z = 0):
+ *   d_k = x_ik - y_jk,  D = (d0*d0 + d1*d1) + d2*d2 (SQEUCLID) or (|d0| + |d1|) + |d2| (L1),
+ *   C_ij = D * scale,   every operation rounded to fp32 in exactly this order,
+ * so C never occupies memory (the on-the-fly cost of Sec. 5.1) and equals the matrix a caller
+ * would build with the same fp32 operations.  scale is normally 1 / max_ij D. */
+typedef enum mdot_cost_kind {
+    MDOT_COST_SQEUCLID = 1,
+    MDOT_COST_L1 = 2
+} mdot_cost_kind;
+
 /* Parameters of Alg. 1 / Alg. 2 / App. B.  Fill with mdot_default_params, then override. */
 typedef struct mdot_params {
     double  gamma_i;        /* first inverse temperature; Sec. 5.2 default 2^4                     */
@@ -174,6 +185,24 @@ mdot_status mdot_solve(mdot_handle* h, const double* r, const double* c, const f
                        int64_t n, double eps_target, const mdot_params* prm,
                        double* u_out, double* v_out, double* cost_out, double* gap_out,
                        mdot_info* info);
+
+/*
+ * mdot_solve with the cost regenerated from coordinates (see mdot_cost_kind): x, y are device
+ * arrays of n x 3 floats; no n x n buffer is read or written (memory O(n)).  Other arguments,
+ * outputs and errors as mdot_solve; INVALID_ARG also for an unknown kind or scale <= 0.
+ */
+mdot_status mdot_solve_points(mdot_handle* h, const double* r, const double* c, const float* x,
+                              const float* y, int32_t cost_kind, float scale, int64_t n,
+                              double eps_target, const mdot_params* prm, double* u_out,
+                              double* v_out, double* cost_out, double* gap_out, mdot_info* info);
+
+/*
+ * mdot_dual_eval with the cost regenerated from coordinates (see mdot_cost_kind).
+ */
+mdot_status mdot_dual_eval_points(mdot_handle* h, const double* u, const double* v, double gamma,
+                                  const float* x, const float* y, int32_t cost_kind, float scale,
+                                  int64_t n, const double* ref_log_rP, int32_t precision,
+                                  double* log_rP, double* log_cP);
 
 /*
  * mdot_solve with every array in HOST memory: copies r, c (n doubles) and C (n*n floats) to the

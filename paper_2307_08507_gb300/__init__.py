@@ -23,6 +23,7 @@ MDOT_ERR_TIMEOUT = 4
 MDOT_ERR_OOM = 5
 MDOT_ERR_CUDA = 6
 PREC_AUTO, PREC_FP32, PREC_FP64, PREC_FP32A = 0, 1, 2, 3
+COST_SQEUCLID, COST_L1 = 1, 2
 
 
 class Params(ct.Structure):
@@ -82,8 +83,13 @@ def lib():
     L.mdot_solve.argtypes = [_P, _P, _P, _P, ct.c_int64, ct.c_double, ct.POINTER(Params), _P, _P,
                              ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), ct.POINTER(Info)]
     L.mdot_solve_host.argtypes = L.mdot_solve.argtypes
+    L.mdot_solve_points.argtypes = [_P, _P, _P, _P, _P, ct.c_int32, ct.c_float, ct.c_int64, ct.c_double,
+                                    ct.POINTER(Params), _P, _P, ct.POINTER(ct.c_double),
+                                    ct.POINTER(ct.c_double), ct.POINTER(Info)]
+    L.mdot_dual_eval_points.argtypes = [_P, _P, _P, ct.c_double, _P, _P, ct.c_int32, ct.c_float, ct.c_int64,
+                                        _P, ct.c_int32, _P, _P]
     for name in ("mdot_create", "mdot_destroy", "mdot_dual_eval", "mdot_round", "mdot_lower_bound",
-                 "mdot_solve", "mdot_solve_host"):
+                 "mdot_solve", "mdot_solve_host", "mdot_solve_points", "mdot_dual_eval_points"):
         getattr(L, name).restype = ct.c_int32
     _lib = L
     return L
@@ -215,6 +221,40 @@ class Handle:
                              ct.byref(cost), ct.byref(gap), ct.byref(info))
         if check and s not in (MDOT_OK, MDOT_ERR_NOT_CONVERGED):
             raise MdotError(s, "mdot_solve")
+        return u, v, SolveResult(s, cost.value, gap.value, info)
+
+    def dual_eval_points(self, u, v, gamma: float, x, y, kind: int, scale: float, ref_log_rP=None,
+                         precision: int = PREC_FP32):
+        """mdot_dual_eval_points: C regenerated from coordinates x, y (CUDA float32 tensors n x 3)."""
+        import torch
+        n = u.numel()
+        lr = torch.empty(n, dtype=torch.float64, device=u.device)
+        lc = torch.empty(n, dtype=torch.float64, device=u.device)
+        ref = _ptr(ref_log_rP, torch.float64, n, "ref_log_rP") if ref_log_rP is not None else None
+        s = lib().mdot_dual_eval_points(self._h, _ptr(u, torch.float64, n, "u"), _ptr(v, torch.float64, n, "v"),
+                                        float(gamma), _ptr(x, torch.float32, 3 * n, "x"),
+                                        _ptr(y, torch.float32, 3 * n, "y"), int(kind), float(scale), n, ref,
+                                        int(precision), _ptr(lr, torch.float64), _ptr(lc, torch.float64))
+        if s != MDOT_OK:
+            raise MdotError(s, "mdot_dual_eval_points")
+        return lr, lc
+
+    def solve_points(self, r, c, x, y, kind: int, scale: float, eps_target: float = 1e-6,
+                     params: Params | None = None, u_out=None, v_out=None, check: bool = True):
+        """mdot_solve_points: MDOT-PNCG with C regenerated from coordinates (memory O(n))."""
+        import torch
+        n = r.numel()
+        u = u_out if u_out is not None else torch.empty(n, dtype=torch.float64, device=r.device)
+        v = v_out if v_out is not None else torch.empty(n, dtype=torch.float64, device=r.device)
+        cost, gap, info = ct.c_double(0.0), ct.c_double(0.0), Info()
+        s = lib().mdot_solve_points(self._h, _ptr(r, torch.float64, n, "r"), _ptr(c, torch.float64, n, "c"),
+                                    _ptr(x, torch.float32, 3 * n, "x"), _ptr(y, torch.float32, 3 * n, "y"),
+                                    int(kind), float(scale), n, float(eps_target),
+                                    ct.byref(params) if params is not None else None,
+                                    _ptr(u, torch.float64, n, "u_out"), _ptr(v, torch.float64, n, "v_out"),
+                                    ct.byref(cost), ct.byref(gap), ct.byref(info))
+        if check and s not in (MDOT_OK, MDOT_ERR_NOT_CONVERGED):
+            raise MdotError(s, "mdot_solve_points")
         return u, v, SolveResult(s, cost.value, gap.value, info)
 
     def solve_host(self, r, c, C, eps_target: float = 1e-6, params: Params | None = None,

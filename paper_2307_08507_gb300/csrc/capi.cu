@@ -269,11 +269,33 @@ mdot_status check_marginals(mdot_handle* h, const WS& ws, double* H)
     return MDOT_OK;
 }
 
-mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const float* C, int64_t n,
+// Where C comes from: a dense matrix, or coordinates (n x 3 each) with a kind and a scale.
+struct CostSpec {
+    const float* C = nullptr;
+    const float* X = nullptr;
+    const float* Y = nullptr;
+    int kind = COST_DENSE;
+    float scale = 1.0f;
+    bool valid() const
+    {
+        if (kind == COST_DENSE) return C != nullptr;
+        return (kind == COST_SQEUCLID || kind == COST_L1) && X && Y && std::isfinite(scale) && scale > 0.0f;
+    }
+    void apply(WS& ws) const
+    {
+        ws.C = C;
+        ws.X = X;
+        ws.Y = Y;
+        ws.ckind = kind;
+        ws.cscale = scale;
+    }
+};
+
+mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const CostSpec& cs, int64_t n,
                        double eps_target, const mdot_params* prm, double* u_out, double* v_out,
                        double* cost_out, double* gap_out, mdot_info* info)
 {
-    if (!h || !r || !c || !C || !u_out || !v_out || n < 1 || n > h->max_n) return MDOT_ERR_INVALID_ARG;
+    if (!h || !r || !c || !cs.valid() || !u_out || !v_out || n < 1 || n > h->max_n) return MDOT_ERR_INVALID_ARG;
     mdot_params P;
     if (prm) P = *prm; else mdot_default_params(&P);
     if (params_ok(P) != MDOT_OK) return MDOT_ERR_INVALID_ARG;
@@ -282,7 +304,7 @@ mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const f
     ws.n = (int)n;
     ws.r = r;
     ws.c = c;
-    ws.C = C;
+    cs.apply(ws);
     double H = 0.0;
     mdot_status ms = check_marginals(h, ws, &H);
     if (ms != MDOT_OK) return ms;
@@ -437,7 +459,23 @@ mdot_status mdot_solve(mdot_handle* h, const double* r, const double* c, const f
                        double eps_target, const mdot_params* prm, double* u_out, double* v_out,
                        double* cost_out, double* gap_out, mdot_info* info)
 {
-    return solve_core(h, r, c, C, n, eps_target, prm, u_out, v_out, cost_out, gap_out, info);
+    CostSpec cs;
+    cs.C = C;
+    return solve_core(h, r, c, cs, n, eps_target, prm, u_out, v_out, cost_out, gap_out, info);
+}
+
+mdot_status mdot_solve_points(mdot_handle* h, const double* r, const double* c, const float* x, const float* y,
+                              int32_t cost_kind, float scale, int64_t n, double eps_target,
+                              const mdot_params* prm, double* u_out, double* v_out, double* cost_out,
+                              double* gap_out, mdot_info* info)
+{
+    CostSpec cs;
+    cs.X = x;
+    cs.Y = y;
+    cs.kind = cost_kind;
+    cs.scale = scale;
+    if (cost_kind == COST_DENSE) return MDOT_ERR_INVALID_ARG;
+    return solve_core(h, r, c, cs, n, eps_target, prm, u_out, v_out, cost_out, gap_out, info);
 }
 
 mdot_status mdot_solve_host(mdot_handle* h, const double* r_host, const double* c_host, const float* C_host,
@@ -464,7 +502,9 @@ mdot_status mdot_solve_host(mdot_handle* h, const double* r_host, const double* 
     CKR(cudaMemcpyAsync(h->d_r, r_host, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CKR(cudaMemcpyAsync(h->d_c, c_host, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CKR(cudaMemcpyAsync(h->d_C, C_host, (size_t)n * n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
-    mdot_status s = solve_core(h, h->d_r, h->d_c, h->d_C, n, eps_target, prm, h->d_u, h->d_v,
+    CostSpec cs;
+    cs.C = h->d_C;
+    mdot_status s = solve_core(h, h->d_r, h->d_c, cs, n, eps_target, prm, h->d_u, h->d_v,
                                cost_out, gap_out, info);
     if (s == MDOT_ERR_INVALID_ARG || s == MDOT_ERR_CUDA) return s;
     CKR(cudaMemcpyAsync(u_host, h->d_u, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -473,16 +513,16 @@ mdot_status mdot_solve_host(mdot_handle* h, const double* r_host, const double* 
     return s;
 }
 
-mdot_status mdot_dual_eval(mdot_handle* h, const double* u, const double* v, double gamma, const float* C,
-                           int64_t n, const double* ref_log_rP, int32_t precision, double* log_rP,
-                           double* log_cP)
+static mdot_status dual_eval_core(mdot_handle* h, const double* u, const double* v, double gamma,
+                                  const CostSpec& cs, int64_t n, const double* ref_log_rP, int32_t precision,
+                                  double* log_rP, double* log_cP)
 {
-    if (!h || !u || !v || !C || !log_rP || !log_cP || n < 1 || n > h->max_n || !(gamma > 0.0) ||
+    if (!h || !u || !v || !cs.valid() || !log_rP || !log_cP || n < 1 || n > h->max_n || !(gamma > 0.0) ||
         !std::isfinite(gamma) || precision < 0 || precision > 3)
         return MDOT_ERR_INVALID_ARG;
     WS ws = h->ws;
     ws.n = (int)n;
-    ws.C = C;
+    cs.apply(ws);
     EvalArgs a{};
     a.gamma = gamma;
     a.G64 = gamma * kLog2e;
@@ -497,6 +537,28 @@ mdot_status mdot_dual_eval(mdot_handle* h, const double* u, const double* v, dou
     CKR(cudaMemcpyAsync(h->h_state, ws.st, sizeof(State), cudaMemcpyDeviceToHost, h->stream));
     CKR(cudaStreamSynchronize(h->stream));
     return h->h_state->status == ST_OK ? MDOT_OK : MDOT_ERR_TIMEOUT;
+}
+
+mdot_status mdot_dual_eval(mdot_handle* h, const double* u, const double* v, double gamma, const float* C,
+                           int64_t n, const double* ref_log_rP, int32_t precision, double* log_rP,
+                           double* log_cP)
+{
+    CostSpec cs;
+    cs.C = C;
+    return dual_eval_core(h, u, v, gamma, cs, n, ref_log_rP, precision, log_rP, log_cP);
+}
+
+mdot_status mdot_dual_eval_points(mdot_handle* h, const double* u, const double* v, double gamma,
+                                  const float* x, const float* y, int32_t cost_kind, float scale, int64_t n,
+                                  const double* ref_log_rP, int32_t precision, double* log_rP, double* log_cP)
+{
+    CostSpec cs;
+    cs.X = x;
+    cs.Y = y;
+    cs.kind = cost_kind;
+    cs.scale = scale;
+    if (cost_kind == COST_DENSE) return MDOT_ERR_INVALID_ARG;
+    return dual_eval_core(h, u, v, gamma, cs, n, ref_log_rP, precision, log_rP, log_cP);
 }
 
 mdot_status mdot_round(mdot_handle* h, const double* u, const double* v, double gamma, const float* C,

@@ -13,35 +13,43 @@ static cudaError_t coop(K kernel, int G, size_t smem, cudaStream_t s, void** arg
     return cudaLaunchCooperativeKernel((const void*)kernel, dim3(G), dim3(kStageThreads), args, smem, s);
 }
 
+cudaError_t launch_stage_regen(int tier, const WS& ws, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_dual_eval_regen(int tier, const WS& ws, const EvalArgs& a, cudaStream_t s);
+cudaError_t configure_regen_kernels(int max_n, int G, int* min_blocks);
+
 cudaError_t launch_stage(int tier, const WS& ws, const StageArgs& a, cudaStream_t s)
 {
+    if (ws.ckind != COST_DENSE) return launch_stage_regen(tier, ws, a, s);
     WS w = ws;
     StageArgs aa = a;
     void* args[] = {(void*)&w, (void*)&aa};
     const size_t smem = stage_smem_bytes(ws.n, ws.G, tier);
-    if (tier == TIER_F64) return coop(stage_kernel<TIER_F64>, ws.G, smem, s, args);
-    if (tier == TIER_F32A) return coop(stage_kernel<TIER_F32A>, ws.G, smem, s, args);
-    return coop(stage_kernel<TIER_F32>, ws.G, smem, s, args);
+    if (tier == TIER_F64) return coop(stage_kernel<TIER_F64, COST_DENSE>, ws.G, smem, s, args);
+    if (tier == TIER_F32A) return coop(stage_kernel<TIER_F32A, COST_DENSE>, ws.G, smem, s, args);
+    return coop(stage_kernel<TIER_F32, COST_DENSE>, ws.G, smem, s, args);
 }
 
 cudaError_t launch_dual_eval(int tier, const WS& ws, const EvalArgs& a, cudaStream_t s)
 {
+    if (ws.ckind != COST_DENSE) return launch_dual_eval_regen(tier, ws, a, s);
     WS w = ws;
     EvalArgs aa = a;
     void* args[] = {(void*)&w, (void*)&aa};
     const size_t smem = stage_smem_bytes(ws.n, ws.G, tier);
-    if (tier == TIER_F64) return coop(dual_eval_kernel<TIER_F64>, ws.G, smem, s, args);
-    if (tier == TIER_F32A) return coop(dual_eval_kernel<TIER_F32A>, ws.G, smem, s, args);
-    return coop(dual_eval_kernel<TIER_F32>, ws.G, smem, s, args);
+    if (tier == TIER_F64) return coop(dual_eval_kernel<TIER_F64, COST_DENSE>, ws.G, smem, s, args);
+    if (tier == TIER_F32A) return coop(dual_eval_kernel<TIER_F32A, COST_DENSE>, ws.G, smem, s, args);
+    return coop(dual_eval_kernel<TIER_F32, COST_DENSE>, ws.G, smem, s, args);
 }
 
 cudaError_t configure_stage_kernels(int max_n, int G, int* min_blocks)
 {
     struct K { const void* f; int tier; } ks[] = {
-        {(const void*)stage_kernel<TIER_F32>, TIER_F32}, {(const void*)stage_kernel<TIER_F64>, TIER_F64},
-        {(const void*)stage_kernel<TIER_F32A>, TIER_F32A},
-        {(const void*)dual_eval_kernel<TIER_F32>, TIER_F32}, {(const void*)dual_eval_kernel<TIER_F64>, TIER_F64},
-        {(const void*)dual_eval_kernel<TIER_F32A>, TIER_F32A}};
+        {(const void*)stage_kernel<TIER_F32, COST_DENSE>, TIER_F32},
+        {(const void*)stage_kernel<TIER_F64, COST_DENSE>, TIER_F64},
+        {(const void*)stage_kernel<TIER_F32A, COST_DENSE>, TIER_F32A},
+        {(const void*)dual_eval_kernel<TIER_F32, COST_DENSE>, TIER_F32},
+        {(const void*)dual_eval_kernel<TIER_F64, COST_DENSE>, TIER_F64},
+        {(const void*)dual_eval_kernel<TIER_F32A, COST_DENSE>, TIER_F32A}};
     for (auto& k : ks) {
         const size_t smem = stage_smem_bytes(max_n, G, k.tier);
         cudaError_t e = cudaFuncSetAttribute(k.f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -51,7 +59,7 @@ cudaError_t configure_stage_kernels(int max_n, int G, int* min_blocks)
         if (e != cudaSuccess) return e;
         *min_blocks = std::min(*min_blocks, nb);
     }
-    return cudaSuccess;
+    return configure_regen_kernels(max_n, G, min_blocks);
 }
 
 }  // namespace mdot

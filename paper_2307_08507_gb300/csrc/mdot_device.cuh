@@ -31,7 +31,12 @@ constexpr int kThreads = 256;                  // CTA size of the cooperative ke
 constexpr int kK = 4;                          // float4 column groups per thread per sweep
 constexpr int kRG = 4;                         // rows per group in the passes (keeps the loop body small)
 
-enum Tier { TIER_F32 = 0, TIER_F64 = 1, TIER_F32A = 2 };   // F32A: fp32 with an accurate exponent and exp2
+enum Tier { TIER_F32 = 0, TIER_F64 = 1, TIER_F32A = 2 };
+// Cost source: a dense row-major matrix, or regenerated from coordinates x_i, y_j (n x 3 each)
+// inside the pass: squared Euclidean or L1 distance times a scale s (App. C point clouds; grids
+// use z = 0).  Both regenerated forms round every operation in a fixed order, so the value equals
+// the one a caller would materialise with the same fp32 operations.
+enum CostKind { COST_DENSE = 0, COST_SQEUCLID = 1, COST_L1 = 2 };   // F32A: fp32 with an accurate exponent and exp2
 enum EvalKind { KIND_INIT = 0, KIND_TRIAL = 1, KIND_FORCE = 2 };
 enum Phase { PH_RUN = 0, PH_DONE = 1 };
 enum SolveStatus { ST_OK = 0, ST_CAP = 1, ST_LSFAIL = 2, ST_NUMERIC = 3, ST_TIMEOUT = 4 };
@@ -66,6 +71,10 @@ struct State {
 struct WS {
     int n, G;
     const float* C;
+    const float* X;                   // n x 3 source coordinates (regenerated cost)
+    const float* Y;                   // n x 3 target coordinates
+    float cscale;                     // s = 1 / max distance
+    int ckind;                        // CostKind
     const double *r, *c;              // original marginals
     double *rt, *ct, *lrt, *lct;      // smoothed marginals and logs (Alg. 1)
     double *u, *v, *pu, *pv, *uprev, *vprev;
@@ -147,6 +156,20 @@ __device__ __forceinline__ float exp2_acc(float th, float tl)
     p = fmaf(p, x, 1.0f);
     const float r = __int_as_float(__float_as_int(p) + ((int)kf << 23));
     return under ? 0.0f : r;
+}
+
+// C_ij regenerated from coordinates: d_k = x_ik - y_jk, D = (d0 d0 + d1 d1) + d2 d2 (or
+// (|d0| + |d1|) + |d2|), C = D s, every operation rounded to fp32 in that order (no contraction).
+template <int KIND>
+__device__ __forceinline__ float point_cost(float x0, float x1, float x2, float y0, float y1, float y2, float s)
+{
+    const float d0 = __fsub_rn(x0, y0), d1 = __fsub_rn(x1, y1), d2 = __fsub_rn(x2, y2);
+    float D;
+    if (KIND == COST_SQEUCLID)
+        D = __fadd_rn(__fadd_rn(__fmul_rn(d0, d0), __fmul_rn(d1, d1)), __fmul_rn(d2, d2));
+    else
+        D = __fadd_rn(__fadd_rn(fabsf(d0), fabsf(d1)), fabsf(d2));
+    return __fmul_rn(D, s);
 }
 
 // log2 P_ij - A_i for the accurate tier as an unevaluated sum th + tl: the product G32 * d and
@@ -661,12 +684,158 @@ __device__ __forceinline__ void pass_f32_tma(const float* __restrict__ C, int n,
     __syncthreads();
 }
 
+// Pass over the CTA's rows with C regenerated from coordinates (no C in memory): same structure
+// as pass_f32 with two float4 column groups per thread; the row coordinates come from shared
+// memory (sX: 3 floats per local row), the column coordinates sit in registers per sweep.
+template <bool ACC, int KIND>
+__device__ __forceinline__ void pass_f32_regen(const float* __restrict__ Y, float cs, int n, int r0, int r1,
+                                               const float* Hh, const float* Wc, const float* sFh,
+                                               const float* sWr, const float* sS, const float* sX,
+                                               float G32, float Glo, float* sRow, int nloc,
+                                               float* colpart_b)
+{
+    constexpr int KR = 2;
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int BN = 4 * KR * T;
+    for (int cb = 0; cb < n; cb += BN) {
+        float hh[KR][4], wc[KR][4], ca[KR][4], y0[KR][4], y1[KR][4], y2[KR][4];
+        int jk[KR];
+#pragma unroll
+        for (int k = 0; k < KR; ++k) {
+            jk[k] = cb + 4 * (tid + k * T);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int j = jk[k] + e;
+                const bool ok = j < n;
+                hh[k][e] = ok ? __ldcg(Hh + j) : 0.0f;
+                wc[k][e] = ok ? __ldcg(Wc + j) : -INFINITY;
+                y0[k][e] = ok ? __ldg(Y + 3 * (size_t)j) : 0.0f;
+                y1[k][e] = ok ? __ldg(Y + 3 * (size_t)j + 1) : 0.0f;
+                y2[k][e] = ok ? __ldg(Y + 3 * (size_t)j + 2) : 0.0f;
+                ca[k][e] = 0.0f;
+            }
+        }
+        for (int rg = r0; rg < r1; rg += kRG) {
+            float rp[kRG];
+#pragma unroll
+            for (int ii = 0; ii < kRG; ++ii) {
+                rp[ii] = 0.0f;
+                const int i = rg + ii;
+                if (i < r1) {
+                    const int il = i - r0;
+                    const float fh = sFh[il], wr = sWr[il], sc = sS[il];
+                    const float x0 = sX[3 * il], x1 = sX[3 * il + 1], x2 = sX[3 * il + 2];
+#pragma unroll
+                    for (int k = 0; k < KR; ++k) {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float cv = point_cost<KIND>(x0, x1, x2, y0[k][e], y1[k][e], y2[k][e], cs);
+                            const float d = (fh + hh[k][e]) - cv;
+                            float E;
+                            if (ACC) {
+                                float tl;
+                                const float th = exponent_acc(d, G32, Glo, wr + wc[k][e], tl);
+                                E = exp2_acc(th, tl);
+                            } else {
+                                E = ex2f(fmaf(Glo, d, fmaf(G32, d, wr + wc[k][e])));
+                            }
+                            rp[ii] += E;
+                            ca[k][e] = fmaf(E, sc, ca[k][e]);
+                        }
+                    }
+                }
+            }
+            butterfly<kRG>(rp, lane);
+            const int il = rg + lane;
+            if (lane < kRG && il < r1) sRow[warp * nloc + (il - r0)] += rp[0];
+        }
+#pragma unroll
+        for (int k = 0; k < KR; ++k)
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (jk[k] + e < n) colpart_b[jk[k] + e] = ca[k][e];
+    }
+}
+
+// fp64 entries with the regenerated cost (the fp32 cost value promoted, as the dense tier does)
+template <int KIND>
+__device__ __forceinline__ void pass_f64_regen(const float* __restrict__ Y, float cs, int n, int r0, int r1,
+                                               const double* Hd, const double* sFd, const double* sS,
+                                               const float* sX, double gamma, double* sRow, int nloc,
+                                               double* colpart_b)
+{
+    constexpr int KR = 2;
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int BN = 4 * KR * T;
+    for (int cb = 0; cb < n; cb += BN) {
+        double hd[KR][4], ca[KR][4];
+        float y0[KR][4], y1[KR][4], y2[KR][4];
+        int jk[KR];
+#pragma unroll
+        for (int k = 0; k < KR; ++k) {
+            jk[k] = cb + 4 * (tid + k * T);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int j = jk[k] + e;
+                const bool ok = j < n;
+                hd[k][e] = ok ? __ldcg(Hd + j) : -INFINITY;
+                y0[k][e] = ok ? __ldg(Y + 3 * (size_t)j) : 0.0f;
+                y1[k][e] = ok ? __ldg(Y + 3 * (size_t)j + 1) : 0.0f;
+                y2[k][e] = ok ? __ldg(Y + 3 * (size_t)j + 2) : 0.0f;
+                ca[k][e] = 0.0;
+            }
+        }
+        for (int rg = r0; rg < r1; rg += kRG) {
+            double rp[kRG];
+#pragma unroll
+            for (int ii = 0; ii < kRG; ++ii) {
+                rp[ii] = 0.0;
+                const int i = rg + ii;
+                if (i < r1) {
+                    const int il = i - r0;
+                    const double fd = sFd[il], s = sS[il];
+                    const float x0 = sX[3 * il], x1 = sX[3 * il + 1], x2 = sX[3 * il + 2];
+#pragma unroll
+                    for (int k = 0; k < KR; ++k) {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const double cv = (double)point_cost<KIND>(x0, x1, x2, y0[k][e], y1[k][e], y2[k][e], cs);
+                            const double E = exp((fd + hd[k][e]) - gamma * cv);
+                            rp[ii] += E;
+                            ca[k][e] = fma(E, s, ca[k][e]);
+                        }
+                    }
+                }
+            }
+            butterfly<kRG>(rp, lane);
+            const int il = rg + lane;
+            if (lane < kRG && il < r1) sRow[warp * nloc + (il - r0)] += rp[0];
+        }
+#pragma unroll
+        for (int k = 0; k < KR; ++k)
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (jk[k] + e < n) colpart_b[jk[k] + e] = ca[k][e];
+    }
+}
+
+// C_ij inside the generic passes: a dense row pointer, or regenerated (scalar loads; the generic
+// evaluation is not on the solver's hot path).
+template <int COST>
+__device__ __forceinline__ float cost_at(const WS& ws, const float* Crow, int i, int j)
+{
+    if (COST == COST_DENSE) return __ldg(Crow + j);
+    return point_cost<COST>(__ldg(ws.X + 3 * (size_t)i), __ldg(ws.X + 3 * (size_t)i + 1), __ldg(ws.X + 3 * (size_t)i + 2),
+                            __ldg(ws.Y + 3 * (size_t)j), __ldg(ws.Y + 3 * (size_t)j + 1), __ldg(ws.Y + 3 * (size_t)j + 2),
+                            ws.cscale);
+}
+
 // Two-scale pass of the generic dual evaluation: the row sum of row i uses exponents relative to
 // the row scale A_i (folded into the row constants sFh/sWr), the column sum of column j uses
 // exponents relative to the column scale B_j (folded into the column constants Hh2/Wc2), so both
 // log-sum-exps stay exact for potentials of any spread.  Two exp2 per entry.
-template <bool VEC4, bool ACC>
-__device__ __forceinline__ void pass2_f32(const float* __restrict__ C, int n, int r0, int r1,
+template <bool VEC4, bool ACC, int COST>
+__device__ __forceinline__ void pass2_f32(const WS& ws, const float* __restrict__ C, int n, int r0, int r1,
                                           const float* Hh, const float* Wc, const float* Hh2,
                                           const float* Wc2, const float* sFh, const float* sWr,
                                           const float* sFh2, const float* sWr2, float G32, float Glo,
@@ -713,7 +882,8 @@ __device__ __forceinline__ void pass2_f32(const float* __restrict__ C, int n, in
                             }
                         } else {
 #pragma unroll
-                            for (int e = 0; e < 4; ++e) cv[e] = (jk[k] + e < n) ? __ldg(Crow + jk[k] + e) : 0.0f;
+                            for (int e = 0; e < 4; ++e)
+                                cv[e] = (jk[k] + e < n) ? cost_at<COST>(ws, Crow, i, jk[k] + e) : 0.0f;
                         }
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
@@ -745,7 +915,8 @@ __device__ __forceinline__ void pass2_f32(const float* __restrict__ C, int n, in
     }
 }
 
-__device__ __forceinline__ void pass2_f64(const float* __restrict__ C, int n, int r0, int r1,
+template <int COST>
+__device__ __forceinline__ void pass2_f64(const WS& ws, const float* __restrict__ C, int n, int r0, int r1,
                                           const double* Hd, const double* Bd, const double* sFd,
                                           const double* sAd, double gamma, double* sRow, int nloc,
                                           double* colpart_b)
@@ -781,7 +952,7 @@ __device__ __forceinline__ void pass2_f64(const float* __restrict__ C, int n, in
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             const int j = jk[k] + e;
-                            const double cv = (j < n) ? (double)__ldg(Crow + j) : 0.0;
+                            const double cv = (j < n) ? (double)cost_at<COST>(ws, Crow, i, j) : 0.0;
                             const double z = (fd + hd[k][e]) - gamma * cv;   // u_i + v_j - gamma C_ij
                             rp[ii] += exp(z - ad);
                             ca[k][e] += exp(z - bd[k][e]);

@@ -59,11 +59,11 @@ cudaError_t setup_device(int dev, DeviceSetup** out)
         if (e != cudaSuccess) return e;
         const int G = std::min(sms, kMaxG);
         const size_t smem = smem_layout(kMaxN, G, TIER_F32, kStageThreads).bytes;
-        e = cudaFuncSetAttribute((const void*)dual_eval_kernel<TIER_F32>,
+        e = cudaFuncSetAttribute((const void*)dual_eval_kernel<TIER_F32, COST_DENSE>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)dual_eval_kernel<TIER_F32>,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)dual_eval_kernel<TIER_F32, COST_DENSE>,
                                                           kStageThreads, smem);
         if (e != cudaSuccess) return e;
         if (nb < 1) return cudaErrorCooperativeLaunchTooLarge;
@@ -123,7 +123,7 @@ extern "C" mdot_status mdot_dual_eval_noalloc(const double* u, const double* v, 
     EvalArgs ak = a;
     void* args[] = {(void*)&wk, (void*)&ak};
     const size_t smem = smem_layout((int)n, s->G, TIER_F32, kStageThreads).bytes;
-    if (cudaLaunchCooperativeKernel((const void*)dual_eval_kernel<TIER_F32>, dim3(s->G), dim3(kStageThreads),
+    if (cudaLaunchCooperativeKernel((const void*)dual_eval_kernel<TIER_F32, COST_DENSE>, dim3(s->G), dim3(kStageThreads),
                                     args, smem, st) != cudaSuccess)
         return MDOT_ERR_CUDA;
     int status = 0;

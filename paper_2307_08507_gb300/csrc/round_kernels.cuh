@@ -14,8 +14,8 @@ enum RoundMode { RM_ROWSUM = 0, RM_COLSUM = 1, RM_ROWFINAL = 2, RM_WRITE = 3 };
 
 // One pass over the CTA's rows.  sRowX: per local row x_i 2^{A_i} (fp64); sAcc: per-warp row sums
 // [warp][3][nloc] fp64 (each slot written by one lane: no atomics, fixed order).
-template <int MODE, int RG>
-__device__ __forceinline__ void pass_round(const float* __restrict__ C, int n, int r0, int r1,
+template <int MODE, int RG, int COST>
+__device__ __forceinline__ void pass_round(const WS& ws, const float* __restrict__ C, int n, int r0, int r1,
                                            const float* Hh, const float* Wc, const float* sFh,
                                            const float* sWr, const double* sRowX, float G32, float Glo,
                                            const double* Y, const double* EC, const double* ER,
@@ -61,7 +61,7 @@ __device__ __forceinline__ void pass_round(const float* __restrict__ C, int n, i
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             const int j = jk[k] + e;
-                            const float cv = (j < n) ? __ldg(Crow + j) : 0.0f;
+                            const float cv = (j < n) ? cost_at<COST>(ws, Crow, i, j) : 0.0f;
                             const float d = (fh + hh[k][e]) - cv;
                             const float t = fmaf(Glo, d, fmaf(G32, d, wr + wc[k][e]));
                             const double E = (double)ex2f(t);
@@ -128,6 +128,7 @@ __host__ __device__ inline RoundSmem round_smem(int n, int G, int nthreads)
     return L;
 }
 
+template <int COST>
 __global__ void __launch_bounds__(kThreads, 1) round_kernel(WS ws, RoundArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(WS ws, RoundArgs a)
             float m = -INFINITY;
             const float* Crow = ws.C + (size_t)i * n;
             for (int j = lane; j < n; j += 32)
-                m = fmaxf(m, fmaf(G32, (fh + __ldcg(ws.Hh + j)) - __ldg(Crow + j), wl + __ldcg(ws.Wc + j)));
+                m = fmaxf(m, fmaf(G32, (fh + __ldcg(ws.Hh + j)) - cost_at<COST>(ws, Crow, i, j), wl + __ldcg(ws.Wc + j)));
 #pragma unroll
             for (int o = 16; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
             if (lane == 0) sA[i - r0] = (int)fmin(fmax(ceil((double)m), -1.0e6), 1.0e6);
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(WS ws, RoundArgs a)
     if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
 
     // pass 1: r(P)_i = 2^{A_i} sum_j E_ij ; x_i = min(r_i / r(P)_i, 1)  (Alg. 3)
-    pass_round<RM_ROWSUM, 4>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sX, G32, Glo, nullptr, nullptr,
+    pass_round<RM_ROWSUM, 4, COST>(ws, ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sX, G32, Glo, nullptr, nullptr,
                               nullptr, 0.0, sAcc, nloc, nullptr, nullptr);
     __syncthreads();
     for (int i = r0 + tid; i < r1; i += T) {
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(WS ws, RoundArgs a)
     }
     __syncthreads();
     // pass 2: c(F)_j = sum_i x_i P_ij  (Alg. 3)
-    pass_round<RM_COLSUM, 4>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sX, G32, Glo, nullptr, nullptr,
+    pass_round<RM_COLSUM, 4, COST>(ws, ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sX, G32, Glo, nullptr, nullptr,
                               nullptr, 0.0, sAcc, nloc, ws.colpartd + (size_t)b * n, nullptr);
     if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
     for (int j0 = c0; j0 < c1; j0 += 32) {
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(WS ws, RoundArgs a)
     for (int x0 = tid; x0 < (T >> 5) * 3 * nloc; x0 += T) sAcc[x0] = 0.0;
     if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
     // pass 3: r(F')_i, <F', C> by rows, (C err_c)_i   (Alg. 3)
-    pass_round<RM_ROWFINAL, 4>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sX, G32, Glo, a.Y, a.EC,
+    pass_round<RM_ROWFINAL, 4, COST>(ws, ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sX, G32, Glo, a.Y, a.EC,
                                nullptr, 0.0, sAcc, nloc, nullptr, nullptr);
     __syncthreads();
 #pragma unroll
@@ -265,7 +266,7 @@ __global__ void __launch_bounds__(kThreads, 1) round_kernel(WS ws, RoundArgs a)
     }
     if (a.G_out != nullptr) {
         // G = F' + err_r err_c^T / ||err_r||_1 (Alg. 3), written row-major in fp64
-        pass_round<RM_WRITE, 4>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sX, G32, Glo, a.Y, a.EC,
+        pass_round<RM_WRITE, 4, COST>(ws, ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sX, G32, Glo, a.Y, a.EC,
                                  a.ER, (e1 > 0.0) ? 1.0 / e1 : 0.0, sAcc, nloc, nullptr, a.G_out);
     }
     return;
@@ -277,6 +278,7 @@ timeout:
 // c-transform lower bound: g'_j = min_i (C_ij - f_i), f'_i = min_j (C_ij - g'_j), fp64
 // ---------------------------------------------------------------------------------------------
 
+template <int COST>
 __global__ void __launch_bounds__(kThreads, 1) lower_bound_kernel(WS ws, LbArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
@@ -299,7 +301,7 @@ __global__ void __launch_bounds__(kThreads, 1) lower_bound_kernel(WS ws, LbArgs 
     // column minima over own rows: thread owns columns j = tid, tid + T, ...
     for (int j = tid; j < n; j += T) {
         double m = INFINITY;
-        for (int i = r0; i < r1; ++i) m = fmin(m, (double)__ldg(ws.C + (size_t)i * n + j) - sf[i - r0]);
+        for (int i = r0; i < r1; ++i) m = fmin(m, (double)cost_elem<COST>(ws, i, j) - sf[i - r0]);
         ws.colpartd[(size_t)b * n + j] = m;
     }
     if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
@@ -315,7 +317,7 @@ __global__ void __launch_bounds__(kThreads, 1) lower_bound_kernel(WS ws, LbArgs 
     for (int i = r0 + warp; i < r1; i += nw) {
         double m = INFINITY;
         const float* Crow = ws.C + (size_t)i * n;
-        for (int j = lane; j < n; j += 32) m = fmin(m, (double)__ldg(Crow + j) - __ldcg(a.gp + j));
+        for (int j = lane; j < n; j += 32) m = fmin(m, (double)cost_at<COST>(ws, Crow, i, j) - __ldcg(a.gp + j));
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (lane == 0) x[0] += m * a.r[i];

@@ -125,7 +125,7 @@ static __device__ void decide(State* S, const double* tot, const StageArgs& a)
 struct SmemLayout {
     int nloc_max;
     size_t off_row, off_c0, off_c1, off_s, off_A, off_x, off_merge, off_ring, off_bars, off_misc,
-        off_rstate, off_cstate, bytes;
+        off_rstate, off_cstate, off_xc, bytes;
     int stages;        // TMA ring slots (fp32 entries)
 };
 
@@ -149,6 +149,7 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int G, int tier, int nt
     L.off_merge = o; o += (size_t)2 * 32 * nw * 8;               o = (o + 15) & ~(size_t)15;
     L.off_rstate = o; o += (size_t)RS_COUNT * L.nloc_max * 8;   o = (o + 15) & ~(size_t)15;
     L.off_cstate = o; o += (size_t)CS_COUNT * L.nloc_max * 8;   o = (o + 15) & ~(size_t)15;
+    L.off_xc = o;    o += (size_t)3 * L.nloc_max * 4;           o = (o + 15) & ~(size_t)15;
     L.off_misc = o;  o += 16;
     L.off_bars = o;  o += (tier != TIER_F64) ? (size_t)2 * kStages * 8 : 0;   o = (o + 127) & ~(size_t)127;
     L.off_ring = o;
@@ -160,6 +161,25 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int G, int tier, int nt
     }
     L.bytes = o;
     return L;
+}
+
+// C_ij for the non-streaming passes (max passes, lower bound): dense load or regenerated.
+template <int COST>
+__device__ __forceinline__ float cost_elem(const WS& ws, int i, int j)
+{
+    if (COST == COST_DENSE) return __ldg(ws.C + (size_t)i * ws.n + j);
+    return point_cost<COST>(__ldg(ws.X + 3 * (size_t)i), __ldg(ws.X + 3 * (size_t)i + 1), __ldg(ws.X + 3 * (size_t)i + 2),
+                            __ldg(ws.Y + 3 * (size_t)j), __ldg(ws.Y + 3 * (size_t)j + 1), __ldg(ws.Y + 3 * (size_t)j + 2),
+                            ws.cscale);
+}
+
+// coordinates of the CTA's rows into shared memory (regenerated cost)
+template <int COST>
+__device__ __forceinline__ void load_row_coords(const WS& ws, int r0, int r1, unsigned char* sm, size_t off)
+{
+    if (COST == COST_DENSE) return;
+    float* sX = reinterpret_cast<float*>(sm + off);
+    for (int q = threadIdx.x; q < 3 * (r1 - r0); q += blockDim.x) sX[q] = __ldg(ws.X + 3 * (size_t)r0 + q);
 }
 
 // Row prep of an evaluation at potential ua (already u + alpha p_u) with row scale A.
@@ -195,8 +215,8 @@ __device__ __forceinline__ void prep_col(const WS& ws, int j, double va, double 
     }
 }
 
-// Phase A for the CTA's rows: pass over C, then the row sums (fp64) into rowsum[il].
-template <int TIER>
+// Phase A for the CTA's rows: pass over C (streamed or regenerated), row sums into sRow.
+template <int TIER, int COST>
 __device__ __forceinline__ void phase_A(const WS& ws, int r0, int r1, double gamma, double G64,
                                         unsigned char* sm, const SmemLayout& L)
 {
@@ -211,7 +231,11 @@ __device__ __forceinline__ void phase_A(const WS& ws, int r0, int r1, double gam
         const float* sFh = reinterpret_cast<const float*>(sm + L.off_c0);
         const float* sWr = reinterpret_cast<const float*>(sm + L.off_c1);
         const float* sS = reinterpret_cast<const float*>(sm + L.off_s);
-        if ((n & 3) == 0 && (reinterpret_cast<uintptr_t>(ws.C) & 15) == 0 && blockDim.x == kStageThreads &&
+        if (COST != COST_DENSE)
+            pass_f32_regen<TIER == TIER_F32A, COST>(ws.Y, ws.cscale, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sS,
+                                                    reinterpret_cast<const float*>(sm + L.off_xc), G32, Glo,
+                                                    sRow, L.nloc_max, ws.colpart + (size_t)b * n);
+        else if ((n & 3) == 0 && (reinterpret_cast<uintptr_t>(ws.C) & 15) == 0 && blockDim.x == kStageThreads &&
             L.stages >= 2)
             pass_f32_tma<TIER == TIER_F32A>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sS, G32, Glo, sRow, L.nloc_max,
                          ws.colpart + (size_t)b * n, reinterpret_cast<float*>(sm + L.off_ring), L.stages,
@@ -227,9 +251,15 @@ __device__ __forceinline__ void phase_A(const WS& ws, int r0, int r1, double gam
         double* sRow = reinterpret_cast<double*>(sm + L.off_row);
         for (int x = threadIdx.x; x < nw * L.nloc_max; x += blockDim.x) sRow[x] = 0.0;
         __syncthreads();
-        pass_f64(ws.C, n, r0, r1, ws.Hd, reinterpret_cast<const double*>(sm + L.off_c0),
-                 reinterpret_cast<const double*>(sm + L.off_s), gamma, sRow, L.nloc_max,
-                 ws.colpartd + (size_t)b * n);
+        if (COST != COST_DENSE)
+            pass_f64_regen<COST>(ws.Y, ws.cscale, n, r0, r1, ws.Hd, reinterpret_cast<const double*>(sm + L.off_c0),
+                                 reinterpret_cast<const double*>(sm + L.off_s),
+                                 reinterpret_cast<const float*>(sm + L.off_xc), gamma, sRow, L.nloc_max,
+                                 ws.colpartd + (size_t)b * n);
+        else
+            pass_f64(ws.C, n, r0, r1, ws.Hd, reinterpret_cast<const double*>(sm + L.off_c0),
+                     reinterpret_cast<const double*>(sm + L.off_s), gamma, sRow, L.nloc_max,
+                     ws.colpartd + (size_t)b * n);
     }
     __syncthreads();
     (void)nloc;
@@ -256,7 +286,7 @@ __device__ __forceinline__ double row_total(const unsigned char* sm, const SmemL
 // words of State before the grid barrier (the part the decision reads and writes)
 constexpr int kStateWords = (int)(offsetof(State, bar) / 8);
 
-template <int TIER>
+template <int TIER, int COST>
 __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel(WS ws, StageArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
@@ -277,6 +307,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel(WS ws, StageArg
     State* S = ws.st;
 
     if (tid == 0) s_gen = ld_acquire(&S->bar.gen);
+    load_row_coords<COST>(ws, r0, r1, sm, L.off_xc);
     __syncthreads();
     unsigned int gen = s_gen;
 
@@ -338,7 +369,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel(WS ws, StageArg
 
     for (;;) {
         // ---------------- phase A: pass over own rows, row epilogue ----------------
-        phase_A<TIER>(ws, r0, r1, gamma, G64, sm, L);
+        phase_A<TIER, COST>(ws, r0, r1, gamma, G64, sm, L);
         double x[kNRed];
 #pragma unroll
         for (int q = 0; q < kNRed; ++q) x[q] = 0.0;
@@ -501,7 +532,7 @@ finish:
 // merge.  Writes log r(P) to ws.lrtr and log c(P) to ws.lcout.
 // ---------------------------------------------------------------------------------------------
 
-template <int TIER>
+template <int TIER, int COST>
 __global__ void __launch_bounds__(kStageThreads, 1) dual_eval_kernel(WS ws, EvalArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
@@ -515,6 +546,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) dual_eval_kernel(WS ws, Eval
     row_range(n, G, b, c0, c1);
     State* S = ws.st;
     if (tid == 0) s_gen = ld_acquire(&S->bar.gen);
+    load_row_coords<COST>(ws, r0, r1, sm, L.off_xc);
     __syncthreads();
     unsigned int gen = s_gen;
     int* sA = reinterpret_cast<int*>(sm + L.off_A);
@@ -562,7 +594,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) dual_eval_kernel(WS ws, Eval
             for (int i = r0 + tid; i < r1; i += T)
                 prep_row<TIER>(a.u[i], sA[i - r0], Aglob, a.gamma, a.G64, sm, L, i - r0);
             __syncthreads();
-            phase_A<TIER>(ws, r0, r1, a.gamma, a.G64, sm, L);
+            phase_A<TIER, COST>(ws, r0, r1, a.gamma, a.G64, sm, L);
             for (int i = r0 + tid; i < r1; i += T) {
                 const int il = i - r0;
                 ws.lrtr[i] = log(row_total<TIER>(sm, L, il)) + (double)sA[il] * kLn2;
@@ -595,17 +627,16 @@ __global__ void __launch_bounds__(kStageThreads, 1) dual_eval_kernel(WS ws, Eval
         // row maxima (one warp per row) in log2 units (F32) or natural-log units (F64)
         for (int i = r0 + warp; i < r1; i += nw) {
             double m = -INFINITY;
-            const float* Crow = ws.C + (size_t)i * n;
             if (TIER != TIER_F64) {
                 const float fh = f2[i - r0], wl = w2[i - r0];
                 float mf = -INFINITY;
                 for (int j = lane; j < n; j += 32)
-                    mf = fmaxf(mf, fmaf(G32, (fh + __ldcg(ws.Hh + j)) - __ldg(Crow + j), wl + __ldcg(ws.Wc + j)));
+                    mf = fmaxf(mf, fmaf(G32, (fh + __ldcg(ws.Hh + j)) - cost_elem<COST>(ws, i, j), wl + __ldcg(ws.Wc + j)));
                 m = (double)mf;
             } else {
                 const double ui = a.u[i];
                 for (int j = lane; j < n; j += 32)
-                    m = fmax(m, (ui + __ldcg(ws.Hd + j)) - a.gamma * (double)__ldg(Crow + j));
+                    m = fmax(m, (ui + __ldcg(ws.Hd + j)) - a.gamma * (double)cost_elem<COST>(ws, i, j));
             }
 #pragma unroll
             for (int o = 16; o >= 1; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -617,13 +648,13 @@ __global__ void __launch_bounds__(kStageThreads, 1) dual_eval_kernel(WS ws, Eval
                 const float gh = __ldcg(ws.Hh + j), wc = __ldcg(ws.Wc + j);
                 float mf = -INFINITY;
                 for (int i = r0; i < r1; ++i)
-                    mf = fmaxf(mf, fmaf(G32, (f2[i - r0] + gh) - __ldg(ws.C + (size_t)i * n + j), w2[i - r0] + wc));
+                    mf = fmaxf(mf, fmaf(G32, (f2[i - r0] + gh) - cost_elem<COST>(ws, i, j), w2[i - r0] + wc));
                 ws.colpart[(size_t)b * n + j] = mf;
             } else {
                 const double vj = __ldcg(ws.Hd + j);
                 double md = -INFINITY;
                 for (int i = r0; i < r1; ++i)
-                    md = fmax(md, (a.u[i] + vj) - a.gamma * (double)__ldg(ws.C + (size_t)i * n + j));
+                    md = fmax(md, (a.u[i] + vj) - a.gamma * (double)cost_elem<COST>(ws, i, j));
                 ws.colpartd[(size_t)b * n + j] = md;
             }
         }
@@ -672,17 +703,17 @@ __global__ void __launch_bounds__(kStageThreads, 1) dual_eval_kernel(WS ws, Eval
             const float* w1 = reinterpret_cast<const float*>(sm + L.off_c1);
             const float* f2 = reinterpret_cast<const float*>(sm + L.off_s);
             const float* w2 = reinterpret_cast<const float*>(sm + L.off_A);
-            if ((n & 3) == 0)
-                pass2_f32<true, TIER == TIER_F32A>(ws.C, n, r0, r1, ws.Hh, ws.Wc, ws.Fh, ws.Wr, f1, w1, f2, w2, G32, Glo, sRow,
+            if ((n & 3) == 0 && COST == COST_DENSE)
+                pass2_f32<true, TIER == TIER_F32A, COST>(ws, ws.C, n, r0, r1, ws.Hh, ws.Wc, ws.Fh, ws.Wr, f1, w1, f2, w2, G32, Glo, sRow,
                                 L.nloc_max, ws.colpart + (size_t)b * n);
             else
-                pass2_f32<false, TIER == TIER_F32A>(ws.C, n, r0, r1, ws.Hh, ws.Wc, ws.Fh, ws.Wr, f1, w1, f2, w2, G32, Glo, sRow,
+                pass2_f32<false, TIER == TIER_F32A, COST>(ws, ws.C, n, r0, r1, ws.Hh, ws.Wc, ws.Fh, ws.Wr, f1, w1, f2, w2, G32, Glo, sRow,
                                  L.nloc_max, ws.colpart + (size_t)b * n);
         } else {
             double* sRow = reinterpret_cast<double*>(sm + L.off_row);
             for (int x = tid; x < nwl * L.nloc_max; x += T) sRow[x] = 0.0;
             __syncthreads();
-            pass2_f64(ws.C, n, r0, r1, ws.Hd, ws.Fd, reinterpret_cast<const double*>(sm + L.off_c0),
+            pass2_f64<COST>(ws, ws.C, n, r0, r1, ws.Hd, ws.Fd, reinterpret_cast<const double*>(sm + L.off_c0),
                       reinterpret_cast<const double*>(sm + L.off_s), a.gamma, sRow, L.nloc_max,
                       ws.colpartd + (size_t)b * n);
         }

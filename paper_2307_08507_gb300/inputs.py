@@ -55,6 +55,16 @@ def grid_coords(k: int) -> np.ndarray:
     return np.stack([a.reshape(-1), b.reshape(-1)], axis=1).astype(np.float32)
 
 
+def coords3(xy: np.ndarray) -> np.ndarray:
+    """n x 3 float32 coordinates (2-D data gets z = 0), the layout of the on-the-fly cost."""
+    xy = np.asarray(xy, dtype=np.float32)
+    if xy.shape[1] == 3:
+        return np.ascontiguousarray(xy)
+    out = np.zeros((xy.shape[0], 3), dtype=np.float32)
+    out[:, : xy.shape[1]] = xy
+    return out
+
+
 def _grid_dist_int(k: int, kind: str) -> np.ndarray:
     xy = grid_coords(k).astype(np.int64)
     da = xy[:, None, 0] - xy[None, :, 0]
