@@ -204,6 +204,55 @@ mdot_status mdot_dual_eval_points(mdot_handle* h, const double* u, const double*
                                   int64_t n, const double* ref_log_rP, int32_t precision,
                                   double* log_rP, double* log_cP);
 
+/* One problem of a batch.  Device pointers; either C (dense n x n fp32) or x, y (n x 3 fp32,
+ * regenerated cost of kind cost_kind with the given scale). */
+typedef struct mdot_problem {
+    int64_t n;                /* 1 .. MDOT_BATCH_MAX_N                                           */
+    const double* r;          /* n, non-negative, sums to 1                                      */
+    const double* c;          /* n, non-negative, sums to 1                                      */
+    const float* C;           /* dense cost or NULL                                              */
+    const float* x;           /* coordinates (when C is NULL)                                    */
+    const float* y;
+    int32_t cost_kind;        /* mdot_cost_kind (when C is NULL)                                 */
+    float scale;              /* cost scale (when C is NULL)                                     */
+    double eps_target;        /* target gap (gamma_f from Prop. 2), used when gamma_f <= 0       */
+    double gamma_f;           /* > 0: final inverse temperature                                  */
+    double* u_out;            /* n or NULL: final potentials (log scale)                         */
+    double* v_out;            /* n or NULL                                                       */
+} mdot_problem;
+
+/* Result of one problem of a batch. */
+typedef struct mdot_result {
+    int32_t status;           /* mdot_status of this problem                                     */
+    int32_t stages;
+    int64_t evals;            /* dual evaluations                                                */
+    int64_t iters;            /* PNCG iterations                                                 */
+    double  cost;             /* <G, C> of the rounded plan                                      */
+    double  lower_bound;      /* c-transform bound (fp32 differences in the batched form)        */
+    double  gap_cert;         /* cost - lower_bound                                              */
+    double  grad_l1;          /* final ||grad g||_1                                              */
+    double  gamma_f;
+    double  H_min;
+} mdot_result;
+
+/* Largest n of a batched problem. */
+#define MDOT_BATCH_MAX_N 4096
+
+/*
+ * Solve nprob independent problems (host array probs, each with device data) in one persistent
+ * launch per cost form: every CTA takes the next problem from a work queue (largest n first) and
+ * runs the whole of Alg. 1 + Alg. 3 on it (PNCG projections, line search, rounding, bound) with
+ * block-level synchronisation.  Each problem gets its own gamma schedule (from its eps_target or
+ * gamma_f), potentials and line-search state; a problem's result does not depend on the rest of
+ * the batch (fixed-order reductions).  Entries use the fp32 tiers (the fp64 tier is not offered
+ * here).  results: host array of nprob.  prm: NULL for defaults.  Workspace (about 0.6 MiB per
+ * SM) is allocated on the first call and kept by the handle.
+ * Returns INVALID_ARG if any problem is malformed (nothing is solved), else MDOT_OK; per-problem
+ * outcomes are in results[k].status.
+ */
+mdot_status mdot_solve_batch(mdot_handle* h, int32_t nprob, const mdot_problem* probs,
+                             const mdot_params* prm, mdot_result* results);
+
 /*
  * mdot_solve with every array in HOST memory: copies r, c (n doubles) and C (n*n floats) to the
  * handle's device, solves, and copies u, v back (n doubles each).  The copies are part of the

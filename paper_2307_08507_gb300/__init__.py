@@ -297,3 +297,71 @@ def dual_eval_noalloc(u, v, gamma: float, C, log_rP, log_cP, ref_log_rP=None, st
                                     _ptr(log_rP, torch.float64, n, "log_rP"),
                                     _ptr(log_cP, torch.float64, n, "log_cP"),
                                     ct.c_void_p(stream.cuda_stream))
+
+
+BATCH_MAX_N = 4096
+
+
+class Problem(ct.Structure):
+    """mdot_problem: one problem of a batch (device pointers)."""
+    _fields_ = [("n", ct.c_int64), ("r", _P), ("c", _P), ("C", _P), ("x", _P), ("y", _P),
+                ("cost_kind", ct.c_int32), ("scale", ct.c_float), ("eps_target", ct.c_double),
+                ("gamma_f", ct.c_double), ("u_out", _P), ("v_out", _P)]
+
+
+class Result(ct.Structure):
+    """mdot_result: outcome of one problem of a batch."""
+    _fields_ = [("status", ct.c_int32), ("stages", ct.c_int32), ("evals", ct.c_int64), ("iters", ct.c_int64),
+                ("cost", ct.c_double), ("lower_bound", ct.c_double), ("gap_cert", ct.c_double),
+                ("grad_l1", ct.c_double), ("gamma_f", ct.c_double), ("H_min", ct.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def make_problem(r, c, C=None, x=None, y=None, kind: int = COST_SQEUCLID, scale: float = 1.0,
+                 eps_target: float = 1e-6, gamma_f: float = 0.0, u_out=None, v_out=None) -> Problem:
+    """Fill an mdot_problem from CUDA tensors (the tensors must outlive the solve)."""
+    import torch
+    n = r.numel()
+    p = Problem()
+    p.n = n
+    p.r = _ptr(r, torch.float64, n, "r")
+    p.c = _ptr(c, torch.float64, n, "c")
+    if C is not None:
+        p.C = _ptr(C, torch.float32, n * n, "C")
+    else:
+        p.x = _ptr(x, torch.float32, 3 * n, "x")
+        p.y = _ptr(y, torch.float32, 3 * n, "y")
+        p.cost_kind = int(kind)
+        p.scale = float(scale)
+    p.eps_target = float(eps_target)
+    p.gamma_f = float(gamma_f)
+    if u_out is not None:
+        p.u_out = _ptr(u_out, torch.float64, n, "u_out")
+    if v_out is not None:
+        p.v_out = _ptr(v_out, torch.float64, n, "v_out")
+    return p
+
+
+def _batch_lib():
+    L = lib()
+    if not hasattr(L, "_batch_typed"):
+        L.mdot_solve_batch.argtypes = [_P, ct.c_int32, ct.POINTER(Problem), ct.POINTER(Params), ct.POINTER(Result)]
+        L.mdot_solve_batch.restype = ct.c_int32
+        L._batch_typed = True
+    return L
+
+
+def _solve_batch(self, problems, params: Params | None = None):
+    """mdot_solve_batch: every problem of the list in one persistent launch (per cost form)."""
+    k = len(problems)
+    arr = (Problem * k)(*problems)
+    res = (Result * k)()
+    s = _batch_lib().mdot_solve_batch(self._h, k, arr, ct.byref(params) if params is not None else None, res)
+    if s != MDOT_OK:
+        raise MdotError(s, "mdot_solve_batch")
+    return list(res)
+
+
+Handle.solve_batch = _solve_batch

@@ -1,0 +1,432 @@
+// Batched MDOT-PNCG: one persistent launch solves many problems of uneven n (up to kBatchMaxN).
+// Each CTA takes the next problem from an atomic work queue (problems ordered by decreasing n)
+// and runs the whole solve of Alg. 1 on it with block-level synchronisation only: validation and
+// entropies, the gamma schedule, every stage's PNCG projection with the App. B line search (same
+// decide() as the cooperative path), rounding (Alg. 3) and the c-transform bound.  All reductions
+// run in a fixed order, so a problem's result does not depend on which CTA solves it or on what
+// else is in the batch.
+#pragma once
+
+#include "solver_kernels.cuh"
+
+namespace mdot {
+
+constexpr int kBatchMaxN = 4096;
+constexpr int kBatchThreads = 256;
+
+struct BatchProblem {
+    int n, kind;               // size, CostKind
+    float scale;               // cost scale (regenerated cost)
+    int pad;
+    double eps, gamma_f;       // target gap (gamma_f <= 0: from eps, Prop. 2) or gamma_f
+    const double *r, *c;
+    const float *C, *X, *Y;
+    double *u_out, *v_out;     // nullable
+};
+
+struct BatchResult {
+    int status, stages;
+    long long evals, iters;
+    double cost, lower_bound, grad_l1, gamma_f, H_min;
+    int stalls, pad;
+};
+
+struct BatchArgs {
+    int nprob;
+    const BatchProblem* probs;
+    BatchResult* results;
+    const int* order;          // solve order (indices into probs)
+    unsigned int* next;        // work-queue counter (zeroed by the host)
+    double* slots;             // per-CTA workspace, slot_doubles each
+    size_t slot_doubles;
+    // parameters of Alg. 1 / App. B
+    double gamma_i, p, q, c1, c2, fp32_floor, final_tol;
+    int ls_max_trials, max_iter, warm_start, precision;
+};
+
+// per-CTA slot layout (doubles, kBatchMaxN each): 17 fp64 vectors, then fp32 vectors
+enum SlotVec { SV_U = 0, SV_V, SV_PU, SV_PV, SV_UP, SV_VP, SV_GR, SV_GC, SV_RT, SV_CT, SV_GRT, SV_GCT,
+               SV_SRT, SV_SCT, SV_LR, SV_Y, SV_EC, SV_COUNT };
+constexpr size_t kSlotF32Vecs = 3;    // Hh, Wc, column sums
+constexpr size_t kSlotDoubles = (size_t)SV_COUNT * kBatchMaxN + (kSlotF32Vecs * kBatchMaxN + 1) / 2;
+
+struct BatchSmem {
+    size_t off_row, off_fh, off_wr, off_s, off_A, bytes;
+};
+
+__host__ __device__ inline BatchSmem batch_smem()
+{
+    BatchSmem L;
+    size_t o = 0;
+    L.off_row = o; o += (size_t)(kBatchThreads / 32) * kBatchMaxN * 4;
+    L.off_fh = o;  o += (size_t)kBatchMaxN * 4;
+    L.off_wr = o;  o += (size_t)kBatchMaxN * 4;
+    L.off_s = o;   o += (size_t)kBatchMaxN * 4;
+    L.off_A = o;   o += (size_t)kBatchMaxN * 4;
+    L.bytes = o;
+    return L;
+}
+
+// One pass over all n rows (the CTA owns the whole problem): row sums into sRow[warp][row],
+// complete column sums into colsum.
+template <bool ACC, int COST>
+__device__ __forceinline__ void batch_pass(const BatchProblem& P, const float* Hh, const float* Wc,
+                                           const float* sFh, const float* sWr, const float* sS,
+                                           float G32, float Glo, float* sRow, float* colsum)
+{
+    const int n = P.n, nw = blockDim.x >> 5;
+    for (int x = threadIdx.x; x < nw * n; x += blockDim.x) sRow[x] = 0.0f;
+    __syncthreads();
+    if (COST != COST_DENSE)
+        pass_f32_regen<ACC, COST>(P.Y, P.scale, n, 0, n, Hh, Wc, sFh, sWr, sS, P.X, G32, Glo, sRow, n, colsum);
+    else if ((n & 3) == 0 && (reinterpret_cast<uintptr_t>(P.C) & 15) == 0)
+        pass_f32<true, ACC>(P.C, n, 0, n, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, n, colsum);
+    else
+        pass_f32<false, ACC>(P.C, n, 0, n, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, n, colsum);
+    __syncthreads();
+}
+
+template <int COST>
+__device__ __forceinline__ float batch_cost(const BatchProblem& P, int i, int j)
+{
+    if (COST == COST_DENSE) return __ldg(P.C + (size_t)i * P.n + j);
+    return point_cost<COST>(__ldg(P.X + 3 * (size_t)i), __ldg(P.X + 3 * (size_t)i + 1), __ldg(P.X + 3 * (size_t)i + 2),
+                            __ldg(P.Y + 3 * (size_t)j), __ldg(P.Y + 3 * (size_t)j + 1), __ldg(P.Y + 3 * (size_t)j + 2),
+                            P.scale);
+}
+
+__device__ __forceinline__ float batch_row_total(const float* sRow, int nw, int n, int i, double& out)
+{
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += (double)sRow[w * n + i];
+    out = s;
+    return (float)s;
+}
+
+// Per-row constants of an evaluation at ua with row scale A (fp32 tiers).
+__device__ __forceinline__ void batch_prep_row(double ua, int A, double inv_gamma, double G64, float* sFh,
+                                               float* sWr, float* sS, int* sA, int i)
+{
+    float fh, wl;
+    split_cost_unit((ua - (double)A * kLn2) * inv_gamma, fh, wl, G64);
+    sFh[i] = fh;
+    sWr[i] = wl;
+    sS[i] = pow2f_int(A);
+    sA[i] = A;
+}
+
+template <int COST>
+__global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ double red_smem[32 * kNRed];
+    __shared__ double s_bc[8];
+    __shared__ State st;
+    __shared__ int s_prob;
+    const BatchSmem L = batch_smem();
+    float* sRow = reinterpret_cast<float*>(sm + L.off_row);
+    float* sFh = reinterpret_cast<float*>(sm + L.off_fh);
+    float* sWr = reinterpret_cast<float*>(sm + L.off_wr);
+    float* sS = reinterpret_cast<float*>(sm + L.off_s);
+    int* sA = reinterpret_cast<int*>(sm + L.off_A);
+    const int tid = threadIdx.x, T = blockDim.x, nw = T >> 5, lane = tid & 31, warp = tid >> 5;
+    double* slot = a.slots + (size_t)blockIdx.x * a.slot_doubles;
+    double* V[SV_COUNT];
+    for (int k = 0; k < SV_COUNT; ++k) V[k] = slot + (size_t)k * kBatchMaxN;
+    float* Hh = reinterpret_cast<float*>(slot + (size_t)SV_COUNT * kBatchMaxN);
+    float* Wc = Hh + kBatchMaxN;
+    float* colsum = Wc + kBatchMaxN;
+
+    for (;;) {
+        if (tid == 0) s_prob = (int)atomicAdd(a.next, 1u);
+        __syncthreads();
+        const int pidx = s_prob;
+        __syncthreads();
+        if (pidx >= a.nprob) break;
+        const int pi = a.order[pidx];
+        const BatchProblem P = a.probs[pi];
+        const int n = P.n;
+        BatchResult res;
+        memset(&res, 0, sizeof(res));
+
+        // ---- validation and H_min (entropies in fp64 sums of fp32 logs) ----
+        double x[kNRed];
+#pragma unroll
+        for (int q = 0; q < kNRed; ++q) x[q] = 0.0;
+        for (int i = tid; i < n; i += T) {
+            const double ri = P.r[i], ci = P.c[i];
+            x[0] += ri;
+            x[1] += ci;
+            if (ri > 0.0) x[2] -= ri * (double)__logf((float)ri);
+            if (ci > 0.0) x[3] -= ci * (double)__logf((float)ci);
+            x[4] += (isfinite(ri) && isfinite(ci) && ri >= 0.0 && ci >= 0.0) ? 0.0 : 1.0;
+        }
+        block_reduce_nred(x, red_smem);
+        if (tid == 0) {
+            const bool bad = x[4] != 0.0 || !(fabs(x[0] - 1.0) <= 1e-9) || !(fabs(x[1] - 1.0) <= 1e-9) || n < 1 ||
+                             n > kBatchMaxN;
+            const double H = fmax(fmin(x[2], x[3]), 1e-12);
+            double gf = P.gamma_f;
+            if (!(gf > 0.0)) {
+                const double target = pow(5.0 * H / (2.0 * P.eps), 1.0 / a.p);       // Prop. 2
+                gf = a.gamma_i;
+                while (gf < target * (1.0 - 1e-12)) gf *= a.q;
+            }
+            s_bc[0] = H;
+            s_bc[1] = gf;
+            s_bc[2] = bad ? 1.0 : 0.0;
+        }
+        __syncthreads();
+        const double H = s_bc[0], gf = s_bc[1];
+        if (s_bc[2] != 0.0) {
+            if (tid == 0) {
+                res.status = ST_NUMERIC + 10;          // invalid problem
+                a.results[pi] = res;
+            }
+            __syncthreads();
+            continue;
+        }
+
+        // ---- MDOT (Alg. 1): stage after stage ----
+        if (tid == 0) memset(&st, 0, sizeof(State));
+        __syncthreads();
+        double gamma = fmin(a.gamma_i, gf), dgamma_prev = gamma, ratio = 0.0;
+        int stages = 0;
+        for (int t = 1;; ++t) {
+            const double eps_d = H / pow(gamma, a.p);
+            double tol = fmax(eps_d / 2.0, 1e-13 + 1e-15 * gamma);
+            const bool last = (gamma == gf);
+            if (last && a.final_tol > 0.0) tol = a.final_tol;
+            const bool acc = a.precision == 3 || (a.precision == 0 && tol < 2e-6);
+            StageArgs sa{};
+            sa.gamma = gamma;
+            sa.G64 = gamma * kLog2e;
+            sa.tol = fmax(tol, a.fp32_floor);
+            sa.c1 = a.c1;
+            sa.c2 = a.c2;
+            sa.ls_max_trials = a.ls_max_trials;
+            sa.max_iter = a.max_iter;
+            sa.tier = acc ? TIER_F32A : TIER_F32;
+            const double inv_gamma = 1.0 / gamma, G64 = sa.G64;
+            const float G32 = (float)G64, Glo = (float)(G64 - (double)G32);
+            // prologue: smoothing, rank-one start or warm start (Eq. (13)), constants at alpha = 0
+            for (int i = tid; i < n; i += T) {
+                const double rt = (1.0 - eps_d / 4.0) * P.r[i] + eps_d / (4.0 * n);
+                const double lrt = log(rt);
+                double u = V[SV_U][i];
+                if (t == 1) { u = lrt; V[SV_UP][i] = u; }
+                else if (a.warm_start == 0) { const double z = u; u = z + ratio * (z - V[SV_UP][i]); V[SV_UP][i] = z; }
+                else if (a.warm_start == 1) { u = ratio * u; }
+                V[SV_U][i] = u; V[SV_PU][i] = 0.0; V[SV_GR][i] = 0.0; V[SV_RT][i] = rt; V[SV_LR][i] = lrt;
+                batch_prep_row(u, row_scale(lrt), inv_gamma, G64, sFh, sWr, sS, sA, i);
+            }
+            for (int j = tid; j < n; j += T) {
+                const double ct = (1.0 - eps_d / 4.0) * P.c[j] + eps_d / (4.0 * n);
+                double v = V[SV_V][j];
+                if (t == 1) { v = log(ct); V[SV_VP][j] = v; }
+                else if (a.warm_start == 0) { const double z = v; v = z + ratio * (z - V[SV_VP][j]); V[SV_VP][j] = z; }
+                else if (a.warm_start == 1) { v = ratio * v; }
+                V[SV_V][j] = v; V[SV_PV][j] = 0.0; V[SV_GC][j] = 0.0; V[SV_CT][j] = ct;
+                float gh, wl;
+                split_cost_unit(v * inv_gamma, gh, wl, G64);
+                Hh[j] = gh;
+                Wc[j] = wl;
+            }
+            if (tid == 0) {
+                st.alpha = 0.0; st.kind = KIND_INIT; st.accept = 0; st.trials = 0; st.k = 0;
+                st.phase = PH_RUN; st.beta = 0.0; st.alpha_commit = 0.0;
+            }
+            __syncthreads();
+            for (;;) {
+                if (acc) batch_pass<true, COST>(P, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, colsum);
+                else     batch_pass<false, COST>(P, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, colsum);
+#pragma unroll
+                for (int q = 0; q < kNRed; ++q) x[q] = 0.0;
+                for (int i = tid; i < n; i += T) {
+                    double sum;
+                    batch_row_total(sRow, nw, n, i, sum);
+                    if (!(sum > 0.0) || !isfinite(sum)) { x[5] += 1.0; continue; }
+                    const double rt = V[SV_RT][i];
+                    const double g = ldexp(sum, sA[i]) - rt;
+                    const double s = -(double)log1pf((float)g / (float)rt);     // Eq. (17)
+                    const double p = V[SV_PU][i], y = g - V[SV_GR][i];
+                    x[0] += p * g; x[1] += fabs(g); x[2] += y * (-s); x[3] += y * p; x[4] += s * g;
+                    V[SV_GRT][i] = g;
+                    V[SV_SRT][i] = s;
+                    V[SV_Y][i] = ((double)__log2f((float)sum) + (double)sA[i]) * kLn2;   // log r(P), scale only
+                }
+                for (int j = tid; j < n; j += T) {
+                    const double cs = (double)colsum[j];
+                    if (!(cs > 0.0) || !isfinite(cs)) { x[5] += 1.0; continue; }
+                    const double ct = V[SV_CT][j];
+                    const double g = cs - ct;
+                    const double s = -(double)log1pf((float)g / (float)ct);
+                    const double p = V[SV_PV][j], y = g - V[SV_GC][j];
+                    x[0] += p * g; x[1] += fabs(g); x[2] += y * (-s); x[3] += y * p; x[4] += s * g;
+                    V[SV_GCT][j] = g;
+                    V[SV_SCT][j] = s;
+                }
+                block_reduce_nred(x, red_smem);
+                if (tid == 0) {
+                    decide(&st, x, sa);
+                    s_bc[0] = st.alpha; s_bc[1] = st.alpha_commit; s_bc[2] = st.beta;
+                    s_bc[3] = (double)st.accept; s_bc[4] = (double)st.phase;
+                }
+                __syncthreads();
+                const double alpha = s_bc[0], acommit = s_bc[1], beta = s_bc[2];
+                const bool accept = s_bc[3] != 0.0, done = s_bc[4] != 0.0;
+                for (int i = tid; i < n; i += T) {
+                    double u = V[SV_U][i], p = V[SV_PU][i];
+                    if (accept) {
+                        u += acommit * p;
+                        V[SV_U][i] = u;
+                        V[SV_GR][i] = V[SV_GRT][i];
+                        V[SV_LR][i] = V[SV_Y][i];
+                        p = V[SV_SRT][i] + beta * p;
+                        V[SV_PU][i] = p;
+                    }
+                    if (!done) batch_prep_row(u + alpha * p, row_scale(V[SV_LR][i] + alpha * p), inv_gamma, G64,
+                                              sFh, sWr, sS, sA, i);
+                }
+                for (int j = tid; j < n; j += T) {
+                    double v = V[SV_V][j], p = V[SV_PV][j];
+                    if (accept) {
+                        v += acommit * p;
+                        V[SV_V][j] = v;
+                        V[SV_GC][j] = V[SV_GCT][j];
+                        p = V[SV_SCT][j] + beta * p;
+                        V[SV_PV][j] = p;
+                    }
+                    if (!done) {
+                        float gh, wl;
+                        split_cost_unit((v + alpha * p) * inv_gamma, gh, wl, G64);
+                        Hh[j] = gh;
+                        Wc[j] = wl;
+                    }
+                }
+                __syncthreads();
+                if (done) break;
+            }
+            ++stages;
+            if (last || st.status >= ST_LSFAIL) break;
+            double dg = (a.q - 1.0) * gamma;
+            const double gnext = fmin(gamma + dg, gf);
+            dg = gnext - gamma;
+            ratio = (a.warm_start == 1) ? gnext / gamma : dg / dgamma_prev;
+            dgamma_prev = dg;
+            gamma = gnext;
+        }
+
+        // ---- rounding (Alg. 3) at gamma_f, cost <G, C> ----
+        {
+            const double inv_gamma = 1.0 / gf, G64 = gf * kLog2e;
+            const float G32 = (float)G64, Glo = (float)(G64 - (double)G32);
+            for (int i = tid; i < n; i += T) batch_prep_row(V[SV_U][i], row_scale(V[SV_LR][i]), inv_gamma, G64, sFh, sWr, sS, sA, i);
+            for (int j = tid; j < n; j += T) {
+                float gh, wl;
+                split_cost_unit(V[SV_V][j] * inv_gamma, gh, wl, G64);
+                Hh[j] = gh;
+                Wc[j] = wl;
+            }
+            __syncthreads();
+            // r(P) and x = min(r / r(P), 1); the column pass then weights row i by x_i 2^{A_i}
+            batch_pass<true, COST>(P, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, colsum);
+            for (int i = tid; i < n; i += T) {
+                double sum;
+                batch_row_total(sRow, nw, n, i, sum);
+                const double rP = ldexp(sum, sA[i]);
+                const double xi = (rP > 0.0) ? fmin(P.r[i] / rP, 1.0) : 1.0;
+                V[SV_GRT][i] = xi;
+                sS[i] = (float)ldexp(xi, sA[i]);
+            }
+            __syncthreads();
+            batch_pass<true, COST>(P, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, colsum);   // colsum = c(F)
+            for (int j = tid; j < n; j += T) {
+                const double cF = (double)colsum[j];
+                const double yj = (cF > 0.0) ? fmin(P.c[j] / cF, 1.0) : 1.0;
+                V[SV_Y][j] = yj;
+                V[SV_EC][j] = P.c[j] - cF * yj;
+            }
+            __syncthreads();
+            // rows of F' = X P Y: r(F')_i, <F', C>_i and (C err_c)_i, one warp per row (fixed order)
+#pragma unroll
+            for (int q = 0; q < kNRed; ++q) x[q] = 0.0;
+            for (int i = warp; i < n; i += nw) {
+                const float fh = sFh[i], wr = sWr[i];
+                double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+                for (int j = lane; j < n; j += 32) {
+                    const float cv = batch_cost<COST>(P, i, j);
+                    const float d = (fh + Hh[j]) - cv;
+                    float tl;
+                    const float th = exponent_acc(d, G32, Glo, wr + Wc[j], tl);
+                    const double Ey = (double)exp2_acc(th, tl) * V[SV_Y][j];
+                    a0 += Ey;
+                    a1 = fma(Ey, (double)cv, a1);
+                    a2 = fma((double)cv, V[SV_EC][j], a2);
+                }
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) {
+                    a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+                    a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+                    a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+                }
+                if (lane == 0) {
+                    const double xs = ldexp(V[SV_GRT][i], sA[i]);
+                    const double er = P.r[i] - xs * a0;
+                    x[0] += xs * a1;
+                    x[1] += fabs(er);
+                    x[2] += er * a2;
+                }
+            }
+            block_reduce_nred(x, red_smem);
+            if (tid == 0) res.cost = x[0] + ((x[1] > 0.0) ? x[2] / x[1] : 0.0);
+        }
+
+        // ---- c-transform lower bound from f = u / gamma_f (fp32 differences, fp64 sums) ----
+        {
+            const double inv_gamma = 1.0 / gf;
+            for (int i = tid; i < n; i += T) {
+                const double f = V[SV_U][i] * inv_gamma;
+                sFh[i] = (float)f;
+                sWr[i] = (float)(f - (double)sFh[i]);
+            }
+            __syncthreads();
+            for (int j = tid; j < n; j += T) {           // g'_j = min_i (C_ij - f_i)
+                float m = INFINITY;
+                for (int i = 0; i < n; ++i) m = fminf(m, (batch_cost<COST>(P, i, j) - sFh[i]) - sWr[i]);
+                colsum[j] = m;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < kNRed; ++q) x[q] = 0.0;
+            for (int i = warp; i < n; i += nw) {         // f'_i = min_j (C_ij - g'_j)
+                float m = INFINITY;
+                for (int j = lane; j < n; j += 32) m = fminf(m, batch_cost<COST>(P, i, j) - colsum[j]);
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                if (lane == 0) x[0] += (double)m * P.r[i];
+            }
+            for (int j = tid; j < n; j += T) x[1] += (double)colsum[j] * P.c[j];
+            block_reduce_nred(x, red_smem);
+            if (tid == 0) res.lower_bound = x[0] + x[1];
+        }
+        for (int i = tid; i < n; i += T) {
+            if (P.u_out) P.u_out[i] = V[SV_U][i];
+            if (P.v_out) P.v_out[i] = V[SV_V][i];
+        }
+        if (tid == 0) {
+            res.status = st.status;
+            res.stages = stages;
+            res.evals = st.evals;
+            res.iters = st.iters;
+            res.grad_l1 = st.gnorm;
+            res.gamma_f = gf;
+            res.H_min = H;
+            res.stalls = st.stalls;
+            a.results[pi] = res;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace mdot

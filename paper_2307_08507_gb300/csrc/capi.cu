@@ -9,6 +9,7 @@
 #include <cstring>
 #include <vector>
 
+#include "batch_kernels.cuh"
 #include "launch.h"
 #include "mdot.h"
 
@@ -43,7 +44,26 @@ struct mdot_handle {
     double *d_r = nullptr, *d_c = nullptr, *d_u = nullptr, *d_v = nullptr;
     float* d_C = nullptr;
     int64_t host_n = 0;
+    // batched solver workspace (allocated on first use)
+    double* b_slots = nullptr;
+    int b_grid = 0;
+    BatchProblem* b_probs = nullptr;
+    BatchResult* b_results = nullptr;
+    int* b_order = nullptr;
+    unsigned int* b_next = nullptr;
+    int b_cap = 0;
+    ~mdot_handle()
+    {
+        cudaFree(d_r); cudaFree(d_c); cudaFree(d_u); cudaFree(d_v); cudaFree(d_C);
+        cudaFree(b_slots); cudaFree(b_probs); cudaFree(b_results); cudaFree(b_order); cudaFree(b_next);
+    }
 };
+
+namespace mdot {
+size_t batch_smem_bytes();
+cudaError_t configure_batch_kernels(int* blocks_per_sm);
+cudaError_t launch_batch(int kind, int grid, const BatchArgs& a, cudaStream_t s);
+}
 
 #define CKR(call)                                                                                  \
     do {                                                                                           \
@@ -537,6 +557,102 @@ static mdot_status dual_eval_core(mdot_handle* h, const double* u, const double*
     CKR(cudaMemcpyAsync(h->h_state, ws.st, sizeof(State), cudaMemcpyDeviceToHost, h->stream));
     CKR(cudaStreamSynchronize(h->stream));
     return h->h_state->status == ST_OK ? MDOT_OK : MDOT_ERR_TIMEOUT;
+}
+
+mdot_status mdot_solve_batch(mdot_handle* h, int32_t nprob, const mdot_problem* probs, const mdot_params* prm,
+                             mdot_result* results)
+{
+    if (!h || nprob < 0 || (nprob > 0 && (!probs || !results))) return MDOT_ERR_INVALID_ARG;
+    if (nprob == 0) return MDOT_OK;
+    mdot_params P;
+    if (prm) P = *prm; else mdot_default_params(&P);
+    if (params_ok(P) != MDOT_OK || P.precision == MDOT_PREC_FP64) return MDOT_ERR_INVALID_ARG;
+    std::vector<BatchProblem> bp(nprob);
+    for (int k = 0; k < nprob; ++k) {
+        const mdot_problem& q = probs[k];
+        BatchProblem& b = bp[k];
+        memset(&b, 0, sizeof(b));
+        const bool dense = q.C != nullptr;
+        if (q.n < 1 || q.n > MDOT_BATCH_MAX_N || !q.r || !q.c ||
+            (!dense && (!q.x || !q.y || (q.cost_kind != MDOT_COST_SQEUCLID && q.cost_kind != MDOT_COST_L1) ||
+                        !(q.scale > 0.0f) || !std::isfinite(q.scale))) ||
+            (!(q.gamma_f > 0.0) && !(q.eps_target > 0.0 && std::isfinite(q.eps_target))))
+            return MDOT_ERR_INVALID_ARG;
+        b.n = (int)q.n;
+        b.kind = dense ? COST_DENSE : q.cost_kind;
+        b.scale = q.scale;
+        b.eps = q.eps_target;
+        b.gamma_f = q.gamma_f;
+        b.r = q.r; b.c = q.c; b.C = q.C; b.X = q.x; b.Y = q.y;
+        b.u_out = q.u_out; b.v_out = q.v_out;
+    }
+    if (!h->b_slots) {
+        int bps = 0;
+        CKR(configure_batch_kernels(&bps));
+        if (bps < 1) return MDOT_ERR_INVALID_ARG;
+        h->b_grid = h->sms * bps;
+        if (cudaMalloc(&h->b_slots, (size_t)h->b_grid * kSlotDoubles * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&h->b_next, 4 * sizeof(unsigned int)) != cudaSuccess) {
+            snprintf(g_err, sizeof g_err, "batch workspace allocation failed");
+            return MDOT_ERR_OOM;
+        }
+    }
+    if (h->b_cap < nprob) {
+        cudaFree(h->b_probs); cudaFree(h->b_results); cudaFree(h->b_order);
+        h->b_probs = nullptr; h->b_results = nullptr; h->b_order = nullptr; h->b_cap = 0;
+        if (cudaMalloc(&h->b_probs, nprob * sizeof(BatchProblem)) != cudaSuccess ||
+            cudaMalloc(&h->b_results, nprob * sizeof(BatchResult)) != cudaSuccess ||
+            cudaMalloc(&h->b_order, nprob * sizeof(int)) != cudaSuccess) {
+            snprintf(g_err, sizeof g_err, "batch descriptor allocation failed");
+            return MDOT_ERR_OOM;
+        }
+        h->b_cap = nprob;
+    }
+    // one launch per cost form; inside it, problems by decreasing n (longest first)
+    std::vector<BatchResult> br(nprob);
+    CKR(cudaMemcpyAsync(h->b_probs, bp.data(), nprob * sizeof(BatchProblem), cudaMemcpyHostToDevice, h->stream));
+    for (int kind = 0; kind < 3; ++kind) {
+        std::vector<int> order;
+        for (int k = 0; k < nprob; ++k)
+            if (bp[k].kind == kind) order.push_back(k);
+        if (order.empty()) continue;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return bp[x].n > bp[y].n; });
+        CKR(cudaMemcpyAsync(h->b_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+        CKR(cudaMemsetAsync(h->b_next, 0, sizeof(unsigned int), h->stream));
+        BatchArgs a{};
+        a.nprob = (int)order.size();
+        a.probs = h->b_probs;
+        a.results = h->b_results;
+        a.order = h->b_order;
+        a.next = h->b_next;
+        a.slots = h->b_slots;
+        a.slot_doubles = kSlotDoubles;
+        a.gamma_i = P.gamma_i; a.p = P.p; a.q = P.q; a.c1 = P.ls_c1; a.c2 = P.ls_c2;
+        a.fp32_floor = P.fp32_floor; a.final_tol = P.final_tol;
+        a.ls_max_trials = P.ls_max_trials; a.max_iter = P.max_iter; a.warm_start = P.warm_start;
+        a.precision = P.precision;
+        CKR(launch_batch(kind, h->b_grid, a, h->stream));
+        CKR(cudaStreamSynchronize(h->stream));     // the order buffer is reused by the next form
+    }
+    CKR(cudaMemcpyAsync(br.data(), h->b_results, nprob * sizeof(BatchResult), cudaMemcpyDeviceToHost, h->stream));
+    CKR(cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < nprob; ++k) {
+        const BatchResult& b = br[k];
+        mdot_result& r = results[k];
+        memset(&r, 0, sizeof(r));
+        r.status = (b.status >= 10) ? MDOT_ERR_INVALID_ARG : map_status(b.status);
+        if (r.status == MDOT_OK && !(std::isfinite(b.cost) && std::isfinite(b.lower_bound))) r.status = MDOT_ERR_NUMERIC;
+        r.stages = b.stages;
+        r.evals = b.evals;
+        r.iters = b.iters;
+        r.cost = b.cost;
+        r.lower_bound = b.lower_bound;
+        r.gap_cert = b.cost - b.lower_bound;
+        r.grad_l1 = b.grad_l1;
+        r.gamma_f = b.gamma_f;
+        r.H_min = b.H_min;
+    }
+    return MDOT_OK;
 }
 
 mdot_status mdot_dual_eval(mdot_handle* h, const double* u, const double* v, double gamma, const float* C,

@@ -1,0 +1,103 @@
+"""Batched solver (one persistent launch for many problems of uneven n): every result matches the
+CPU oracle on its problem, and a problem solved alone and inside a mixed batch gives the same
+result bit for bit (its reductions run in a fixed order on one CTA)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2307_08507_gb300 as M
+from paper_2307_08507_gb300 import inputs as I
+
+pytestmark = [pytest.mark.gpu, pytest.mark.timeout(600)]
+DEV = "cuda:0"
+
+
+def t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+@pytest.fixture(scope="module")
+def h():
+    torch.cuda.set_device(0)
+    with M.Handle(4096) as handle:
+        yield handle
+
+
+def _point_problems(sizes, seed0):
+    out = []
+    for k, n in enumerate(sizes):
+        p = I.point_cloud_problem(int(n), seed0 + k)
+        out.append(p)
+    return out
+
+
+def _tensors(p, dense=False):
+    d = {"r": t(p.r), "c": t(p.c), "u": torch.empty(p.n, dtype=torch.float64, device=DEV),
+         "v": torch.empty(p.n, dtype=torch.float64, device=DEV)}
+    if dense:
+        d["C"] = t(p.C)
+    else:
+        d["x"], d["y"] = t(p.x), t(p.y)
+    return d
+
+
+def _problem(p, d, gamma_f):
+    if "C" in d:
+        return M.make_problem(d["r"], d["c"], C=d["C"], gamma_f=gamma_f, u_out=d["u"], v_out=d["v"])
+    return M.make_problem(d["r"], d["c"], x=d["x"], y=d["y"], kind=M.COST_SQEUCLID, scale=p.scale,
+                          gamma_f=gamma_f, u_out=d["u"], v_out=d["v"])
+
+
+def test_batch_matches_oracle_and_single_solves(h):
+    sizes = [300, 64, 129, 257, 40]
+    probs = _point_problems(sizes, 4100)
+    gf = 2.0 ** 10
+    tens = [_tensors(p) for p in probs]
+    res = h.solve_batch([_problem(p, d, gf) for p, d in zip(probs, tens)])
+    for p, r in zip(probs, res):
+        assert r.status == M.MDOT_OK, M.status_string(r.status)
+        ref = O.solve(p.C.astype(np.float64), p.r, p.c, gamma_f=gf)
+        eps_d = r.H_min / gf ** 1.5      # both sides stop inside eps_d / 2 (see test_gpu_regen)
+        assert abs(r.cost - ref.cost) <= max(1e-7, eps_d), (p.n, r.cost, ref.cost)
+        assert r.lower_bound <= ref.cost + 1e-6
+        assert r.evals > 0 and r.stages == ref.stats.stages
+
+
+def test_batch_result_same_alone_and_in_the_mix(h):
+    """Same problem, same inputs: alone in a batch of one and inside a batch of 9 uneven problems
+    -> bitwise identical cost, bound, potentials and iteration counts."""
+    gf = 2.0 ** 11
+    probs = _point_problems([200, 513, 96, 1000, 33, 700, 256, 128, 400], 4200)
+    target = 3                      # n = 1000
+    tens = [_tensors(p) for p in probs]
+    mixed = h.solve_batch([_problem(p, d, gf) for p, d in zip(probs, tens)])
+    u_mix, v_mix = tens[target]["u"].clone(), tens[target]["v"].clone()
+    alone = h.solve_batch([_problem(probs[target], tens[target], gf)])[0]
+    assert alone.status == M.MDOT_OK
+    a, m = alone, mixed[target]
+    assert (a.cost, a.lower_bound, a.evals, a.iters) == (m.cost, m.lower_bound, m.evals, m.iters)
+    assert torch.equal(u_mix, tens[target]["u"]) and torch.equal(v_mix, tens[target]["v"])
+
+
+def test_batch_dense_and_mixed_forms(h):
+    """Dense and regenerated problems in one call (one launch per form)."""
+    gf = 2.0 ** 10
+    pa = I.grid_problem(12, 31)
+    pb = I.point_cloud_problem(150, 4300)
+    da, db = _tensors(pa, dense=True), _tensors(pb)
+    res = h.solve_batch([_problem(pa, da, gf), _problem(pb, db, gf)])
+    for p, r in zip((pa, pb), res):
+        ref = O.solve(p.C.astype(np.float64), p.r, p.c, gamma_f=gf)
+        assert r.status == M.MDOT_OK
+        assert abs(r.cost - ref.cost) <= max(1e-7, r.H_min / gf ** 1.5)
+
+
+def test_batch_rejects_malformed_problems(h):
+    p = I.point_cloud_problem(50, 4400)
+    d = _tensors(p)
+    bad = _problem(p, d, 2.0 ** 8)
+    bad.scale = -1.0
+    with pytest.raises(M.MdotError) as e:
+        h.solve_batch([bad])
+    assert e.value.status == M.MDOT_ERR_INVALID_ARG
