@@ -39,10 +39,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample-evals", type=int, default=0, help="oracle evaluations in the CPU sample")
-    ap.add_argument("--case", default="solve", choices=["solve", "dual_eval", "stage"],
+    ap.add_argument("--case", default="solve", choices=["solve", "dual_eval", "stage", "batch"],
                     help="dual_eval / stage: run only that kernel (for profiler captures)")
     ap.add_argument("--grid", type=int, default=64, help="k of the k x k grid for --case runs")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
     return ap.parse_args()
 
 
@@ -176,6 +177,78 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------------------------
+# batched form: 512 point-cloud problems, n uniform in [256, 4096], one persistent launch
+# ---------------------------------------------------------------------------------------------
+BATCH_COUNT = 512
+BATCH_EPS = 1e-5
+BATCH_SEED = 4000
+
+
+def batch_problems(dev, count=BATCH_COUNT, seed=BATCH_SEED):
+    """Point clouds x ~ N(0, I3), y ~ U[-1, 1]^3, uniform weights (App. C style), sizes from the
+    seeded generator; the cost scale 1 / max D uses the generator's fp32 formula (on the GPU)."""
+    import numpy as np
+    import torch
+    from paper_2307_08507_gb300 import inputs as I
+    sizes = I.batch_sizes(count, seed)
+    out = []
+    for k, n in enumerate(sizes):
+        rng = I.rng_for(seed + k)
+        x = rng.standard_normal((int(n), 3)).astype(np.float32)
+        y = rng.uniform(-1.0, 1.0, size=(int(n), 3)).astype(np.float32)
+        xt, yt = torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev)
+        d0 = xt[:, None, 0] - yt[None, :, 0]
+        d1 = xt[:, None, 1] - yt[None, :, 1]
+        d2 = xt[:, None, 2] - yt[None, :, 2]
+        dmax = float(((d0 * d0 + d1 * d1) + d2 * d2).max().item())
+        w = torch.full((int(n),), 1.0 / int(n), dtype=torch.float64, device=dev)
+        out.append({"n": int(n), "x": xt, "y": yt, "r": w, "c": w.clone(),
+                    "scale": float(np.float32(1.0 / dmax))})
+        del d0, d1, d2
+    return out
+
+
+def measure_batch(h, dev, stream, sample_single=32):
+    import torch
+    import paper_2307_08507_gb300 as M
+    probs = batch_problems(dev)
+    plist = [M.make_problem(q["r"], q["c"], x=q["x"], y=q["y"], kind=M.COST_SQEUCLID, scale=q["scale"],
+                            eps_target=BATCH_EPS) for q in probs]
+    h.solve_batch(plist[:8])                                       # warm-up (small subset)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    res = h.solve_batch(plist)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_batch = ev0.elapsed_time(ev1) / 1e3
+    ok = sum(1 for r in res if r.status == M.MDOT_OK)
+    # one problem per launch (cooperative multi-CTA solve) on a stratified sample, same accuracy
+    order = sorted(range(len(probs)), key=lambda k: probs[k]["n"])
+    pick = order[:: max(1, len(order) // sample_single)][:sample_single]
+    t_single, dcost, evals_b, evals_s = 0.0, [], 0, 0
+    for k in pick:
+        q = probs[k]
+        ev0.record(stream)
+        _, _, rs = h.solve_points(q["r"], q["c"], q["x"], q["y"], M.COST_SQEUCLID, q["scale"], BATCH_EPS)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t_single += ev0.elapsed_time(ev1) / 1e3
+        dcost.append(abs(rs.cost - res[k].cost))
+        evals_b += res[k].evals
+        evals_s += rs.info.evals
+    t_single_all = t_single * len(probs) / len(pick)
+    return {"problems": len(probs), "n_range": [min(q["n"] for q in probs), max(q["n"] for q in probs)],
+            "eps_target": BATCH_EPS, "cost": "regenerated squared Euclidean (point clouds)",
+            "seconds": t_batch, "problems_per_s": len(probs) / t_batch, "ok": ok,
+            "one_per_launch_sample": len(pick), "one_per_launch_seconds_sample": t_single,
+            "one_per_launch_problems_per_s": len(probs) / t_single_all,
+            "speedup_vs_one_per_launch": t_single_all / t_batch,
+            "max_abs_cost_diff_vs_one_per_launch": max(dcost), "evals_batch_sample": evals_b,
+            "evals_single_sample": evals_s}
+
+
+# ---------------------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------------------
 def run_ours(args, rank, world):
@@ -275,6 +348,8 @@ def run_ours(args, rank, world):
         dual[f"n{q.n}"] = {"us": tmed * 1e6, "GBps": gbs, "frac_hbm": gbs / hbm}
         del Cq
 
+    batch = measure_batch(h, dev, stream) if (rank == 0 and not args.no_batch) else None
+
     # end to end through the public C ABI with host buffers (copies inside the timed region)
     Ch = torch.from_numpy(p.C).pin_memory().numpy()
     rh = torch.from_numpy(p.r).pin_memory().numpy()
@@ -324,6 +399,7 @@ def run_ours(args, rank, world):
                          "launch_times_ms": {"stage_fp32": ip.t_stage_fp32_ms, "stage_fp64": ip.t_stage_fp64_ms,
                                              "round": ip.t_round_ms, "bound": ip.t_bound_ms}},
             "dual_eval": dual,
+            "batched": batch,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_t, "unit": "s", "h2d_bytes_per_step": 4 * n * n + 16 * n,
                     "d2h_bytes_per_step": 16 * n},
@@ -348,6 +424,11 @@ def run_case(args):
     p = I.grid_problem(args.grid, SEED)
     h = M.Handle(p.n)
     C = torch.from_numpy(p.C).to(dev)
+    if args.case == "batch":
+        stream = torch.cuda.current_stream()
+        print(json.dumps(measure_batch(h, dev, stream)))
+        h.close()
+        return
     if args.case == "dual_eval":
         u = torch.from_numpy(np.log(p.r)).to(dev)
         v = torch.from_numpy(np.log(p.c)).to(dev)
