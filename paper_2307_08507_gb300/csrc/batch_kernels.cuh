@@ -77,12 +77,13 @@ __device__ __forceinline__ void batch_pass(const BatchProblem& P, const float* H
     const int n = P.n, nw = blockDim.x >> 5;
     for (int x = threadIdx.x; x < nw * n; x += blockDim.x) sRow[x] = 0.0f;
     __syncthreads();
+    const ColPlain io{Hh, Wc, colsum};
     if (COST != COST_DENSE)
-        pass_f32_regen<ACC, COST>(P.Y, P.scale, n, 0, n, Hh, Wc, sFh, sWr, sS, P.X, G32, Glo, sRow, n, colsum);
+        pass_f32_regen<ACC, COST>(P.Y, P.scale, n, 0, n, io, sFh, sWr, sS, P.X, G32, Glo, sRow, n);
     else if ((n & 3) == 0 && (reinterpret_cast<uintptr_t>(P.C) & 15) == 0)
-        pass_f32<true, ACC>(P.C, n, 0, n, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, n, colsum);
+        pass_f32<true, ACC>(P.C, n, 0, n, io, sFh, sWr, sS, G32, Glo, sRow, n);
     else
-        pass_f32<false, ACC>(P.C, n, 0, n, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, n, colsum);
+        pass_f32<false, ACC>(P.C, n, 0, n, io, sFh, sWr, sS, G32, Glo, sRow, n);
     __syncthreads();
 }
 
@@ -357,9 +358,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a)
                 for (int j = lane; j < n; j += 32) {
                     const float cv = batch_cost<COST>(P, i, j);
                     const float d = (fh + Hh[j]) - cv;
-                    float tl;
-                    const float th = exponent_acc(d, G32, Glo, wr + Wc[j], tl);
-                    const double Ey = (double)exp2_acc(th, tl) * V[SV_Y][j];
+                    const double Ey = (double)exp2_acc(d, G32, Glo, wr + Wc[j]) * V[SV_Y][j];
                     a0 += Ey;
                     a1 = fma(Ey, (double)cv, a1);
                     a2 = fma((double)cv, V[SV_EC][j], a2);

@@ -52,6 +52,10 @@ struct mdot_handle {
     int* b_order = nullptr;
     unsigned int* b_next = nullptr;
     int b_cap = 0;
+    // tags consumed by the stage kernel's tagged words since they were last cleared (an upper
+    // bound, from the evaluation counts); cleared well before the 32-bit tag could wrap
+    unsigned long long tags_used = 0;
+    size_t tag_bytes = 0;
     ~mdot_handle()
     {
         cudaFree(d_r); cudaFree(d_c); cudaFree(d_u); cudaFree(d_v); cudaFree(d_C);
@@ -152,10 +156,14 @@ mdot_status mdot_create(mdot_handle** out, int64_t max_n, void* stream)
     double* blockred = (double*)dalloc(G * kNRed * sizeof(double));
     double* scratch = (double*)dalloc(G * 8 * sizeof(double));
     State* st = (State*)dalloc(sizeof(State));
+    // tagged words: column constants [n][2], column partials [G][n], scalar partials [G][2 kNRed],
+    // then the tag base (one 16-byte slot)
+    const size_t tag_words = 2 * n + G * n + G * 2 * kNRed + 2;
+    unsigned long long* tagw = (unsigned long long*)dalloc(tag_words * sizeof(unsigned long long));
     h->d_out = (double*)dalloc(16 * sizeof(double));
     void* hp = nullptr;
     if (cudaMallocHost(&hp, 16 * sizeof(double) + sizeof(State)) == cudaSuccess) h->mem.host.push_back(hp);
-    if (!vec || !f32 || !A || !colpart || !colpartd || !blockred || !scratch || !st || !h->d_out || !hp) {
+    if (!vec || !f32 || !A || !colpart || !colpartd || !blockred || !scratch || !st || !tagw || !h->d_out || !hp) {
         snprintf(g_err, sizeof g_err, "workspace allocation failed for max_n = %lld", (long long)max_n);
         delete h;
         return MDOT_ERR_OOM;
@@ -177,8 +185,14 @@ mdot_status mdot_create(mdot_handle** out, int64_t max_n, void* stream)
     w.blockred = blockred;
     w.scratch = scratch;
     w.st = st;
+    w.tcc = tagw;
+    w.tcp = tagw + 2 * n;
+    w.tsp = tagw + 2 * n + G * n;
+    w.epoch = reinterpret_cast<unsigned int*>(tagw + 2 * n + G * n + G * 2 * kNRed);
+    h->tag_bytes = tag_words * sizeof(unsigned long long);
     w.G = h->G;
     if (cudaMemsetAsync(st, 0, sizeof(State), h->stream) != cudaSuccess ||
+        cudaMemsetAsync(tagw, 0, h->tag_bytes, h->stream) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess) {
         snprintf(g_err, sizeof g_err, "state initialisation failed");
         delete h;
@@ -337,6 +351,11 @@ mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const C
     const bool all64 = P.precision == MDOT_PREC_FP64 || (P.precision == MDOT_PREC_AUTO && n <= 512);
     const bool polish = P.precision == MDOT_PREC_AUTO && !all64;
     CKR(reset_state(h));
+    if (h->tags_used > (1ull << 31)) {
+        // restart the stage kernel's tags from zero long before the 32-bit tag could wrap
+        CKR(cudaMemsetAsync(h->ws.tcc, 0, h->tag_bytes, h->stream));
+        h->tags_used = 0;
+    }
     Timer tm;
     tm.on = P.profile != 0;
     tm.s = h->stream;
@@ -439,6 +458,7 @@ mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const C
     CKR(cudaMemcpyAsync(h->h_state, ws.st, sizeof(State), cudaMemcpyDeviceToHost, h->stream));
     CKR(cudaStreamSynchronize(h->stream));
     const State& S = *h->h_state;
+    h->tags_used += (unsigned long long)S.evals + 4ull * (unsigned long long)(launches + 1);
     double tsum[8] = {0};
     tm.collect(tsum);
     const double cost = h->h_out[0], lb = h->h_out[8];

@@ -90,6 +90,11 @@ struct WS {
     double* blockred;                 // [G][kNRed]
     double* scratch;                  // [G][8] misc per-CTA values
     State* st;
+    // tagged words of the stage kernel (value | evaluation tag << 32, see tag_pack)
+    unsigned long long* tcc;          // [n][2] per-trial column constants {Hh, tag}, {Wc, tag}
+    unsigned long long* tcp;          // [G][n] column partials
+    unsigned long long* tsp;          // [G][2 kNRed] per-CTA scalar partials (fp64 as two halves)
+    unsigned int* epoch;              // tag base; grows monotonically over the workspace's life
 };
 
 struct StageArgs {
@@ -128,6 +133,10 @@ struct LbArgs {
 // ---------------------------------------------------------------------------------------------
 // small helpers
 // ---------------------------------------------------------------------------------------------
+// Exponent remainder of a padding column (j >= n): large and finite, so that both exponent paths
+// (ex2.approx and exp2_acc, whose range reduction would turn -inf into inf - inf) give exactly 0.
+constexpr float kPadW = -1.0e30f;
+
 __device__ __forceinline__ float ex2f(float x)
 {
     float y;
@@ -135,18 +144,22 @@ __device__ __forceinline__ float ex2f(float x)
     return y;
 }
 
-// 2^(th + tl) for th <= 127 (tl a small correction), relative error ~1.3 ulp and unbiased (unlike
-// ex2.approx, whose error on this GPU averages -5e-8): th = k + f with k = rint(th); 2^(f + tl)
-// by a degree-6 minimax polynomial for 2^x on [-1/2, 1/2] (Remez fit made for this library,
-// relative error 1.9e-9 before fp32 rounding); 2^k applied to the exponent bits.  Results below
-// 2^-125 are returned as 0.
-__device__ __forceinline__ float exp2_acc(float th, float tl)
+// Accurate tier: 2^(G d + W) with G = G32 + Glo (gamma log2 e split in two floats), d the exact
+// cost-unit difference and W the row + column remainders.  k = rint(G32 d + W) is taken from one
+// rounded fma (1.5 * 2^23 added and subtracted leaves the nearest integer); the reduced argument
+// x = (G32 d - k) + W + Glo d is then formed with the product exact inside the fma, so its error is
+// a few 2^-25 whatever the size of G d.  2^x on [-1/2, 1/2] by a degree-6 minimax polynomial (Remez
+// fit made for this library, relative error 1.9e-9 before fp32 rounding), 2^k by ex2.approx on the
+// integer k (exact there; 0 below 2^-126 and inf above 2^127, so no clamping is needed).  Relative
+// error ~1 ulp and unbiased, unlike ex2.approx on a general argument, whose error on this GPU
+// averages -5e-8.
+__device__ __forceinline__ float exp2_acc(float d, float G32, float Glo, float W)
 {
-    th = fminf(th, 127.0f);
-    const bool under = th < -125.0f;
-    th = fmaxf(th, -125.0f);
-    const float kf = rintf(th);
-    const float x = (th - kf) + tl;
+    const float th = fmaf(G32, d, W);
+    const float t = th + 12582912.0f;
+    const float kf = t - 12582912.0f;
+    float x = fmaf(G32, d, -kf);
+    x = fmaf(Glo, d, x + W);
     float p = 1.53458124e-4f;
     p = fmaf(p, x, 1.33999309e-3f);
     p = fmaf(p, x, 9.61848907e-3f);
@@ -154,8 +167,7 @@ __device__ __forceinline__ float exp2_acc(float th, float tl)
     p = fmaf(p, x, 2.40226462e-1f);
     p = fmaf(p, x, 6.93147182e-1f);
     p = fmaf(p, x, 1.0f);
-    const float r = __int_as_float(__float_as_int(p) + ((int)kf << 23));
-    return under ? 0.0f : r;
+    return p * ex2f(kf);
 }
 
 // C_ij regenerated from coordinates: d_k = x_ik - y_jk, D = (d0 d0 + d1 d1) + d2 d2 (or
@@ -170,19 +182,6 @@ __device__ __forceinline__ float point_cost(float x0, float x1, float x2, float 
     else
         D = __fadd_rn(__fadd_rn(fabsf(d0), fabsf(d1)), fabsf(d2));
     return __fmul_rn(D, s);
-}
-
-// log2 P_ij - A_i for the accurate tier as an unevaluated sum th + tl: the product G32 * d and
-// its exact error, the row + column remainders, their TwoSum error and the small G - G32 term.
-__device__ __forceinline__ float exponent_acc(float d, float G32, float Glo, float W, float& tl)
-{
-    const float p = G32 * d;
-    const float pe = fmaf(G32, d, -p);
-    const float th = p + W;
-    const float bb = th - p;
-    const float e = (p - (th - bb)) + (W - bb);
-    tl = e + fmaf(Glo, d, pe);
-    return th;
 }
 
 __device__ __forceinline__ float4 ldg4(const float* p)
@@ -338,6 +337,134 @@ __device__ __forceinline__ bool grid_sync(GridBar* gb, unsigned int nblocks, uns
 }
 
 // ---------------------------------------------------------------------------------------------
+// Tagged words: a 32-bit value in the low half and the evaluation's tag in the high half of one
+// 64-bit word, written and read as single 64-bit accesses (each is single-copy atomic).  A reader
+// waits on exactly the words it consumes until they carry the expected tag; no grid barrier.
+// Tags grow by one per evaluation and never repeat within a workspace, so a word is never read
+// one generation early or late: the producer of generation t + 1 of any word has itself waited,
+// through the chain pass -> column merge -> scalar partials -> next column constants, on every
+// consumer of generation t.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long tag_pack(float v, unsigned int tag)
+{
+    return ((unsigned long long)tag << 32) | (unsigned long long)__float_as_uint(v);
+}
+__device__ __forceinline__ unsigned long long tag_pack_u(unsigned int v, unsigned int tag)
+{
+    return ((unsigned long long)tag << 32) | (unsigned long long)v;
+}
+__device__ __forceinline__ unsigned int tag_of(unsigned long long w) { return (unsigned int)(w >> 32); }
+__device__ __forceinline__ float tag_val(unsigned long long w) { return __uint_as_float((unsigned int)w); }
+
+__device__ __forceinline__ void st_tag(unsigned long long* p, unsigned long long w)
+{
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
+}
+__device__ __forceinline__ void st_tag2(unsigned long long* p, unsigned long long a, unsigned long long b)
+{
+    asm volatile("st.relaxed.gpu.global.v2.b64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_tag(const unsigned long long* p)
+{
+    unsigned long long w;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+    return w;
+}
+__device__ __forceinline__ void ld_tag2(const unsigned long long* p, unsigned long long& a, unsigned long long& b)
+{
+    asm volatile("ld.relaxed.gpu.global.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+}
+
+// One step of a bounded wait on tagged words: back off, and give up (raising the shared abort
+// flag) after kBarrierTimeoutNs or when another CTA has raised it.  Returns false to give up.
+__device__ __forceinline__ bool tag_backoff(unsigned int& spins, unsigned long long& t0, unsigned int* abort)
+{
+    ++spins;
+    if (spins > 4u) __nanosleep(32);
+    if ((spins & 63u) == 0u) {
+        if (ld_acquire(abort)) return false;
+        const unsigned long long now = globaltimer();
+        if (t0 == 0ull) {
+            t0 = now;
+        } else if (now - t0 > kBarrierTimeoutNs) {
+            atomicExch(abort, 1u);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Column constants and column partials of one pass over C, as plain arrays (standalone dual
+// evaluation; a grid barrier orders them).
+struct ColPlain {
+    const float* Hh;
+    const float* Wc;
+    float* out;                       // this CTA's row of column partials
+    __device__ __forceinline__ bool load4(int j0, int n, float hh[4], float wc[4]) const
+    {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int j = j0 + e;
+            const bool ok = j < n;
+            // per-trial constants are rewritten inside the launch: read through L2, never the
+            // non-coherent path
+            hh[e] = ok ? __ldcg(Hh + j) : 0.0f;
+            wc[e] = ok ? __ldcg(Wc + j) : kPadW;     // padding column: its entry is exactly 0
+        }
+        return true;
+    }
+    __device__ __forceinline__ void store4(int j0, int n, const float ca[4]) const
+    {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (j0 + e < n) out[j0 + e] = ca[e];
+    }
+};
+
+// The same as tagged words (stage kernel): column j's constants are cc[2j] = {Hh, tag},
+// cc[2j + 1] = {Wc, tag}; the partials go to out[j] = {partial, tag}.
+struct ColTagged {
+    const unsigned long long* cc;
+    unsigned long long* out;
+    unsigned int tag;
+    unsigned int* abort;
+    __device__ __forceinline__ bool load4(int j0, int n, float hh[4], float wc[4]) const
+    {
+        unsigned int spins = 0;
+        unsigned long long t0 = 0;
+        for (;;) {
+            bool all = true;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int j = j0 + e;
+                if (j < n) {
+                    unsigned long long a, b;
+                    ld_tag2(cc + 2 * (size_t)j, a, b);
+                    hh[e] = tag_val(a);
+                    wc[e] = tag_val(b);
+                    all = all && tag_of(a) == tag && tag_of(b) == tag;
+                } else {
+                    hh[e] = 0.0f;
+                    wc[e] = kPadW;
+                }
+            }
+            if (all) return true;
+            if (!tag_backoff(spins, t0, abort)) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) { hh[e] = 0.0f; wc[e] = kPadW; }
+                return false;
+            }
+        }
+    }
+    __device__ __forceinline__ void store4(int j0, int n, const float ca[4]) const
+    {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (j0 + e < n) st_tag(out + j0 + e, tag_pack(ca[e], tag));
+    }
+};
+
+// ---------------------------------------------------------------------------------------------
 // per-row / per-column constants of an evaluation at u + alpha p_u, v + alpha p_v
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ void split_cost_unit(double x, float& hi, float& lo, double G64)
@@ -361,12 +488,10 @@ __device__ __forceinline__ int row_scale(double log_r_pred)
 // Phase A: one pass over the rows [r0, r1) of C.  Row sums go to sRow[warp][local row]
 // (accumulated, fp32 or fp64), column partials to colpart_b[j].
 // ---------------------------------------------------------------------------------------------
-template <bool VEC4, bool ACC>
-__device__ __forceinline__ void pass_f32(const float* __restrict__ C, int n, int r0, int r1,
-                                         const float* Hh, const float* Wc,
+template <bool VEC4, bool ACC, class IO>
+__device__ __forceinline__ void pass_f32(const float* __restrict__ C, int n, int r0, int r1, const IO& io,
                                          const float* sFh, const float* sWr, const float* sS,
-                                         float G32, float Glo, float* sRow, int nloc,
-                                         float* colpart_b)
+                                         float G32, float Glo, float* sRow, int nloc)
 {
     const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int BN = 4 * kK * T;
@@ -376,16 +501,9 @@ __device__ __forceinline__ void pass_f32(const float* __restrict__ C, int n, int
 #pragma unroll
         for (int k = 0; k < kK; ++k) {
             jk[k] = cb + 4 * (tid + k * T);
+            io.load4(jk[k], n, hh[k], wc[k]);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int j = jk[k] + e;
-                const bool ok = j < n;
-                // per-trial constants are rewritten inside the launch: read through L2, never the
-                // non-coherent path
-                hh[k][e] = ok ? __ldcg(Hh + j) : 0.0f;
-                wc[k][e] = ok ? __ldcg(Wc + j) : -INFINITY;     // invalid column: exp2(-inf) = 0
-                ca[k][e] = 0.0f;
-            }
+            for (int e = 0; e < 4; ++e) ca[k][e] = 0.0f;
         }
         for (int rg = r0; rg < r1; rg += kRG) {
             float rp[kRG];
@@ -415,9 +533,7 @@ __device__ __forceinline__ void pass_f32(const float* __restrict__ C, int n, int
                             const float d = (fh + hh[k][e]) - cv[e];
                             float E;
                             if (ACC) {
-                                float tl;
-                                const float th = exponent_acc(d, G32, Glo, wr + wc[k][e], tl);
-                                E = exp2_acc(th, tl);
+                                E = exp2_acc(d, G32, Glo, wr + wc[k][e]);
                             } else {
                                 E = ex2f(fmaf(Glo, d, fmaf(G32, d, wr + wc[k][e])));
                             }
@@ -432,10 +548,7 @@ __device__ __forceinline__ void pass_f32(const float* __restrict__ C, int n, int
             if (lane < kRG && il < r1) sRow[warp * nloc + (il - r0)] += rp[0];
         }
 #pragma unroll
-        for (int k = 0; k < kK; ++k)
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (jk[k] + e < n) colpart_b[jk[k] + e] = ca[k][e];
+        for (int k = 0; k < kK; ++k) io.store4(jk[k], n, ca[k]);
     }
 }
 
@@ -561,13 +674,11 @@ __device__ __forceinline__ void tma_load_1d(void* dst_smem, const void* src_gmem
 
 // Requires n % 4 == 0 and C 16-byte aligned.  ring: kStages * kSegFloats floats (16-byte aligned);
 // bars: 2 * kStages mbarriers (full, empty).  Block = kStageThreads threads.
-template <bool ACC>
-__device__ __forceinline__ void pass_f32_tma(const float* __restrict__ C, int n, int r0, int r1,
-                                             const float* Hh, const float* Wc, const float* sFh,
-                                             const float* sWr, const float* sS, float G32, float Glo,
-                                             float* sRow, int nloc, float* colpart_b, float* ring,
-                                             int nst, unsigned long long* bars, int* s_issued,
-                                             unsigned int* abort)
+template <bool ACC, class IO>
+__device__ __forceinline__ void pass_f32_tma(const float* __restrict__ C, int n, int r0, int r1, const IO& io,
+                                             const float* sFh, const float* sWr, const float* sS, float G32,
+                                             float Glo, float* sRow, int nloc, float* ring, int nst,
+                                             unsigned long long* bars, int* s_issued, unsigned int* abort)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nrows = r1 - r0;
@@ -614,14 +725,11 @@ __device__ __forceinline__ void pass_f32_tma(const float* __restrict__ C, int n,
 #pragma unroll
             for (int k = 0; k < kK; ++k) {
                 jk[k] = cb + 4 * (tid + k * kConsumerThreads);
+                // a constant that never arrives (timeout) turns this consumer into a pass-through:
+                // it still releases every ring slot so that the producer can finish
+                if (!io.load4(jk[k], n, hh[k], wc[k])) ok = false;
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int j = jk[k] + e;
-                    const bool okj = j < n;
-                    hh[k][e] = okj ? __ldcg(Hh + j) : 0.0f;
-                    wc[k][e] = okj ? __ldcg(Wc + j) : -INFINITY;
-                    ca[k][e] = 0.0f;
-                }
+                for (int e = 0; e < 4; ++e) ca[k][e] = 0.0f;
             }
             for (int rg = r0; rg < r1; rg += kRG) {
                 float rp[kRG];
@@ -646,9 +754,7 @@ __device__ __forceinline__ void pass_f32_tma(const float* __restrict__ C, int n,
                                 const float d = (fh + hh[k][e]) - cv[e];
                                 float E;
                                 if (ACC) {
-                                    float tl;
-                                    const float th = exponent_acc(d, G32, Glo, wr + wc[k][e], tl);
-                                    E = exp2_acc(th, tl);
+                                    E = exp2_acc(d, G32, Glo, wr + wc[k][e]);
                                 } else {
                                     E = ex2f(fmaf(Glo, d, fmaf(G32, d, wr + wc[k][e])));
                                 }
@@ -667,10 +773,7 @@ __device__ __forceinline__ void pass_f32_tma(const float* __restrict__ C, int n,
                 if (lane < kRG && il < r1) sRow[warp * nloc + (il - r0)] += rp[0];
             }
 #pragma unroll
-            for (int k = 0; k < kK; ++k)
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (jk[k] + e < n) colpart_b[jk[k] + e] = ca[k][e];
+            for (int k = 0; k < kK; ++k) io.store4(jk[k], n, ca[k]);
         }
         if (!ok && lane == 0) atomicExch(abort, 1u);
     }
@@ -687,12 +790,11 @@ __device__ __forceinline__ void pass_f32_tma(const float* __restrict__ C, int n,
 // Pass over the CTA's rows with C regenerated from coordinates (no C in memory): same structure
 // as pass_f32 with two float4 column groups per thread; the row coordinates come from shared
 // memory (sX: 3 floats per local row), the column coordinates sit in registers per sweep.
-template <bool ACC, int KIND>
+template <bool ACC, int KIND, class IO>
 __device__ __forceinline__ void pass_f32_regen(const float* __restrict__ Y, float cs, int n, int r0, int r1,
-                                               const float* Hh, const float* Wc, const float* sFh,
+                                               const IO& io, const float* sFh,
                                                const float* sWr, const float* sS, const float* sX,
-                                               float G32, float Glo, float* sRow, int nloc,
-                                               float* colpart_b)
+                                               float G32, float Glo, float* sRow, int nloc)
 {
     constexpr int KR = 2;
     const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -703,12 +805,11 @@ __device__ __forceinline__ void pass_f32_regen(const float* __restrict__ Y, floa
 #pragma unroll
         for (int k = 0; k < KR; ++k) {
             jk[k] = cb + 4 * (tid + k * T);
+            io.load4(jk[k], n, hh[k], wc[k]);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int j = jk[k] + e;
                 const bool ok = j < n;
-                hh[k][e] = ok ? __ldcg(Hh + j) : 0.0f;
-                wc[k][e] = ok ? __ldcg(Wc + j) : -INFINITY;
                 y0[k][e] = ok ? __ldg(Y + 3 * (size_t)j) : 0.0f;
                 y1[k][e] = ok ? __ldg(Y + 3 * (size_t)j + 1) : 0.0f;
                 y2[k][e] = ok ? __ldg(Y + 3 * (size_t)j + 2) : 0.0f;
@@ -733,9 +834,7 @@ __device__ __forceinline__ void pass_f32_regen(const float* __restrict__ Y, floa
                             const float d = (fh + hh[k][e]) - cv;
                             float E;
                             if (ACC) {
-                                float tl;
-                                const float th = exponent_acc(d, G32, Glo, wr + wc[k][e], tl);
-                                E = exp2_acc(th, tl);
+                                E = exp2_acc(d, G32, Glo, wr + wc[k][e]);
                             } else {
                                 E = ex2f(fmaf(Glo, d, fmaf(G32, d, wr + wc[k][e])));
                             }
@@ -750,10 +849,7 @@ __device__ __forceinline__ void pass_f32_regen(const float* __restrict__ Y, floa
             if (lane < kRG && il < r1) sRow[warp * nloc + (il - r0)] += rp[0];
         }
 #pragma unroll
-        for (int k = 0; k < KR; ++k)
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (jk[k] + e < n) colpart_b[jk[k] + e] = ca[k][e];
+        for (int k = 0; k < KR; ++k) io.store4(jk[k], n, ca[k]);
     }
 }
 
@@ -855,9 +951,9 @@ __device__ __forceinline__ void pass2_f32(const WS& ws, const float* __restrict_
                 const int j = jk[k] + e;
                 const bool ok = j < n;
                 hh[k][e] = ok ? __ldcg(Hh + j) : 0.0f;
-                wc[k][e] = ok ? __ldcg(Wc + j) : -INFINITY;
+                wc[k][e] = ok ? __ldcg(Wc + j) : kPadW;
                 hh2[k][e] = ok ? __ldcg(Hh2 + j) : 0.0f;
-                wc2[k][e] = ok ? __ldcg(Wc2 + j) : -INFINITY;
+                wc2[k][e] = ok ? __ldcg(Wc2 + j) : kPadW;
                 ca[k][e] = 0.0f;
             }
         }
@@ -890,11 +986,8 @@ __device__ __forceinline__ void pass2_f32(const WS& ws, const float* __restrict_
                             const float d = (fh + hh[k][e]) - cv[e];
                             const float d2 = (fh2 + hh2[k][e]) - cv[e];
                             if (ACC) {
-                                float tl, tl2;
-                                const float th = exponent_acc(d, G32, Glo, wr + wc[k][e], tl);
-                                const float th2 = exponent_acc(d2, G32, Glo, wr2 + wc2[k][e], tl2);
-                                rp[ii] += exp2_acc(th, tl);
-                                ca[k][e] += exp2_acc(th2, tl2);
+                                rp[ii] += exp2_acc(d, G32, Glo, wr + wc[k][e]);
+                                ca[k][e] += exp2_acc(d2, G32, Glo, wr2 + wc2[k][e]);
                             } else {
                                 rp[ii] += ex2f(fmaf(Glo, d, fmaf(G32, d, wr + wc[k][e])));
                                 ca[k][e] += ex2f(fmaf(Glo, d2, fmaf(G32, d2, wr2 + wc2[k][e])));
@@ -988,6 +1081,49 @@ __device__ __forceinline__ double merge_cols_f32(const float* colpart, int n, in
     for (int k = 0; k < kMaxPer; ++k) {
         const int b = warp + k * nw;
         vals[k] = (j < j1 && b < G) ? __ldcg(colpart + (size_t)b * n + j) : 0.0f;
+    }
+    float s = 0.0f, comp = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kMaxPer; ++k) kahan_add(s, comp, vals[k]);
+    sm[warp * 32 + lane] = s;
+    sm[(nw + warp) * 32 + lane] = -comp;
+    __syncthreads();
+    double tot = 0.0;
+    if (warp == 0)
+        for (int w = 0; w < nw; ++w) tot += (double)sm[w * 32 + lane] + (double)sm[(nw + w) * 32 + lane];
+    __syncthreads();
+    return tot;
+}
+
+// merge_cols_f32 over tagged column partials: waits (bounded) until every word this thread reads
+// carries `tag`; ok turns false if the wait gave up.
+__device__ __forceinline__ double merge_cols_tag(const unsigned long long* colpart, int n, int G, int j0, int j1,
+                                                 float* sm, unsigned int tag, unsigned int* abort, bool& ok)
+{
+    constexpr int kMaxPer = 24;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int j = j0 + lane;
+    float vals[kMaxPer];
+    unsigned int spins = 0;
+    unsigned long long t0 = 0;
+    for (;;) {
+        bool all = true;
+#pragma unroll
+        for (int k = 0; k < kMaxPer; ++k) {
+            const int b = warp + k * nw;
+            if (j < j1 && b < G) {
+                const unsigned long long w = ld_tag(colpart + (size_t)b * n + j);
+                vals[k] = tag_val(w);
+                all = all && tag_of(w) == tag;
+            } else {
+                vals[k] = 0.0f;
+            }
+        }
+        if (all) break;
+        if (!tag_backoff(spins, t0, abort)) {
+            ok = false;
+            break;
+        }
     }
     float s = 0.0f, comp = 0.0f;
 #pragma unroll

@@ -38,7 +38,7 @@ __device__ __forceinline__ void pass_round(const WS& ws, const float* __restrict
                 const int j = jk[k] + e;
                 const bool ok = j < n;
                 hh[k][e] = ok ? __ldcg(Hh + j) : 0.0f;
-                wc[k][e] = ok ? __ldcg(Wc + j) : -INFINITY;
+                wc[k][e] = ok ? __ldcg(Wc + j) : kPadW;
                 yv[k][e] = (MODE >= RM_ROWFINAL && ok) ? __ldcg(Y + j) : 0.0;
                 ev[k][e] = ((MODE == RM_ROWFINAL || MODE == RM_WRITE) && ok) ? __ldcg(EC + j) : 0.0;
                 ca[k][e] = 0.0;

@@ -216,8 +216,10 @@ __device__ __forceinline__ void prep_col(const WS& ws, int j, double va, double 
 }
 
 // Phase A for the CTA's rows: pass over C (streamed or regenerated), row sums into sRow.
-template <int TIER, int COST>
-__device__ __forceinline__ void phase_A(const WS& ws, int r0, int r1, double gamma, double G64,
+// io: where the column constants come from and the column partials go (plain arrays ordered by
+// grid barriers, or tagged words).
+template <int TIER, int COST, class IO>
+__device__ __forceinline__ void phase_A(const WS& ws, const IO& io, int r0, int r1, double gamma, double G64,
                                         unsigned char* sm, const SmemLayout& L)
 {
     const int n = ws.n, nloc = r1 - r0, nw = blockDim.x >> 5;
@@ -232,21 +234,19 @@ __device__ __forceinline__ void phase_A(const WS& ws, int r0, int r1, double gam
         const float* sWr = reinterpret_cast<const float*>(sm + L.off_c1);
         const float* sS = reinterpret_cast<const float*>(sm + L.off_s);
         if (COST != COST_DENSE)
-            pass_f32_regen<TIER == TIER_F32A, COST>(ws.Y, ws.cscale, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sS,
+            pass_f32_regen<TIER == TIER_F32A, COST>(ws.Y, ws.cscale, n, r0, r1, io, sFh, sWr, sS,
                                                     reinterpret_cast<const float*>(sm + L.off_xc), G32, Glo,
-                                                    sRow, L.nloc_max, ws.colpart + (size_t)b * n);
+                                                    sRow, L.nloc_max);
         else if ((n & 3) == 0 && (reinterpret_cast<uintptr_t>(ws.C) & 15) == 0 && blockDim.x == kStageThreads &&
             L.stages >= 2)
-            pass_f32_tma<TIER == TIER_F32A>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sS, G32, Glo, sRow, L.nloc_max,
-                         ws.colpart + (size_t)b * n, reinterpret_cast<float*>(sm + L.off_ring), L.stages,
+            pass_f32_tma<TIER == TIER_F32A>(ws.C, n, r0, r1, io, sFh, sWr, sS, G32, Glo, sRow, L.nloc_max,
+                         reinterpret_cast<float*>(sm + L.off_ring), L.stages,
                          reinterpret_cast<unsigned long long*>(sm + L.off_bars),
                          reinterpret_cast<int*>(sm + L.off_misc), &ws.st->bar.abort);
         else if ((n & 3) == 0)
-            pass_f32<true, TIER == TIER_F32A>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sS, G32, Glo, sRow, L.nloc_max,
-                           ws.colpart + (size_t)b * n);
+            pass_f32<true, TIER == TIER_F32A>(ws.C, n, r0, r1, io, sFh, sWr, sS, G32, Glo, sRow, L.nloc_max);
         else
-            pass_f32<false, TIER == TIER_F32A>(ws.C, n, r0, r1, ws.Hh, ws.Wc, sFh, sWr, sS, G32, Glo, sRow, L.nloc_max,
-                            ws.colpart + (size_t)b * n);
+            pass_f32<false, TIER == TIER_F32A>(ws.C, n, r0, r1, io, sFh, sWr, sS, G32, Glo, sRow, L.nloc_max);
     } else {
         double* sRow = reinterpret_cast<double*>(sm + L.off_row);
         for (int x = threadIdx.x; x < nw * L.nloc_max; x += blockDim.x) sRow[x] = 0.0;
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel(WS ws, StageArg
 
     for (;;) {
         // ---------------- phase A: pass over own rows, row epilogue ----------------
-        phase_A<TIER, COST>(ws, r0, r1, gamma, G64, sm, L);
+        phase_A<TIER, COST>(ws, ColPlain{ws.Hh, ws.Wc, ws.colpart + (size_t)b * n}, r0, r1, gamma, G64, sm, L);
         double x[kNRed];
 #pragma unroll
         for (int q = 0; q < kNRed; ++q) x[q] = 0.0;
@@ -528,6 +528,284 @@ finish:
 }
 
 // ---------------------------------------------------------------------------------------------
+// the stage kernel without grid barriers (fp32-entry tiers): the same evaluation sequence as
+// stage_kernel, but every cross-CTA hand-off is a tagged word that its reader waits on:
+//   column constants (owner -> every pass), column partials (every pass -> column owner), and
+//   per-CTA scalar partials (every CTA -> every CTA).  Each CTA reduces the G scalar partials in
+//   the same fixed order and takes the line-search / PNCG decision on its own copy of the stage
+//   state, so all copies stay identical and no decision has to be broadcast.
+// ---------------------------------------------------------------------------------------------
+
+// Local rows (or columns) of this thread: lane * 8 + warp (+ 256 m) for the eight consumer warps,
+// so the fp64 epilogues are spread over all four SM sub-partitions.
+__device__ __forceinline__ int first_local(int count)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    return (warp < 8) ? lane * 8 + warp : count;
+}
+constexpr int kLocalStride = 256;
+
+template <int TIER>
+__device__ __forceinline__ void prep_col_tag(const WS& ws, int j, double va, double gamma, double G64, unsigned int tag)
+{
+    float gh, wl;
+    split_cost_unit(va * (1.0 / gamma), gh, wl, G64);
+    st_tag2(ws.tcc + 2 * (size_t)j, tag_pack(gh, tag), tag_pack(wl, tag));
+}
+
+template <int TIER, int COST>
+__global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_tag(WS ws, StageArgs a)
+{
+    static_assert(TIER != TIER_F64, "the tagged stage kernel carries fp32 partials");
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ double red_smem[32 * kNRed];
+    __shared__ State sst;                 // this CTA's copy of the stage state
+    __shared__ unsigned int s_base;
+    __shared__ int s_ok;
+
+    const int n = ws.n, G = ws.G, b = blockIdx.x, T = blockDim.x, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const SmemLayout L = smem_layout(n, G, TIER, T);
+    int r0, r1, c0, c1;
+    row_range(n, G, b, r0, r1);
+    row_range(n, G, b, c0, c1);
+    const int NL = L.nloc_max, nrl = r1 - r0, ncl = c1 - c0;
+    double* R = reinterpret_cast<double*>(sm + L.off_rstate);     // R[k * NL + local row]
+    double* Q = reinterpret_cast<double*>(sm + L.off_cstate);     // Q[k * NL + local column]
+    const double gamma = a.gamma, G64 = a.G64, w = a.w;
+    unsigned int* abort = &ws.st->bar.abort;
+    unsigned int t = 0;                   // evaluations of this launch so far
+
+    if (tid == 0) {
+        s_base = *reinterpret_cast<volatile unsigned int*>(ws.epoch);
+        const volatile unsigned long long* src = reinterpret_cast<const volatile unsigned long long*>(ws.st);
+        unsigned long long* dst = reinterpret_cast<unsigned long long*>(&sst);
+        for (int k = 0; k < kStateWords; ++k) dst[k] = src[k];
+        sst.alpha = 0.0;
+        sst.kind = KIND_INIT;
+        sst.accept = 0;
+        sst.trials = 0;
+        sst.k = 0;
+        sst.phase = PH_RUN;
+        sst.beta = 0.0;
+        sst.alpha_commit = 0.0;
+        s_ok = 1;
+    }
+    load_row_coords<COST>(ws, r0, r1, sm, L.off_xc);
+    __syncthreads();
+    const unsigned int base = s_base;
+
+    // ---- prologue (Alg. 1): smoothing, rank-one start or warm start, constants at alpha = 0 ----
+    for (int il = first_local(nrl); il < nrl; il += kLocalStride) {
+        const int i = r0 + il;
+        const double rt = (1.0 - w / 4.0) * ws.r[i] + w / (4.0 * n);
+        const double lrt = log(rt);
+        double u = ws.u[i];
+        if (a.first) {
+            u = lrt;
+            ws.uprev[i] = u;
+        } else if (a.warm_start == 0) {
+            const double z = u;
+            u = z + a.ratio * (z - ws.uprev[i]);             // Eq. (13)
+            ws.uprev[i] = z;
+        } else if (a.warm_start == 1) {
+            u = a.ratio * u;                                    // eps-scaling
+        }
+        R[RS_U * NL + il] = u;
+        R[RS_P * NL + il] = 0.0;
+        R[RS_G * NL + il] = 0.0;
+        R[RS_T * NL + il] = rt;
+        R[RS_LT * NL + il] = lrt;
+        R[RS_L * NL + il] = lrt;
+        prep_row<TIER>(u, row_scale(lrt), a.Aglob, gamma, G64, sm, L, il);
+    }
+    for (int jl = first_local(ncl); jl < ncl; jl += kLocalStride) {
+        const int j = c0 + jl;
+        const double ct = (1.0 - w / 4.0) * ws.c[j] + w / (4.0 * n);
+        double v = ws.v[j];
+        if (a.first) {
+            v = log(ct);
+            ws.vprev[j] = v;
+        } else if (a.warm_start == 0) {
+            const double z = v;
+            v = z + a.ratio * (z - ws.vprev[j]);
+            ws.vprev[j] = z;
+        } else if (a.warm_start == 1) {
+            v = a.ratio * v;
+        }
+        Q[CS_V * NL + jl] = v;
+        Q[CS_P * NL + jl] = 0.0;
+        Q[CS_G * NL + jl] = 0.0;
+        Q[CS_T * NL + jl] = ct;
+        prep_col_tag<TIER>(ws, j, v, gamma, G64, base + 1u);
+    }
+    __syncthreads();
+
+    for (;; ++t) {
+        const unsigned int tag = base + 1u + t;
+        // ---------------- phase A: pass over own rows (column constants awaited word by word) ----------------
+        phase_A<TIER, COST>(ws, ColTagged{ws.tcc, ws.tcp + (size_t)b * n, tag, abort}, r0, r1, gamma, G64, sm, L);
+        double x[kNRed];
+#pragma unroll
+        for (int q = 0; q < kNRed; ++q) x[q] = 0.0;
+        {
+            const int* sA = reinterpret_cast<const int*>(sm + L.off_A);
+            for (int il = first_local(nrl); il < nrl; il += kLocalStride) {
+                const double sum = row_total<TIER>(sm, L, il);
+                if (!(sum > 0.0) || !isfinite(sum)) { x[5] += 1.0; continue; }
+                const double rt = R[RS_T * NL + il];
+                const double g = ldexp(sum, sA[il]) - rt;
+                // Eq. (17): s = log r~ - log r(P) = -log1p(g / r~) (sign of s opposite to g, so
+                // <s, grad> < 0 holds numerically, Sec. 4); fp32 accuracy suffices for a direction
+                const double s = -(double)log1pf((float)g / (float)rt);
+                const double p = R[RS_P * NL + il];
+                const double y = g - R[RS_G * NL + il];
+                x[0] += p * g;
+                x[1] += fabs(g);
+                x[2] += y * (-s);
+                x[3] += y * p;
+                x[4] += s * g;
+                R[RS_GT * NL + il] = g;
+                R[RS_ST * NL + il] = s;
+                R[RS_LTR * NL + il] = ((double)__log2f((float)sum) + (double)sA[il]) * kLn2;   // scale only
+            }
+        }
+
+        // ---------------- phase B: column merge (tagged partials) and epilogue ----------------
+        bool ok = true;
+        for (int j0 = c0; j0 < c1; j0 += 32) {
+            const double colsum = merge_cols_tag(ws.tcp, n, G, j0, c1, reinterpret_cast<float*>(sm + L.off_merge),
+                                                 tag, abort, ok);
+            const int j = j0 + tid;
+            if (tid < 32 && j < c1) {
+                if (!(colsum > 0.0) || !isfinite(colsum)) { x[5] += 1.0; continue; }
+                const int jl = j - c0;
+                const double ct = Q[CS_T * NL + jl];
+                const double g = ldexp(colsum, a.Aglob) - ct;
+                const double s = -(double)log1pf((float)g / (float)ct);   // Eq. (17), see rows
+                const double p = Q[CS_P * NL + jl];
+                const double y = g - Q[CS_G * NL + jl];
+                x[0] += p * g;
+                x[1] += fabs(g);
+                x[2] += y * (-s);
+                x[3] += y * p;
+                x[4] += s * g;
+                Q[CS_GT * NL + jl] = g;
+                Q[CS_ST * NL + jl] = s;
+            }
+        }
+        block_reduce_nred(x, red_smem);
+        if (tid == 0) {
+#pragma unroll
+            for (int q = 0; q < kNRed; ++q) {
+                const unsigned long long bits = (unsigned long long)__double_as_longlong(x[q]);
+                st_tag2(ws.tsp + (size_t)b * 2 * kNRed + 2 * q, tag_pack_u((unsigned int)bits, tag),
+                        tag_pack_u((unsigned int)(bits >> 32), tag));
+            }
+        }
+
+        // ---------------- every CTA: the G partials in a fixed order, then the decision ----------------
+        if (warp < kNRed) {
+            double v5[5];
+            unsigned int spins = 0;
+            unsigned long long t0 = 0;
+            for (;;) {
+                bool all = true;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    const int bb = lane + 32 * k;
+                    v5[k] = 0.0;
+                    if (bb < G) {
+                        unsigned long long lo, hi;
+                        ld_tag2(ws.tsp + (size_t)bb * 2 * kNRed + 2 * warp, lo, hi);
+                        all = all && tag_of(lo) == tag && tag_of(hi) == tag;
+                        v5[k] = __longlong_as_double((long long)(((hi & 0xffffffffull) << 32) | (lo & 0xffffffffull)));
+                    }
+                }
+                if (__all_sync(0xffffffffu, all)) break;
+                const bool go_on = tag_backoff(spins, t0, abort);
+                if (!__all_sync(0xffffffffu, go_on)) {      // the warp gives up together
+                    ok = false;
+                    break;
+                }
+            }
+            double sacc = 0.0;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) sacc += v5[k];
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+            if (lane == 0) red_smem[warp] = sacc;
+        }
+        if (!ok) s_ok = 0;
+        __syncthreads();
+        if (tid == 0) {
+            if (!s_ok) {
+                sst.phase = PH_DONE;
+                sst.accept = 0;
+            } else {
+                double tot[kNRed];
+                for (int q = 0; q < kNRed; ++q) tot[q] = red_smem[q];
+                decide(&sst, tot, a);
+            }
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        const double alpha = sst.alpha, acommit = sst.alpha_commit, beta = sst.beta;
+        const bool accept = sst.accept != 0, done = sst.phase != PH_RUN;
+
+        // ---------------- phase C: commit, new direction, next trial constants ----------------
+        for (int il = first_local(nrl); il < nrl; il += kLocalStride) {
+            double u = R[RS_U * NL + il], p = R[RS_P * NL + il];
+            if (accept) {
+                u = u + acommit * p;                            // (u, v) += alpha p (Alg. 2)
+                R[RS_U * NL + il] = u;
+                R[RS_G * NL + il] = R[RS_GT * NL + il];
+                R[RS_L * NL + il] = R[RS_LTR * NL + il];
+                p = R[RS_ST * NL + il] + beta * p;              // p = s + beta p, beta = 0 on reset (Alg. 2)
+                R[RS_P * NL + il] = p;
+            }
+            if (!done) prep_row<TIER>(u + alpha * p, row_scale(R[RS_L * NL + il] + alpha * p), a.Aglob,
+                                      gamma, G64, sm, L, il);
+        }
+        for (int jl = first_local(ncl); jl < ncl; jl += kLocalStride) {
+            const int j = c0 + jl;
+            double v = Q[CS_V * NL + jl], p = Q[CS_P * NL + jl];
+            if (accept) {
+                v = v + acommit * p;
+                Q[CS_V * NL + jl] = v;
+                Q[CS_G * NL + jl] = Q[CS_GT * NL + jl];
+                p = Q[CS_ST * NL + jl] + beta * p;
+                Q[CS_P * NL + jl] = p;
+            }
+            if (!done) prep_col_tag<TIER>(ws, j, v + alpha * p, gamma, G64, tag + 1u);
+        }
+        if (done) break;
+        __syncthreads();
+    }
+    // the stage's iterate (also on a timeout: the best iterate so far) goes back to global memory
+    __syncthreads();
+    for (int il = first_local(nrl); il < nrl; il += kLocalStride) {
+        ws.u[r0 + il] = R[RS_U * NL + il];
+        ws.lr[r0 + il] = R[RS_L * NL + il];
+    }
+    for (int jl = first_local(ncl); jl < ncl; jl += kLocalStride) ws.v[c0 + jl] = Q[CS_V * NL + jl];
+    if (tid == 0) {
+        // tags of the next launch start above every tag this one may have written (t + 1 for the
+        // constants of a trial that was never evaluated)
+        atomicMax(ws.epoch, base + t + 3u);
+        if (b == 0) {
+            if (*reinterpret_cast<volatile unsigned int*>(abort)) {
+                sst.status = max((int)sst.status, (int)ST_TIMEOUT);
+                sst.phase = PH_DONE;
+            }
+            volatile unsigned long long* dw = reinterpret_cast<volatile unsigned long long*>(ws.st);
+            const unsigned long long* lw = reinterpret_cast<const unsigned long long*>(&sst);
+            for (int k = 0; k < kStateWords; ++k) dw[k] = lw[k];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
 // standalone dual evaluation (mdot_dual_eval): optional max pass for the row scales, one pass,
 // merge.  Writes log r(P) to ws.lrtr and log c(P) to ws.lcout.
 // ---------------------------------------------------------------------------------------------
@@ -594,7 +872,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) dual_eval_kernel(WS ws, Eval
             for (int i = r0 + tid; i < r1; i += T)
                 prep_row<TIER>(a.u[i], sA[i - r0], Aglob, a.gamma, a.G64, sm, L, i - r0);
             __syncthreads();
-            phase_A<TIER, COST>(ws, r0, r1, a.gamma, a.G64, sm, L);
+            phase_A<TIER, COST>(ws, ColPlain{ws.Hh, ws.Wc, ws.colpart + (size_t)b * n}, r0, r1, a.gamma, a.G64, sm, L);
             for (int i = r0 + tid; i < r1; i += T) {
                 const int il = i - r0;
                 ws.lrtr[i] = log(row_total<TIER>(sm, L, il)) + (double)sA[il] * kLn2;

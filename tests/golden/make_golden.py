@@ -6,6 +6,7 @@ from the CUDA library.  Each record holds, for one (cost kind, seed, target gap)
   evaluation counts, and the exact OT value (column generation priced over all n^2 arcs).
 Usage:  python tests/golden/make_golden.py [k] [eps ...]   (defaults: k = 64, eps = 1e-6)
         python tests/golden/make_golden.py --exact-only [k]   (only the exact OT values)
+        python tests/golden/make_golden.py --oracle-only k kind eps   (one oracle solve, no exact value)
 Runs the cases in parallel worker processes (spawn) and merges each finished case into
 tests/golden/grid{n}.json (or exact{n}.json) as soon as it completes.
 """
@@ -25,7 +26,8 @@ SEED = 2000          # problem seed of the n = 4096 benchmark instance
 
 
 def one_case(args):
-    k, kind, seed, eps = args
+    k, kind, seed, eps = args[:4]
+    with_exact = args[4] if len(args) > 4 else True
     import numpy as np
     import oracle as O
     from oracle import exact as E
@@ -39,9 +41,11 @@ def one_case(args):
     t_solve = time.time() - t0
     # exact optimum: candidate arcs = arcs that are nearly tight for the oracle's potentials
     f, g = res.u / res.gamma_f, res.v / res.gamma_f
-    t0 = time.time()
-    val, fd, gd, rounds = E.exact_ot_colgen(C, p.r, p.c, k_init=4)
-    t_exact = time.time() - t0
+    val, rounds, t_exact = None, None, None
+    if with_exact:
+        t0 = time.time()
+        val, fd, gd, rounds = E.exact_ot_colgen(C, p.r, p.c, k_init=4)
+        t_exact = time.time() - t0
     return {
         "k": k, "n": p.n, "kind": kind, "seed": seed, "eps_target": eps, "H_min": H,
         "gamma_f": res.gamma_f, "oracle_cost": res.cost, "oracle_lb": res.lb,
@@ -49,7 +53,7 @@ def one_case(args):
         "oracle_ls_trials": int(res.stats.ls_trials), "oracle_stages": int(res.stats.stages),
         "oracle_status": int(res.status), "oracle_grad_l1": res.stats.grad_l1,
         "oracle_seconds": t_solve, "exact_ot": val, "exact_rounds": rounds,
-        "exact_seconds": t_exact, "true_gap": res.cost - val,
+        "exact_seconds": t_exact, "true_gap": (res.cost - val) if val is not None else None,
         "f_g_span": [float(f.min()), float(f.max()), float(g.min()), float(g.max())],
     }
 
@@ -89,6 +93,12 @@ def main():
             for rec in pool.imap_unordered(exact_case, cases):
                 _merge(path, rec, lambda c: (c["kind"], c["seed"]))
                 print(json.dumps(rec), flush=True)
+        return
+    if len(sys.argv) > 1 and sys.argv[1] == "--oracle-only":
+        k, kind, eps = int(sys.argv[2]), sys.argv[3], float(sys.argv[4])
+        rec = one_case((k, kind, SEED, eps, False))
+        _merge(os.path.join(HERE, f"grid{k * k}.json"), rec, lambda c: (c["kind"], c["seed"], c["eps_target"]))
+        print(json.dumps(rec), flush=True)
         return
     k = int(sys.argv[1]) if len(sys.argv) > 1 else 64
     eps_list = [float(a) for a in sys.argv[2:]] or [1e-6]
