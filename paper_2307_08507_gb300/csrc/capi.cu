@@ -52,10 +52,10 @@ struct mdot_handle {
     int* b_order = nullptr;
     unsigned int* b_next = nullptr;
     int b_cap = 0;
-    // tags consumed by the stage kernel's tagged words since they were last cleared (an upper
+    // evaluation tags consumed by the stage kernel's flags since they were last cleared (an upper
     // bound, from the evaluation counts); cleared well before the 32-bit tag could wrap
     unsigned long long tags_used = 0;
-    size_t tag_bytes = 0;
+    size_t flag_bytes = 0;
     ~mdot_handle()
     {
         cudaFree(d_r); cudaFree(d_c); cudaFree(d_u); cudaFree(d_v); cudaFree(d_C);
@@ -131,7 +131,8 @@ mdot_status mdot_create(mdot_handle** out, int64_t max_n, void* stream)
         delete h;
         return MDOT_ERR_CUDA;
     }
-    h->G = h->sms;                       // one CTA per SM (cooperative, persistent per launch)
+    h->G = std::min(h->sms, 160);        // one CTA per SM (cooperative, persistent per launch); the
+                                         // fixed-order reductions handle at most 160 CTAs
     int mb = 0;
     e = configure_kernels((int)max_n, h->G, &mb);
     if (e != cudaSuccess || mb < 1) {
@@ -156,14 +157,14 @@ mdot_status mdot_create(mdot_handle** out, int64_t max_n, void* stream)
     double* blockred = (double*)dalloc(G * kNRed * sizeof(double));
     double* scratch = (double*)dalloc(G * 8 * sizeof(double));
     State* st = (State*)dalloc(sizeof(State));
-    // tagged words: column constants [n][2], column partials [G][n], scalar partials [G][2 kNRed],
-    // then the tag base (one 16-byte slot)
-    const size_t tag_words = 2 * n + G * n + G * 2 * kNRed + 2;
-    unsigned long long* tagw = (unsigned long long*)dalloc(tag_words * sizeof(unsigned long long));
+    // stage-kernel flags [2][G] and the tag base; published column state (v, p double-floats, s)
+    const size_t flag_words = 2 * G + 1;
+    unsigned int* flagw = (unsigned int*)dalloc(flag_words * sizeof(unsigned int));
+    float* pubw = (float*)dalloc(5 * n * sizeof(float));
     h->d_out = (double*)dalloc(16 * sizeof(double));
     void* hp = nullptr;
     if (cudaMallocHost(&hp, 16 * sizeof(double) + sizeof(State)) == cudaSuccess) h->mem.host.push_back(hp);
-    if (!vec || !f32 || !A || !colpart || !colpartd || !blockred || !scratch || !st || !tagw || !h->d_out || !hp) {
+    if (!vec || !f32 || !A || !colpart || !colpartd || !blockred || !scratch || !st || !flagw || !pubw || !h->d_out || !hp) {
         snprintf(g_err, sizeof g_err, "workspace allocation failed for max_n = %lld", (long long)max_n);
         delete h;
         return MDOT_ERR_OOM;
@@ -185,14 +186,15 @@ mdot_status mdot_create(mdot_handle** out, int64_t max_n, void* stream)
     w.blockred = blockred;
     w.scratch = scratch;
     w.st = st;
-    w.tcc = tagw;
-    w.tcp = tagw + 2 * n;
-    w.tsp = tagw + 2 * n + G * n;
-    w.epoch = reinterpret_cast<unsigned int*>(tagw + 2 * n + G * n + G * 2 * kNRed);
-    h->tag_bytes = tag_words * sizeof(unsigned long long);
+    w.flags = flagw;
+    w.epoch = flagw + 2 * G;
+    w.pub_v = reinterpret_cast<float2*>(pubw);
+    w.pub_p = reinterpret_cast<float2*>(pubw + 2 * n);
+    w.pub_s = pubw + 4 * n;
+    h->flag_bytes = flag_words * sizeof(unsigned int);
     w.G = h->G;
     if (cudaMemsetAsync(st, 0, sizeof(State), h->stream) != cudaSuccess ||
-        cudaMemsetAsync(tagw, 0, h->tag_bytes, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(flagw, 0, h->flag_bytes, h->stream) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess) {
         snprintf(g_err, sizeof g_err, "state initialisation failed");
         delete h;
@@ -353,7 +355,7 @@ mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const C
     CKR(reset_state(h));
     if (h->tags_used > (1ull << 31)) {
         // restart the stage kernel's tags from zero long before the 32-bit tag could wrap
-        CKR(cudaMemsetAsync(h->ws.tcc, 0, h->tag_bytes, h->stream));
+        CKR(cudaMemsetAsync(h->ws.flags, 0, h->flag_bytes, h->stream));
         h->tags_used = 0;
     }
     Timer tm;

@@ -25,8 +25,8 @@ cudaError_t launch_stage(int tier, const WS& ws, const StageArgs& a, cudaStream_
     void* args[] = {(void*)&w, (void*)&aa};
     const size_t smem = stage_smem_bytes(ws.n, ws.G, tier);
     if (tier == TIER_F64) return coop(stage_kernel<TIER_F64, COST_DENSE>, ws.G, smem, s, args);
-    if (tier == TIER_F32A) return coop(stage_kernel_tag<TIER_F32A, COST_DENSE>, ws.G, smem, s, args);
-    return coop(stage_kernel_tag<TIER_F32, COST_DENSE>, ws.G, smem, s, args);
+    if (tier == TIER_F32A) return coop(stage_kernel_flag<TIER_F32A, COST_DENSE>, ws.G, smem, s, args);
+    return coop(stage_kernel_flag<TIER_F32, COST_DENSE>, ws.G, smem, s, args);
 }
 
 cudaError_t launch_dual_eval(int tier, const WS& ws, const EvalArgs& a, cudaStream_t s)
@@ -44,9 +44,9 @@ cudaError_t launch_dual_eval(int tier, const WS& ws, const EvalArgs& a, cudaStre
 cudaError_t configure_stage_kernels(int max_n, int G, int* min_blocks)
 {
     struct K { const void* f; int tier; } ks[] = {
-        {(const void*)stage_kernel_tag<TIER_F32, COST_DENSE>, TIER_F32},
+        {(const void*)stage_kernel_flag<TIER_F32, COST_DENSE>, TIER_F32},
         {(const void*)stage_kernel<TIER_F64, COST_DENSE>, TIER_F64},
-        {(const void*)stage_kernel_tag<TIER_F32A, COST_DENSE>, TIER_F32A},
+        {(const void*)stage_kernel_flag<TIER_F32A, COST_DENSE>, TIER_F32A},
         {(const void*)dual_eval_kernel<TIER_F32, COST_DENSE>, TIER_F32},
         {(const void*)dual_eval_kernel<TIER_F64, COST_DENSE>, TIER_F64},
         {(const void*)dual_eval_kernel<TIER_F32A, COST_DENSE>, TIER_F32A}};

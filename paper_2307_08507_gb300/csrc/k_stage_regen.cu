@@ -15,8 +15,8 @@ static cudaError_t launch_stage_kind(int tier, const WS& ws, const StageArgs& a,
     void* args[] = {(void*)&w, (void*)&aa};
     const size_t smem = stage_smem_bytes(ws.n, ws.G, tier);
     const void* f = tier == TIER_F64 ? (const void*)stage_kernel<TIER_F64, COST>
-                  : tier == TIER_F32A ? (const void*)stage_kernel_tag<TIER_F32A, COST>
-                                      : (const void*)stage_kernel_tag<TIER_F32, COST>;
+                  : tier == TIER_F32A ? (const void*)stage_kernel_flag<TIER_F32A, COST>
+                                      : (const void*)stage_kernel_flag<TIER_F32, COST>;
     return cudaLaunchCooperativeKernel(f, dim3(ws.G), dim3(kStageThreads), args, smem, s);
 }
 
@@ -48,12 +48,12 @@ cudaError_t launch_dual_eval_regen(int tier, const WS& ws, const EvalArgs& a, cu
 cudaError_t configure_regen_kernels(int max_n, int G, int* min_blocks)
 {
     struct K { const void* f; int tier; } ks[] = {
-        {(const void*)stage_kernel_tag<TIER_F32, COST_SQEUCLID>, TIER_F32},
+        {(const void*)stage_kernel_flag<TIER_F32, COST_SQEUCLID>, TIER_F32},
         {(const void*)stage_kernel<TIER_F64, COST_SQEUCLID>, TIER_F64},
-        {(const void*)stage_kernel_tag<TIER_F32A, COST_SQEUCLID>, TIER_F32A},
-        {(const void*)stage_kernel_tag<TIER_F32, COST_L1>, TIER_F32},
+        {(const void*)stage_kernel_flag<TIER_F32A, COST_SQEUCLID>, TIER_F32A},
+        {(const void*)stage_kernel_flag<TIER_F32, COST_L1>, TIER_F32},
         {(const void*)stage_kernel<TIER_F64, COST_L1>, TIER_F64},
-        {(const void*)stage_kernel_tag<TIER_F32A, COST_L1>, TIER_F32A},
+        {(const void*)stage_kernel_flag<TIER_F32A, COST_L1>, TIER_F32A},
         {(const void*)dual_eval_kernel<TIER_F32, COST_SQEUCLID>, TIER_F32},
         {(const void*)dual_eval_kernel<TIER_F64, COST_SQEUCLID>, TIER_F64},
         {(const void*)dual_eval_kernel<TIER_F32A, COST_SQEUCLID>, TIER_F32A},

@@ -90,11 +90,12 @@ struct WS {
     double* blockred;                 // [G][kNRed]
     double* scratch;                  // [G][8] misc per-CTA values
     State* st;
-    // tagged words of the stage kernel (value | evaluation tag << 32, see tag_pack)
-    unsigned long long* tcc;          // [n][2] per-trial column constants {Hh, tag}, {Wc, tag}
-    unsigned long long* tcp;          // [G][n] column partials
-    unsigned long long* tsp;          // [G][2 kNRed] per-CTA scalar partials (fp64 as two halves)
-    unsigned int* epoch;              // tag base; grows monotonically over the workspace's life
+    // flags of the stage kernel: [2][G] evaluation tags (column partials written, scalar partials
+    // and column state published), and the tag base, which grows over the workspace's life
+    unsigned int* flags;
+    unsigned int* epoch;
+    float2 *pub_v, *pub_p;            // [n] committed column potentials / directions (double-float)
+    float* pub_s;                     // [n] Sinkhorn direction of the last evaluation (columns)
 };
 
 struct StageArgs {
@@ -336,48 +337,10 @@ __device__ __forceinline__ bool grid_sync(GridBar* gb, unsigned int nblocks, uns
     return bar_wait(gb, gen, s_flag);
 }
 
-// ---------------------------------------------------------------------------------------------
-// Tagged words: a 32-bit value in the low half and the evaluation's tag in the high half of one
-// 64-bit word, written and read as single 64-bit accesses (each is single-copy atomic).  A reader
-// waits on exactly the words it consumes until they carry the expected tag; no grid barrier.
-// Tags grow by one per evaluation and never repeat within a workspace, so a word is never read
-// one generation early or late: the producer of generation t + 1 of any word has itself waited,
-// through the chain pass -> column merge -> scalar partials -> next column constants, on every
-// consumer of generation t.
-// ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long tag_pack(float v, unsigned int tag)
-{
-    return ((unsigned long long)tag << 32) | (unsigned long long)__float_as_uint(v);
-}
-__device__ __forceinline__ unsigned long long tag_pack_u(unsigned int v, unsigned int tag)
-{
-    return ((unsigned long long)tag << 32) | (unsigned long long)v;
-}
-__device__ __forceinline__ unsigned int tag_of(unsigned long long w) { return (unsigned int)(w >> 32); }
-__device__ __forceinline__ float tag_val(unsigned long long w) { return __uint_as_float((unsigned int)w); }
-
-__device__ __forceinline__ void st_tag(unsigned long long* p, unsigned long long w)
-{
-    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
-}
-__device__ __forceinline__ void st_tag2(unsigned long long* p, unsigned long long a, unsigned long long b)
-{
-    asm volatile("st.relaxed.gpu.global.v2.b64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
-}
-__device__ __forceinline__ unsigned long long ld_tag(const unsigned long long* p)
-{
-    unsigned long long w;
-    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
-    return w;
-}
-__device__ __forceinline__ void ld_tag2(const unsigned long long* p, unsigned long long& a, unsigned long long& b)
-{
-    asm volatile("ld.relaxed.gpu.global.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
-}
-
-// One step of a bounded wait on tagged words: back off, and give up (raising the shared abort
-// flag) after kBarrierTimeoutNs or when another CTA has raised it.  Returns false to give up.
-__device__ __forceinline__ bool tag_backoff(unsigned int& spins, unsigned long long& t0, unsigned int* abort)
+// One step of a bounded wait on flags written by other CTAs: back off, and give up (raising the
+// shared abort flag) after kBarrierTimeoutNs or when another CTA has raised it.  Returns false to
+// give up.
+__device__ __forceinline__ bool wait_backoff(unsigned int& spins, unsigned long long& t0, unsigned int* abort)
 {
     ++spins;
     if (spins > 4u) __nanosleep(32);
@@ -394,8 +357,9 @@ __device__ __forceinline__ bool tag_backoff(unsigned int& spins, unsigned long l
     return true;
 }
 
-// Column constants and column partials of one pass over C, as plain arrays (standalone dual
-// evaluation; a grid barrier orders them).
+// Column constants and column partials of one pass over C (plain arrays; a grid barrier or the
+// stage kernel's flags order them).  Other sources (e.g. constants computed in place) can supply
+// the same two calls.
 struct ColPlain {
     const float* Hh;
     const float* Wc;
@@ -421,46 +385,117 @@ struct ColPlain {
     }
 };
 
-// The same as tagged words (stage kernel): column j's constants are cc[2j] = {Hh, tag},
-// cc[2j + 1] = {Wc, tag}; the partials go to out[j] = {partial, tag}.
-struct ColTagged {
-    const unsigned long long* cc;
-    unsigned long long* out;
-    unsigned int tag;
-    unsigned int* abort;
+
+// ---------------------------------------------------------------------------------------------
+// Double-float arithmetic (a value as an unevaluated sum hi + lo of two floats, ~48 bits): Knuth's
+// TwoSum, the fast variant for |a| >= |b|, and products through the fma's exact error term.
+// Every operation is an explicitly rounded intrinsic, so no contraction can change the results.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ float2 df_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return make_float2(s, e);
+}
+__device__ __forceinline__ float2 df_fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ float2 df_add(float2 a, float2 b)
+{
+    const float2 s = df_two_sum(a.x, b.x);
+    return df_fast_two_sum(s.x, __fadd_rn(s.y, __fadd_rn(a.y, b.y)));
+}
+// a * b for a double-float a and a float b
+__device__ __forceinline__ float2 df_mul_f(float2 a, float b)
+{
+    const float p = __fmul_rn(a.x, b);
+    const float e = __fmaf_rn(a.y, b, __fmaf_rn(a.x, b, -p));
+    return df_fast_two_sum(p, e);
+}
+// a * b for double-floats a and b
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b)
+{
+    const float p = __fmul_rn(a.x, b.x);
+    const float e = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, __fmaf_rn(a.x, b.x, -p)));
+    return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ float2 df_from_double(double x)
+{
+    const float h = (float)x;
+    return make_float2(h, (float)(x - (double)h));
+}
+__device__ __forceinline__ double df_to_double(float2 a) { return (double)a.x + (double)a.y; }
+
+// Decision of one evaluation as every thread of the stage kernel sees it: commit (v += alpha_c p,
+// p = s + beta p) when accepted, then the trial point v + alpha p.  Steps are fp32 numbers (the
+// line search rounds them), so the same arithmetic on the same inputs gives the same bits in
+// every CTA.
+struct ColStep {
+    int accept;
+    float alpha_c, beta, alpha;
+};
+
+// Commit of one column's (v, p) (double-floats) for a decision.
+__device__ __forceinline__ void col_commit(const ColStep& d, float2& v, float2& p, float s)
+{
+    if (d.accept) {
+        v = df_add(v, df_mul_f(p, d.alpha_c));                 // (u, v) += alpha p (Alg. 2)
+        p = df_add(df_mul_f(p, d.beta), make_float2(s, 0.0f));  // p = s + beta p (Alg. 2, Eq. (18))
+    }
+}
+
+// Trial constants of one column: x = (v + alpha p) / gamma in cost units, split into a part
+// quantised to 2^-21 (hh, exact in fp32 while |x| < 8) and the remainder in exponent units
+// (wc = gamma log2 e (x - hh)), as split_cost_unit does in fp64.
+__device__ __forceinline__ void col_trial(const ColStep& d, float2 v, float2 p, float2 inv_gamma, float G32,
+                                          float Glo, float& hh, float& wc)
+{
+    const float2 x = df_mul(df_add(v, df_mul_f(p, d.alpha)), inv_gamma);
+    const float h = __fmul_rn(rintf(__fmul_rn(x.x, 2097152.0f)), 1.0f / 2097152.0f);
+    const float lo = __fadd_rn(__fsub_rn(x.x, h), x.y);       // x.x - h is exact
+    hh = h;
+    wc = __fmaf_rn(lo, G32, __fmul_rn(lo, Glo));
+}
+
+// Column constants derived in place by each consumer thread from the owners' published state
+// (committed v, p and the new direction s of the last evaluation) and the decision: no hand-off
+// of constants between CTAs.  Partials go to plain arrays.
+struct ColDerived {
+    const float2* pv;
+    const float2* pp;
+    const float* ps;
+    float* out;
+    ColStep d;
+    float2 inv_gamma;
+    float G32, Glo;
     __device__ __forceinline__ bool load4(int j0, int n, float hh[4], float wc[4]) const
     {
-        unsigned int spins = 0;
-        unsigned long long t0 = 0;
-        for (;;) {
-            bool all = true;
+        float2 v[4], p[4];
+        float sv[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int j = j0 + e;
-                if (j < n) {
-                    unsigned long long a, b;
-                    ld_tag2(cc + 2 * (size_t)j, a, b);
-                    hh[e] = tag_val(a);
-                    wc[e] = tag_val(b);
-                    all = all && tag_of(a) == tag && tag_of(b) == tag;
-                } else {
-                    hh[e] = 0.0f;
-                    wc[e] = kPadW;
-                }
-            }
-            if (all) return true;
-            if (!tag_backoff(spins, t0, abort)) {
-#pragma unroll
-                for (int e = 0; e < 4; ++e) { hh[e] = 0.0f; wc[e] = kPadW; }
-                return false;
-            }
+        for (int e = 0; e < 4; ++e) {
+            const int j = j0 + e;
+            const bool ok = j < n;
+            v[e] = ok ? __ldcg(pv + j) : make_float2(0.0f, 0.0f);
+            p[e] = ok ? __ldcg(pp + j) : make_float2(0.0f, 0.0f);
+            sv[e] = ok ? __ldcg(ps + j) : 0.0f;
         }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            col_commit(d, v[e], p[e], sv[e]);
+            col_trial(d, v[e], p[e], inv_gamma, G32, Glo, hh[e], wc[e]);
+            if (j0 + e >= n) { hh[e] = 0.0f; wc[e] = kPadW; }
+        }
+        return true;
     }
     __device__ __forceinline__ void store4(int j0, int n, const float ca[4]) const
     {
 #pragma unroll
         for (int e = 0; e < 4; ++e)
-            if (j0 + e < n) st_tag(out + j0 + e, tag_pack(ca[e], tag));
+            if (j0 + e < n) out[j0 + e] = ca[e];
     }
 };
 
@@ -1081,49 +1116,6 @@ __device__ __forceinline__ double merge_cols_f32(const float* colpart, int n, in
     for (int k = 0; k < kMaxPer; ++k) {
         const int b = warp + k * nw;
         vals[k] = (j < j1 && b < G) ? __ldcg(colpart + (size_t)b * n + j) : 0.0f;
-    }
-    float s = 0.0f, comp = 0.0f;
-#pragma unroll
-    for (int k = 0; k < kMaxPer; ++k) kahan_add(s, comp, vals[k]);
-    sm[warp * 32 + lane] = s;
-    sm[(nw + warp) * 32 + lane] = -comp;
-    __syncthreads();
-    double tot = 0.0;
-    if (warp == 0)
-        for (int w = 0; w < nw; ++w) tot += (double)sm[w * 32 + lane] + (double)sm[(nw + w) * 32 + lane];
-    __syncthreads();
-    return tot;
-}
-
-// merge_cols_f32 over tagged column partials: waits (bounded) until every word this thread reads
-// carries `tag`; ok turns false if the wait gave up.
-__device__ __forceinline__ double merge_cols_tag(const unsigned long long* colpart, int n, int G, int j0, int j1,
-                                                 float* sm, unsigned int tag, unsigned int* abort, bool& ok)
-{
-    constexpr int kMaxPer = 24;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int j = j0 + lane;
-    float vals[kMaxPer];
-    unsigned int spins = 0;
-    unsigned long long t0 = 0;
-    for (;;) {
-        bool all = true;
-#pragma unroll
-        for (int k = 0; k < kMaxPer; ++k) {
-            const int b = warp + k * nw;
-            if (j < j1 && b < G) {
-                const unsigned long long w = ld_tag(colpart + (size_t)b * n + j);
-                vals[k] = tag_val(w);
-                all = all && tag_of(w) == tag;
-            } else {
-                vals[k] = 0.0f;
-            }
-        }
-        if (all) break;
-        if (!tag_backoff(spins, t0, abort)) {
-            ok = false;
-            break;
-        }
     }
     float s = 0.0f, comp = 0.0f;
 #pragma unroll

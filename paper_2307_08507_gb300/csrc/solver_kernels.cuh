@@ -529,37 +529,69 @@ finish:
 
 // ---------------------------------------------------------------------------------------------
 // the stage kernel without grid barriers (fp32-entry tiers): the same evaluation sequence as
-// stage_kernel, but every cross-CTA hand-off is a tagged word that its reader waits on:
-//   column constants (owner -> every pass), column partials (every pass -> column owner), and
-//   per-CTA scalar partials (every CTA -> every CTA).  Each CTA reduces the G scalar partials in
-//   the same fixed order and takes the line-search / PNCG decision on its own copy of the stage
-//   state, so all copies stay identical and no decision has to be broadcast.
+// stage_kernel with two hand-offs per evaluation, each announced by a per-CTA flag that its
+// readers wait on (no central counter, no last arriver):
+//   fcp[b]: CTA b's column partials are written (read by every column owner);
+//   fsp[b]: CTA b's partial sums of the six scalars and the committed state (v, p) and new
+//           direction s of its columns are published (read by every CTA).
+// Each CTA reduces the G scalar partials in the same fixed order and takes the line-search /
+// PNCG decision on its own copy of the stage state, so all copies stay identical.  Every consumer
+// thread then derives the next trial's constants of its own columns from the published column
+// state and that decision (double-float arithmetic, identical in every CTA), so the column
+// constants never travel between CTAs.  The fp64 epilogues stay packed into as few warps as
+// possible: on this GPU an fp64 warp instruction holds the SM's fp64 pipe for ~16 cycles however
+// few of its lanes are active.
 // ---------------------------------------------------------------------------------------------
 
-// Local rows (or columns) of this thread: lane * 8 + warp (+ 256 m) for the eight consumer warps,
-// so the fp64 epilogues are spread over all four SM sub-partitions.
-__device__ __forceinline__ int first_local(int count)
+// Publish `tag` in flag (thread 0, after a __syncthreads that follows the CTA's data writes).
+__device__ __forceinline__ void post_flag(unsigned int* flag, unsigned int tag)
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    return (warp < 8) ? lane * 8 + warp : count;
+    __threadfence();
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(flag), "r"(tag) : "memory");
 }
-constexpr int kLocalStride = 256;
 
-template <int TIER>
-__device__ __forceinline__ void prep_col_tag(const WS& ws, int j, double va, double gamma, double G64, unsigned int tag)
+// One warp waits (bounded) until every flags[0..G) has reached tag; false if it gave up.
+__device__ __forceinline__ bool wait_flags(const unsigned int* flags, int G, unsigned int tag, unsigned int* abort)
 {
-    float gh, wl;
-    split_cost_unit(va * (1.0 / gamma), gh, wl, G64);
-    st_tag2(ws.tcc + 2 * (size_t)j, tag_pack(gh, tag), tag_pack(wl, tag));
+    const int lane = threadIdx.x & 31;
+    unsigned int spins = 0;
+    unsigned long long t0 = 0;
+    for (;;) {
+        bool ready = true;
+        for (int b = lane; b < G; b += 32) {
+            unsigned int f;
+            asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(flags + b) : "memory");
+            ready = ready && (int)(f - tag) >= 0;
+        }
+        if (__all_sync(0xffffffffu, ready)) {
+            __threadfence();
+            return true;
+        }
+        const bool go_on = wait_backoff(spins, t0, abort);
+        if (!__all_sync(0xffffffffu, go_on)) return false;
+    }
+}
+
+// Warp 0 waits on the flags; the whole CTA learns the outcome (s_ok) after a __syncthreads.
+__device__ __forceinline__ bool cta_wait_flags(const unsigned int* flags, int G, unsigned int tag,
+                                               unsigned int* abort, int* s_ok)
+{
+    if (threadIdx.x < 32) {
+        const bool ok = wait_flags(flags, G, tag, abort);
+        if (threadIdx.x == 0 && !ok) *s_ok = 0;
+    }
+    __syncthreads();
+    return *s_ok != 0;
 }
 
 template <int TIER, int COST>
-__global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_tag(WS ws, StageArgs a)
+__global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, StageArgs a)
 {
-    static_assert(TIER != TIER_F64, "the tagged stage kernel carries fp32 partials");
+    static_assert(TIER != TIER_F64, "the flag-synchronised stage kernel carries fp32 partials");
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ double red_smem[32 * kNRed];
     __shared__ State sst;                 // this CTA's copy of the stage state
+    __shared__ ColStep s_step;            // the last decision, as the column arithmetic uses it
     __shared__ unsigned int s_base;
     __shared__ int s_ok;
 
@@ -569,11 +601,19 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_tag(WS ws, Stag
     int r0, r1, c0, c1;
     row_range(n, G, b, r0, r1);
     row_range(n, G, b, c0, c1);
-    const int NL = L.nloc_max, nrl = r1 - r0, ncl = c1 - c0;
+    const int NL = L.nloc_max, nrl = r1 - r0;
     double* R = reinterpret_cast<double*>(sm + L.off_rstate);     // R[k * NL + local row]
     double* Q = reinterpret_cast<double*>(sm + L.off_cstate);     // Q[k * NL + local column]
+    float2* QV = reinterpret_cast<float2*>(Q + CS_V * NL);        // column v and p as double-floats
+    float2* QP = reinterpret_cast<float2*>(Q + CS_P * NL);
     const double gamma = a.gamma, G64 = a.G64, w = a.w;
+    const float G32 = (float)G64, Glo = (float)(G64 - (double)G32);
+    const float2 inv_gamma = df_from_double(1.0 / gamma);
     unsigned int* abort = &ws.st->bar.abort;
+    unsigned int* fcp = ws.flags;
+    unsigned int* fsp = ws.flags + G;
+    // warps holding epilogue sums: rows sit in threads 0 .. nrl - 1, columns in warp 0
+    const int red_warps = max(1, min((nrl + 31) / 32, T / 32));
     unsigned int t = 0;                   // evaluations of this launch so far
 
     if (tid == 0) {
@@ -589,6 +629,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_tag(WS ws, Stag
         sst.phase = PH_RUN;
         sst.beta = 0.0;
         sst.alpha_commit = 0.0;
+        s_step = ColStep{0, 0.0f, 0.0f, 0.0f};
         s_ok = 1;
     }
     load_row_coords<COST>(ws, r0, r1, sm, L.off_xc);
@@ -596,8 +637,8 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_tag(WS ws, Stag
     const unsigned int base = s_base;
 
     // ---- prologue (Alg. 1): smoothing, rank-one start or warm start, constants at alpha = 0 ----
-    for (int il = first_local(nrl); il < nrl; il += kLocalStride) {
-        const int i = r0 + il;
+    for (int i = r0 + tid; i < r1; i += T) {
+        const int il = i - r0;
         const double rt = (1.0 - w / 4.0) * ws.r[i] + w / (4.0 * n);
         const double lrt = log(rt);
         double u = ws.u[i];
@@ -619,8 +660,8 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_tag(WS ws, Stag
         R[RS_L * NL + il] = lrt;
         prep_row<TIER>(u, row_scale(lrt), a.Aglob, gamma, G64, sm, L, il);
     }
-    for (int jl = first_local(ncl); jl < ncl; jl += kLocalStride) {
-        const int j = c0 + jl;
+    for (int j = c0 + tid; j < c1; j += T) {
+        const int jl = j - c0;
         const double ct = (1.0 - w / 4.0) * ws.c[j] + w / (4.0 * n);
         double v = ws.v[j];
         if (a.first) {
@@ -633,24 +674,35 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_tag(WS ws, Stag
         } else if (a.warm_start == 1) {
             v = a.ratio * v;
         }
-        Q[CS_V * NL + jl] = v;
-        Q[CS_P * NL + jl] = 0.0;
+        QV[jl] = df_from_double(v);
+        QP[jl] = make_float2(0.0f, 0.0f);
         Q[CS_G * NL + jl] = 0.0;
         Q[CS_T * NL + jl] = ct;
-        prep_col_tag<TIER>(ws, j, v, gamma, G64, base + 1u);
+        Q[CS_ST * NL + jl] = 0.0;
+        ws.pub_v[j] = QV[jl];
+        ws.pub_p[j] = QP[jl];
+        ws.pub_s[j] = 0.0f;
     }
+    // tags: base + 1 for this prologue, base + 2 + t for evaluation t (flags start at 0, and every
+    // tag of an earlier launch is at most its base + t + 3 <= this base)
     __syncthreads();
+    if (tid == 0) post_flag(fsp + b, base + 1u);
+    cta_wait_flags(fsp, G, base + 1u, abort, &s_ok);
 
-    for (;; ++t) {
-        const unsigned int tag = base + 1u + t;
-        // ---------------- phase A: pass over own rows (column constants awaited word by word) ----------------
-        phase_A<TIER, COST>(ws, ColTagged{ws.tcc, ws.tcp + (size_t)b * n, tag, abort}, r0, r1, gamma, G64, sm, L);
+    for (; s_ok; ++t) {
+        const unsigned int tag = base + 2u + t;
+        // ---------------- phase A: pass over own rows; column constants derived in place ----------------
+        phase_A<TIER, COST>(ws, ColDerived{ws.pub_v, ws.pub_p, ws.pub_s, ws.colpart + (size_t)b * n, s_step, inv_gamma,
+                                           G32, Glo},
+                            r0, r1, gamma, G64, sm, L);
+        if (tid == 0) post_flag(fcp + b, tag);             // phase_A ends with a __syncthreads
         double x[kNRed];
 #pragma unroll
         for (int q = 0; q < kNRed; ++q) x[q] = 0.0;
         {
             const int* sA = reinterpret_cast<const int*>(sm + L.off_A);
-            for (int il = first_local(nrl); il < nrl; il += kLocalStride) {
+            for (int i = r0 + tid; i < r1; i += T) {
+                const int il = i - r0;
                 const double sum = row_total<TIER>(sm, L, il);
                 if (!(sum > 0.0) || !isfinite(sum)) { x[5] += 1.0; continue; }
                 const double rt = R[RS_T * NL + il];
@@ -671,63 +723,63 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_tag(WS ws, Stag
             }
         }
 
-        // ---------------- phase B: column merge (tagged partials) and epilogue ----------------
-        bool ok = true;
+        // ---------------- phase B: column merge and epilogue; publish the column state ----------------
+        if (!cta_wait_flags(fcp, G, tag, abort, &s_ok)) break;
         for (int j0 = c0; j0 < c1; j0 += 32) {
-            const double colsum = merge_cols_tag(ws.tcp, n, G, j0, c1, reinterpret_cast<float*>(sm + L.off_merge),
-                                                 tag, abort, ok);
+            const double colsum = merge_cols_f32(ws.colpart, n, G, j0, c1, reinterpret_cast<float*>(sm + L.off_merge));
             const int j = j0 + tid;
             if (tid < 32 && j < c1) {
-                if (!(colsum > 0.0) || !isfinite(colsum)) { x[5] += 1.0; continue; }
                 const int jl = j - c0;
-                const double ct = Q[CS_T * NL + jl];
-                const double g = ldexp(colsum, a.Aglob) - ct;
-                const double s = -(double)log1pf((float)g / (float)ct);   // Eq. (17), see rows
-                const double p = Q[CS_P * NL + jl];
-                const double y = g - Q[CS_G * NL + jl];
-                x[0] += p * g;
-                x[1] += fabs(g);
-                x[2] += y * (-s);
-                x[3] += y * p;
-                x[4] += s * g;
-                Q[CS_GT * NL + jl] = g;
-                Q[CS_ST * NL + jl] = s;
+                float sf = 0.0f;
+                if (!(colsum > 0.0) || !isfinite(colsum)) {
+                    x[5] += 1.0;
+                } else {
+                    const double ct = Q[CS_T * NL + jl];
+                    const double g = ldexp(colsum, a.Aglob) - ct;
+                    sf = -log1pf((float)g / (float)ct);             // Eq. (17), see rows
+                    const double s = (double)sf;
+                    const double p = df_to_double(QP[jl]);
+                    const double y = g - Q[CS_G * NL + jl];
+                    x[0] += p * g;
+                    x[1] += fabs(g);
+                    x[2] += y * (-s);
+                    x[3] += y * p;
+                    x[4] += s * g;
+                    Q[CS_GT * NL + jl] = g;
+                }
+                Q[CS_ST * NL + jl] = (double)sf;
+                ws.pub_v[j] = QV[jl];
+                ws.pub_p[j] = QP[jl];
+                ws.pub_s[j] = sf;
             }
         }
-        block_reduce_nred(x, red_smem);
-        if (tid == 0) {
+        // CTA partial sums: only the warps that hold rows (columns sit in warp 0) take part
+        if (warp < red_warps) {
 #pragma unroll
-            for (int q = 0; q < kNRed; ++q) {
-                const unsigned long long bits = (unsigned long long)__double_as_longlong(x[q]);
-                st_tag2(ws.tsp + (size_t)b * 2 * kNRed + 2 * q, tag_pack_u((unsigned int)bits, tag),
-                        tag_pack_u((unsigned int)(bits >> 32), tag));
-            }
+            for (int q = 0; q < kNRed; ++q)
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) x[q] += __shfl_xor_sync(0xffffffffu, x[q], o);
+            if (lane == 0)
+#pragma unroll
+                for (int q = 0; q < kNRed; ++q) red_smem[warp * kNRed + q] = x[q];
         }
+        __syncthreads();
+        if (tid < kNRed) {
+            double acc = 0.0;
+            for (int ww = 0; ww < red_warps; ++ww) acc += red_smem[ww * kNRed + tid];
+            ws.blockred[(size_t)b * kNRed + tid] = acc;
+        }
+        __syncthreads();
+        if (tid == 0) post_flag(fsp + b, tag);
 
         // ---------------- every CTA: the G partials in a fixed order, then the decision ----------------
+        if (!cta_wait_flags(fsp, G, tag, abort, &s_ok)) break;
         if (warp < kNRed) {
             double v5[5];
-            unsigned int spins = 0;
-            unsigned long long t0 = 0;
-            for (;;) {
-                bool all = true;
 #pragma unroll
-                for (int k = 0; k < 5; ++k) {
-                    const int bb = lane + 32 * k;
-                    v5[k] = 0.0;
-                    if (bb < G) {
-                        unsigned long long lo, hi;
-                        ld_tag2(ws.tsp + (size_t)bb * 2 * kNRed + 2 * warp, lo, hi);
-                        all = all && tag_of(lo) == tag && tag_of(hi) == tag;
-                        v5[k] = __longlong_as_double((long long)(((hi & 0xffffffffull) << 32) | (lo & 0xffffffffull)));
-                    }
-                }
-                if (__all_sync(0xffffffffu, all)) break;
-                const bool go_on = tag_backoff(spins, t0, abort);
-                if (!__all_sync(0xffffffffu, go_on)) {      // the warp gives up together
-                    ok = false;
-                    break;
-                }
+            for (int k = 0; k < 5; ++k) {
+                const int bb = lane + 32 * k;
+                v5[k] = (bb < G) ? __ldcg(ws.blockred + (size_t)bb * kNRed + warp) : 0.0;
             }
             double sacc = 0.0;
 #pragma unroll
@@ -736,25 +788,23 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_tag(WS ws, Stag
             for (int o = 16; o >= 1; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
             if (lane == 0) red_smem[warp] = sacc;
         }
-        if (!ok) s_ok = 0;
         __syncthreads();
         if (tid == 0) {
-            if (!s_ok) {
-                sst.phase = PH_DONE;
-                sst.accept = 0;
-            } else {
-                double tot[kNRed];
-                for (int q = 0; q < kNRed; ++q) tot[q] = red_smem[q];
-                decide(&sst, tot, a);
-            }
+            double tot[kNRed];
+            for (int q = 0; q < kNRed; ++q) tot[q] = red_smem[q];
+            decide(&sst, tot, a);
+            // steps as fp32 numbers: the column arithmetic uses them exactly, rows too
+            sst.alpha = (double)(float)sst.alpha;
+            sst.beta = (double)(float)sst.beta;
+            s_step = ColStep{sst.accept, (float)sst.alpha_commit, (float)sst.beta, (float)sst.alpha};
         }
         __syncthreads();
-        if (!s_ok) break;
         const double alpha = sst.alpha, acommit = sst.alpha_commit, beta = sst.beta;
         const bool accept = sst.accept != 0, done = sst.phase != PH_RUN;
 
-        // ---------------- phase C: commit, new direction, next trial constants ----------------
-        for (int il = first_local(nrl); il < nrl; il += kLocalStride) {
+        // ---------------- phase C: commit, new direction, next trial constants (rows) ----------------
+        for (int i = r0 + tid; i < r1; i += T) {
+            const int il = i - r0;
             double u = R[RS_U * NL + il], p = R[RS_P * NL + il];
             if (accept) {
                 u = u + acommit * p;                            // (u, v) += alpha p (Alg. 2)
@@ -767,34 +817,27 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_tag(WS ws, Stag
             if (!done) prep_row<TIER>(u + alpha * p, row_scale(R[RS_L * NL + il] + alpha * p), a.Aglob,
                                       gamma, G64, sm, L, il);
         }
-        for (int jl = first_local(ncl); jl < ncl; jl += kLocalStride) {
-            const int j = c0 + jl;
-            double v = Q[CS_V * NL + jl], p = Q[CS_P * NL + jl];
-            if (accept) {
-                v = v + acommit * p;
-                Q[CS_V * NL + jl] = v;
-                Q[CS_G * NL + jl] = Q[CS_GT * NL + jl];
-                p = Q[CS_ST * NL + jl] + beta * p;
-                Q[CS_P * NL + jl] = p;
-            }
-            if (!done) prep_col_tag<TIER>(ws, j, v + alpha * p, gamma, G64, tag + 1u);
+        // own columns: the same commit every consumer applies to the published state
+        for (int j = c0 + tid; j < c1; j += T) {
+            const int jl = j - c0;
+            if (accept) Q[CS_G * NL + jl] = Q[CS_GT * NL + jl];
+            col_commit(s_step, QV[jl], QP[jl], (float)Q[CS_ST * NL + jl]);
         }
         if (done) break;
         __syncthreads();
     }
     // the stage's iterate (also on a timeout: the best iterate so far) goes back to global memory
     __syncthreads();
-    for (int il = first_local(nrl); il < nrl; il += kLocalStride) {
-        ws.u[r0 + il] = R[RS_U * NL + il];
-        ws.lr[r0 + il] = R[RS_L * NL + il];
+    for (int i = r0 + tid; i < r1; i += T) {
+        ws.u[i] = R[RS_U * NL + i - r0];
+        ws.lr[i] = R[RS_L * NL + i - r0];
     }
-    for (int jl = first_local(ncl); jl < ncl; jl += kLocalStride) ws.v[c0 + jl] = Q[CS_V * NL + jl];
+    for (int j = c0 + tid; j < c1; j += T) ws.v[j] = df_to_double(QV[j - c0]);
     if (tid == 0) {
-        // tags of the next launch start above every tag this one may have written (t + 1 for the
-        // constants of a trial that was never evaluated)
+        // the next launch's tags start above every tag this one may have posted
         atomicMax(ws.epoch, base + t + 3u);
         if (b == 0) {
-            if (*reinterpret_cast<volatile unsigned int*>(abort)) {
+            if (!s_ok || *reinterpret_cast<volatile unsigned int*>(abort)) {
                 sst.status = max((int)sst.status, (int)ST_TIMEOUT);
                 sst.phase = PH_DONE;
             }
