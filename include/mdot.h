@@ -56,9 +56,9 @@ typedef enum mdot_precision {
                              fp64 entries for the final stage when it is not (and for n <= 512) */
     MDOT_PREC_FP32 = 1,   /* always fp32 entries (exact cost-unit difference, ex2.approx)      */
     MDOT_PREC_FP64 = 2,   /* always fp64 entries                                              */
-    MDOT_PREC_FP32A = 3   /* fp32 entries with a double-float exponent and a polynomial exp2
-                             (about 1 ulp, unbiased); AUTO uses it once a stage's tolerance is
-                             below 2e-6                                                         */
+    MDOT_PREC_FP32A = 3   /* fp32 entries with an accurately reduced exponent (the product
+                             exact inside an fma) and a polynomial exp2 (about 1 ulp, unbiased);
+                             AUTO uses it once a stage's tolerance is below 2e-6               */
 } mdot_precision;
 
 /* Source of the cost matrix for the *_points entry points: C_ij regenerated inside every pass

@@ -161,10 +161,11 @@ mdot_status mdot_create(mdot_handle** out, int64_t max_n, void* stream)
     const size_t flag_words = 2 * G + 1;
     unsigned int* flagw = (unsigned int*)dalloc(flag_words * sizeof(unsigned int));
     float* pubw = (float*)dalloc(5 * n * sizeof(float));
+    unsigned long long* tspw = (unsigned long long*)dalloc(G * 2 * kNRed * sizeof(unsigned long long));
     h->d_out = (double*)dalloc(16 * sizeof(double));
     void* hp = nullptr;
     if (cudaMallocHost(&hp, 16 * sizeof(double) + sizeof(State)) == cudaSuccess) h->mem.host.push_back(hp);
-    if (!vec || !f32 || !A || !colpart || !colpartd || !blockred || !scratch || !st || !flagw || !pubw || !h->d_out || !hp) {
+    if (!vec || !f32 || !A || !colpart || !colpartd || !blockred || !scratch || !st || !flagw || !pubw || !tspw || !h->d_out || !hp) {
         snprintf(g_err, sizeof g_err, "workspace allocation failed for max_n = %lld", (long long)max_n);
         delete h;
         return MDOT_ERR_OOM;
@@ -188,6 +189,7 @@ mdot_status mdot_create(mdot_handle** out, int64_t max_n, void* stream)
     w.st = st;
     w.flags = flagw;
     w.epoch = flagw + 2 * G;
+    w.tsp = tspw;
     w.pub_v = reinterpret_cast<float2*>(pubw);
     w.pub_p = reinterpret_cast<float2*>(pubw + 2 * n);
     w.pub_s = pubw + 4 * n;
@@ -195,6 +197,7 @@ mdot_status mdot_create(mdot_handle** out, int64_t max_n, void* stream)
     w.G = h->G;
     if (cudaMemsetAsync(st, 0, sizeof(State), h->stream) != cudaSuccess ||
         cudaMemsetAsync(flagw, 0, h->flag_bytes, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(tspw, 0, G * 2 * kNRed * sizeof(unsigned long long), h->stream) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess) {
         snprintf(g_err, sizeof g_err, "state initialisation failed");
         delete h;
@@ -356,6 +359,7 @@ mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const C
     if (h->tags_used > (1ull << 31)) {
         // restart the stage kernel's tags from zero long before the 32-bit tag could wrap
         CKR(cudaMemsetAsync(h->ws.flags, 0, h->flag_bytes, h->stream));
+        CKR(cudaMemsetAsync(h->ws.tsp, 0, (size_t)h->G * 2 * kNRed * sizeof(unsigned long long), h->stream));
         h->tags_used = 0;
     }
     Timer tm;

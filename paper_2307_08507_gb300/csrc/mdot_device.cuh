@@ -90,10 +90,11 @@ struct WS {
     double* blockred;                 // [G][kNRed]
     double* scratch;                  // [G][8] misc per-CTA values
     State* st;
-    // flags of the stage kernel: [2][G] evaluation tags (column partials written, scalar partials
-    // and column state published), and the tag base, which grows over the workspace's life
+    // flags of the stage kernel: [2][G] evaluation tags (column partials written; initial column
+    // state published), and the tag base, which grows over the workspace's life
     unsigned int* flags;
     unsigned int* epoch;
+    unsigned long long* tsp;          // [G][2 kNRed] tagged per-CTA scalar partials (fp64 halves)
     float2 *pub_v, *pub_p;            // [n] committed column potentials / directions (double-float)
     float* pub_s;                     // [n] Sinkhorn direction of the last evaluation (columns)
 };
@@ -337,13 +338,34 @@ __device__ __forceinline__ bool grid_sync(GridBar* gb, unsigned int nblocks, uns
     return bar_wait(gb, gen, s_flag);
 }
 
+// Tagged 64-bit words: a 32-bit value in the low half and the evaluation's tag in the high half,
+// written and read as single 64-bit accesses (each is single-copy atomic), so a reader that sees
+// the tag also sees the value: the word is its own ready flag.
+__device__ __forceinline__ unsigned long long tag_pack(unsigned int v, unsigned int tag)
+{
+    return ((unsigned long long)tag << 32) | (unsigned long long)v;
+}
+__device__ __forceinline__ unsigned int tag_of(unsigned long long w) { return (unsigned int)(w >> 32); }
+// A release store: every write the thread has observed before it (including other threads'
+// writes ordered by a preceding __syncthreads) is visible to a reader that acquires the word.
+__device__ __forceinline__ void st_tag_release(unsigned long long* p, unsigned long long w)
+{
+    asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
+}
+__device__ __forceinline__ void ld_tag2(const unsigned long long* p, unsigned long long& a, unsigned long long& b)
+{
+    asm volatile("ld.relaxed.gpu.global.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+}
+
 // One step of a bounded wait on flags written by other CTAs: back off, and give up (raising the
 // shared abort flag) after kBarrierTimeoutNs or when another CTA has raised it.  Returns false to
 // give up.
 __device__ __forceinline__ bool wait_backoff(unsigned int& spins, unsigned long long& t0, unsigned int* abort)
 {
     ++spins;
-    if (spins > 4u) __nanosleep(32);
+    // poll without sleeping at first: a flag poll is a handful of loads by one warp, and the
+    // sleep's granularity would add to every hand-off
+    if (spins > 4096u) __nanosleep(64);
     if ((spins & 63u) == 0u) {
         if (ld_acquire(abort)) return false;
         const unsigned long long now = globaltimer();
@@ -819,6 +841,147 @@ __device__ __forceinline__ void pass_f32_tma(const float* __restrict__ C, int n,
         const int issued = *s_issued;
         for (int q = max(0, issued - nst); q < issued; ++q) mbar_wait(&full[q % nst], (q / nst) & 1);
     }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------------------
+// TMA ring that persists over the passes of one launch (stage kernel): C does not change within a
+// stage, so the producer never stops: while the CTA is in its epilogue and hand-offs it already
+// holds the first rows of the next pass.  Items are numbered over all passes; item Q is row
+// (Q mod items) % nrows, segment (Q mod items) / nrows, in slot Q % nst with parity (Q / nst) & 1.
+// ---------------------------------------------------------------------------------------------
+struct RingGeom {
+    const float* C;
+    int n, r0, nrows, ncb, nst;
+    float* ring;
+    unsigned long long* full;     // [kStages]
+    unsigned long long* empty;    // [kStages]
+    __device__ __forceinline__ int items() const { return nrows * ncb; }
+};
+
+__device__ __forceinline__ void ring_init(const RingGeom& g)
+{
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < g.nst; ++s) {
+            mbar_init(&g.full[s], 1);
+            mbar_init(&g.empty[s], kConsumerThreads / 32);
+        }
+        mbar_fence_init();
+    }
+}
+
+// Producer thread: issue items up to (not including) `upto`; false if a slot never came free.
+// (Slot, parity, row and segment advance incrementally: no integer division per item.)
+__device__ __forceinline__ bool ring_issue(const RingGeom& g, int& issued, int upto)
+{
+    const int items = g.items();
+    if (items == 0 || issued >= upto) return true;
+    int s = issued % g.nst, ph = (issued / g.nst) & 1;
+    const int loc = issued % items;
+    int il = loc % g.nrows, cbi = loc / g.nrows;
+    for (; issued < upto; ++issued) {
+        if (issued >= g.nst && !mbar_wait(&g.empty[s], ph ^ 1)) return false;
+        const int cb = cbi * kSegFloats;
+        const unsigned int bytes = (unsigned int)(min(kSegFloats, g.n - cb) * 4);
+        mbar_arrive_expect_tx(&g.full[s], bytes);
+        tma_load_1d(g.ring + (size_t)s * kSegFloats, g.C + (size_t)(g.r0 + il) * g.n + cb, bytes, &g.full[s]);
+        if (++s == g.nst) { s = 0; ph ^= 1; }
+        if (++il == g.nrows) {
+            il = 0;
+            if (++cbi == g.ncb) cbi = 0;
+        }
+    }
+    return true;
+}
+
+// Before the CTA exits: every issued copy lands (bounded) so that none writes shared memory late.
+__device__ __forceinline__ void ring_drain(const RingGeom& g, int consumed, int issued)
+{
+    for (int Q = max(consumed, issued - g.nst); Q < issued; ++Q) mbar_wait(&g.full[Q % g.nst], (Q / g.nst) & 1);
+}
+
+// One pass over the CTA's rows through the persistent ring (same arithmetic as pass_f32_tma).
+// consumed: items consumed before this pass (identical in every thread); issued: the producer
+// thread's count.  Both advance here.
+// pre_hh / pre_wc (nullable): this thread's column constants of segment 0, already computed.
+template <bool ACC, class IO>
+__device__ __forceinline__ void pass_f32_ring(const RingGeom& g, int r1, const IO& io, const float (*pre_hh)[4],
+                                              const float (*pre_wc)[4], const float* sFh, const float* sWr,
+                                              const float* sS, float G32, float Glo, float* sRow, int nloc,
+                                              int& consumed, int& issued, unsigned int* abort)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = g.n, r0 = g.r0, items = g.items();
+    if (warp == kConsumerThreads / 32) {
+        // ------------------------------ producer warp ------------------------------
+        if (lane == 0 && !ring_issue(g, issued, consumed + items + g.nst)) atomicExch(abort, 1u);
+        __syncwarp();
+    } else {
+        // ------------------------------ consumer warps ------------------------------
+        int sl = consumed % g.nst, ph = (consumed / g.nst) & 1;   // slot and parity of the next item
+        bool ok = true;
+        for (int cbi = 0; cbi < g.ncb; ++cbi) {
+            const int cb = cbi * kSegFloats;
+            float hh[kK][4], wc[kK][4], ca[kK][4];
+            int jk[kK];
+#pragma unroll
+            for (int k = 0; k < kK; ++k) {
+                jk[k] = cb + 4 * (tid + k * kConsumerThreads);
+                if (pre_hh != nullptr && cbi == 0) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) { hh[k][e] = pre_hh[k][e]; wc[k][e] = pre_wc[k][e]; }
+                } else {
+                    io.load4(jk[k], n, hh[k], wc[k]);
+                }
+#pragma unroll
+                for (int e = 0; e < 4; ++e) ca[k][e] = 0.0f;
+            }
+            for (int rg = r0; rg < r1; rg += kRG) {
+                float rp[kRG];
+#pragma unroll
+                for (int ii = 0; ii < kRG; ++ii) {
+                    rp[ii] = 0.0f;
+                    const int i = rg + ii;
+                    if (i < r1) {
+                        const int s = sl;
+                        if (ok) ok = mbar_wait(&g.full[s], ph);
+                        const float fh = sFh[i - r0], wr = sWr[i - r0], sc = sS[i - r0];
+                        const float4* seg = reinterpret_cast<const float4*>(g.ring + (size_t)s * kSegFloats);
+#pragma unroll
+                        for (int k = 0; k < kK; ++k) {
+                            float cv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                            if (ok && jk[k] < n) {
+                                const float4 t4 = seg[tid + k * kConsumerThreads];
+                                cv[0] = t4.x; cv[1] = t4.y; cv[2] = t4.z; cv[3] = t4.w;
+                            }
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const float d = (fh + hh[k][e]) - cv[e];
+                                float E;
+                                if (ACC) {
+                                    E = exp2_acc(d, G32, Glo, wr + wc[k][e]);
+                                } else {
+                                    E = ex2f(fmaf(Glo, d, fmaf(G32, d, wr + wc[k][e])));
+                                }
+                                rp[ii] += E;
+                                ca[k][e] = fmaf(E, sc, ca[k][e]);
+                            }
+                        }
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&g.empty[s]);
+                        if (++sl == g.nst) { sl = 0; ph ^= 1; }
+                    }
+                }
+                butterfly<kRG>(rp, lane);
+                const int il = rg + lane;
+                if (lane < kRG && il < r1) sRow[warp * nloc + (il - r0)] += rp[0];
+            }
+#pragma unroll
+            for (int k = 0; k < kK; ++k) io.store4(jk[k], n, ca[k]);
+        }
+        if (!ok && lane == 0) atomicExch(abort, 1u);
+    }
+    consumed += items;
     __syncthreads();
 }
 

@@ -529,11 +529,12 @@ finish:
 
 // ---------------------------------------------------------------------------------------------
 // the stage kernel without grid barriers (fp32-entry tiers): the same evaluation sequence as
-// stage_kernel with two hand-offs per evaluation, each announced by a per-CTA flag that its
-// readers wait on (no central counter, no last arriver):
-//   fcp[b]: CTA b's column partials are written (read by every column owner);
-//   fsp[b]: CTA b's partial sums of the six scalars and the committed state (v, p) and new
-//           direction s of its columns are published (read by every CTA).
+// stage_kernel with two hand-offs per evaluation, neither through a central counter or a last
+// arriver:
+//   fcp[b]: a per-CTA flag, CTA b's column partials are written (read by every column owner);
+//   tsp[b]: CTA b's partial sums of the six scalars as tagged words (release stores), read by
+//           every CTA; acquiring them also makes CTA b's published column state visible: the
+//           committed (v, p) and the new direction s of its columns.
 // Each CTA reduces the G scalar partials in the same fixed order and takes the line-search /
 // PNCG decision on its own copy of the stage state, so all copies stay identical.  Every consumer
 // thread then derives the next trial's constants of its own columns from the published column
@@ -543,11 +544,12 @@ finish:
 // few of its lanes are active.
 // ---------------------------------------------------------------------------------------------
 
-// Publish `tag` in flag (thread 0, after a __syncthreads that follows the CTA's data writes).
+// Publish `tag` in flag (thread 0, after a __syncthreads that follows the CTA's data writes): a
+// release store, so every write the CTA made before the barrier is visible to a reader that
+// observes the tag.
 __device__ __forceinline__ void post_flag(unsigned int* flag, unsigned int tag)
 {
-    __threadfence();
-    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(flag), "r"(tag) : "memory");
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(flag), "r"(tag) : "memory");
 }
 
 // One warp waits (bounded) until every flags[0..G) has reached tag; false if it gave up.
@@ -564,7 +566,7 @@ __device__ __forceinline__ bool wait_flags(const unsigned int* flags, int G, uns
             ready = ready && (int)(f - tag) >= 0;
         }
         if (__all_sync(0xffffffffu, ready)) {
-            __threadfence();
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");     // acquire for the relaxed polls
             return true;
         }
         const bool go_on = wait_backoff(spins, t0, abort);
@@ -611,10 +613,17 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
     const float2 inv_gamma = df_from_double(1.0 / gamma);
     unsigned int* abort = &ws.st->bar.abort;
     unsigned int* fcp = ws.flags;
-    unsigned int* fsp = ws.flags + G;
+    unsigned int* fpro = ws.flags + G;      // prologue: the initial column state is published
     // warps holding epilogue sums: rows sit in threads 0 .. nrl - 1, columns in warp 0
     const int red_warps = max(1, min((nrl + 31) / 32, T / 32));
     unsigned int t = 0;                   // evaluations of this launch so far
+    // dense C streamed through a TMA ring that stays alive over the launch (see pass_f32_ring)
+    const bool use_ring = COST == COST_DENSE && (n & 3) == 0 && (reinterpret_cast<uintptr_t>(ws.C) & 15) == 0 &&
+                          T == kStageThreads && L.stages >= 2;
+    RingGeom ring{ws.C, n, r0, nrl, (n + kSegFloats - 1) / kSegFloats, L.stages,
+                  reinterpret_cast<float*>(sm + L.off_ring), reinterpret_cast<unsigned long long*>(sm + L.off_bars),
+                  reinterpret_cast<unsigned long long*>(sm + L.off_bars) + kStages};
+    int consumed = 0, issued = 0;
 
     if (tid == 0) {
         s_base = *reinterpret_cast<volatile unsigned int*>(ws.epoch);
@@ -632,9 +641,12 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
         s_step = ColStep{0, 0.0f, 0.0f, 0.0f};
         s_ok = 1;
     }
+    if (use_ring) ring_init(ring);
     load_row_coords<COST>(ws, r0, r1, sm, L.off_xc);
     __syncthreads();
     const unsigned int base = s_base;
+    // the first rows of the first pass load while the prologue runs
+    if (use_ring && tid == kConsumerThreads && !ring_issue(ring, issued, ring.nst)) atomicExch(abort, 1u);
 
     // ---- prologue (Alg. 1): smoothing, rank-one start or warm start, constants at alpha = 0 ----
     for (int i = r0 + tid; i < r1; i += T) {
@@ -686,15 +698,27 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
     // tags: base + 1 for this prologue, base + 2 + t for evaluation t (flags start at 0, and every
     // tag of an earlier launch is at most its base + t + 3 <= this base)
     __syncthreads();
-    if (tid == 0) post_flag(fsp + b, base + 1u);
-    cta_wait_flags(fsp, G, base + 1u, abort, &s_ok);
+    if (tid == 0) post_flag(fpro + b, base + 1u);
+    cta_wait_flags(fpro, G, base + 1u, abort, &s_ok);
 
     for (; s_ok; ++t) {
         const unsigned int tag = base + 2u + t;
         // ---------------- phase A: pass over own rows; column constants derived in place ----------------
-        phase_A<TIER, COST>(ws, ColDerived{ws.pub_v, ws.pub_p, ws.pub_s, ws.colpart + (size_t)b * n, s_step, inv_gamma,
-                                           G32, Glo},
-                            r0, r1, gamma, G64, sm, L);
+        {
+            const ColDerived io{ws.pub_v, ws.pub_p, ws.pub_s, ws.colpart + (size_t)b * n, s_step, inv_gamma, G32, Glo};
+            if (use_ring) {
+                float* sRow = reinterpret_cast<float*>(sm + L.off_row);
+                for (int x = tid; x < (T >> 5) * NL; x += T) sRow[x] = 0.0f;
+                __syncthreads();
+                pass_f32_ring<TIER == TIER_F32A>(ring, r1, io, nullptr, nullptr,
+                                                 reinterpret_cast<const float*>(sm + L.off_c0),
+                                                 reinterpret_cast<const float*>(sm + L.off_c1),
+                                                 reinterpret_cast<const float*>(sm + L.off_s), G32, Glo, sRow, NL,
+                                                 consumed, issued, abort);
+            } else {
+                phase_A<TIER, COST>(ws, io, r0, r1, gamma, G64, sm, L);
+            }
+        }
         if (tid == 0) post_flag(fcp + b, tag);             // phase_A ends with a __syncthreads
         double x[kNRed];
 #pragma unroll
@@ -765,22 +789,43 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
         }
         __syncthreads();
         if (tid < kNRed) {
+            // the CTA's partial sum as two tagged words (release: the column state written above
+            // is visible to whoever acquires them)
             double acc = 0.0;
             for (int ww = 0; ww < red_warps; ++ww) acc += red_smem[ww * kNRed + tid];
-            ws.blockred[(size_t)b * kNRed + tid] = acc;
+            const unsigned long long bits = (unsigned long long)__double_as_longlong(acc);
+            unsigned long long* dst = ws.tsp + (size_t)b * 2 * kNRed + 2 * tid;
+            st_tag_release(dst, tag_pack((unsigned int)bits, tag));
+            st_tag_release(dst + 1, tag_pack((unsigned int)(bits >> 32), tag));
         }
-        __syncthreads();
-        if (tid == 0) post_flag(fsp + b, tag);
 
         // ---------------- every CTA: the G partials in a fixed order, then the decision ----------------
-        if (!cta_wait_flags(fsp, G, tag, abort, &s_ok)) break;
+        bool ok = true;
         if (warp < kNRed) {
             double v5[5];
+            unsigned int spins = 0;
+            unsigned long long t0 = 0;
+            for (;;) {
+                bool ready = true;
 #pragma unroll
-            for (int k = 0; k < 5; ++k) {
-                const int bb = lane + 32 * k;
-                v5[k] = (bb < G) ? __ldcg(ws.blockred + (size_t)bb * kNRed + warp) : 0.0;
+                for (int k = 0; k < 5; ++k) {
+                    const int bb = lane + 32 * k;
+                    v5[k] = 0.0;
+                    if (bb < G) {
+                        unsigned long long lo, hi;
+                        ld_tag2(ws.tsp + (size_t)bb * 2 * kNRed + 2 * warp, lo, hi);
+                        ready = ready && tag_of(lo) == tag && tag_of(hi) == tag;
+                        v5[k] = __longlong_as_double((long long)(((hi & 0xffffffffull) << 32) | (lo & 0xffffffffull)));
+                    }
+                }
+                if (__all_sync(0xffffffffu, ready)) break;
+                const bool go_on = wait_backoff(spins, t0, abort);
+                if (!__all_sync(0xffffffffu, go_on)) {      // the warp gives up together
+                    ok = false;
+                    break;
+                }
             }
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");     // acquire: the published column state
             double sacc = 0.0;
 #pragma unroll
             for (int k = 0; k < 5; ++k) sacc += v5[k];
@@ -788,7 +833,9 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
             for (int o = 16; o >= 1; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
             if (lane == 0) red_smem[warp] = sacc;
         }
+        if (!ok) s_ok = 0;
         __syncthreads();
+        if (!s_ok) break;
         if (tid == 0) {
             double tot[kNRed];
             for (int q = 0; q < kNRed; ++q) tot[q] = red_smem[q];
@@ -833,6 +880,8 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
         ws.lr[i] = R[RS_L * NL + i - r0];
     }
     for (int j = c0 + tid; j < c1; j += T) ws.v[j] = df_to_double(QV[j - c0]);
+    // rows prefetched for a pass that never came must land before the CTA exits
+    if (use_ring && tid == kConsumerThreads) ring_drain(ring, consumed, issued);
     if (tid == 0) {
         // the next launch's tags start above every tag this one may have posted
         atomicMax(ws.epoch, base + t + 3u);
