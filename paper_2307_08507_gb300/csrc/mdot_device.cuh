@@ -90,8 +90,8 @@ struct WS {
     double* blockred;                 // [G][kNRed]
     double* scratch;                  // [G][8] misc per-CTA values
     State* st;
-    // flags of the stage kernel: [2][G] evaluation tags (column partials written; initial column
-    // state published), and the tag base, which grows over the workspace's life
+    // flags of the stage kernel: [2][G] evaluation tags (column partials written; column state
+    // published), and the tag base, which grows over the workspace's life
     unsigned int* flags;
     unsigned int* epoch;
     unsigned long long* tsp;          // [G][2 kNRed] tagged per-CTA scalar partials (fp64 halves)
@@ -346,11 +346,9 @@ __device__ __forceinline__ unsigned long long tag_pack(unsigned int v, unsigned 
     return ((unsigned long long)tag << 32) | (unsigned long long)v;
 }
 __device__ __forceinline__ unsigned int tag_of(unsigned long long w) { return (unsigned int)(w >> 32); }
-// A release store: every write the thread has observed before it (including other threads'
-// writes ordered by a preceding __syncthreads) is visible to a reader that acquires the word.
-__device__ __forceinline__ void st_tag_release(unsigned long long* p, unsigned long long w)
+__device__ __forceinline__ void st_tag(unsigned long long* p, unsigned long long w)
 {
-    asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
 }
 __device__ __forceinline__ void ld_tag2(const unsigned long long* p, unsigned long long& a, unsigned long long& b)
 {

@@ -532,9 +532,9 @@ finish:
 // stage_kernel with two hand-offs per evaluation, neither through a central counter or a last
 // arriver:
 //   fcp[b]: a per-CTA flag, CTA b's column partials are written (read by every column owner);
-//   tsp[b]: CTA b's partial sums of the six scalars as tagged words (release stores), read by
-//           every CTA; acquiring them also makes CTA b's published column state visible: the
-//           committed (v, p) and the new direction s of its columns.
+//   tsp[b]: CTA b's partial sums of the six scalars as tagged words (each word is its own ready
+//           flag), read by every CTA, with fpub[b]: CTA b's column state is published (the
+//           committed (v, p) and the new direction s of its columns), awaited in parallel.
 // Each CTA reduces the G scalar partials in the same fixed order and takes the line-search /
 // PNCG decision on its own copy of the stage state, so all copies stay identical.  Every consumer
 // thread then derives the next trial's constants of its own columns from the published column
@@ -613,7 +613,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
     const float2 inv_gamma = df_from_double(1.0 / gamma);
     unsigned int* abort = &ws.st->bar.abort;
     unsigned int* fcp = ws.flags;
-    unsigned int* fpro = ws.flags + G;      // prologue: the initial column state is published
+    unsigned int* fpub = ws.flags + G;      // the column state is published (prologue included)
     // warps holding epilogue sums: rows sit in threads 0 .. nrl - 1, columns in warp 0
     const int red_warps = max(1, min((nrl + 31) / 32, T / 32));
     unsigned int t = 0;                   // evaluations of this launch so far
@@ -698,8 +698,8 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
     // tags: base + 1 for this prologue, base + 2 + t for evaluation t (flags start at 0, and every
     // tag of an earlier launch is at most its base + t + 3 <= this base)
     __syncthreads();
-    if (tid == 0) post_flag(fpro + b, base + 1u);
-    cta_wait_flags(fpro, G, base + 1u, abort, &s_ok);
+    if (tid == 0) post_flag(fpub + b, base + 1u);
+    cta_wait_flags(fpub, G, base + 1u, abort, &s_ok);
 
     for (; s_ok; ++t) {
         const unsigned int tag = base + 2u + t;
@@ -789,18 +789,21 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
         }
         __syncthreads();
         if (tid < kNRed) {
-            // the CTA's partial sum as two tagged words (release: the column state written above
-            // is visible to whoever acquires them)
+            // the CTA's partial sum as two tagged words
             double acc = 0.0;
             for (int ww = 0; ww < red_warps; ++ww) acc += red_smem[ww * kNRed + tid];
             const unsigned long long bits = (unsigned long long)__double_as_longlong(acc);
             unsigned long long* dst = ws.tsp + (size_t)b * 2 * kNRed + 2 * tid;
-            st_tag_release(dst, tag_pack((unsigned int)bits, tag));
-            st_tag_release(dst + 1, tag_pack((unsigned int)(bits >> 32), tag));
+            st_tag(dst, tag_pack((unsigned int)bits, tag));
+            st_tag(dst + 1, tag_pack((unsigned int)(bits >> 32), tag));
         }
+        // the column state written in phase B is published by a thread with nothing else to do:
+        // the release store waits for those writes, and only this thread waits with it
+        if (tid == kConsumerThreads) post_flag(fpub + b, tag);
 
         // ---------------- every CTA: the G partials in a fixed order, then the decision ----------------
         bool ok = true;
+        if (warp == kNRed) ok = wait_flags(fpub, G, tag, abort);      // acquire: the column state
         if (warp < kNRed) {
             double v5[5];
             unsigned int spins = 0;
@@ -825,7 +828,6 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
                     break;
                 }
             }
-            asm volatile("fence.acq_rel.gpu;" ::: "memory");     // acquire: the published column state
             double sacc = 0.0;
 #pragma unroll
             for (int k = 0; k < 5; ++k) sacc += v5[k];
