@@ -39,11 +39,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample-evals", type=int, default=0, help="oracle evaluations in the CPU sample")
-    ap.add_argument("--case", default="solve", choices=["solve", "dual_eval", "stage", "batch"],
+    ap.add_argument("--case", default="solve", choices=["solve", "dual_eval", "stage", "batch", "serve"],
                     help="dual_eval / stage: run only that kernel (for profiler captures)")
     ap.add_argument("--grid", type=int, default=64, help="k of the k x k grid for --case runs")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
+    ap.add_argument("--serve-count", type=int, default=600, help="requests of the replayed serving trace (0: skip)")
     return ap.parse_args()
 
 
@@ -249,6 +250,76 @@ def measure_batch(h, dev, stream, sample_single=32):
 
 
 # ---------------------------------------------------------------------------------------------
+# served form: a Poisson trace of grid-histogram requests replayed in real time
+# ---------------------------------------------------------------------------------------------
+SERVE_SEED = 5000
+SERVE_WORKSPACE = 2 << 30          # HBM budget of the server's workspace pool (bytes)
+
+
+def serving_requests(dev, count, seed=SERVE_SEED):
+    """Requests of the serving trace: k x k grid histograms (Sec. 5.1 shapes), squared-Euclidean
+    cost regenerated from the cell coordinates, target gap from the trace; inputs resident on the
+    device before the replay starts."""
+    import torch
+    import paper_2307_08507_gb300 as M
+    from paper_2307_08507_gb300 import inputs as I
+    coords = {}
+    reqs = []
+    for (ta, k, eps, sd) in I.serving_trace(count, seed):
+        if k not in coords:
+            xy = torch.from_numpy(I.coords3(I.grid_coords(k))).to(dev)
+            coords[k] = (xy, float(I.grid_cost_scale(k, "l2sq")))
+        xy, scale = coords[k]
+        r = torch.from_numpy(I.grid_histogram(k, 2 * sd)).to(dev)
+        c = torch.from_numpy(I.grid_histogram(k, 2 * sd + 1)).to(dev)
+        prob = M.make_problem(r, c, x=xy, y=xy, kind=M.COST_SQEUCLID, scale=scale, eps_target=eps)
+        reqs.append((ta, k * k, eps, prob, (r, c)))
+    return reqs
+
+
+def measure_serving(dev, count):
+    import numpy as np
+    import torch
+    import paper_2307_08507_gb300 as M
+    reqs = serving_requests(dev, count)
+    torch.cuda.synchronize()
+    srv = M.Server(SERVE_WORKSPACE)
+    lat, done_at, evals, status_ok = [], [], 0, 0
+    try:
+        # warm-up request (kernel load, first launch)
+        srv.wait(srv.submit(reqs[0][3], keep=reqs[0][4]), timeout=600)
+        pending = {}
+        i = 0
+        t0 = time.perf_counter()
+        while i < len(reqs) or pending:
+            now = time.perf_counter() - t0
+            while i < len(reqs) and reqs[i][0] <= now:
+                pending[srv.submit(reqs[i][3], keep=reqs[i][4])] = reqs[i][0]
+                i += 1
+            for tk in list(pending):
+                r = srv.poll(tk)
+                if r is not None:
+                    tn = time.perf_counter() - t0
+                    lat.append(tn - pending.pop(tk))
+                    done_at.append(tn)
+                    evals += r.evals
+                    status_ok += int(r.status == M.MDOT_OK)
+            time.sleep(0.0002)
+        span = max(done_at) - reqs[0][0]
+    finally:
+        srv.close()
+    lat = np.array(lat)
+    n = np.array([q[1] for q in reqs])
+    return {"requests": len(reqs), "offered_rate_per_s": len(reqs) / reqs[-1][0],
+            "n_range": [int(n.min()), int(n.max())], "n_median": float(np.median(n)),
+            "gaps": [1e-4, 1e-5, 1e-6, 1e-7], "workspace_bytes": SERVE_WORKSPACE,
+            "cost": "regenerated squared Euclidean (grid histograms)",
+            "problems_per_s": len(lat) / span, "latency_p50_s": float(np.percentile(lat, 50)),
+            "latency_p99_s": float(np.percentile(lat, 99)), "latency_max_s": float(lat.max()),
+            "ok": status_ok, "evals_total": int(evals), "seconds": span}
+
+
+# ---------------------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------------------
 def run_ours(args, rank, world):
@@ -349,6 +420,7 @@ def run_ours(args, rank, world):
         del Cq
 
     batch = measure_batch(h, dev, stream) if (rank == 0 and not args.no_batch) else None
+    serving = measure_serving(dev, args.serve_count) if (rank == 0 and args.serve_count > 0) else None
 
     # end to end through the public C ABI with host buffers (copies inside the timed region)
     Ch = torch.from_numpy(p.C).pin_memory().numpy()
@@ -400,6 +472,7 @@ def run_ours(args, rank, world):
                                              "round": ip.t_round_ms, "bound": ip.t_bound_ms}},
             "dual_eval": dual,
             "batched": batch,
+            "serving": serving,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_t, "unit": "s", "h2d_bytes_per_step": 4 * n * n + 16 * n,
                     "d2h_bytes_per_step": 16 * n},
@@ -427,6 +500,10 @@ def run_case(args):
     if args.case == "batch":
         stream = torch.cuda.current_stream()
         print(json.dumps(measure_batch(h, dev, stream)))
+        h.close()
+        return
+    if args.case == "serve":
+        print(json.dumps(measure_serving(dev, args.serve_count)))
         h.close()
         return
     if args.case == "dual_eval":

@@ -236,7 +236,7 @@ typedef struct mdot_result {
 } mdot_result;
 
 /* Largest n of a batched problem. */
-#define MDOT_BATCH_MAX_N 4096
+#define MDOT_BATCH_MAX_N 8192
 
 /*
  * Solve nprob independent problems (host array probs, each with device data) in one persistent
@@ -245,13 +245,40 @@ typedef struct mdot_result {
  * block-level synchronisation.  Each problem gets its own gamma schedule (from its eps_target or
  * gamma_f), potentials and line-search state; a problem's result does not depend on the rest of
  * the batch (fixed-order reductions).  Entries use the fp32 tiers (the fp64 tier is not offered
- * here).  results: host array of nprob.  prm: NULL for defaults.  Workspace (about 0.6 MiB per
+ * here).  results: host array of nprob.  prm: NULL for defaults.  Workspace (about 1.4 MiB per
  * SM) is allocated on the first call and kept by the handle.
  * Returns INVALID_ARG if any problem is malformed (nothing is solved), else MDOT_OK; per-problem
  * outcomes are in results[k].status.
  */
 mdot_status mdot_solve_batch(mdot_handle* h, int32_t nprob, const mdot_problem* probs,
                              const mdot_params* prm, mdot_result* results);
+
+/*
+ * Serving: a request loop with continuous batching (the benchmark spec pattern 5; the paper has no
+ * counterpart).  mdot_server_create starts a background worker on the current device with a
+ * workspace pool of workspace_bytes (the HBM budget): a request of size n needs
+ * 180 * ceil32(n) bytes of it (ceil32: n rounded up to a multiple of 32).  Requests are admitted in arrival order as soon as their workspace
+ * fits; each admission round is one persistent batched launch (the solver of mdot_solve_batch,
+ * one CTA per problem) on one of several streams, so work admitted while other launches run
+ * overlaps with them on the device, and a problem's workspace returns to the pool as soon as that
+ * problem finishes.  Results do not depend on what else runs (fixed-order reductions): a problem
+ * gives the same result alone and in any mix.
+ *   prm: NULL for defaults (the fp64 tier is not offered here).
+ *   submit: non-blocking; validates the problem (same rules as mdot_solve_batch, n up to
+ *     MDOT_BATCH_MAX_N) and returns a ticket.  The problem's arrays (r, c, C or x/y, u_out,
+ *     v_out) are used in place and must stay valid until poll/wait returns MDOT_OK for it.
+ *     INVALID_ARG if malformed or larger than the whole pool; MDOT_ERR_CUDA after a device failure.
+ *   poll: MDOT_OK and *out filled once the problem is solved (the ticket is then released),
+ *     MDOT_NOT_READY before, INVALID_ARG for an unknown ticket.
+ *   wait: poll that blocks up to timeout_s seconds.
+ *   destroy: finishes every queued and admitted request, then frees everything.
+ */
+typedef struct mdot_server mdot_server;
+mdot_status mdot_server_create(mdot_server** s, uint64_t workspace_bytes, const mdot_params* prm);
+mdot_status mdot_server_submit(mdot_server* s, const mdot_problem* prob, uint64_t* ticket);
+mdot_status mdot_server_poll(mdot_server* s, uint64_t ticket, mdot_result* out);
+mdot_status mdot_server_wait(mdot_server* s, uint64_t ticket, double timeout_s, mdot_result* out);
+mdot_status mdot_server_destroy(mdot_server* s);
 
 /*
  * mdot_solve with every array in HOST memory: copies r, c (n doubles) and C (n*n floats) to the

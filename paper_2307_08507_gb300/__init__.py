@@ -299,7 +299,7 @@ def dual_eval_noalloc(u, v, gamma: float, C, log_rP, log_cP, ref_log_rP=None, st
                                     ct.c_void_p(stream.cuda_stream))
 
 
-BATCH_MAX_N = 4096
+BATCH_MAX_N = 8192
 
 
 class Problem(ct.Structure):
@@ -365,3 +365,77 @@ def _solve_batch(self, problems, params: Params | None = None):
 
 
 Handle.solve_batch = _solve_batch
+
+
+MDOT_NOT_READY = 7
+
+
+def _server_lib():
+    L = lib()
+    if not hasattr(L, "_server_typed"):
+        L.mdot_server_create.argtypes = [ct.POINTER(_P), ct.c_uint64, ct.POINTER(Params)]
+        L.mdot_server_submit.argtypes = [_P, ct.POINTER(Problem), ct.POINTER(ct.c_uint64)]
+        L.mdot_server_poll.argtypes = [_P, ct.c_uint64, ct.POINTER(Result)]
+        L.mdot_server_wait.argtypes = [_P, ct.c_uint64, ct.c_double, ct.POINTER(Result)]
+        L.mdot_server_destroy.argtypes = [_P]
+        for name in ("mdot_server_create", "mdot_server_submit", "mdot_server_poll", "mdot_server_wait",
+                     "mdot_server_destroy"):
+            getattr(L, name).restype = ct.c_int32
+        L._server_typed = True
+    return L
+
+
+class Server:
+    """mdot_server_*: request loop with continuous batching on the current device.
+
+    submit() takes an mdot_problem (see make_problem) and returns a ticket; the problem's tensors
+    are kept referenced here until its result has been collected (poll/wait returned it)."""
+
+    def __init__(self, workspace_bytes: int, params: Params | None = None):
+        L = _server_lib()
+        self._s = _P()
+        s = L.mdot_server_create(ct.byref(self._s), int(workspace_bytes), ct.byref(params) if params is not None else None)
+        if s != MDOT_OK:
+            raise MdotError(s, "mdot_server_create")
+        self._keep = {}
+
+    def submit(self, problem: Problem, keep=()) -> int:
+        t = ct.c_uint64(0)
+        s = _server_lib().mdot_server_submit(self._s, ct.byref(problem), ct.byref(t))
+        if s != MDOT_OK:
+            raise MdotError(s, "mdot_server_submit")
+        self._keep[t.value] = (problem, keep)
+        return t.value
+
+    def poll(self, ticket: int):
+        """Result once solved, else None."""
+        r = Result()
+        s = _server_lib().mdot_server_poll(self._s, int(ticket), ct.byref(r))
+        if s == MDOT_NOT_READY:
+            return None
+        if s != MDOT_OK:
+            raise MdotError(s, "mdot_server_poll")
+        self._keep.pop(int(ticket), None)
+        return r
+
+    def wait(self, ticket: int, timeout: float = 60.0):
+        r = Result()
+        s = _server_lib().mdot_server_wait(self._s, int(ticket), float(timeout), ct.byref(r))
+        if s == MDOT_NOT_READY:
+            return None
+        if s != MDOT_OK:
+            raise MdotError(s, "mdot_server_wait")
+        self._keep.pop(int(ticket), None)
+        return r
+
+    def close(self):
+        if getattr(self, "_s", None):
+            _server_lib().mdot_server_destroy(self._s)
+            self._s = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -11,8 +11,9 @@
 
 namespace mdot {
 
-constexpr int kBatchMaxN = 4096;
+constexpr int kBatchMaxN = 8192;
 constexpr int kBatchThreads = 256;
+constexpr int kRowChunk = 4096;        // rows whose per-warp partial sums sit in shared memory at once
 
 struct BatchProblem {
     int n, kind;               // size, CostKind
@@ -22,7 +23,16 @@ struct BatchProblem {
     const double *r, *c;
     const float *C, *X, *Y;
     double *u_out, *v_out;     // nullable
+    double* slot;              // nullable: this problem's workspace (else the CTA's slot)
+    int slot_stride;           // vector stride of that workspace (>= n), see batch_slot_doubles
+    int pad2;
 };
+
+// Doubles of a workspace whose vectors have the given stride (18 fp64 and 7 fp32/int32 vectors).
+__host__ __device__ inline size_t batch_slot_doubles(int stride)
+{
+    return (size_t)19 * stride + ((size_t)7 * stride + 1) / 2;
+}
 
 struct BatchResult {
     int status, stages;
@@ -37,6 +47,7 @@ struct BatchArgs {
     BatchResult* results;
     const int* order;          // solve order (indices into probs)
     unsigned int* next;        // work-queue counter (zeroed by the host)
+    int* done;                 // nullable: done[i] = 1 once results[i] is written (may be host memory)
     double* slots;             // per-CTA workspace, slot_doubles each
     size_t slot_doubles;
     // parameters of Alg. 1 / App. B
@@ -44,47 +55,72 @@ struct BatchArgs {
     int ls_max_trials, max_iter, warm_start, precision;
 };
 
-// per-CTA slot layout (doubles, kBatchMaxN each): 17 fp64 vectors, then fp32 vectors
+// slot layout (vectors of `stride` elements): 18 fp64 vectors, then 7 fp32 / int32 vectors
 enum SlotVec { SV_U = 0, SV_V, SV_PU, SV_PV, SV_UP, SV_VP, SV_GR, SV_GC, SV_RT, SV_CT, SV_GRT, SV_GCT,
-               SV_SRT, SV_SCT, SV_LR, SV_Y, SV_EC, SV_COUNT };
-constexpr size_t kSlotF32Vecs = 3;    // Hh, Wc, column sums
-constexpr size_t kSlotDoubles = (size_t)SV_COUNT * kBatchMaxN + (kSlotF32Vecs * kBatchMaxN + 1) / 2;
+               SV_SRT, SV_SCT, SV_LR, SV_Y, SV_EC, SV_RS, SV_COUNT };
+enum SlotF32 { SF_HH = 0, SF_WC, SF_COL, SF_FH, SF_WR, SF_S, SF_A, SF_COUNT };
+static_assert(SV_COUNT <= 19 && SF_COUNT <= 7, "batch_slot_doubles covers the slot layout");
+constexpr size_t kSlotDoubles = (size_t)SV_COUNT * kBatchMaxN + ((size_t)SF_COUNT * kBatchMaxN + 1) / 2;
 
 struct BatchSmem {
-    size_t off_row, off_fh, off_wr, off_s, off_A, bytes;
+    size_t off_row, bytes;
 };
 
 __host__ __device__ inline BatchSmem batch_smem()
 {
     BatchSmem L;
-    size_t o = 0;
-    L.off_row = o; o += (size_t)(kBatchThreads / 32) * kBatchMaxN * 4;
-    L.off_fh = o;  o += (size_t)kBatchMaxN * 4;
-    L.off_wr = o;  o += (size_t)kBatchMaxN * 4;
-    L.off_s = o;   o += (size_t)kBatchMaxN * 4;
-    L.off_A = o;   o += (size_t)kBatchMaxN * 4;
-    L.bytes = o;
+    L.off_row = 0;
+    L.bytes = (size_t)(kBatchThreads / 32) * kRowChunk * 4;     // per-warp row partials of one chunk
     return L;
 }
 
-// One pass over all n rows (the CTA owns the whole problem): row sums into sRow[warp][row],
-// complete column sums into colsum.
+// Column partials of a row chunk added to the sums of the earlier chunks (the same thread owns
+// column j in every chunk, so the order is fixed).
+struct ColAccum {
+    const float* Hh;
+    const float* Wc;
+    float* out;
+    bool first;
+    __device__ __forceinline__ bool load4(int j0, int n, float hh[4], float wc[4]) const
+    {
+        return ColPlain{Hh, Wc, out}.load4(j0, n, hh, wc);
+    }
+    __device__ __forceinline__ void store4(int j0, int n, const float ca[4]) const
+    {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (j0 + e < n) out[j0 + e] = first ? ca[e] : out[j0 + e] + ca[e];
+    }
+};
+
+// One pass over all n rows (the CTA owns the whole problem), in chunks of kRowChunk rows: the
+// fp64 row sums (relative to 2^{A_i}) go to rowsum, the complete column sums to colsum.
 template <bool ACC, int COST>
 __device__ __forceinline__ void batch_pass(const BatchProblem& P, const float* Hh, const float* Wc,
-                                           const float* sFh, const float* sWr, const float* sS,
-                                           float G32, float Glo, float* sRow, float* colsum)
+                                           const float* Fh, const float* Wr, const float* S,
+                                           float G32, float Glo, float* sRow, float* colsum, double* rowsum)
 {
     const int n = P.n, nw = blockDim.x >> 5;
-    for (int x = threadIdx.x; x < nw * n; x += blockDim.x) sRow[x] = 0.0f;
-    __syncthreads();
-    const ColPlain io{Hh, Wc, colsum};
-    if (COST != COST_DENSE)
-        pass_f32_regen<ACC, COST>(P.Y, P.scale, n, 0, n, io, sFh, sWr, sS, P.X, G32, Glo, sRow, n);
-    else if ((n & 3) == 0 && (reinterpret_cast<uintptr_t>(P.C) & 15) == 0)
-        pass_f32<true, ACC>(P.C, n, 0, n, io, sFh, sWr, sS, G32, Glo, sRow, n);
-    else
-        pass_f32<false, ACC>(P.C, n, 0, n, io, sFh, sWr, sS, G32, Glo, sRow, n);
-    __syncthreads();
+    for (int r0 = 0; r0 < n; r0 += kRowChunk) {
+        const int r1 = min(n, r0 + kRowChunk), nc = r1 - r0;
+        for (int x = threadIdx.x; x < nw * nc; x += blockDim.x) sRow[x] = 0.0f;
+        __syncthreads();
+        const ColAccum io{Hh, Wc, colsum, r0 == 0};
+        if (COST != COST_DENSE)
+            pass_f32_regen<ACC, COST>(P.Y, P.scale, n, r0, r1, io, Fh + r0, Wr + r0, S + r0, P.X + 3 * (size_t)r0,
+                                      G32, Glo, sRow, nc);
+        else if ((n & 3) == 0 && (reinterpret_cast<uintptr_t>(P.C) & 15) == 0)
+            pass_f32<true, ACC>(P.C, n, r0, r1, io, Fh + r0, Wr + r0, S + r0, G32, Glo, sRow, nc);
+        else
+            pass_f32<false, ACC>(P.C, n, r0, r1, io, Fh + r0, Wr + r0, S + r0, G32, Glo, sRow, nc);
+        __syncthreads();
+        for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += (double)sRow[w * nc + (i - r0)];
+            rowsum[i] = t;
+        }
+        __syncthreads();
+    }
 }
 
 template <int COST>
@@ -94,14 +130,6 @@ __device__ __forceinline__ float batch_cost(const BatchProblem& P, int i, int j)
     return point_cost<COST>(__ldg(P.X + 3 * (size_t)i), __ldg(P.X + 3 * (size_t)i + 1), __ldg(P.X + 3 * (size_t)i + 2),
                             __ldg(P.Y + 3 * (size_t)j), __ldg(P.Y + 3 * (size_t)j + 1), __ldg(P.Y + 3 * (size_t)j + 2),
                             P.scale);
-}
-
-__device__ __forceinline__ float batch_row_total(const float* sRow, int nw, int n, int i, double& out)
-{
-    double s = 0.0;
-    for (int w = 0; w < nw; ++w) s += (double)sRow[w * n + i];
-    out = s;
-    return (float)s;
 }
 
 // Per-row constants of an evaluation at ua with row scale A (fp32 tiers).
@@ -126,17 +154,8 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a)
     __shared__ int s_prob;
     const BatchSmem L = batch_smem();
     float* sRow = reinterpret_cast<float*>(sm + L.off_row);
-    float* sFh = reinterpret_cast<float*>(sm + L.off_fh);
-    float* sWr = reinterpret_cast<float*>(sm + L.off_wr);
-    float* sS = reinterpret_cast<float*>(sm + L.off_s);
-    int* sA = reinterpret_cast<int*>(sm + L.off_A);
     const int tid = threadIdx.x, T = blockDim.x, nw = T >> 5, lane = tid & 31, warp = tid >> 5;
-    double* slot = a.slots + (size_t)blockIdx.x * a.slot_doubles;
-    double* V[SV_COUNT];
-    for (int k = 0; k < SV_COUNT; ++k) V[k] = slot + (size_t)k * kBatchMaxN;
-    float* Hh = reinterpret_cast<float*>(slot + (size_t)SV_COUNT * kBatchMaxN);
-    float* Wc = Hh + kBatchMaxN;
-    float* colsum = Wc + kBatchMaxN;
+    double* const cta_slot = a.slots + (size_t)blockIdx.x * a.slot_doubles;
 
     for (;;) {
         if (tid == 0) s_prob = (int)atomicAdd(a.next, 1u);
@@ -147,6 +166,19 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a)
         const int pi = a.order[pidx];
         const BatchProblem P = a.probs[pi];
         const int n = P.n;
+        // workspace: the problem's own slot if it has one, else this CTA's
+        double* slot = P.slot ? P.slot : cta_slot;
+        const size_t sd = P.slot ? (size_t)P.slot_stride : (size_t)kBatchMaxN;
+        double* V[SV_COUNT];
+        for (int k = 0; k < SV_COUNT; ++k) V[k] = slot + (size_t)k * sd;
+        float* F32 = reinterpret_cast<float*>(slot + (size_t)SV_COUNT * sd);
+        float* Hh = F32 + (size_t)SF_HH * sd;
+        float* Wc = F32 + (size_t)SF_WC * sd;
+        float* colsum = F32 + (size_t)SF_COL * sd;
+        float* sFh = F32 + (size_t)SF_FH * sd;      // per-row constants (read through L1)
+        float* sWr = F32 + (size_t)SF_WR * sd;
+        float* sS = F32 + (size_t)SF_S * sd;
+        int* sA = reinterpret_cast<int*>(F32 + (size_t)SF_A * sd);
         BatchResult res;
         memset(&res, 0, sizeof(res));
 
@@ -183,6 +215,10 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a)
             if (tid == 0) {
                 res.status = ST_NUMERIC + 10;          // invalid problem
                 a.results[pi] = res;
+                if (a.done) {
+                    __threadfence_system();
+                    reinterpret_cast<volatile int*>(a.done)[pi] = 1;
+                }
             }
             __syncthreads();
             continue;
@@ -239,13 +275,12 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a)
             }
             __syncthreads();
             for (;;) {
-                if (acc) batch_pass<true, COST>(P, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, colsum);
-                else     batch_pass<false, COST>(P, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, colsum);
+                if (acc) batch_pass<true, COST>(P, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, colsum, V[SV_RS]);
+                else     batch_pass<false, COST>(P, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, colsum, V[SV_RS]);
 #pragma unroll
                 for (int q = 0; q < kNRed; ++q) x[q] = 0.0;
                 for (int i = tid; i < n; i += T) {
-                    double sum;
-                    batch_row_total(sRow, nw, n, i, sum);
+                    const double sum = V[SV_RS][i];
                     if (!(sum > 0.0) || !isfinite(sum)) { x[5] += 1.0; continue; }
                     const double rt = V[SV_RT][i];
                     const double g = ldexp(sum, sA[i]) - rt;
@@ -331,17 +366,15 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a)
             }
             __syncthreads();
             // r(P) and x = min(r / r(P), 1); the column pass then weights row i by x_i 2^{A_i}
-            batch_pass<true, COST>(P, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, colsum);
+            batch_pass<true, COST>(P, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, colsum, V[SV_RS]);
             for (int i = tid; i < n; i += T) {
-                double sum;
-                batch_row_total(sRow, nw, n, i, sum);
-                const double rP = ldexp(sum, sA[i]);
+                const double rP = ldexp(V[SV_RS][i], sA[i]);
                 const double xi = (rP > 0.0) ? fmin(P.r[i] / rP, 1.0) : 1.0;
                 V[SV_GRT][i] = xi;
                 sS[i] = (float)ldexp(xi, sA[i]);
             }
             __syncthreads();
-            batch_pass<true, COST>(P, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, colsum);   // colsum = c(F)
+            batch_pass<true, COST>(P, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, colsum, V[SV_RS]);   // colsum = c(F)
             for (int j = tid; j < n; j += T) {
                 const double cF = (double)colsum[j];
                 const double yj = (cF > 0.0) ? fmin(P.c[j] / cF, 1.0) : 1.0;
@@ -413,6 +446,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a)
             if (P.u_out) P.u_out[i] = V[SV_U][i];
             if (P.v_out) P.v_out[i] = V[SV_V][i];
         }
+        __syncthreads();           // every output is written before the result (and done flag)
         if (tid == 0) {
             res.status = st.status;
             res.stages = stages;
@@ -423,6 +457,10 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a)
             res.H_min = H;
             res.stalls = st.stalls;
             a.results[pi] = res;
+            if (a.done) {
+                __threadfence_system();
+                reinterpret_cast<volatile int*>(a.done)[pi] = 1;
+            }
         }
         __syncthreads();
     }

@@ -218,6 +218,15 @@ mdot_status mdot_destroy(mdot_handle* h)
 
 }  // extern "C"
 
+namespace mdot {
+
+// Shared with the serving runtime (server.cu).
+mdot_status params_valid(const mdot_params& P);
+mdot_status status_of(int st);
+void set_last_error(const char* msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
+
+}  // namespace mdot
+
 namespace {
 
 mdot_status params_ok(const mdot_params& P)
@@ -240,6 +249,15 @@ mdot_status map_status(int st)
     default: return MDOT_ERR_TIMEOUT;
     }
 }
+
+}  // namespace
+
+namespace mdot {
+mdot_status params_valid(const mdot_params& P) { return params_ok(P); }
+mdot_status status_of(int st) { return map_status(st); }
+}  // namespace mdot
+
+namespace {
 
 // Optional per-launch timing with CUDA events on the handle's stream.
 struct Timer {

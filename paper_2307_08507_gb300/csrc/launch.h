@@ -7,6 +7,8 @@
 
 namespace mdot {
 
+struct BatchArgs;
+
 size_t stage_smem_bytes(int n, int G, int tier);
 size_t round_smem_bytes(int n, int G);
 size_t lb_smem_bytes(int n, int G);
@@ -19,5 +21,9 @@ cudaError_t launch_dual_eval(int tier, const WS& ws, const EvalArgs& a, cudaStre
 cudaError_t launch_round(const WS& ws, const RoundArgs& a, cudaStream_t s);
 cudaError_t launch_lower_bound(const WS& ws, const LbArgs& a, cudaStream_t s);
 cudaError_t launch_validate(const WS& ws, double* out, cudaStream_t s);
+
+// batched solver (k_batch.cu)
+cudaError_t configure_batch_kernels(int* blocks_per_sm);
+cudaError_t launch_batch(int kind, int grid, const BatchArgs& a, cudaStream_t s);
 
 }  // namespace mdot

@@ -147,10 +147,11 @@ def batch_sizes(count: int, seed: int, lo: int = 256, hi: int = 4096) -> np.ndar
 def serving_trace(count: int, seed: int, rate: float = 200.0, n_lo: int = 128, n_hi: int = 8192,
                   gaps=(1e-4, 1e-5, 1e-6, 1e-7)):
     """Poisson arrivals (mean `rate`/s); n log-uniform on [n_lo, n_hi] rounded to the nearest
-    square grid k*k; target gap uniform over `gaps`.  Returns a list of (t_arrival, k, eps, seed)."""
+    square grid k*k (k*k <= n_hi); target gap uniform over `gaps`.  Returns a list of
+    (t_arrival, k, eps, seed)."""
     rng = rng_for(seed)
     t = np.cumsum(rng.exponential(1.0 / rate, size=count))
     n = np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), size=count))
-    k = np.maximum(2, np.rint(np.sqrt(n))).astype(int)
+    k = np.clip(np.rint(np.sqrt(n)), 2, math.isqrt(n_hi)).astype(int)      # n = k^2 stays <= n_hi
     eps = rng.choice(np.asarray(gaps), size=count)
     return [(float(t[i]), int(k[i]), float(eps[i]), int(seed * 100000 + i)) for i in range(count)]

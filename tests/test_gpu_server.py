@@ -1,0 +1,115 @@
+"""Serving runtime (mdot_server_*): continuous batching of requests on one GPU.  A request's
+result equals the batched solver's on the same problem bit for bit, whether it runs alone or in
+a stream of other requests; requests above n = 4096 (row sums in chunks) match the cooperative
+single-problem solver; tickets and malformed requests behave as documented."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2307_08507_gb300 as M
+from paper_2307_08507_gb300 import inputs as I
+
+pytestmark = [pytest.mark.gpu, pytest.mark.timeout(900)]
+DEV = "cuda:0"
+
+
+def t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def grid_request(k, seed, eps=None, gamma_f=0.0):
+    """k x k grid histograms, squared-Euclidean cost regenerated from the cell coordinates."""
+    p = I.grid_problem(k, seed, dense=False)
+    xy = I.coords3(p.x)
+    d = {"r": t(p.r), "c": t(p.c), "x": t(xy), "y": t(xy.copy()),
+         "u": torch.empty(p.n, dtype=torch.float64, device=DEV), "v": torch.empty(p.n, dtype=torch.float64, device=DEV)}
+    prob = M.make_problem(d["r"], d["c"], x=d["x"], y=d["y"], kind=M.COST_SQEUCLID, scale=p.scale,
+                          eps_target=eps or 1e-4, gamma_f=gamma_f, u_out=d["u"], v_out=d["v"])
+    return p, d, prob
+
+
+@pytest.fixture(scope="module")
+def h():
+    torch.cuda.set_device(0)
+    with M.Handle(8192) as handle:
+        yield handle
+
+
+def test_server_matches_batch_alone_and_in_a_stream(h):
+    gf = 2.0 ** 10
+    ks = [12, 40, 9, 23, 31, 16, 50, 20, 11, 27]
+    target = 4
+    reqs = [grid_request(k, 7000 + i, gamma_f=gf) for i, k in enumerate(ks)]
+    ref = h.solve_batch([grid_request(ks[target], 7000 + target, gamma_f=gf)[2]])[0]
+    assert ref.status == M.MDOT_OK
+    srv = M.Server(256 << 20)
+    try:
+        # alone
+        p, d, prob = grid_request(ks[target], 7000 + target, gamma_f=gf)
+        alone = srv.wait(srv.submit(prob, keep=(d,)), timeout=120)
+        assert alone is not None and alone.status == M.MDOT_OK
+        # in a stream: submitted one by one while the earlier ones run
+        tickets = []
+        for _, dd, pr in reqs:
+            tickets.append(srv.submit(pr, keep=(dd,)))
+            time.sleep(0.002)
+        results = [srv.wait(tk, timeout=300) for tk in tickets]
+    finally:
+        srv.close()
+    for r in results:
+        assert r is not None and r.status == M.MDOT_OK
+    m = results[target]
+    for a in (alone, m):
+        assert (a.cost, a.lower_bound, a.evals, a.iters, a.stages) == (ref.cost, ref.lower_bound, ref.evals,
+                                                                       ref.iters, ref.stages)
+    assert torch.equal(reqs[target][1]["u"], d["u"]) and torch.equal(reqs[target][1]["v"], d["v"])
+
+
+def test_server_admits_within_a_small_budget():
+    """A pool that holds about two requests still serves a queue of eight, in order."""
+    reqs = [grid_request(k, 7100 + i, gamma_f=2.0 ** 8) for i, k in enumerate([30, 28, 26, 24, 22, 20, 18, 16])]
+    per = 180 * 928          # workspace of one n = 900 request (180 bytes per padded element)
+    srv = M.Server(2 * per + 4096)
+    try:
+        tickets = [srv.submit(pr, keep=(dd,)) for _, dd, pr in reqs]
+        results = [srv.wait(tk, timeout=300) for tk in tickets]
+    finally:
+        srv.close()
+    assert all(r is not None and r.status == M.MDOT_OK for r in results)
+
+
+def test_batch_above_4096_matches_single_solver(h):
+    """n = 5041 (71 x 71 grid, row sums in two chunks): batched result against the cooperative
+    solver on the same problem, within max(1e-7, eps_d) (both stop inside eps_d / 2)."""
+    gf = 2.0 ** 11
+    p, d, prob = grid_request(71, 7200, gamma_f=gf)
+    r = h.solve_batch([prob])[0]
+    assert r.status == M.MDOT_OK
+    prm = M.default_params(gamma_f=gf)
+    _, _, s = h.solve_points(d["r"], d["c"], d["x"], d["y"], M.COST_SQEUCLID, p.scale, 1e-6, prm)
+    eps_d = r.H_min / gf ** 1.5
+    assert abs(r.cost - s.cost) <= max(1e-7, eps_d), (r.cost, s.cost)
+
+
+def test_server_tickets_and_malformed_requests():
+    srv = M.Server(64 << 20)
+    try:
+        p, d, prob = grid_request(8, 7300, gamma_f=2.0 ** 6)
+        bad = M.make_problem(d["r"], d["c"], x=d["x"], y=d["y"], kind=M.COST_SQEUCLID, scale=-1.0, gamma_f=64.0)
+        with pytest.raises(M.MdotError):
+            srv.submit(bad)
+        big = M.Problem()
+        big.n = M.BATCH_MAX_N + 1
+        with pytest.raises(M.MdotError):
+            srv.submit(big)
+        with pytest.raises(M.MdotError):
+            srv.poll(123456789)
+        tk = srv.submit(prob, keep=(d,))
+        r = srv.wait(tk, timeout=120)
+        assert r is not None and r.status == M.MDOT_OK
+        with pytest.raises(M.MdotError):     # the ticket is released once collected
+            srv.poll(tk)
+    finally:
+        srv.close()
