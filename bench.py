@@ -59,6 +59,18 @@ def golden_case(kind="l2sq"):
     return None
 
 
+def exact_value(kind="l2sq"):
+    """Exact OT value of the benchmark instance (column generation, tests/golden/make_golden.py)."""
+    path = os.path.join(ROOT, "tests", "golden", f"exact{N_GRID * N_GRID}.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        for c in json.load(fh)["cases"]:
+            if c["kind"] == kind and c["seed"] == SEED and c.get("exact_ot") is not None:
+                return c["exact_ot"]
+    return None
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -439,7 +451,8 @@ def run_ours(args, rank, world):
     e2e_t = sum(e2e) / len(e2e)
 
     g = golden_case()
-    true_gap = (res.cost - g["exact_ot"]) if g else None
+    exact = exact_value()
+    true_gap = (res.cost - exact) if exact is not None else None
     cpu = None
     if rank == 0 and world == 1:
         n_evals = args.cpu_sample_evals or 40
