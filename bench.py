@@ -296,7 +296,7 @@ def measure_serving(dev, count):
     reqs = serving_requests(dev, count)
     torch.cuda.synchronize()
     srv = M.Server(SERVE_WORKSPACE)
-    lat, done_at, evals, status_ok = [], [], 0, 0
+    lat, done_at, evals, status_ok, statuses, big_lat = [], [], 0, 0, {}, []
     try:
         # warm-up request (kernel load, first launch)
         srv.wait(srv.submit(reqs[0][3], keep=reqs[0][4]), timeout=600)
@@ -306,16 +306,21 @@ def measure_serving(dev, count):
         while i < len(reqs) or pending:
             now = time.perf_counter() - t0
             while i < len(reqs) and reqs[i][0] <= now:
-                pending[srv.submit(reqs[i][3], keep=reqs[i][4])] = reqs[i][0]
+                pending[srv.submit(reqs[i][3], keep=reqs[i][4])] = (reqs[i][0], reqs[i][1])
                 i += 1
             for tk in list(pending):
                 r = srv.poll(tk)
                 if r is not None:
                     tn = time.perf_counter() - t0
-                    lat.append(tn - pending.pop(tk))
+                    ta, nq = pending.pop(tk)
+                    lat.append(tn - ta)
+                    if nq > 2048:
+                        big_lat.append(tn - ta)
                     done_at.append(tn)
                     evals += r.evals
                     status_ok += int(r.status == M.MDOT_OK)
+                    key = M.status_string(r.status)
+                    statuses[key] = statuses.get(key, 0) + 1
             time.sleep(0.0002)
         span = max(done_at) - reqs[0][0]
     finally:
@@ -328,7 +333,8 @@ def measure_serving(dev, count):
             "cost": "regenerated squared Euclidean (grid histograms)",
             "problems_per_s": len(lat) / span, "latency_p50_s": float(np.percentile(lat, 50)),
             "latency_p99_s": float(np.percentile(lat, 99)), "latency_max_s": float(lat.max()),
-            "ok": status_ok, "evals_total": int(evals), "seconds": span}
+            "latency_p50_n_gt_2048_s": float(np.percentile(big_lat, 50)) if big_lat else None,
+            "ok": status_ok, "statuses": statuses, "evals_total": int(evals), "seconds": span}
 
 
 # ---------------------------------------------------------------------------------------------

@@ -81,9 +81,10 @@ struct ColAccum {
     const float* Wc;
     float* out;
     bool first;
-    __device__ __forceinline__ bool load4(int j0, int n, float hh[4], float wc[4]) const
+    template <int KK>
+    __device__ __forceinline__ bool load_seg(const int (&jk)[KK], int n, float (&hh)[KK][4], float (&wc)[KK][4]) const
     {
-        return ColPlain{Hh, Wc, out}.load4(j0, n, hh, wc);
+        return ColPlain{Hh, Wc, out}.load_seg(jk, n, hh, wc);
     }
     __device__ __forceinline__ void store4(int j0, int n, const float ca[4]) const
     {

@@ -255,6 +255,19 @@ mdot_status map_status(int st)
 namespace mdot {
 mdot_status params_valid(const mdot_params& P) { return params_ok(P); }
 mdot_status status_of(int st) { return map_status(st); }
+
+// Run the handle's cooperative kernels on G CTAs instead of one per SM (the serving runtime
+// gives large requests a share of the GPU); the workspace was sized for more.
+mdot_status handle_set_grid(mdot_handle* h, int G)
+{
+    if (!h || G < 1 || G > std::min(h->sms, 160)) return MDOT_ERR_INVALID_ARG;
+    int mb = 0;
+    cudaError_t e = configure_kernels((int)h->max_n, G, &mb);
+    if (e != cudaSuccess || mb < 1) return MDOT_ERR_CUDA;
+    h->G = G;
+    h->ws.G = G;
+    return MDOT_OK;
+}
 }  // namespace mdot
 
 namespace {

@@ -2,6 +2,7 @@
 #include <algorithm>
 
 #include "batch_kernels.cuh"
+#include "launch.h"
 
 namespace mdot {
 
@@ -20,8 +21,7 @@ cudaError_t configure_batch_kernels(int* blocks_per_sm)
 {
     int mb = 1 << 30;
     for (int k = 0; k < 3; ++k) {
-        cudaError_t e = cudaFuncSetAttribute(batch_fn(k), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)batch_smem_bytes());
+        cudaError_t e = raise_smem_limit(batch_fn(k), batch_smem_bytes());
         if (e != cudaSuccess) return e;
         int nb = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_fn(k), kBatchThreads, batch_smem_bytes());

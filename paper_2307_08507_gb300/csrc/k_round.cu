@@ -68,7 +68,7 @@ cudaError_t configure_kernels(int max_n, int G, int* min_blocks_per_sm)
         {lb_fn(COST_L1), lb_smem_bytes(max_n, G)},
         {(const void*)validate_kernel, 0}};
     for (auto& k : ks) {
-        e = cudaFuncSetAttribute(k.f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
+        e = raise_smem_limit(k.f, k.smem);
         if (e != cudaSuccess) return e;
         int nb = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k.f, kThreads, k.smem);

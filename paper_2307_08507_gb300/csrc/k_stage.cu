@@ -52,7 +52,7 @@ cudaError_t configure_stage_kernels(int max_n, int G, int* min_blocks)
         {(const void*)dual_eval_kernel<TIER_F32A, COST_DENSE>, TIER_F32A}};
     for (auto& k : ks) {
         const size_t smem = stage_smem_bytes(max_n, G, k.tier);
-        cudaError_t e = cudaFuncSetAttribute(k.f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = raise_smem_limit(k.f, smem);
         if (e != cudaSuccess) return e;
         int nb = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k.f, kStageThreads, smem);

@@ -3,11 +3,26 @@
 
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "mdot_device.cuh"
 
 namespace mdot {
 
 struct BatchArgs;
+
+// Raise (never lower) a kernel's dynamic shared-memory limit: handles of different sizes, the
+// serving runtime and the no-allocation entry share the kernels of one process.
+inline cudaError_t raise_smem_limit(const void* f, size_t bytes)
+{
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, f);
+    if (e != cudaSuccess) return e;
+    if ((long long)bytes <= (long long)fa.maxDynamicSharedSizeBytes) return cudaSuccess;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
 
 size_t stage_smem_bytes(int n, int G, int tier);
 size_t round_smem_bytes(int n, int G);

@@ -378,8 +378,9 @@ __device__ __forceinline__ bool wait_backoff(unsigned int& spins, unsigned long 
 }
 
 // Column constants and column partials of one pass over C (plain arrays; a grid barrier or the
-// stage kernel's flags order them).  Other sources (e.g. constants computed in place) can supply
-// the same two calls.
+// stage kernel's flags order them).  Other sources (e.g. constants computed in place) supply the
+// same calls: load_seg (the constants of all of a thread's column groups of a segment at once, so
+// every load is in flight before any arithmetic) and store4.
 struct ColPlain {
     const float* Hh;
     const float* Wc;
@@ -395,6 +396,13 @@ struct ColPlain {
             hh[e] = ok ? __ldcg(Hh + j) : 0.0f;
             wc[e] = ok ? __ldcg(Wc + j) : kPadW;     // padding column: its entry is exactly 0
         }
+        return true;
+    }
+    template <int KK>
+    __device__ __forceinline__ bool load_seg(const int (&jk)[KK], int n, float (&hh)[KK][4], float (&wc)[KK][4]) const
+    {
+#pragma unroll
+        for (int k = 0; k < KK; ++k) load4(jk[k], n, hh[k], wc[k]);
         return true;
     }
     __device__ __forceinline__ void store4(int j0, int n, const float ca[4]) const
@@ -491,24 +499,29 @@ struct ColDerived {
     ColStep d;
     float2 inv_gamma;
     float G32, Glo;
-    __device__ __forceinline__ bool load4(int j0, int n, float hh[4], float wc[4]) const
+    template <int KK>
+    __device__ __forceinline__ bool load_seg(const int (&jk)[KK], int n, float (&hh)[KK][4], float (&wc)[KK][4]) const
     {
-        float2 v[4], p[4];
-        float sv[4];
+        float2 v[KK][4], p[KK][4];
+        float sv[KK][4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int j = j0 + e;
-            const bool ok = j < n;
-            v[e] = ok ? __ldcg(pv + j) : make_float2(0.0f, 0.0f);
-            p[e] = ok ? __ldcg(pp + j) : make_float2(0.0f, 0.0f);
-            sv[e] = ok ? __ldcg(ps + j) : 0.0f;
-        }
+        for (int k = 0; k < KK; ++k)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            col_commit(d, v[e], p[e], sv[e]);
-            col_trial(d, v[e], p[e], inv_gamma, G32, Glo, hh[e], wc[e]);
-            if (j0 + e >= n) { hh[e] = 0.0f; wc[e] = kPadW; }
-        }
+            for (int e = 0; e < 4; ++e) {
+                const int j = jk[k] + e;
+                const bool ok = j < n;
+                v[k][e] = ok ? __ldcg(pv + j) : make_float2(0.0f, 0.0f);
+                p[k][e] = ok ? __ldcg(pp + j) : make_float2(0.0f, 0.0f);
+                sv[k][e] = ok ? __ldcg(ps + j) : 0.0f;
+            }
+#pragma unroll
+        for (int k = 0; k < KK; ++k)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                col_commit(d, v[k][e], p[k][e], sv[k][e]);
+                col_trial(d, v[k][e], p[k][e], inv_gamma, G32, Glo, hh[k][e], wc[k][e]);
+                if (jk[k] + e >= n) { hh[k][e] = 0.0f; wc[k][e] = kPadW; }
+            }
         return true;
     }
     __device__ __forceinline__ void store4(int j0, int n, const float ca[4]) const
@@ -556,10 +569,10 @@ __device__ __forceinline__ void pass_f32(const float* __restrict__ C, int n, int
 #pragma unroll
         for (int k = 0; k < kK; ++k) {
             jk[k] = cb + 4 * (tid + k * T);
-            io.load4(jk[k], n, hh[k], wc[k]);
 #pragma unroll
             for (int e = 0; e < 4; ++e) ca[k][e] = 0.0f;
         }
+        io.load_seg(jk, n, hh, wc);
         for (int rg = r0; rg < r1; rg += kRG) {
             float rp[kRG];
 #pragma unroll
@@ -780,12 +793,12 @@ __device__ __forceinline__ void pass_f32_tma(const float* __restrict__ C, int n,
 #pragma unroll
             for (int k = 0; k < kK; ++k) {
                 jk[k] = cb + 4 * (tid + k * kConsumerThreads);
-                // a constant that never arrives (timeout) turns this consumer into a pass-through:
-                // it still releases every ring slot so that the producer can finish
-                if (!io.load4(jk[k], n, hh[k], wc[k])) ok = false;
 #pragma unroll
                 for (int e = 0; e < 4; ++e) ca[k][e] = 0.0f;
             }
+            // a constant that never arrives (timeout) turns this consumer into a pass-through: it
+            // still releases every ring slot so that the producer can finish
+            if (!io.load_seg(jk, n, hh, wc)) ok = false;
             for (int rg = r0; rg < r1; rg += kRG) {
                 float rp[kRG];
 #pragma unroll
@@ -925,14 +938,16 @@ __device__ __forceinline__ void pass_f32_ring(const RingGeom& g, int r1, const I
 #pragma unroll
             for (int k = 0; k < kK; ++k) {
                 jk[k] = cb + 4 * (tid + k * kConsumerThreads);
-                if (pre_hh != nullptr && cbi == 0) {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) { hh[k][e] = pre_hh[k][e]; wc[k][e] = pre_wc[k][e]; }
-                } else {
-                    io.load4(jk[k], n, hh[k], wc[k]);
-                }
 #pragma unroll
                 for (int e = 0; e < 4; ++e) ca[k][e] = 0.0f;
+            }
+            if (pre_hh != nullptr && cbi == 0) {
+#pragma unroll
+                for (int k = 0; k < kK; ++k)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) { hh[k][e] = pre_hh[k][e]; wc[k][e] = pre_wc[k][e]; }
+            } else {
+                io.load_seg(jk, n, hh, wc);
             }
             for (int rg = r0; rg < r1; rg += kRG) {
                 float rp[kRG];
@@ -999,9 +1014,10 @@ __device__ __forceinline__ void pass_f32_regen(const float* __restrict__ Y, floa
         float hh[KR][4], wc[KR][4], ca[KR][4], y0[KR][4], y1[KR][4], y2[KR][4];
         int jk[KR];
 #pragma unroll
+        for (int k = 0; k < KR; ++k) jk[k] = cb + 4 * (tid + k * T);
+        io.load_seg(jk, n, hh, wc);
+#pragma unroll
         for (int k = 0; k < KR; ++k) {
-            jk[k] = cb + 4 * (tid + k * T);
-            io.load4(jk[k], n, hh[k], wc[k]);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int j = jk[k] + e;

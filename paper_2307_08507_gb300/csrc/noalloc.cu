@@ -8,6 +8,7 @@
 #include <mutex>
 
 #include "mdot.h"
+#include "launch.h"
 #include "solver_kernels.cuh"
 
 namespace {
@@ -59,8 +60,7 @@ cudaError_t setup_device(int dev, DeviceSetup** out)
         if (e != cudaSuccess) return e;
         const int G = std::min(sms, kMaxG);
         const size_t smem = smem_layout(kMaxN, G, TIER_F32, kStageThreads).bytes;
-        e = cudaFuncSetAttribute((const void*)dual_eval_kernel<TIER_F32, COST_DENSE>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = raise_smem_limit((const void*)dual_eval_kernel<TIER_F32, COST_DENSE>, smem);
         if (e != cudaSuccess) return e;
         int nb = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)dual_eval_kernel<TIER_F32, COST_DENSE>,

@@ -1,10 +1,14 @@
 // Serving runtime (declared in include/mdot.h): a request loop with continuous batching on one
-// GPU.  Requests are admitted in arrival order as soon as their workspace fits the pool (the
-// HBM budget given at creation); every admission round becomes one persistent batched launch
-// (one CTA per problem, the solver of batch_kernels.cuh) on one of a few streams, so launches
-// admitted while others still run overlap on the device and take SMs as earlier problems finish.
-// Each problem reports completion through a flag in mapped host memory, so its workspace returns
-// to the pool (and the next request is admitted) without waiting for the rest of its launch.
+// GPU.  Requests up to kBigN are admitted in arrival order as soon as their workspace fits the
+// pool (the HBM budget given at creation); every admission round becomes one persistent batched
+// launch (one CTA per problem, the solver of batch_kernels.cuh) on one of a few streams, so
+// launches admitted while others still run overlap on the device and take SMs as earlier problems
+// finish.  Each problem reports completion through a flag in mapped host memory, so its workspace
+// returns to the pool (and the next request is admitted) without waiting for the rest of its
+// launch.  Larger requests would hold one SM for a long time; they go to a few "big lanes", each
+// a cooperative solve (the stage kernels of the single-problem solver) on a share of the SMs.
+// The SMs are partitioned so that every resident CTA fits at once: batched problems in flight
+// <= SMs - lanes x CTAs per lane.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -12,6 +16,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -38,6 +43,9 @@ constexpr int kLanes = 4;            // streams the launches rotate over
 constexpr int kRecords = 32;         // launches in flight at most
 constexpr int kRecordCap = 256;      // problems per launch at most
 constexpr int kStrideAlign = 32;     // workspace vector stride granularity (elements)
+constexpr int64_t kBigN = 2048;      // larger requests are solved by a big lane
+constexpr int kBigLanes = 2;         // concurrent cooperative solves
+constexpr int kBigShare = 4;         // each big lane runs on SMs / kBigShare CTAs
 
 // First-fit allocator over the workspace pool (offsets and lengths in doubles).
 struct Pool {
@@ -120,7 +128,19 @@ bool problem_ok(const mdot_problem& q)
            ((q.gamma_f > 0.0 && std::isfinite(q.gamma_f)) || (q.eps_target > 0.0 && std::isfinite(q.eps_target)));
 }
 
+// A big lane: one cooperative solver handle on a share of the SMs, served by its own thread.
+struct BigLane {
+    mdot_handle* h = nullptr;
+    cudaStream_t stream = nullptr;
+    double *u = nullptr, *v = nullptr;   // potentials when the request has no output buffers
+    std::thread thread;
+};
+
 }  // namespace
+
+namespace mdot {
+mdot_status handle_set_grid(mdot_handle* h, int G);
+}
 
 struct mdot_server {
     int dev = 0;
@@ -133,7 +153,10 @@ struct mdot_server {
     std::mutex mu;
     std::condition_variable cv_work;     // wakes the worker
     std::condition_variable cv_done;     // wakes waiters
-    std::deque<Request> pending;
+    std::deque<Request> pending;         // batched route
+    std::deque<Request> big_pending;     // big lanes
+    BigLane big[kBigLanes];
+    int batch_inflight = 0, batch_cap = 0;
     std::unordered_map<uint64_t, int> state;          // 0 queued, 1 running, 2 finished
     std::unordered_map<uint64_t, mdot_result> finished;
     uint64_t next_ticket = 1;
@@ -177,6 +200,7 @@ bool collect(mdot_server* s)
             s->finished[r.ticket[i]] = to_result(b);
             s->state[r.ticket[i]] = 2;
             s->pool.release(r.off[i], r.len[i]);
+            --s->batch_inflight;
             r.reported[i] = true;
             --r.remaining;
             s->cv_done.notify_all();
@@ -199,10 +223,12 @@ cudaError_t admit(mdot_server* s)
         if (!r) return cudaSuccess;
         const int kind = s->pending.front().kind;
         int m = 0;
-        while (!s->pending.empty() && m < kRecordCap && s->pending.front().kind == kind) {
+        while (!s->pending.empty() && m < kRecordCap && s->pending.front().kind == kind &&
+               s->batch_inflight < s->batch_cap) {
             Request& q = s->pending.front();
             size_t off = 0;
             if (!s->pool.alloc(q.len, off)) break;          // strict arrival order: wait for room
+            ++s->batch_inflight;
             BatchProblem& b = r->h_probs[m];
             memset(&b, 0, sizeof(b));
             b.n = (int)q.p.n;
@@ -269,6 +295,7 @@ void fail_all(mdot_server* s)
         kv.second = 2;
     }
     s->pending.clear();
+    s->big_pending.clear();
     for (Record& r : s->rec) r.busy = false;
     s->cv_done.notify_all();
 }
@@ -295,6 +322,60 @@ void worker_loop(mdot_server* s)
         } else {
             s->cv_work.wait(lk, [&] { return s->stop || (!s->pending.empty() && s->fatal == cudaSuccess); });
         }
+    }
+}
+
+mdot_result solve_big(mdot_server* s, BigLane& L, const Request& q)
+{
+    mdot_params P = s->prm;
+    if (q.p.gamma_f > 0.0) P.gamma_f = q.p.gamma_f;
+    const double eps = q.p.eps_target > 0.0 ? q.p.eps_target : 1.0;     // unused when gamma_f is set
+    double* u = q.p.u_out ? q.p.u_out : L.u;
+    double* v = q.p.v_out ? q.p.v_out : L.v;
+    double cost = 0.0, gap = 0.0;
+    mdot_info info;
+    memset(&info, 0, sizeof(info));
+    const mdot_status st = q.p.C ? mdot_solve(L.h, q.p.r, q.p.c, q.p.C, q.p.n, eps, &P, u, v, &cost, &gap, &info)
+                                 : mdot_solve_points(L.h, q.p.r, q.p.c, q.p.x, q.p.y, q.p.cost_kind, q.p.scale, q.p.n,
+                                                     eps, &P, u, v, &cost, &gap, &info);
+    if (st == MDOT_ERR_CUDA)
+        fprintf(stderr, "mdot server: cooperative solve of n = %lld failed: %s\n", (long long)q.p.n,
+                mdot_last_error());
+    mdot_result r;
+    memset(&r, 0, sizeof(r));
+    r.status = st;
+    r.stages = info.stages;
+    r.evals = info.evals;
+    r.iters = info.iters;
+    r.cost = cost;
+    r.lower_bound = info.lower_bound;
+    r.gap_cert = gap;
+    r.grad_l1 = info.grad_l1;
+    r.gamma_f = info.gamma_f;
+    r.H_min = info.H_min;
+    return r;
+}
+
+void big_loop(mdot_server* s, int lane)
+{
+    cudaSetDevice(s->dev);
+    BigLane& L = s->big[lane];
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        s->cv_work.wait(lk, [&] { return s->stop || !s->big_pending.empty(); });
+        if (s->big_pending.empty()) {
+            if (s->stop) break;
+            continue;
+        }
+        const Request q = s->big_pending.front();
+        s->big_pending.pop_front();
+        s->state[q.ticket] = 1;
+        lk.unlock();
+        const mdot_result r = solve_big(s, L, q);
+        lk.lock();
+        s->finished[q.ticket] = r;
+        s->state[q.ticket] = 2;
+        s->cv_done.notify_all();
     }
 }
 
@@ -341,8 +422,28 @@ mdot_status mdot_server_create(mdot_server** out, uint64_t workspace_bytes, cons
         if (e == cudaSuccess) e = cudaHostGetDevicePointer(&r.d_done, r.h_done, 0);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.ev, cudaEventDisableTiming);
     }
+    int sms = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->dev);
+    const int share = std::max(1, std::min(sms, 160) / kBigShare);
+    mdot_status hs = MDOT_OK;
+    for (BigLane& L : s->big) {
+        if (e != cudaSuccess || hs != MDOT_OK) break;
+        e = cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaMalloc(&L.u, MDOT_BATCH_MAX_N * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&L.v, MDOT_BATCH_MAX_N * sizeof(double));
+        if (e == cudaSuccess) hs = mdot_create(&L.h, MDOT_BATCH_MAX_N, L.stream);
+        if (e == cudaSuccess && hs == MDOT_OK) hs = handle_set_grid(L.h, share);
+    }
+    if (e == cudaSuccess && hs != MDOT_OK) e = cudaErrorInvalidConfiguration;
+    s->batch_cap = std::max(1, sms - kBigLanes * share);
     if (e != cudaSuccess) {
         set_last_error(cudaGetErrorString(e));
+        for (BigLane& L : s->big) {
+            if (L.h) mdot_destroy(L.h);
+            cudaFree(L.u);
+            cudaFree(L.v);
+            if (L.stream) cudaStreamDestroy(L.stream);
+        }
         destroy_records(s);
         cudaFree(s->pool_mem);
         for (auto& l : s->lanes)
@@ -352,6 +453,7 @@ mdot_status mdot_server_create(mdot_server** out, uint64_t workspace_bytes, cons
     }
     s->pool.init(pool_doubles);
     s->worker = std::thread(worker_loop, s);
+    for (int i = 0; i < kBigLanes; ++i) s->big[i].thread = std::thread(big_loop, s, i);
     *out = s;
     return MDOT_OK;
 }
@@ -366,12 +468,13 @@ mdot_status mdot_server_submit(mdot_server* s, const mdot_problem* prob, uint64_
     q.len = batch_slot_doubles(q.stride);
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->fatal != cudaSuccess) return MDOT_ERR_CUDA;
-    if (q.len > s->pool.total) return MDOT_ERR_INVALID_ARG;     // could never be admitted
+    const bool big = prob->n > kBigN;
+    if (!big && q.len > s->pool.total) return MDOT_ERR_INVALID_ARG;     // could never be admitted
     q.ticket = s->next_ticket++;
     s->state[q.ticket] = 0;
-    s->pending.push_back(q);
+    (big ? s->big_pending : s->pending).push_back(q);
     *ticket = q.ticket;
-    s->cv_work.notify_one();
+    s->cv_work.notify_all();
     return MDOT_OK;
 }
 
@@ -418,6 +521,13 @@ mdot_status mdot_server_destroy(mdot_server* s)
     for (auto& l : s->lanes) {
         cudaStreamSynchronize(l);
         cudaStreamDestroy(l);
+    }
+    for (BigLane& L : s->big) {
+        if (L.thread.joinable()) L.thread.join();
+        if (L.h) mdot_destroy(L.h);
+        cudaFree(L.u);
+        cudaFree(L.v);
+        if (L.stream) cudaStreamDestroy(L.stream);
     }
     destroy_records(s);
     cudaFree(s->pool_mem);

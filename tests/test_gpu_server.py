@@ -113,3 +113,33 @@ def test_server_tickets_and_malformed_requests():
             srv.poll(tk)
     finally:
         srv.close()
+
+
+def test_big_request_same_alone_and_in_a_stream(h):
+    """Requests above 2048 go to a big lane (a cooperative solve on a share of the SMs): the same
+    result bit for bit alone and while batched requests run beside it, and within
+    max(1e-7, eps_d) of the full-GPU solver on the same problem."""
+    gf = 2.0 ** 11
+    small = [grid_request(k, 7400 + i, gamma_f=gf) for i, k in enumerate([20, 33, 14, 41, 27, 18])]
+    srv = M.Server(256 << 20)
+    try:
+        p, d, prob = grid_request(48, 7450, gamma_f=gf)            # n = 2304
+        alone = srv.wait(srv.submit(prob, keep=(d,)), timeout=300)
+        u_alone = d["u"].clone()
+        p2, d2, prob2 = grid_request(48, 7450, gamma_f=gf)
+        tickets = [srv.submit(pr, keep=(dd,)) for _, dd, pr in small[:3]]
+        tk = srv.submit(prob2, keep=(d2,))
+        tickets += [srv.submit(pr, keep=(dd,)) for _, dd, pr in small[3:]]
+        mixed = srv.wait(tk, timeout=300)
+        others = [srv.wait(x, timeout=300) for x in tickets]
+    finally:
+        srv.close()
+    assert alone is not None and mixed is not None
+    assert alone.status == M.MDOT_OK and all(o is not None and o.status == M.MDOT_OK for o in others)
+    assert (alone.cost, alone.lower_bound, alone.evals, alone.iters) == (mixed.cost, mixed.lower_bound, mixed.evals,
+                                                                         mixed.iters)
+    assert torch.equal(u_alone, d2["u"])
+    prm = M.default_params(gamma_f=gf)
+    _, _, s = h.solve_points(d["r"], d["c"], d["x"], d["y"], M.COST_SQEUCLID, p.scale, 1e-6, prm)
+    eps_d = alone.H_min / gf ** 1.5
+    assert abs(alone.cost - s.cost) <= max(1e-7, eps_d), (alone.cost, s.cost)
