@@ -71,6 +71,16 @@ def exact_value(kind="l2sq"):
     return None
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """Largest value over the ranks (the job's time is its slowest replica's)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -393,11 +403,7 @@ def run_ours(args, rank, world):
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
-    t_step = sum(times) / len(times)
-    if dist is not None:
-        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step = max_over_ranks(sum(times) / len(times), dist, dev)
     res = results[-1]
     info = res.info
 

@@ -86,7 +86,9 @@ typedef struct mdot_params {
     double  final_tol;      /* > 0: ||grad g||_1 target of the final stage instead of eps_d / 2     */
     double  fp32_floor;     /* ||grad g||_1 below which fp32 entries are not trusted; 5e-8          */
     int32_t profile;        /* non-zero: time each kernel launch with CUDA events (mdot_info t_*)    */
-    int32_t reserved[7];
+    int32_t smoothing;      /* 0: smoothing weight eps_d of the stage (Alg. 1); 1: fixed weight       */
+                            /*    H_min / gamma_f^p in every stage (the fixed-smoothing ablation)     */
+    int32_t reserved[6];
 } mdot_params;
 
 /* Diagnostics of one solve. */

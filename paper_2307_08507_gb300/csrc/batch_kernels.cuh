@@ -52,7 +52,7 @@ struct BatchArgs {
     size_t slot_doubles;
     // parameters of Alg. 1 / App. B
     double gamma_i, p, q, c1, c2, fp32_floor, final_tol;
-    int ls_max_trials, max_iter, warm_start, precision;
+    int ls_max_trials, max_iter, warm_start, precision, smoothing;
 };
 
 // slot layout (vectors of `stride` elements): 18 fp64 vectors, then 7 fp32 / int32 vectors
@@ -232,6 +232,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a)
         int stages = 0;
         for (int t = 1;; ++t) {
             const double eps_d = H / pow(gamma, a.p);
+            const double w = (a.smoothing == 1) ? H / pow(gf, a.p) : eps_d;    // smoothing weight (Alg. 1)
             double tol = fmax(eps_d / 2.0, 1e-13 + 1e-15 * gamma);
             const bool last = (gamma == gf);
             if (last && a.final_tol > 0.0) tol = a.final_tol;
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a)
             const float G32 = (float)G64, Glo = (float)(G64 - (double)G32);
             // prologue: smoothing, rank-one start or warm start (Eq. (13)), constants at alpha = 0
             for (int i = tid; i < n; i += T) {
-                const double rt = (1.0 - eps_d / 4.0) * P.r[i] + eps_d / (4.0 * n);
+                const double rt = (1.0 - w / 4.0) * P.r[i] + w / (4.0 * n);
                 const double lrt = log(rt);
                 double u = V[SV_U][i];
                 if (t == 1) { u = lrt; V[SV_UP][i] = u; }
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a)
                 batch_prep_row(u, row_scale(lrt), inv_gamma, G64, sFh, sWr, sS, sA, i);
             }
             for (int j = tid; j < n; j += T) {
-                const double ct = (1.0 - eps_d / 4.0) * P.c[j] + eps_d / (4.0 * n);
+                const double ct = (1.0 - w / 4.0) * P.c[j] + w / (4.0 * n);
                 double v = V[SV_V][j];
                 if (t == 1) { v = log(ct); V[SV_VP][j] = v; }
                 else if (a.warm_start == 0) { const double z = v; v = z + ratio * (z - V[SV_VP][j]); V[SV_VP][j] = z; }

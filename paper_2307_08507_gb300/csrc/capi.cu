@@ -234,6 +234,7 @@ mdot_status params_ok(const mdot_params& P)
     if (!(P.gamma_i > 0.0) || !(P.p >= 1.0) || !(P.q > 1.0) || !(P.ls_c1 > 0.0) ||
         !(P.ls_c2 > P.ls_c1) || !(P.ls_c2 < 1.0) || P.ls_max_trials < 1 || P.max_iter < 1 ||
         P.precision < 0 || P.precision > 3 || P.warm_start < 0 || P.warm_start > 2 ||
+        P.smoothing < 0 || P.smoothing > 1 ||
         !(P.fp32_floor >= 0.0) || !std::isfinite(P.gamma_f))
         return MDOT_ERR_INVALID_ARG;
     return MDOT_OK;
@@ -411,7 +412,8 @@ mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const C
         StageArgs a{};
         a.gamma = gamma;
         a.G64 = gamma * kLog2e;
-        a.w = eps_d;                                                       // smoothing weight
+        // smoothing weight: eps_d of the stage (Alg. 1), or fixed at its gamma_f value (ablation)
+        a.w = (P.smoothing == 1) ? H / std::pow(gf, P.p) : eps_d;
         a.ratio = ratio;
         a.c1 = P.ls_c1;
         a.c2 = P.ls_c2;
@@ -688,6 +690,7 @@ mdot_status mdot_solve_batch(mdot_handle* h, int32_t nprob, const mdot_problem* 
         a.fp32_floor = P.fp32_floor; a.final_tol = P.final_tol;
         a.ls_max_trials = P.ls_max_trials; a.max_iter = P.max_iter; a.warm_start = P.warm_start;
         a.precision = P.precision;
+        a.smoothing = P.smoothing;
         CKR(launch_batch(kind, h->b_grid, a, h->stream));
         CKR(cudaStreamSynchronize(h->stream));     // the order buffer is reused by the next form
     }

@@ -52,10 +52,13 @@ cudaError_t configure_stage_kernels(int max_n, int G, int* min_blocks)
         {(const void*)dual_eval_kernel<TIER_F32A, COST_DENSE>, TIER_F32A}};
     for (auto& k : ks) {
         const size_t smem = stage_smem_bytes(max_n, G, k.tier);
-        cudaError_t e = raise_smem_limit(k.f, smem);
+        // the limit goes to the largest layout any n may take (fewer rows per CTA leave room for
+        // more ring slots), not just to the layout of max_n
+        (void)smem;
+        cudaError_t e = raise_smem_limit(k.f, kSmemLimit);
         if (e != cudaSuccess) return e;
         int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k.f, kStageThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k.f, kStageThreads, kSmemLimit);
         if (e != cudaSuccess) return e;
         *min_blocks = std::min(*min_blocks, nb);
     }

@@ -684,7 +684,8 @@ __device__ __forceinline__ void pass_f64(const float* __restrict__ C, int n, int
 constexpr int kConsumerThreads = 256;
 constexpr int kStageThreads = kConsumerThreads + 32;    // + one producer warp
 constexpr int kStages = 12;                            // ring slots at most (fewer if smem is short)
-constexpr size_t kSmemLimit = 227 * 1024;
+constexpr size_t kSmemLimit = 223 * 1024;      // dynamic shared memory of a CTA (227 KB less room
+                                                // for the kernels' static shared memory)
 constexpr int kSegFloats = 4 * kK * kConsumerThreads;   // 4096 floats = 16 KiB per slot
 constexpr unsigned int kWaitSpins = 1u << 24;           // bounded mbarrier wait (with backoff)
 

@@ -276,6 +276,7 @@ cudaError_t admit(mdot_server* s)
         a.fp32_floor = P.fp32_floor; a.final_tol = P.final_tol;
         a.ls_max_trials = P.ls_max_trials; a.max_iter = P.max_iter; a.warm_start = P.warm_start;
         a.precision = P.precision;
+        a.smoothing = P.smoothing;
         e = launch_batch(kind, m, a, st);
         if (e == cudaSuccess) e = cudaEventRecord(r->ev, st);
         if (e != cudaSuccess) return e;
@@ -335,9 +336,17 @@ mdot_result solve_big(mdot_server* s, BigLane& L, const Request& q)
     double cost = 0.0, gap = 0.0;
     mdot_info info;
     memset(&info, 0, sizeof(info));
-    const mdot_status st = q.p.C ? mdot_solve(L.h, q.p.r, q.p.c, q.p.C, q.p.n, eps, &P, u, v, &cost, &gap, &info)
-                                 : mdot_solve_points(L.h, q.p.r, q.p.c, q.p.x, q.p.y, q.p.cost_kind, q.p.scale, q.p.n,
-                                                     eps, &P, u, v, &cost, &gap, &info);
+    // A cooperative launch is refused (not queued) while the SMs it needs are busy; the SM
+    // partition makes that rare, and the solve is then simply started again a moment later.
+    mdot_status st = MDOT_ERR_CUDA;
+    for (int attempt = 0; attempt < 2000; ++attempt) {
+        st = q.p.C ? mdot_solve(L.h, q.p.r, q.p.c, q.p.C, q.p.n, eps, &P, u, v, &cost, &gap, &info)
+                   : mdot_solve_points(L.h, q.p.r, q.p.c, q.p.x, q.p.y, q.p.cost_kind, q.p.scale, q.p.n, eps, &P, u,
+                                       v, &cost, &gap, &info);
+        if (st != MDOT_ERR_CUDA || cudaGetLastError() != cudaErrorCooperativeLaunchTooLarge) break;
+        cudaStreamSynchronize(L.stream);
+        std::this_thread::sleep_for(std::chrono::microseconds(500));
+    }
     if (st == MDOT_ERR_CUDA)
         fprintf(stderr, "mdot server: cooperative solve of n = %lld failed: %s\n", (long long)q.p.n,
                 mdot_last_error());
@@ -435,7 +444,8 @@ mdot_status mdot_server_create(mdot_server** out, uint64_t workspace_bytes, cons
         if (e == cudaSuccess && hs == MDOT_OK) hs = handle_set_grid(L.h, share);
     }
     if (e == cudaSuccess && hs != MDOT_OK) e = cudaErrorInvalidConfiguration;
-    s->batch_cap = std::max(1, sms - kBigLanes * share);
+    // a few SMs of slack: a batched CTA that has reported its problem may not have left its SM yet
+    s->batch_cap = std::max(1, sms - kBigLanes * share - 8);
     if (e != cudaSuccess) {
         set_last_error(cudaGetErrorString(e));
         for (BigLane& L : s->big) {

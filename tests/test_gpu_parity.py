@@ -197,3 +197,19 @@ def test_invalid_arguments_are_rejected(h):
     # the handle still works after rejected calls
     u, v, res = h.solve(t(p.r), t(p.c), t(p.C), 1e-5)
     assert res.status == M.MDOT_OK
+
+
+@pytest.mark.parametrize("warm_start,smoothing,prec", [(1, 0, 0), (2, 0, 0), (0, 1, 0), (1, 0, 3), (0, 1, 3)])
+def test_solve_ablation_variants_match_oracle(h, warm_start, smoothing, prec):
+    """The ablation switches of Sec. 5 (eps-scaling or no warm start instead of Eq. (13); the
+    smoothing weight fixed at its gamma_f value instead of eps_d), on the fp64 tier (n <= 512)
+    and on the accurate fp32 tier (a 30 x 30 grid), against the oracle run with the same switch."""
+    p = I.grid_problem(16 if prec == 0 else 30, 40 + warm_start + 3 * smoothing, kind="l2sq")
+    gamma_f = 2.0 ** 12
+    prm = M.default_params(gamma_f=gamma_f, warm_start=warm_start, smoothing=smoothing, precision=prec)
+    u, v, res = h.solve(t(p.r), t(p.c), t(p.C), 1e-6, prm)
+    ref = O.solve(p.C.astype(np.float64), p.r, p.c, gamma_f=gamma_f, warm_start=warm_start, smoothing=smoothing)
+    assert res.status == M.MDOT_OK, M.status_string(res.status)
+    eps_d = res.info.H_min / gamma_f ** 1.5
+    assert abs(res.cost - ref.cost) <= max(1e-7, eps_d), (res.cost, ref.cost)
+    assert res.info.stages == ref.stats.stages
