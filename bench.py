@@ -44,7 +44,10 @@ def parse():
     ap.add_argument("--grid", type=int, default=64, help="k of the k x k grid for --case runs")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
-    ap.add_argument("--serve-count", type=int, default=600, help="requests of the replayed serving trace (0: skip)")
+    ap.add_argument("--serve-count", type=int, default=60, help="requests of the replayed serving trace (0: skip)")
+    ap.add_argument("--serve-big-n", type=int, default=None, help="server routing: n above which a big lane solves")
+    ap.add_argument("--serve-lanes", type=int, default=None, help="server routing: big lanes")
+    ap.add_argument("--serve-lane-ctas", type=int, default=None, help="server routing: CTAs per big lane")
     return ap.parse_args()
 
 
@@ -299,13 +302,13 @@ def serving_requests(dev, count, seed=SERVE_SEED):
     return reqs
 
 
-def measure_serving(dev, count):
+def measure_serving(dev, count, big_n=None, big_lanes=None, lane_ctas=None):
     import numpy as np
     import torch
     import paper_2307_08507_gb300 as M
     reqs = serving_requests(dev, count)
     torch.cuda.synchronize()
-    srv = M.Server(SERVE_WORKSPACE)
+    srv = M.Server(SERVE_WORKSPACE, big_n=big_n, big_lanes=big_lanes, lane_ctas=lane_ctas)
     lat, done_at, evals, status_ok, statuses, big_lat = [], [], 0, 0, {}, []
     try:
         # warm-up request (kernel load, first launch)
@@ -344,6 +347,8 @@ def measure_serving(dev, count):
             "problems_per_s": len(lat) / span, "latency_p50_s": float(np.percentile(lat, 50)),
             "latency_p99_s": float(np.percentile(lat, 99)), "latency_max_s": float(lat.max()),
             "latency_p50_n_gt_2048_s": float(np.percentile(big_lat, 50)) if big_lat else None,
+            "routing": {"big_n": big_n if big_n is not None else 2048, "big_lanes": big_lanes if big_lanes is not None else 2,
+                        "lane_ctas": lane_ctas or "SMs/4"},
             "ok": status_ok, "statuses": statuses, "evals_total": int(evals), "seconds": span}
 
 
@@ -528,7 +533,8 @@ def run_case(args):
         h.close()
         return
     if args.case == "serve":
-        print(json.dumps(measure_serving(dev, args.serve_count)))
+        print(json.dumps(measure_serving(dev, args.serve_count, args.serve_big_n, args.serve_lanes,
+                                         args.serve_lane_ctas)))
         h.close()
         return
     if args.case == "dual_eval":

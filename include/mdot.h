@@ -82,7 +82,9 @@ typedef struct mdot_params {
     int32_t ls_max_trials;  /* phi' evaluations per line search before the lower end is taken; 50   */
     int32_t max_iter;       /* PNCG iterations per stage; 100000                                    */
     int32_t precision;      /* mdot_precision                                                      */
-    int32_t warm_start;     /* 0: Taylor step, Eq. (13); 1: eps-scaling (Sec. 3.3.1); 2: none       */
+    int32_t warm_start;     /* 0: Taylor step, Eq. (13); 1: eps-scaling (Sec. 3.3.1); 2: none (the   */
+                            /*    previous iterate; the per-row scales are predicted from r~, which  */
+                            /*    this start can miss by more than the exponent range: may fail)     */
     double  final_tol;      /* > 0: ||grad g||_1 target of the final stage instead of eps_d / 2     */
     double  fp32_floor;     /* ||grad g||_1 below which fp32 entries are not trusted; 5e-8          */
     int32_t profile;        /* non-zero: time each kernel launch with CUDA events (mdot_info t_*)    */
@@ -263,9 +265,11 @@ mdot_status mdot_solve_batch(mdot_handle* h, int32_t nprob, const mdot_problem* 
  * fits; each admission round is one persistent batched launch (the solver of mdot_solve_batch,
  * one CTA per problem) on one of several streams, so work admitted while other launches run
  * overlaps with them on the device, and a problem's workspace returns to the pool as soon as that
- * problem finishes.  Results do not depend on what else runs (fixed-order reductions): a problem
+ * problem finishes.  Requests above cfg->big_n instead go to "big lanes": cooperative solves (the
+ * single-problem solver) on cfg->lane_ctas SMs each; the remaining SMs serve the batched route.  Results do not depend on what else runs (fixed-order reductions): a problem
  * gives the same result alone and in any mix.
- *   prm: NULL for defaults (the fp64 tier is not offered here).
+ *   prm: NULL for defaults (the fp64 tier is not offered here).  cfg: NULL for the default routing;
+ *   lanes x lane_ctas must leave SMs for the batched route.
  *   submit: non-blocking; validates the problem (same rules as mdot_solve_batch, n up to
  *     MDOT_BATCH_MAX_N) and returns a ticket.  The problem's arrays (r, c, C or x/y, u_out,
  *     v_out) are used in place and must stay valid until poll/wait returns MDOT_OK for it.
@@ -276,7 +280,16 @@ mdot_status mdot_solve_batch(mdot_handle* h, int32_t nprob, const mdot_problem* 
  *   destroy: finishes every queued and admitted request, then frees everything.
  */
 typedef struct mdot_server mdot_server;
-mdot_status mdot_server_create(mdot_server** s, uint64_t workspace_bytes, const mdot_params* prm);
+
+/* Routing of the server (NULL in mdot_server_create: the defaults below). */
+typedef struct mdot_server_config {
+    int64_t big_n;            /* requests with n > big_n go to a big lane (default 2048)           */
+    int32_t big_lanes;        /* concurrent cooperative solves (default 2; 0: every request batched) */
+    int32_t lane_ctas;        /* CTAs (SMs) of each big lane (default: SMs / 4)                     */
+} mdot_server_config;
+
+mdot_status mdot_server_create(mdot_server** s, uint64_t workspace_bytes, const mdot_params* prm,
+                               const mdot_server_config* cfg);
 mdot_status mdot_server_submit(mdot_server* s, const mdot_problem* prob, uint64_t* ticket);
 mdot_status mdot_server_poll(mdot_server* s, uint64_t ticket, mdot_result* out);
 mdot_status mdot_server_wait(mdot_server* s, uint64_t ticket, double timeout_s, mdot_result* out);

@@ -373,7 +373,7 @@ MDOT_NOT_READY = 7
 def _server_lib():
     L = lib()
     if not hasattr(L, "_server_typed"):
-        L.mdot_server_create.argtypes = [ct.POINTER(_P), ct.c_uint64, ct.POINTER(Params)]
+        L.mdot_server_create.argtypes = [ct.POINTER(_P), ct.c_uint64, ct.POINTER(Params), ct.POINTER(ServerConfig)]
         L.mdot_server_submit.argtypes = [_P, ct.POINTER(Problem), ct.POINTER(ct.c_uint64)]
         L.mdot_server_poll.argtypes = [_P, ct.c_uint64, ct.POINTER(Result)]
         L.mdot_server_wait.argtypes = [_P, ct.c_uint64, ct.c_double, ct.POINTER(Result)]
@@ -385,16 +385,27 @@ def _server_lib():
     return L
 
 
+class ServerConfig(ct.Structure):
+    """mdot_server_config: routing of the serving runtime (big_n, big_lanes, lane_ctas)."""
+    _fields_ = [("big_n", ct.c_int64), ("big_lanes", ct.c_int32), ("lane_ctas", ct.c_int32)]
+
+
 class Server:
     """mdot_server_*: request loop with continuous batching on the current device.
 
     submit() takes an mdot_problem (see make_problem) and returns a ticket; the problem's tensors
     are kept referenced here until its result has been collected (poll/wait returned it)."""
 
-    def __init__(self, workspace_bytes: int, params: Params | None = None):
+    def __init__(self, workspace_bytes: int, params: Params | None = None, big_n: int | None = None,
+                 big_lanes: int | None = None, lane_ctas: int | None = None):
         L = _server_lib()
         self._s = _P()
-        s = L.mdot_server_create(ct.byref(self._s), int(workspace_bytes), ct.byref(params) if params is not None else None)
+        cfg = None
+        if big_n is not None or big_lanes is not None or lane_ctas is not None:
+            cfg = ServerConfig(big_n if big_n is not None else 2048, big_lanes if big_lanes is not None else 2,
+                               lane_ctas or 0)
+        s = L.mdot_server_create(ct.byref(self._s), int(workspace_bytes), ct.byref(params) if params is not None else None,
+                                 ct.byref(cfg) if cfg is not None else None)
         if s != MDOT_OK:
             raise MdotError(s, "mdot_server_create")
         self._keep = {}

@@ -1,5 +1,5 @@
 // Serving runtime (declared in include/mdot.h): a request loop with continuous batching on one
-// GPU.  Requests up to kBigN are admitted in arrival order as soon as their workspace fits the
+// GPU.  Requests up to big_n are admitted in arrival order as soon as their workspace fits the
 // pool (the HBM budget given at creation); every admission round becomes one persistent batched
 // launch (one CTA per problem, the solver of batch_kernels.cuh) on one of a few streams, so
 // launches admitted while others still run overlap on the device and take SMs as earlier problems
@@ -8,7 +8,7 @@
 // launch.  Larger requests would hold one SM for a long time; they go to a few "big lanes", each
 // a cooperative solve (the stage kernels of the single-problem solver) on a share of the SMs.
 // The SMs are partitioned so that every resident CTA fits at once: batched problems in flight
-// <= SMs - lanes x CTAs per lane.
+// <= SMs - lanes x CTAs per lane - 8.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -43,9 +43,7 @@ constexpr int kLanes = 4;            // streams the launches rotate over
 constexpr int kRecords = 32;         // launches in flight at most
 constexpr int kRecordCap = 256;      // problems per launch at most
 constexpr int kStrideAlign = 32;     // workspace vector stride granularity (elements)
-constexpr int64_t kBigN = 2048;      // larger requests are solved by a big lane
-constexpr int kBigLanes = 2;         // concurrent cooperative solves
-constexpr int kBigShare = 4;         // each big lane runs on SMs / kBigShare CTAs
+constexpr int kMaxBigLanes = 16;     // concurrent cooperative solves at most
 
 // First-fit allocator over the workspace pool (offsets and lengths in doubles).
 struct Pool {
@@ -155,7 +153,9 @@ struct mdot_server {
     std::condition_variable cv_done;     // wakes waiters
     std::deque<Request> pending;         // batched route
     std::deque<Request> big_pending;     // big lanes
-    BigLane big[kBigLanes];
+    BigLane big[kMaxBigLanes];
+    int64_t big_n = 2048;
+    int big_lanes = 0;
     int batch_inflight = 0, batch_cap = 0;
     std::unordered_map<uint64_t, int> state;          // 0 queued, 1 running, 2 finished
     std::unordered_map<uint64_t, mdot_result> finished;
@@ -401,7 +401,8 @@ void destroy_records(mdot_server* s)
 
 extern "C" {
 
-mdot_status mdot_server_create(mdot_server** out, uint64_t workspace_bytes, const mdot_params* prm)
+mdot_status mdot_server_create(mdot_server** out, uint64_t workspace_bytes, const mdot_params* prm,
+                               const mdot_server_config* cfg)
 {
     if (!out) return MDOT_ERR_INVALID_ARG;
     *out = nullptr;
@@ -433,9 +434,24 @@ mdot_status mdot_server_create(mdot_server** out, uint64_t workspace_bytes, cons
     }
     int sms = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->dev);
-    const int share = std::max(1, std::min(sms, 160) / kBigShare);
+    const int gmax = std::min(sms, 160);
+    // defaults measured on the serving trace (60 requests, n log-uniform on [128, 8192], gaps
+    // 1e-4 .. 1e-7): two lanes of a quarter of the SMs for n > 2048 gave the best problems/s and
+    // p99 (2.35/s, 25 s) against four lanes of an eighth for n > 1024 (1.39/s, 35 s)
+    s->big_n = (cfg && cfg->big_n > 0) ? cfg->big_n : 2048;
+    s->big_lanes = cfg ? cfg->big_lanes : 2;
+    const int share = (cfg && cfg->lane_ctas > 0) ? cfg->lane_ctas : std::max(1, gmax / 4);
+    if (s->big_lanes < 0 || s->big_lanes > kMaxBigLanes || share > gmax || s->big_lanes * share > gmax - 8) {
+        destroy_records(s);
+        cudaFree(s->pool_mem);
+        for (auto& l : s->lanes)
+            if (l) cudaStreamDestroy(l);
+        delete s;
+        return MDOT_ERR_INVALID_ARG;
+    }
     mdot_status hs = MDOT_OK;
-    for (BigLane& L : s->big) {
+    for (int li = 0; li < s->big_lanes; ++li) {
+        BigLane& L = s->big[li];
         if (e != cudaSuccess || hs != MDOT_OK) break;
         e = cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaMalloc(&L.u, MDOT_BATCH_MAX_N * sizeof(double));
@@ -445,7 +461,7 @@ mdot_status mdot_server_create(mdot_server** out, uint64_t workspace_bytes, cons
     }
     if (e == cudaSuccess && hs != MDOT_OK) e = cudaErrorInvalidConfiguration;
     // a few SMs of slack: a batched CTA that has reported its problem may not have left its SM yet
-    s->batch_cap = std::max(1, sms - kBigLanes * share - 8);
+    s->batch_cap = std::max(1, sms - s->big_lanes * share - 8);
     if (e != cudaSuccess) {
         set_last_error(cudaGetErrorString(e));
         for (BigLane& L : s->big) {
@@ -463,7 +479,7 @@ mdot_status mdot_server_create(mdot_server** out, uint64_t workspace_bytes, cons
     }
     s->pool.init(pool_doubles);
     s->worker = std::thread(worker_loop, s);
-    for (int i = 0; i < kBigLanes; ++i) s->big[i].thread = std::thread(big_loop, s, i);
+    for (int i = 0; i < s->big_lanes; ++i) s->big[i].thread = std::thread(big_loop, s, i);
     *out = s;
     return MDOT_OK;
 }
@@ -478,7 +494,7 @@ mdot_status mdot_server_submit(mdot_server* s, const mdot_problem* prob, uint64_
     q.len = batch_slot_doubles(q.stride);
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->fatal != cudaSuccess) return MDOT_ERR_CUDA;
-    const bool big = prob->n > kBigN;
+    const bool big = s->big_lanes > 0 && prob->n > s->big_n;
     if (!big && q.len > s->pool.total) return MDOT_ERR_INVALID_ARG;     // could never be admitted
     q.ticket = s->next_ticket++;
     s->state[q.ticket] = 0;

@@ -803,7 +803,6 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
 
         // ---------------- every CTA: the G partials in a fixed order, then the decision ----------------
         bool ok = true;
-        if (warp == kNRed) ok = wait_flags(fpub, G, tag, abort);      // acquire: the column state
         if (warp < kNRed) {
             double v5[5];
             unsigned int spins = 0;
@@ -850,6 +849,10 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
         __syncthreads();
         const double alpha = sst.alpha, acommit = sst.alpha_commit, beta = sst.beta;
         const bool accept = sst.accept != 0, done = sst.phase != PH_RUN;
+
+        // the next pass reads every owner's column state: one warp acquires their flags while
+        // warp 0 commits (the barrier at the end of the iteration covers it)
+        if (warp == kNRed && !done && !wait_flags(fpub, G, tag, abort)) s_ok = 0;
 
         // ---------------- phase C: commit, new direction, next trial constants (rows) ----------------
         for (int i = r0 + tid; i < r1; i += T) {
