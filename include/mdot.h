@@ -90,7 +90,9 @@ typedef struct mdot_params {
     int32_t profile;        /* non-zero: time each kernel launch with CUDA events (mdot_info t_*)    */
     int32_t smoothing;      /* 0: smoothing weight eps_d of the stage (Alg. 1); 1: fixed weight       */
                             /*    H_min / gamma_f^p in every stage (the fixed-smoothing ablation)     */
-    int32_t reserved[6];
+    int32_t projector;      /* 0: PNCG (Alg. 2); 1: Sinkhorn (Alg. 4) as the projection of each      */
+                            /*    stage (MDOT-Sinkhorn; not in mdot_solve_batch or the server)        */
+    int32_t reserved[5];
 } mdot_params;
 
 /* Diagnostics of one solve. */

@@ -31,7 +31,8 @@ class Params(ct.Structure):
                 ("q", ct.c_double), ("ls_c1", ct.c_double), ("ls_c2", ct.c_double),
                 ("ls_max_trials", ct.c_int32), ("max_iter", ct.c_int32), ("precision", ct.c_int32),
                 ("warm_start", ct.c_int32), ("final_tol", ct.c_double), ("fp32_floor", ct.c_double),
-                ("profile", ct.c_int32), ("smoothing", ct.c_int32), ("reserved", ct.c_int32 * 6)]
+                ("profile", ct.c_int32), ("smoothing", ct.c_int32), ("projector", ct.c_int32),
+                ("reserved", ct.c_int32 * 5)]
 
 
 class Info(ct.Structure):

@@ -234,7 +234,7 @@ mdot_status params_ok(const mdot_params& P)
     if (!(P.gamma_i > 0.0) || !(P.p >= 1.0) || !(P.q > 1.0) || !(P.ls_c1 > 0.0) ||
         !(P.ls_c2 > P.ls_c1) || !(P.ls_c2 < 1.0) || P.ls_max_trials < 1 || P.max_iter < 1 ||
         P.precision < 0 || P.precision > 3 || P.warm_start < 0 || P.warm_start > 2 ||
-        P.smoothing < 0 || P.smoothing > 1 ||
+        P.smoothing < 0 || P.smoothing > 1 || P.projector < 0 || P.projector > 1 ||
         !(P.fp32_floor >= 0.0) || !std::isfinite(P.gamma_f))
         return MDOT_ERR_INVALID_ARG;
     return MDOT_OK;
@@ -426,7 +426,7 @@ mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const C
             a.tier = TIER_F64;
             a.tol = tol;
             tm.begin(1);
-            CKR(launch_stage(TIER_F64, ws, a, h->stream));
+            CKR(launch_projection(P.projector, TIER_F64, ws, a, h->stream));
             tm.end();
             ++launches;
         } else {
@@ -435,7 +435,7 @@ mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const C
             a.tier = tier;
             a.tol = std::max(tol, (double)P.fp32_floor);
             tm.begin(0);
-            CKR(launch_stage(tier, ws, a, h->stream));
+            CKR(launch_projection(P.projector, tier, ws, a, h->stream));
             tm.end();
             ++launches;
             ++launches32;
@@ -448,7 +448,7 @@ mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const C
                 b.first = 0;
                 b.warm_start = 2;
                 tm.begin(1);
-                CKR(launch_stage(TIER_F64, ws, b, h->stream));
+                CKR(launch_projection(P.projector, TIER_F64, ws, b, h->stream));
                 tm.end();
                 ++launches;
             }
@@ -625,7 +625,7 @@ mdot_status mdot_solve_batch(mdot_handle* h, int32_t nprob, const mdot_problem* 
     if (nprob == 0) return MDOT_OK;
     mdot_params P;
     if (prm) P = *prm; else mdot_default_params(&P);
-    if (params_ok(P) != MDOT_OK || P.precision == MDOT_PREC_FP64) return MDOT_ERR_INVALID_ARG;
+    if (params_ok(P) != MDOT_OK || P.precision == MDOT_PREC_FP64 || P.projector != 0) return MDOT_ERR_INVALID_ARG;
     std::vector<BatchProblem> bp(nprob);
     for (int k = 0; k < nprob; ++k) {
         const mdot_problem& q = probs[k];

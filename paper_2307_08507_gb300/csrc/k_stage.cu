@@ -6,6 +6,8 @@
 namespace mdot {
 
 size_t stage_smem_bytes(int n, int G, int tier) { return smem_layout(n, G, tier, kStageThreads).bytes; }
+// the standalone dual evaluation (wide column merge)
+size_t eval_smem_bytes(int n, int G, int tier) { return smem_layout(n, G, tier, kStageThreads, true).bytes; }
 
 template <typename K>
 static cudaError_t coop(K kernel, int G, size_t smem, cudaStream_t s, void** args)
@@ -29,13 +31,27 @@ cudaError_t launch_stage(int tier, const WS& ws, const StageArgs& a, cudaStream_
     return coop(stage_kernel_flag<TIER_F32, COST_DENSE>, ws.G, smem, s, args);
 }
 
+cudaError_t launch_sinkhorn_regen(int tier, const WS& ws, const StageArgs& a, cudaStream_t s);
+
+cudaError_t launch_sinkhorn(int tier, const WS& ws, const StageArgs& a, cudaStream_t s)
+{
+    if (ws.ckind != COST_DENSE) return launch_sinkhorn_regen(tier, ws, a, s);
+    WS w = ws;
+    StageArgs aa = a;
+    void* args[] = {(void*)&w, (void*)&aa};
+    const size_t smem = stage_smem_bytes(ws.n, ws.G, tier);
+    if (tier == TIER_F64) return coop(sinkhorn_kernel<TIER_F64, COST_DENSE>, ws.G, smem, s, args);
+    if (tier == TIER_F32A) return coop(sinkhorn_kernel<TIER_F32A, COST_DENSE>, ws.G, smem, s, args);
+    return coop(sinkhorn_kernel<TIER_F32, COST_DENSE>, ws.G, smem, s, args);
+}
+
 cudaError_t launch_dual_eval(int tier, const WS& ws, const EvalArgs& a, cudaStream_t s)
 {
     if (ws.ckind != COST_DENSE) return launch_dual_eval_regen(tier, ws, a, s);
     WS w = ws;
     EvalArgs aa = a;
     void* args[] = {(void*)&w, (void*)&aa};
-    const size_t smem = stage_smem_bytes(ws.n, ws.G, tier);
+    const size_t smem = eval_smem_bytes(ws.n, ws.G, tier);
     if (tier == TIER_F64) return coop(dual_eval_kernel<TIER_F64, COST_DENSE>, ws.G, smem, s, args);
     if (tier == TIER_F32A) return coop(dual_eval_kernel<TIER_F32A, COST_DENSE>, ws.G, smem, s, args);
     return coop(dual_eval_kernel<TIER_F32, COST_DENSE>, ws.G, smem, s, args);
@@ -49,7 +65,10 @@ cudaError_t configure_stage_kernels(int max_n, int G, int* min_blocks)
         {(const void*)stage_kernel_flag<TIER_F32A, COST_DENSE>, TIER_F32A},
         {(const void*)dual_eval_kernel<TIER_F32, COST_DENSE>, TIER_F32},
         {(const void*)dual_eval_kernel<TIER_F64, COST_DENSE>, TIER_F64},
-        {(const void*)dual_eval_kernel<TIER_F32A, COST_DENSE>, TIER_F32A}};
+        {(const void*)dual_eval_kernel<TIER_F32A, COST_DENSE>, TIER_F32A},
+        {(const void*)sinkhorn_kernel<TIER_F32, COST_DENSE>, TIER_F32},
+        {(const void*)sinkhorn_kernel<TIER_F64, COST_DENSE>, TIER_F64},
+        {(const void*)sinkhorn_kernel<TIER_F32A, COST_DENSE>, TIER_F32A}};
     for (auto& k : ks) {
         const size_t smem = stage_smem_bytes(max_n, G, k.tier);
         // the limit goes to the largest layout any n may take (fewer rows per CTA leave room for

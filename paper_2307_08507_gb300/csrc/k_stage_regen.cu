@@ -26,11 +26,30 @@ static cudaError_t launch_eval_kind(int tier, const WS& ws, const EvalArgs& a, c
     WS w = ws;
     EvalArgs aa = a;
     void* args[] = {(void*)&w, (void*)&aa};
-    const size_t smem = stage_smem_bytes(ws.n, ws.G, tier);
+    const size_t smem = eval_smem_bytes(ws.n, ws.G, tier);
     const void* f = tier == TIER_F64 ? (const void*)dual_eval_kernel<TIER_F64, COST>
                   : tier == TIER_F32A ? (const void*)dual_eval_kernel<TIER_F32A, COST>
                                       : (const void*)dual_eval_kernel<TIER_F32, COST>;
     return cudaLaunchCooperativeKernel(f, dim3(ws.G), dim3(kStageThreads), args, smem, s);
+}
+
+template <int COST>
+static cudaError_t launch_sinkhorn_kind(int tier, const WS& ws, const StageArgs& a, cudaStream_t s)
+{
+    WS w = ws;
+    StageArgs aa = a;
+    void* args[] = {(void*)&w, (void*)&aa};
+    const size_t smem = stage_smem_bytes(ws.n, ws.G, tier);
+    const void* f = tier == TIER_F64 ? (const void*)sinkhorn_kernel<TIER_F64, COST>
+                  : tier == TIER_F32A ? (const void*)sinkhorn_kernel<TIER_F32A, COST>
+                                      : (const void*)sinkhorn_kernel<TIER_F32, COST>;
+    return cudaLaunchCooperativeKernel(f, dim3(ws.G), dim3(kStageThreads), args, smem, s);
+}
+
+cudaError_t launch_sinkhorn_regen(int tier, const WS& ws, const StageArgs& a, cudaStream_t s)
+{
+    return ws.ckind == COST_L1 ? launch_sinkhorn_kind<COST_L1>(tier, ws, a, s)
+                               : launch_sinkhorn_kind<COST_SQEUCLID>(tier, ws, a, s);
 }
 
 cudaError_t launch_stage_regen(int tier, const WS& ws, const StageArgs& a, cudaStream_t s)
@@ -59,7 +78,13 @@ cudaError_t configure_regen_kernels(int max_n, int G, int* min_blocks)
         {(const void*)dual_eval_kernel<TIER_F32A, COST_SQEUCLID>, TIER_F32A},
         {(const void*)dual_eval_kernel<TIER_F32, COST_L1>, TIER_F32},
         {(const void*)dual_eval_kernel<TIER_F64, COST_L1>, TIER_F64},
-        {(const void*)dual_eval_kernel<TIER_F32A, COST_L1>, TIER_F32A}};
+        {(const void*)dual_eval_kernel<TIER_F32A, COST_L1>, TIER_F32A},
+        {(const void*)sinkhorn_kernel<TIER_F32, COST_SQEUCLID>, TIER_F32},
+        {(const void*)sinkhorn_kernel<TIER_F64, COST_SQEUCLID>, TIER_F64},
+        {(const void*)sinkhorn_kernel<TIER_F32A, COST_SQEUCLID>, TIER_F32A},
+        {(const void*)sinkhorn_kernel<TIER_F32, COST_L1>, TIER_F32},
+        {(const void*)sinkhorn_kernel<TIER_F64, COST_L1>, TIER_F64},
+        {(const void*)sinkhorn_kernel<TIER_F32A, COST_L1>, TIER_F32A}};
     for (auto& k : ks) {
         const size_t smem = stage_smem_bytes(max_n, G, k.tier);
         // the limit goes to the largest layout any n may take (fewer rows per CTA leave room for

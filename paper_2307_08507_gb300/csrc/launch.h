@@ -25,6 +25,7 @@ inline cudaError_t raise_smem_limit(const void* f, size_t bytes)
 }
 
 size_t stage_smem_bytes(int n, int G, int tier);
+size_t eval_smem_bytes(int n, int G, int tier);
 size_t round_smem_bytes(int n, int G);
 size_t lb_smem_bytes(int n, int G);
 // Raise the dynamic shared-memory limit of every kernel to what max_n needs; returns the number
@@ -32,6 +33,12 @@ size_t lb_smem_bytes(int n, int G);
 cudaError_t configure_kernels(int max_n, int G, int* min_blocks_per_sm);
 
 cudaError_t launch_stage(int tier, const WS& ws, const StageArgs& a, cudaStream_t s);
+cudaError_t launch_sinkhorn(int tier, const WS& ws, const StageArgs& a, cudaStream_t s);
+// one stage's projection: PNCG (projector 0) or Sinkhorn (1)
+inline cudaError_t launch_projection(int projector, int tier, const WS& ws, const StageArgs& a, cudaStream_t s)
+{
+    return projector == 1 ? launch_sinkhorn(tier, ws, a, s) : launch_stage(tier, ws, a, s);
+}
 cudaError_t launch_dual_eval(int tier, const WS& ws, const EvalArgs& a, cudaStream_t s);
 cudaError_t launch_round(const WS& ws, const RoundArgs& a, cudaStream_t s);
 cudaError_t launch_lower_bound(const WS& ws, const LbArgs& a, cudaStream_t s);

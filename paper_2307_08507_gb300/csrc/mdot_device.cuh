@@ -1308,6 +1308,42 @@ __device__ __forceinline__ double merge_cols_f32(const float* colpart, int n, in
     return tot;
 }
 
+// merge_cols_f32 for up to 32 MC columns [j0, j1) in one round trip: every load of every column
+// group is in flight before any addition; the column totals (fp64) go to out[j - j0].
+template <int MC>
+__device__ __forceinline__ void merge_cols_f32_wide(const float* colpart, int n, int G, int j0, int j1, float* sm,
+                                                    double* out)
+{
+    constexpr int kMaxPer = 24;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float vals[MC][kMaxPer];
+#pragma unroll
+    for (int m = 0; m < MC; ++m) {
+        const int j = j0 + lane + 32 * m;
+#pragma unroll
+        for (int k = 0; k < kMaxPer; ++k) {
+            const int b = warp + k * nw;
+            vals[m][k] = (j < j1 && b < G) ? __ldcg(colpart + (size_t)b * n + j) : 0.0f;
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < MC; ++m) {
+        float s = 0.0f, comp = 0.0f;
+#pragma unroll
+        for (int k = 0; k < kMaxPer; ++k) kahan_add(s, comp, vals[m][k]);
+        sm[(m * nw + warp) * 32 + lane] = s;
+        sm[((MC + m) * nw + warp) * 32 + lane] = -comp;
+    }
+    __syncthreads();
+    if (warp < MC) {
+        double tot = 0.0;
+        for (int w = 0; w < nw; ++w)
+            tot += (double)sm[(warp * nw + w) * 32 + lane] + (double)sm[((MC + warp) * nw + w) * 32 + lane];
+        out[warp * 32 + lane] = tot;
+    }
+    __syncthreads();
+}
+
 __device__ __forceinline__ double merge_cols_f64(const double* colpart, int n, int G,
                                                  int j0, int j1, double* sm)
 {

@@ -59,7 +59,7 @@ cudaError_t setup_device(int dev, DeviceSetup** out)
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
         const int G = std::min(sms, kMaxG);
-        const size_t smem = smem_layout(kMaxN, G, TIER_F32, kStageThreads).bytes;
+        const size_t smem = kSmemLimit;        // the largest layout any n up to kMaxN takes
         e = raise_smem_limit((const void*)dual_eval_kernel<TIER_F32, COST_DENSE>, smem);
         if (e != cudaSuccess) return e;
         int nb = 0;
@@ -122,7 +122,7 @@ extern "C" mdot_status mdot_dual_eval_noalloc(const double* u, const double* v, 
     WS wk = ws;
     EvalArgs ak = a;
     void* args[] = {(void*)&wk, (void*)&ak};
-    const size_t smem = smem_layout((int)n, s->G, TIER_F32, kStageThreads).bytes;
+    const size_t smem = smem_layout((int)n, s->G, TIER_F32, kStageThreads, true).bytes;
     if (cudaLaunchCooperativeKernel((const void*)dual_eval_kernel<TIER_F32, COST_DENSE>, dim3(s->G), dim3(kStageThreads),
                                     args, smem, st) != cudaSuccess)
         return MDOT_ERR_CUDA;

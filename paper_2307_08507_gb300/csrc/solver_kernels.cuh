@@ -133,7 +133,10 @@ struct SmemLayout {
 enum RowState { RS_U = 0, RS_P, RS_G, RS_T, RS_LT, RS_L, RS_GT, RS_ST, RS_LTR, RS_COUNT };
 enum ColState { CS_V = 0, CS_P, CS_G, CS_T, CS_GT, CS_ST, CS_COUNT };
 
-__host__ __device__ inline SmemLayout smem_layout(int n, int G, int tier, int nthreads)
+constexpr int kMergeGroups = 4;        // 32-column groups merged in one round trip by dual_eval_kernel
+
+// wide: the merge scratch of merge_cols_f32_wide (standalone dual evaluation)
+__host__ __device__ inline SmemLayout smem_layout(int n, int G, int tier, int nthreads, bool wide = false)
 {
     SmemLayout L;
     const int nw = nthreads / 32;
@@ -146,7 +149,11 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int G, int tier, int nt
     L.off_s = o;     o += (size_t)L.nloc_max * el;               o = (o + 15) & ~(size_t)15;
     L.off_A = o;     o += (size_t)L.nloc_max * 4;                o = (o + 15) & ~(size_t)15;
     L.off_x = o;     o += (size_t)L.nloc_max * 8;                o = (o + 15) & ~(size_t)15;
-    L.off_merge = o; o += (size_t)2 * 32 * nw * 8;               o = (o + 15) & ~(size_t)15;
+    // merge scratch: one 32-column group (stage kernels) or kMergeGroups of them plus their totals
+    // (standalone evaluation, merge_cols_f32_wide)
+    L.off_merge = o; o += !wide ? (size_t)2 * 32 * nw * 8
+                                : (size_t)2 * kMergeGroups * 32 * nw * 4 + (size_t)kMergeGroups * 32 * 8;
+    o = (o + 15) & ~(size_t)15;
     L.off_rstate = o; o += (size_t)RS_COUNT * L.nloc_max * 8;   o = (o + 15) & ~(size_t)15;
     L.off_cstate = o; o += (size_t)CS_COUNT * L.nloc_max * 8;   o = (o + 15) & ~(size_t)15;
     L.off_xc = o;    o += (size_t)3 * L.nloc_max * 4;           o = (o + 15) & ~(size_t)15;
@@ -903,6 +910,186 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
 }
 
 // ---------------------------------------------------------------------------------------------
+// MDOT-Sinkhorn stage (Alg. 4 as the projector of Alg. 1): alternate exact row and column
+// normalisations in the log domain until ||r(P) - r~||_1 <= tol (after a column update c(P) = c~
+// exactly, so this is ||grad g||_1).  Each half step is one fused pass over C of which one
+// reduction is used: the row update needs r(P) at (u, v), the column update c(P) at the new u.
+// ---------------------------------------------------------------------------------------------
+template <int TIER, int COST>
+__global__ void __launch_bounds__(kStageThreads, 1) sinkhorn_kernel(WS ws, StageArgs a)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ double red_smem[32 * kNRed];
+    __shared__ int s_flag[2];
+    __shared__ unsigned int s_gen;
+    __shared__ double s_gn;
+
+    const int n = ws.n, G = ws.G, b = blockIdx.x, T = blockDim.x, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const SmemLayout L = smem_layout(n, G, TIER, T);
+    int r0, r1, c0, c1;
+    row_range(n, G, b, r0, r1);
+    row_range(n, G, b, c0, c1);
+    const int NL = L.nloc_max;
+    double* R = reinterpret_cast<double*>(sm + L.off_rstate);
+    double* Q = reinterpret_cast<double*>(sm + L.off_cstate);
+    const double gamma = a.gamma, G64 = a.G64, w = a.w;
+    State* S = ws.st;
+    long long evals = 0, iters = 0;
+    int status = ST_OK;
+    double gn = INFINITY;
+
+    if (tid == 0) s_gen = ld_acquire(&S->bar.gen);
+    load_row_coords<COST>(ws, r0, r1, sm, L.off_xc);
+    __syncthreads();
+    unsigned int gen = s_gen;
+
+    // ---- prologue (Alg. 1): smoothing, rank-one start or warm start ----
+    for (int i = r0 + tid; i < r1; i += T) {
+        const int il = i - r0;
+        const double rt = (1.0 - w / 4.0) * ws.r[i] + w / (4.0 * n);
+        const double lrt = log(rt);
+        double u = ws.u[i];
+        if (a.first) {
+            u = lrt;
+            ws.uprev[i] = u;
+        } else if (a.warm_start == 0) {
+            const double z = u;
+            u = z + a.ratio * (z - ws.uprev[i]);             // Eq. (13)
+            ws.uprev[i] = z;
+        } else if (a.warm_start == 1) {
+            u = a.ratio * u;
+        }
+        R[RS_U * NL + il] = u;
+        R[RS_T * NL + il] = rt;
+        R[RS_LT * NL + il] = lrt;
+        R[RS_L * NL + il] = lrt;
+        prep_row<TIER>(u, row_scale(lrt), a.Aglob, gamma, G64, sm, L, il);
+    }
+    for (int j = c0 + tid; j < c1; j += T) {
+        const int jl = j - c0;
+        const double ct = (1.0 - w / 4.0) * ws.c[j] + w / (4.0 * n);
+        double v = ws.v[j];
+        if (a.first) {
+            v = log(ct);
+            ws.vprev[j] = v;
+        } else if (a.warm_start == 0) {
+            const double z = v;
+            v = z + a.ratio * (z - ws.vprev[j]);
+            ws.vprev[j] = z;
+        } else if (a.warm_start == 1) {
+            v = a.ratio * v;
+        }
+        Q[CS_V * NL + jl] = v;
+        Q[CS_T * NL + jl] = ct;
+        prep_col<TIER>(ws, j, v, gamma, G64);
+    }
+    if (!grid_sync(&S->bar, G, gen, s_flag)) goto finish;
+
+    for (;;) {
+        // ---- half step 1: r(P) at (u, v); ||r(P) - r~||_1; the row update u += log r~ - log r(P) ----
+        phase_A<TIER, COST>(ws, ColPlain{ws.Hh, ws.Wc, ws.colpart + (size_t)b * n}, r0, r1, gamma, G64, sm, L);
+        ++evals;
+        {
+            double x = 0.0, bad = 0.0;
+            const int* sA = reinterpret_cast<const int*>(sm + L.off_A);
+            for (int i = r0 + tid; i < r1; i += T) {
+                const int il = i - r0;
+                const double sum = row_total<TIER>(sm, L, il);
+                if (!(sum > 0.0) || !isfinite(sum)) { bad += 1.0; continue; }
+                const double lrP = log(sum) + (double)sA[il] * kLn2;
+                x += fabs(exp(lrP) - R[RS_T * NL + il]);
+                R[RS_ST * NL + il] = R[RS_LT * NL + il] - lrP;      // the row update (Alg. 4)
+                R[RS_L * NL + il] = lrP;
+            }
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+                x += __shfl_xor_sync(0xffffffffu, x, o);
+                bad += __shfl_xor_sync(0xffffffffu, bad, o);
+            }
+            if (lane == 0) { red_smem[2 * warp] = x; red_smem[2 * warp + 1] = bad; }
+            __syncthreads();
+            if (tid == 0) {
+                double tx = 0.0, tb = 0.0;
+                for (int ww = 0; ww < (T >> 5); ++ww) { tx += red_smem[2 * ww]; tb += red_smem[2 * ww + 1]; }
+                ws.blockred[(size_t)b * kNRed] = tx;
+                ws.blockred[(size_t)b * kNRed + 1] = tb;
+            }
+        }
+        if (!grid_sync(&S->bar, G, gen, s_flag)) goto finish;
+        if (warp == 0) {
+            // every CTA sums the G partials in the same fixed order
+            double x = 0.0, bad = 0.0;
+            for (int k = 0; k < 5; ++k) {
+                const int bb = lane + 32 * k;
+                if (bb < G) {
+                    x += __ldcg(ws.blockred + (size_t)bb * kNRed);
+                    bad += __ldcg(ws.blockred + (size_t)bb * kNRed + 1);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+                x += __shfl_xor_sync(0xffffffffu, x, o);
+                bad += __shfl_xor_sync(0xffffffffu, bad, o);
+            }
+            if (lane == 0) s_gn = (bad > 0.0) ? -1.0 : x;
+        }
+        __syncthreads();
+        gn = s_gn;
+        if (gn < 0.0) { status = ST_NUMERIC; break; }
+        if (gn <= a.tol) break;                                  // (u, v) meets the stage tolerance
+        if (iters >= a.max_iter) { status = ST_CAP; break; }
+        ++iters;
+        for (int i = r0 + tid; i < r1; i += T) {
+            const int il = i - r0;
+            const double u = R[RS_U * NL + il] + R[RS_ST * NL + il];
+            R[RS_U * NL + il] = u;
+            R[RS_L * NL + il] = R[RS_LT * NL + il];             // r(P) = r~ after the row update
+            prep_row<TIER>(u, row_scale(R[RS_LT * NL + il]), a.Aglob, gamma, G64, sm, L, il);
+        }
+        __syncthreads();
+
+        // ---- half step 2: c(P) at the new u; the column update v += log c~ - log c(P) ----
+        phase_A<TIER, COST>(ws, ColPlain{ws.Hh, ws.Wc, ws.colpart + (size_t)b * n}, r0, r1, gamma, G64, sm, L);
+        ++evals;
+        if (!grid_sync(&S->bar, G, gen, s_flag)) goto finish;
+        for (int j0 = c0; j0 < c1; j0 += 32) {
+            double colsum;
+            if (TIER != TIER_F64)
+                colsum = merge_cols_f32(ws.colpart, n, G, j0, c1, reinterpret_cast<float*>(sm + L.off_merge));
+            else
+                colsum = merge_cols_f64(ws.colpartd, n, G, j0, c1, reinterpret_cast<double*>(sm + L.off_merge));
+            const int j = j0 + tid;
+            if (tid < 32 && j < c1) {
+                const int jl = j - c0;
+                double v = Q[CS_V * NL + jl];
+                if (colsum > 0.0 && isfinite(colsum))
+                    v += log(Q[CS_T * NL + jl]) - (log(colsum) + (double)a.Aglob * kLn2);
+                Q[CS_V * NL + jl] = v;
+                prep_col<TIER>(ws, j, v, gamma, G64);
+            }
+        }
+        if (!grid_sync(&S->bar, G, gen, s_flag)) goto finish;
+    }
+finish:
+    __syncthreads();
+    for (int i = r0 + tid; i < r1; i += T) {
+        ws.u[i] = R[RS_U * NL + i - r0];
+        ws.lr[i] = R[RS_L * NL + i - r0];
+    }
+    for (int j = c0 + tid; j < c1; j += T) ws.v[j] = Q[CS_V * NL + j - c0];
+    if (b == 0 && tid == 0) {
+        if (*reinterpret_cast<volatile unsigned int*>(&S->bar.abort)) status = ST_TIMEOUT;
+        S->evals += evals;
+        if (TIER == TIER_F64) S->evals64 += evals;
+        S->iters += iters;
+        S->gnorm = gn;
+        S->status = max((int)S->status, status);
+        S->phase = PH_DONE;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
 // standalone dual evaluation (mdot_dual_eval): optional max pass for the row scales, one pass,
 // merge.  Writes log r(P) to ws.lrtr and log c(P) to ws.lcout.
 // ---------------------------------------------------------------------------------------------
@@ -915,7 +1102,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) dual_eval_kernel(WS ws, Eval
     __shared__ unsigned int s_gen;
     const int n = ws.n, G = ws.G, b = blockIdx.x, T = blockDim.x, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5, nw = T >> 5;
-    const SmemLayout L = smem_layout(n, G, TIER, T);
+    const SmemLayout L = smem_layout(n, G, TIER, T, true);
     int r0, r1, c0, c1;
     row_range(n, G, b, r0, r1);
     row_range(n, G, b, c0, c1);
@@ -975,14 +1162,23 @@ __global__ void __launch_bounds__(kStageThreads, 1) dual_eval_kernel(WS ws, Eval
                 ws.lrtr[i] = log(row_total<TIER>(sm, L, il)) + (double)sA[il] * kLn2;
             }
             if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
-            for (int j0 = c0; j0 < c1; j0 += 32) {
-                double colsum;
-                if (TIER != TIER_F64)
-                    colsum = merge_cols_f32(ws.colpart, n, G, j0, c1, reinterpret_cast<float*>(sm + L.off_merge));
-                else
-                    colsum = merge_cols_f64(ws.colpartd, n, G, j0, c1, reinterpret_cast<double*>(sm + L.off_merge));
-                const int j = j0 + tid;
-                if (tid < 32 && j < c1) ws.lcout[j] = log(colsum) + (double)Aglob * kLn2;
+            if (TIER != TIER_F64) {
+                // up to kMergeGroups x 32 columns per round trip
+                float* msm = reinterpret_cast<float*>(sm + L.off_merge);
+                double* tot = reinterpret_cast<double*>(msm + 2 * kMergeGroups * 32 * nw);
+                for (int j0 = c0; j0 < c1; j0 += 32 * kMergeGroups) {
+                    merge_cols_f32_wide<kMergeGroups>(ws.colpart, n, G, j0, c1, msm, tot);
+                    const int j = j0 + tid;
+                    if (tid < 32 * kMergeGroups && j < c1) ws.lcout[j] = log(tot[tid]) + (double)Aglob * kLn2;
+                    __syncthreads();
+                }
+            } else {
+                for (int j0 = c0; j0 < c1; j0 += 32) {
+                    const double colsum = merge_cols_f64(ws.colpartd, n, G, j0, c1,
+                                                         reinterpret_cast<double*>(sm + L.off_merge));
+                    const int j = j0 + tid;
+                    if (tid < 32 && j < c1) ws.lcout[j] = log(colsum) + (double)Aglob * kLn2;
+                }
             }
         }
         return;
