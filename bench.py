@@ -39,8 +39,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample-evals", type=int, default=0, help="oracle evaluations in the CPU sample")
-    ap.add_argument("--case", default="solve", choices=["solve", "dual_eval", "stage", "batch", "serve"],
-                    help="dual_eval / stage: run only that kernel (for profiler captures)")
+    ap.add_argument("--case", default="solve",
+                    choices=["solve", "dual_eval", "stage", "batch", "serve", "sinkhorn", "large_n", "nscale", "hmin"],
+                    help="dual_eval / stage: run only that kernel (for profiler captures); sinkhorn, large_n, "
+                         "nscale, hmin: the comparison studies (one JSON line per solve)")
     ap.add_argument("--grid", type=int, default=64, help="k of the k x k grid for --case runs")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
@@ -515,6 +517,90 @@ def run_ours(args, rank, world):
         dist.destroy_process_group()
 
 
+def _study_line(M, case, res, seconds, **extra):
+    i = res.info
+    d = {"study": case, **extra, "status": M.status_string(res.status), "seconds": seconds, "cost": res.cost,
+         "gap_cert": res.gap_cert, "evals": i.evals, "evals_fp64": i.evals_fp64, "iters": i.iters,
+         "ls_trials": i.ls_trials, "stages": i.stages, "gamma_f": i.gamma_f, "H_min": i.H_min,
+         "grad_l1": i.grad_l1}
+    print(json.dumps(d), flush=True)
+
+
+def run_study(args):
+    """Comparison studies, one timed solve per configuration (after one untimed solve of the same
+    problem), wall time on the host around the synchronous call:
+      sinkhorn: MDOT-PNCG against MDOT-Sinkhorn (Alg. 4 as the projector) on 32x32 and 64x64 grids
+                at target gaps 1e-4, 1e-5, 1e-6;
+      large_n:  points on a line (squared distance, regenerated cost, no n x n matrix) at
+                n = 16384 ... 131072, against the exact cost of the monotone coupling;
+      nscale:   time and evaluations against n = 36 ... 16384 (k x k grids), gap 1e-6 (Fig. 6 shape);
+      hmin:     App. C: r drawn with H(r) / log n in {0.03, 0.1, 0.3, 0.9}, c uniform, 3-D normal
+                points with L1 or squared-L2 cost; H_min against log n in the stage tolerance."""
+    import numpy as np
+    import torch
+    import paper_2307_08507_gb300 as M
+    from paper_2307_08507_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+
+    def to(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, time.perf_counter() - t0
+
+    if args.case == "sinkhorn":
+        h = M.Handle(4096)
+        for k in (32, 64):
+            p = I.grid_problem(k, 7)
+            r, c, C = to(p.r), to(p.c), to(p.C)
+            for eps in (1e-4, 1e-5, 1e-6):
+                for proj in (0, 1):
+                    prm = M.default_params(projector=proj)
+                    (_, _, res), dt = timed(lambda: h.solve(r, c, C, eps, prm))
+                    _study_line(M, "sinkhorn", res, dt, n=p.n, eps_target=eps,
+                                projector="sinkhorn" if proj else "pncg")
+    elif args.case == "large_n":
+        # exact costs (monotone coupling on the line) stored by tests/golden/make_golden.py --line
+        with open(os.path.join(ROOT, "tests", "golden", "line_exact.json")) as fh:
+            exact_of = {(c["n"], c["seed"]): c["exact_ot"] for c in json.load(fh)["cases"]}
+        h = M.Handle(131072)
+        for n, eps in ((16384, 1e-5), (16384, 1e-6), (65536, 1e-5), (65536, 1e-6), (131072, 1e-5)):
+            p = I.line_problem(n, 11)
+            exact = exact_of[(n, 11)]
+            r, c, x, y = to(p.r), to(p.c), to(p.x), to(p.y)
+            (_, _, res), dt = timed(lambda: h.solve_points(r, c, x, y, M.COST_SQEUCLID, p.scale, eps,
+                                                           M.default_params(), check=False))
+            _study_line(M, "large_n", res, dt, n=n, eps_target=eps, exact=exact, true_gap=res.cost - exact)
+    elif args.case == "nscale":
+        h = M.Handle(16384)
+        for k in (6, 8, 12, 16, 24, 32, 48, 64, 96, 128):
+            p = I.grid_problem(k, 7)
+            r, c, C = to(p.r), to(p.c), to(p.C)
+            (_, _, res), dt = timed(lambda: h.solve(r, c, C, 1e-6))
+            _study_line(M, "nscale", res, dt, n=p.n, eps_target=1e-6)
+    elif args.case == "hmin":
+        n = 4096
+        h = M.Handle(n)
+        for kind, ck in (("l2sq", M.COST_SQEUCLID), ("l1", M.COST_L1)):
+            for frac in (0.03, 0.1, 0.3, 0.9):
+                p = I.entropy_problem(n, frac, 17, kind)
+                r, c, x = to(p.r), to(p.c), to(p.x)
+                for gf in (2.0 ** 10, 2.0 ** 13, 2.0 ** 16):
+                    for se in (0, 1):
+                        prm = M.default_params(gamma_f=gf, stop_entropy=se)
+                        (_, _, res), dt = timed(lambda: h.solve_points(r, c, x, x, ck, p.scale, 1e-6, prm,
+                                                                       check=False))
+                        _study_line(M, "hmin", res, dt, n=n, cost_kind=kind, H_frac=frac,
+                                    stop_entropy="log n" if se else "H_min")
+    h.close()
+
+
 def run_case(args):
     """Small fixed workloads for profiler captures: the one-pass dual evaluation (fp32 entries,
     row scales given) or one full solve of a k x k grid problem."""
@@ -555,6 +641,9 @@ def run_case(args):
 
 def main():
     args = parse()
+    if args.case in ("sinkhorn", "large_n", "nscale", "hmin"):
+        run_study(args)
+        return
     if args.case != "solve":
         run_case(args)
         return

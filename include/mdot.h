@@ -92,7 +92,10 @@ typedef struct mdot_params {
                             /*    H_min / gamma_f^p in every stage (the fixed-smoothing ablation)     */
     int32_t projector;      /* 0: PNCG (Alg. 2); 1: Sinkhorn (Alg. 4) as the projection of each      */
                             /*    stage (MDOT-Sinkhorn; not in mdot_solve_batch or the server)        */
-    int32_t reserved[5];
+    int32_t stop_entropy;   /* entropy in eps_d = H / gamma^p (Alg. 1): 0: H = H_min(r, c); 1: H = log n, */
+                            /*    the weaker bound App. C compares against (mdot_solve and             */
+                            /*    mdot_solve_points only)                                               */
+    int32_t reserved[4];
 } mdot_params;
 
 /* Diagnostics of one solve. */

@@ -33,6 +33,7 @@ void or_default_params(or_params* prm)
     prm->precond = 0;
     prm->smoothing = 0;
     prm->final_tol = 0.0;
+    prm->stop_entropy = 0;
 }
 
 double or_entropy(int n, const double* r)
@@ -327,7 +328,8 @@ int or_mdot(int n, const double* C, const double* r, const double* c, const or_p
     double dgamma_prev = gamma;   /* reading: stage 0 is gamma = 0 (Prop. 1), so the first step is gamma_i */
     int t = 1;
     for (;;) {                                                      /* MDOT outer loop (Alg. 1) */
-        double eps_d = H / pow(gamma, prm->p);                      /* stopping tolerance eps_d */
+        /* stopping tolerance eps_d; App. C compares H_min with the weaker log n in its place */
+        double eps_d = (prm->stop_entropy == 1 ? log((double)n) : H) / pow(gamma, prm->p);
         double w = (prm->smoothing == 1) ? H / pow(prm->gamma_f, prm->p) : eps_d;
         for (int i = 0; i < n; ++i) rt[i] = (1.0 - w / 4.0) * r[i] + w / (4.0 * n);   /* smoothing */
         for (int j = 0; j < n; ++j) ct[j] = (1.0 - w / 4.0) * c[j] + w / (4.0 * n);

@@ -35,6 +35,7 @@ typedef struct {
     int    precond;        /* 0 = Sinkhorn direction s (Eq. (17)), 1 = diagonal Hessian (Eq. (16)) with fallback */
     int    smoothing;      /* 0 = variable weight eps_d/4 (Alg. 1), 1 = fixed weight at gamma_f */
     double final_tol;      /* if > 0: tolerance used at the final stage instead of eps_d/2         */
+    int    stop_entropy;   /* entropy in eps_d (Alg. 1): 0 = H_min(r, c), 1 = log n (App. C ablation) */
 } or_params;
 
 typedef struct {

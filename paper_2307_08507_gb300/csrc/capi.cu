@@ -234,7 +234,8 @@ mdot_status params_ok(const mdot_params& P)
     if (!(P.gamma_i > 0.0) || !(P.p >= 1.0) || !(P.q > 1.0) || !(P.ls_c1 > 0.0) ||
         !(P.ls_c2 > P.ls_c1) || !(P.ls_c2 < 1.0) || P.ls_max_trials < 1 || P.max_iter < 1 ||
         P.precision < 0 || P.precision > 3 || P.warm_start < 0 || P.warm_start > 2 ||
-        P.smoothing < 0 || P.smoothing > 1 || P.projector < 0 || P.projector > 1 ||
+        P.smoothing < 0 || P.smoothing > 1 || P.projector < 0 || P.projector > 1 || P.stop_entropy < 0 ||
+        P.stop_entropy > 1 ||
         !(P.fp32_floor >= 0.0) || !std::isfinite(P.gamma_f))
         return MDOT_ERR_INVALID_ARG;
     return MDOT_OK;
@@ -404,7 +405,8 @@ mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const C
     double ratio = 0.0;
     int stages = 0;
     for (int t = 1;; ++t) {
-        const double eps_d = H / std::pow(gamma, P.p);                   // stopping tolerance (Alg. 1)
+        // stopping tolerance (Alg. 1); App. C's comparison puts log n in place of H_min
+        const double eps_d = (P.stop_entropy == 1 ? std::log((double)n) : H) / std::pow(gamma, P.p);
         // projection tolerance eps_d / 2, floored at the fp64 resolution of the marginals (~2e-16 gamma relative noise)
         double tol = std::max(eps_d / 2.0, 1e-13 + 1e-15 * gamma);
         const bool last = (gamma == gf);
@@ -625,7 +627,8 @@ mdot_status mdot_solve_batch(mdot_handle* h, int32_t nprob, const mdot_problem* 
     if (nprob == 0) return MDOT_OK;
     mdot_params P;
     if (prm) P = *prm; else mdot_default_params(&P);
-    if (params_ok(P) != MDOT_OK || P.precision == MDOT_PREC_FP64 || P.projector != 0) return MDOT_ERR_INVALID_ARG;
+    if (params_ok(P) != MDOT_OK || P.precision == MDOT_PREC_FP64 || P.projector != 0 || P.stop_entropy != 0)
+        return MDOT_ERR_INVALID_ARG;
     std::vector<BatchProblem> bp(nprob);
     for (int k = 0; k < nprob; ++k) {
         const mdot_problem& q = probs[k];

@@ -23,7 +23,7 @@ import numpy as np
 
 __all__ = [
     "grid_histogram", "grid_coords", "grid_cost", "grid_problem",
-    "point_cloud_problem", "point_cost", "serving_trace", "rng_for",
+    "point_cloud_problem", "point_cost", "line_problem", "entropy_problem", "serving_trace", "rng_for",
 ]
 
 
@@ -137,6 +137,80 @@ def point_cloud_problem(n: int, seed: int, dense: bool = True) -> Problem:
     C = (raw * s).astype(np.float32) if dense else None
     w = np.full(n, 1.0 / n, dtype=np.float64)
     return Problem(n=n, r=w, c=w.copy(), C=C, x=x, y=y, scale=float(s), kind="points_l2sq", seed=seed)
+
+
+def line_problem(n: int, seed: int, dense: bool = False) -> Problem:
+    """Points on a line, for sizes where no n x n matrix is formed: x_i ~ U[0, 1], y_j ~ U[0.25, 1.25]
+    (float32, stored as 3-D coordinates (t, 0, 0)), weights r, c proportional to Gamma(2, 1) draws plus a
+    1e-3 floor, C = squared distance / max.  On a line a convex cost makes the monotone
+    (north-west corner on the sorted supports) coupling optimal, so the exact cost is known at any
+    n.  The cost's maximum is attained at the ends of the two supports (float32 rounding is
+    monotone), so the scale takes O(n) work."""
+    rng = rng_for(seed)
+    t = (rng.uniform(0.0, 1.0, size=(2, n)) + np.array([[0.0], [0.25]])).astype(np.float32)
+    x = np.zeros((n, 3), dtype=np.float32)
+    y = np.zeros((n, 3), dtype=np.float32)
+    x[:, 0], y[:, 0] = t[0], t[1]
+    wr = rng.gamma(2.0, 1.0, size=n) + 1e-3
+    wc = rng.gamma(2.0, 1.0, size=n) + 1e-3
+    r, c = wr / wr.sum(), wc / wc.sum()
+    dmax = max(np.float32(t[0].max() - t[1].min()), np.float32(t[1].max() - t[0].min()))
+    s = np.float32(1.0 / float(np.float32(dmax * dmax)))
+    C = (_point_raw(x, y) * s).astype(np.float32) if dense else None
+    return Problem(n=n, r=r, c=c, C=C, x=x, y=y, scale=float(s), kind="line_l2sq", seed=seed)
+
+
+def _raw_cost(x: np.ndarray, y: np.ndarray, kind: str) -> np.ndarray:
+    """Unscaled cost in float32, in the order the coordinate form computes it: squared distance
+    (d0*d0 + d1*d1) + d2*d2 or L1 distance (|d0| + |d1|) + |d2|."""
+    if kind == "l2sq":
+        return _point_raw(x, y)
+    x, y = x.astype(np.float32), y.astype(np.float32)
+    return (np.abs(x[:, None, 0] - y[None, :, 0]) + np.abs(x[:, None, 1] - y[None, :, 1])) + \
+        np.abs(x[:, None, 2] - y[None, :, 2])
+
+
+def entropy_problem(n: int, frac: float, seed: int, kind: str = "l2sq", dense: bool = False) -> Problem:
+    """App. C's controlled-entropy problems: r with H(r) = frac * log n, c uniform (so H_min = H(r)),
+    cost between n points x_i ~ N(0, I_3) and themselves, ||x_i - x_j||^2 or ||x_i - x_j||_1,
+    divided by its maximum.  Reading of "a Dirichlet draw constructed to meet a target entropy":
+    r proportional to U_i^beta with U_i ~ U(0, 1) (the small-concentration limit of a symmetric
+    Dirichlet draw, whose Gamma(a) components behave like U^(1/a)), beta found by bisection so that
+    H(r) matches the target to 1e-9 relative (H decreases monotonically in beta)."""
+    rng = rng_for(seed)
+    x = rng.standard_normal((n, 3)).astype(np.float32)
+    U = rng.uniform(0.0, 1.0, size=n)
+    target = frac * math.log(n)
+
+    def dist(beta):
+        with np.errstate(divide="ignore", under="ignore"):
+            lw = beta * np.log(U)
+        w = np.exp(lw - lw.max())
+        return w / w.sum()
+
+    def ent(r):
+        nz = r[r > 0]
+        return float(-(nz * np.log(nz)).sum())
+
+    lo, hi = 0.0, 1.0
+    while ent(dist(hi)) > target:
+        hi *= 2.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if ent(dist(mid)) > target:
+            lo = mid
+        else:
+            hi = mid
+        if hi - lo <= 1e-12 * hi:
+            break
+    r = dist(0.5 * (lo + hi))
+    c = np.full(n, 1.0 / n)
+    mx = np.float32(0.0)
+    for i0 in range(0, n, 512):                      # max over all pairs, in row blocks
+        mx = max(mx, _raw_cost(x[i0:i0 + 512], x, kind).max())
+    s = np.float32(1.0 / float(mx))
+    C = (_raw_cost(x, x, kind) * s).astype(np.float32) if dense else None
+    return Problem(n=n, r=r, c=c, C=C, x=x, y=x.copy(), scale=float(s), kind=f"entropy_{kind}", seed=seed)
 
 
 def batch_sizes(count: int, seed: int, lo: int = 256, hi: int = 4096) -> np.ndarray:

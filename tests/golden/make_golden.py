@@ -7,6 +7,8 @@ from the CUDA library.  Each record holds, for one (cost kind, seed, target gap)
 Usage:  python tests/golden/make_golden.py [k] [eps ...]   (defaults: k = 64, eps = 1e-6)
         python tests/golden/make_golden.py --exact-only [k]   (only the exact OT values)
         python tests/golden/make_golden.py --oracle-only k kind eps   (one oracle solve, no exact value)
+        python tests/golden/make_golden.py --line n ...   (exact costs of the points-on-a-line
+            problems, seed 11: the monotone coupling, into tests/golden/line_exact.json)
 Runs the cases in parallel worker processes (spawn) and merges each finished case into
 tests/golden/grid{n}.json (or exact{n}.json) as soon as it completes.
 """
@@ -70,6 +72,18 @@ def exact_case(args):
             "exact_seconds": time.time() - t0}
 
 
+def line_case(n, seed=11):
+    import numpy as np
+    from oracle import exact as E
+    from paper_2307_08507_gb300 import inputs as I
+    p = I.line_problem(n, seed)
+    s32 = np.float32(p.scale)
+    # the cost in the float32 order the problem defines: d = fl(x - y), C = fl(fl(d * d) * s)
+    val = E.monotone_1d(p.x[:, 0], p.y[:, 0], p.r, p.c,
+                        lambda d: float(np.float32(np.float32(d) * np.float32(d)) * s32))
+    return {"n": n, "seed": seed, "exact_ot": val, "method": "monotone coupling of the sorted supports"}
+
+
 def _merge(path, record, key):
     old = []
     if os.path.exists(path):
@@ -93,6 +107,12 @@ def main():
             for rec in pool.imap_unordered(exact_case, cases):
                 _merge(path, rec, lambda c: (c["kind"], c["seed"]))
                 print(json.dumps(rec), flush=True)
+        return
+    if len(sys.argv) > 1 and sys.argv[1] == "--line":
+        for n in [int(a) for a in sys.argv[2:]]:
+            rec = line_case(n)
+            _merge(os.path.join(HERE, "line_exact.json"), rec, lambda c: (c["n"], c["seed"]))
+            print(json.dumps(rec), flush=True)
         return
     if len(sys.argv) > 1 and sys.argv[1] == "--oracle-only":
         k, kind, eps = int(sys.argv[2]), sys.argv[3], float(sys.argv[4])

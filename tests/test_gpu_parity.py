@@ -213,3 +213,19 @@ def test_solve_ablation_variants_match_oracle(h, warm_start, smoothing, prec):
     eps_d = res.info.H_min / gamma_f ** 1.5
     assert abs(res.cost - ref.cost) <= max(1e-7, eps_d), (res.cost, ref.cost)
     assert res.info.stages == ref.stats.stages
+
+
+@pytest.mark.parametrize("prec", [0, 3])
+def test_solve_log_n_stopping_matches_oracle(h, prec):
+    """App. C's comparison: log n in place of H_min in the stage tolerance eps_d, against the
+    oracle run with the same switch (fp64 tier on a 16 x 16 grid, accurate fp32 tier on 30 x 30)."""
+    p = I.grid_problem(16 if prec == 0 else 30, 47, kind="l2sq")
+    gamma_f = 2.0 ** 12
+    prm = M.default_params(gamma_f=gamma_f, stop_entropy=1, precision=prec)
+    u, v, res = h.solve(t(p.r), t(p.c), t(p.C), 1e-6, prm)
+    ref = O.solve(p.C.astype(np.float64), p.r, p.c, gamma_f=gamma_f, stop_entropy=1)
+    assert res.status == M.MDOT_OK, M.status_string(res.status)
+    eps_d = np.log(p.n) / gamma_f ** 1.5
+    assert abs(res.cost - ref.cost) <= max(1e-7, eps_d), (res.cost, ref.cost)
+    assert res.info.stages == ref.stats.stages
+    assert res.info.grad_l1 <= eps_d / 2

@@ -250,6 +250,25 @@ def test_stage_schedule_and_counts():
     assert st1.stages == 1
 
 
+def test_log_n_stopping_bound():
+    """App. C ablation: log n in place of H_min in eps_d.  The stage tolerances become
+    log n / gamma^p (looser, since H_min <= log n), every stage meets its own one, and with uniform
+    marginals (H_min = log n) the two choices run the same iterations."""
+    p = I.grid_problem(5, 4)
+    n = p.n
+    _, _, _, st0, log0 = O.mdot(p.C, p.r, p.c, gamma_f=2.0 ** 9)
+    _, _, _, st1, log1 = O.mdot(p.C, p.r, p.c, gamma_f=2.0 ** 9, stop_entropy=1)
+    np.testing.assert_allclose(log1[:, 1], np.log(n) / log1[:, 0] ** 1.5, rtol=1e-12)
+    assert (log1[:, 4] <= log1[:, 1] / 2).all()
+    assert (log1[:, 1] > log0[:, 1]).all()
+    assert st1.evals <= st0.evals
+    w = np.full(n, 1.0 / n)
+    _, _, _, su0, lu0 = O.mdot(p.C, w, w, gamma_f=2.0 ** 9)
+    _, _, _, su1, lu1 = O.mdot(p.C, w, w, gamma_f=2.0 ** 9, stop_entropy=1)
+    np.testing.assert_allclose(lu1[:, 1], lu0[:, 1], rtol=1e-13)
+    assert su1.evals == su0.evals and su1.iters == su0.iters
+
+
 # ---------------------------------------------------------------------------------------------
 # Rounding (Alg. 3), c-transform bound, end-to-end against exact optima
 # ---------------------------------------------------------------------------------------------
