@@ -95,7 +95,10 @@ typedef struct mdot_params {
     int32_t stop_entropy;   /* entropy in eps_d = H / gamma^p (Alg. 1): 0: H = H_min(r, c); 1: H = log n, */
                             /*    the weaker bound App. C compares against (mdot_solve and             */
                             /*    mdot_solve_points only)                                               */
-    int32_t reserved[4];
+    int32_t precond;        /* 0: Sinkhorn direction s (Eq. (17)); 1: diagonal-Hessian direction       */
+                            /*    (r~ / r(P), c~ / c(P)) - 1 (Eq. (16)) at iterations where every ratio  */
+                            /*    lies in [0.01, 100], else s (mdot_solve and mdot_solve_points only)   */
+    int32_t reserved[3];
 } mdot_params;
 
 /* Diagnostics of one solve. */

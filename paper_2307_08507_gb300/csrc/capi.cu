@@ -154,7 +154,7 @@ mdot_status mdot_create(mdot_handle** out, int64_t max_n, void* stream)
     int* A = (int*)dalloc(n * sizeof(int));
     float* colpart = (float*)dalloc(G * n * sizeof(float));
     double* colpartd = (double*)dalloc(G * n * sizeof(double));
-    double* blockred = (double*)dalloc(G * kNRed * sizeof(double));
+    double* blockred = (double*)dalloc(G * kNRedP * sizeof(double));
     double* scratch = (double*)dalloc(G * 8 * sizeof(double));
     State* st = (State*)dalloc(sizeof(State));
     // stage-kernel flags [2][G] and the tag base; published column state (v, p double-floats, s)
@@ -235,7 +235,7 @@ mdot_status params_ok(const mdot_params& P)
         !(P.ls_c2 > P.ls_c1) || !(P.ls_c2 < 1.0) || P.ls_max_trials < 1 || P.max_iter < 1 ||
         P.precision < 0 || P.precision > 3 || P.warm_start < 0 || P.warm_start > 2 ||
         P.smoothing < 0 || P.smoothing > 1 || P.projector < 0 || P.projector > 1 || P.stop_entropy < 0 ||
-        P.stop_entropy > 1 ||
+        P.stop_entropy > 1 || P.precond < 0 || P.precond > 1 ||
         !(P.fp32_floor >= 0.0) || !std::isfinite(P.gamma_f))
         return MDOT_ERR_INVALID_ARG;
     return MDOT_OK;
@@ -424,6 +424,7 @@ mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const C
         a.ls_max_trials = P.ls_max_trials;
         a.max_iter = P.max_iter;
         a.Aglob = 0;
+        a.precond = P.precond;
         if (all64) {
             a.tier = TIER_F64;
             a.tol = tol;
@@ -627,7 +628,8 @@ mdot_status mdot_solve_batch(mdot_handle* h, int32_t nprob, const mdot_problem* 
     if (nprob == 0) return MDOT_OK;
     mdot_params P;
     if (prm) P = *prm; else mdot_default_params(&P);
-    if (params_ok(P) != MDOT_OK || P.precision == MDOT_PREC_FP64 || P.projector != 0 || P.stop_entropy != 0)
+    if (params_ok(P) != MDOT_OK || P.precision == MDOT_PREC_FP64 || P.projector != 0 || P.stop_entropy != 0 ||
+        P.precond != 0)
         return MDOT_ERR_INVALID_ARG;
     std::vector<BatchProblem> bp(nprob);
     for (int k = 0; k < nprob; ++k) {

@@ -19,8 +19,13 @@ cudaError_t launch_stage_regen(int tier, const WS& ws, const StageArgs& a, cudaS
 cudaError_t launch_dual_eval_regen(int tier, const WS& ws, const EvalArgs& a, cudaStream_t s);
 cudaError_t configure_regen_kernels(int max_n, int G, int* min_blocks);
 
+cudaError_t launch_stage_precond(int tier, const WS& ws, const StageArgs& a, cudaStream_t s);
+cudaError_t configure_precond_kernels(int G, int* min_blocks);
+
 cudaError_t launch_stage(int tier, const WS& ws, const StageArgs& a, cudaStream_t s)
 {
+    // the diagonal-Hessian direction lives in the barrier-synchronised kernel (fp32 tiers: own unit)
+    if (a.precond && tier != TIER_F64) return launch_stage_precond(tier, ws, a, s);
     if (ws.ckind != COST_DENSE) return launch_stage_regen(tier, ws, a, s);
     WS w = ws;
     StageArgs aa = a;
@@ -81,7 +86,9 @@ cudaError_t configure_stage_kernels(int max_n, int G, int* min_blocks)
         if (e != cudaSuccess) return e;
         *min_blocks = std::min(*min_blocks, nb);
     }
-    return configure_regen_kernels(max_n, G, min_blocks);
+    cudaError_t e = configure_regen_kernels(max_n, G, min_blocks);
+    if (e != cudaSuccess) return e;
+    return configure_precond_kernels(G, min_blocks);
 }
 
 }  // namespace mdot

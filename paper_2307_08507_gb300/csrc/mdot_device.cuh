@@ -25,6 +25,9 @@ constexpr double kLog2e = 1.4426950408889634074;
 constexpr double kLn2 = 0.69314718055994530942;
 constexpr double kQuant = 2097152.0;          // 2^21: quantum of the exact part of f, g
 constexpr int kNRed = 6;                       // scalars reduced per evaluation
+// the barrier-synchronised stage kernel adds three for the diagonal-Hessian direction (Eq. (16)):
+// <y, -s_h>, <s_h, grad g> and the count of ratios r~ / r(P) outside [0.01, 100]
+constexpr int kNRedP = 9;
 constexpr int kStallIters = 400;               // accepted iterations without 1 % progress end a stage
                                                // (||grad g||_1 is not monotone along PNCG: a last-resort guard)
 constexpr int kThreads = 256;                  // CTA size of the cooperative kernels
@@ -63,6 +66,7 @@ struct State {
     int status;            // SolveStatus (sticky, worst wins)
     int since_best;        // accepted iterations since ||grad g||_1 last improved by 1 %
     int stalls;            // stages ended by the stall rule (cumulative)
+    int hess;              // the direction committed next uses the diagonal-Hessian form (Eq. (16))
     double best_gnorm;     // smallest ||grad g||_1 seen in this stage
     long long evals, evals64, iters, ls_trials;
     GridBar bar;
@@ -87,7 +91,7 @@ struct WS {
     int* A;                           // per-row log2 scales
     float* colpart;                   // [G][n] fp32 column partials
     double* colpartd;                 // [G][n] fp64 column partials
-    double* blockred;                 // [G][kNRed]
+    double* blockred;                 // [G][kNRedP]
     double* scratch;                  // [G][8] misc per-CTA values
     State* st;
     // flags of the stage kernel: [2][G] evaluation tags (column partials written; column state
@@ -102,6 +106,7 @@ struct WS {
 struct StageArgs {
     double gamma, G64, tol, w, ratio, c1, c2;
     int first, warm_start, tier, ls_max_trials, max_iter, Aglob;
+    int precond;           // 1: diagonal-Hessian direction (Eq. (16)) where every ratio allows it
 };
 
 // Arguments of the standalone dual evaluation (mdot_dual_eval).
@@ -249,27 +254,28 @@ __device__ __forceinline__ void butterfly(T (&v)[N], int lane)
     }
 }
 
-// Block-wide sum of kNRed doubles; result valid in thread 0.  red_smem: >= 32 * kNRed doubles.
-// Fixed reduction tree (deterministic); the last step runs on kNRed lanes in parallel.
-__device__ __forceinline__ void block_reduce_nred(double (&x)[kNRed], double* red_smem)
+// Block-wide sum of NR doubles; result valid in thread 0.  red_smem: >= 32 * NR doubles.
+// Fixed reduction tree (deterministic); the last step runs on NR lanes in parallel.
+template <int NR>
+__device__ __forceinline__ void block_reduce_nred(double (&x)[NR], double* red_smem)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-    for (int q = 0; q < kNRed; ++q)
+    for (int q = 0; q < NR; ++q)
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) x[q] += __shfl_xor_sync(0xffffffffu, x[q], o);
     __syncthreads();
     if (lane == 0)
 #pragma unroll
-        for (int q = 0; q < kNRed; ++q) red_smem[warp * kNRed + q] = x[q];
+        for (int q = 0; q < NR; ++q) red_smem[warp * NR + q] = x[q];
     __syncthreads();
     if (warp == 0) {
         double s = 0.0;
-        if (lane < kNRed)
-            for (int w = 0; w < nw; ++w) s += red_smem[w * kNRed + lane];
+        if (lane < NR)
+            for (int w = 0; w < nw; ++w) s += red_smem[w * NR + lane];
         // move lane q's total into x[q] of thread 0
 #pragma unroll
-        for (int q = 0; q < kNRed; ++q) {
+        for (int q = 0; q < NR; ++q) {
             const double t = __shfl_sync(0xffffffffu, s, q);
             if (lane == 0) x[q] = t;
         }

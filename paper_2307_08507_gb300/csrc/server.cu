@@ -408,7 +408,8 @@ mdot_status mdot_server_create(mdot_server** out, uint64_t workspace_bytes, cons
     *out = nullptr;
     mdot_params P;
     if (prm) P = *prm; else mdot_default_params(&P);
-    if (params_valid(P) != MDOT_OK || P.precision == MDOT_PREC_FP64 || P.projector != 0 || P.stop_entropy != 0)
+    if (params_valid(P) != MDOT_OK || P.precision == MDOT_PREC_FP64 || P.projector != 0 || P.stop_entropy != 0 ||
+        P.precond != 0)
         return MDOT_ERR_INVALID_ARG;
     const size_t pool_doubles = (size_t)(workspace_bytes / sizeof(double));
     if (pool_doubles < batch_slot_doubles(kStrideAlign)) return MDOT_ERR_INVALID_ARG;

@@ -18,7 +18,11 @@ namespace mdot {
 // ---------------------------------------------------------------------------------------------
 static __device__ void decide(State* S, const double* tot, const StageArgs& a)
 {
-    const double phi = tot[0], gn = tot[1], num = tot[2], den = tot[3], S1 = tot[4];
+    const double phi = tot[0], gn = tot[1], den = tot[3];
+    // Sinkhorn direction (Eq. (17)), or the diagonal-Hessian one (Eq. (16)) when asked for and
+    // every ratio allows it; tot[6..8] exist only where precond can be set
+    const bool hess = a.precond && tot[8] == 0.0;
+    const double num = hess ? tot[6] : tot[2], S1 = hess ? tot[7] : tot[4];
     const bool bad = tot[5] > 0.0 || !isfinite(phi) || !isfinite(gn);
     S->evals += 1;
     if (a.tier == TIER_F64) S->evals64 += 1;
@@ -75,6 +79,7 @@ static __device__ void decide(State* S, const double* tot, const StageArgs& a)
     }
     S->accept = accept ? 1 : 0;
     if (!accept) return;
+    S->hess = hess ? 1 : 0;
 
     const bool was_init = (S->kind == KIND_INIT);
     S->alpha_commit = was_init ? 0.0 : S->alpha;
@@ -287,6 +292,20 @@ __device__ __forceinline__ double row_total(const unsigned char* sm, const SmemL
     return s;
 }
 
+// Eq. (16): the diagonal-Hessian direction s_h = r~ / r(P) - 1 = exp(s) - 1 with s of Eq. (17),
+// taken where every ratio r~ / r(P), c~ / c(P) lies in [0.01, 100] (otherwise s itself)
+constexpr double kLogRatioLo = -4.605170185988091;     // log 0.01
+constexpr double kLogRatioHi = 4.605170185988091;      // log 100
+__device__ __forceinline__ double hess_dir(double s) { return (double)expm1f((float)s); }
+__device__ __forceinline__ double dir_of(double s, bool hess) { return hess ? hess_dir(s) : s; }
+__device__ __forceinline__ void hess_terms(double s, double g, double y, double (&x)[kNRedP])
+{
+    const double sh = hess_dir(s);
+    x[6] += y * (-sh);
+    x[7] += sh * g;
+    if (!(s >= kLogRatioLo && s <= kLogRatioHi)) x[8] += 1.0;
+}
+
 // ---------------------------------------------------------------------------------------------
 // the stage kernel
 // ---------------------------------------------------------------------------------------------
@@ -297,7 +316,7 @@ template <int TIER, int COST>
 __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel(WS ws, StageArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
-    __shared__ double red_smem[32 * kNRed];
+    __shared__ double red_smem[32 * kNRedP];
     __shared__ double s_bc[8];
     __shared__ int s_flag[2];
     __shared__ unsigned int s_gen;
@@ -377,9 +396,9 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel(WS ws, StageArg
     for (;;) {
         // ---------------- phase A: pass over own rows, row epilogue ----------------
         phase_A<TIER, COST>(ws, ColPlain{ws.Hh, ws.Wc, ws.colpart + (size_t)b * n}, r0, r1, gamma, G64, sm, L);
-        double x[kNRed];
+        double x[kNRedP];
 #pragma unroll
-        for (int q = 0; q < kNRed; ++q) x[q] = 0.0;
+        for (int q = 0; q < kNRedP; ++q) x[q] = 0.0;
         {
             const int* sA = reinterpret_cast<const int*>(sm + L.off_A);
             for (int i = r0 + tid; i < r1; i += T) {
@@ -400,6 +419,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel(WS ws, StageArg
                 x[2] += y * (-s);
                 x[3] += y * p;
                 x[4] += s * g;
+                if (a.precond) hess_terms(s, g, y, x);
                 R[RS_GT * NL + il] = g;
                 R[RS_ST * NL + il] = s;
                 R[RS_LTR * NL + il] = ((double)__log2f((float)sum) + (double)sA[il]) * kLn2;   // scale only
@@ -428,6 +448,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel(WS ws, StageArg
                 x[2] += y * (-s);
                 x[3] += y * p;
                 x[4] += s * g;
+                if (a.precond) hess_terms(s, g, y, x);
                 Q[CS_GT * NL + jl] = g;
                 Q[CS_ST * NL + jl] = s;
             }
@@ -435,7 +456,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel(WS ws, StageArg
         block_reduce_nred(x, red_smem);
         if (tid == 0) {
 #pragma unroll
-            for (int q = 0; q < kNRed; ++q) ws.blockred[(size_t)b * kNRed + q] = x[q];
+            for (int q = 0; q < kNRedP; ++q) ws.blockred[(size_t)b * kNRedP + q] = x[q];
         }
 
         // ---------------- reduction + decision by the last CTA ----------------
@@ -444,12 +465,12 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel(WS ws, StageArg
             __threadfence();
             // warp q sums scalar q over the G CTAs in a fixed order; all loads issued first
             const int lane = tid & 31, warp = tid >> 5;
-            if (warp < kNRed) {
+            if (warp < (a.precond ? kNRedP : kNRed)) {
                 double v8[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
                     const int bb = lane + 32 * k;
-                    v8[k] = (bb < G) ? __ldcg(ws.blockred + (size_t)bb * kNRed + warp) : 0.0;
+                    v8[k] = (bb < G) ? __ldcg(ws.blockred + (size_t)bb * kNRedP + warp) : 0.0;
                 }
                 double sacc = 0.0;
 #pragma unroll
@@ -460,8 +481,8 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel(WS ws, StageArg
             }
             __syncthreads();
             if (tid == 0) {
-                double tot[kNRed];
-                for (int q = 0; q < kNRed; ++q) tot[q] = red_smem[q];
+                double tot[kNRedP];
+                for (int q = 0; q < kNRedP; ++q) tot[q] = a.precond ? red_smem[q] : (q < kNRed ? red_smem[q] : 0.0);
                 // decide on a local copy: one pipelined load and one store of the state words
                 State loc;
                 unsigned long long* lw = reinterpret_cast<unsigned long long*>(&loc);
@@ -479,16 +500,17 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel(WS ws, StageArg
         if (tid == 0) {
             const volatile State* vS = S;
             const double d0 = vS->alpha, d1 = vS->alpha_commit, d2 = vS->beta;
-            const int i3 = vS->accept, i4 = vS->phase;
+            const int i3 = vS->accept, i4 = vS->phase, i5 = vS->hess;
             s_bc[0] = d0;
             s_bc[1] = d1;
             s_bc[2] = d2;
             s_bc[3] = (double)i3;
             s_bc[4] = (double)i4;
+            s_bc[5] = (double)i5;
         }
         __syncthreads();
         const double alpha = s_bc[0], acommit = s_bc[1], beta = s_bc[2];
-        const bool accept = s_bc[3] != 0.0, done = s_bc[4] != 0.0;
+        const bool accept = s_bc[3] != 0.0, done = s_bc[4] != 0.0, hess = s_bc[5] != 0.0;
 
         // ---------------- phase C: commit, new direction, next trial constants ----------------
         for (int i = r0 + tid; i < r1; i += T) {
@@ -499,7 +521,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel(WS ws, StageArg
                 R[RS_U * NL + il] = u;
                 R[RS_G * NL + il] = R[RS_GT * NL + il];
                 R[RS_L * NL + il] = R[RS_LTR * NL + il];
-                p = R[RS_ST * NL + il] + beta * p;              // p = s + beta p, beta = 0 on reset (Alg. 2)
+                p = dir_of(R[RS_ST * NL + il], hess) + beta * p;   // p = s + beta p, beta = 0 on reset (Alg. 2)
                 R[RS_P * NL + il] = p;
             }
             if (!done) prep_row<TIER>(u + alpha * p, row_scale(R[RS_L * NL + il] + alpha * p), a.Aglob,
@@ -512,7 +534,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel(WS ws, StageArg
                 v = v + acommit * p;
                 Q[CS_V * NL + jl] = v;
                 Q[CS_G * NL + jl] = Q[CS_GT * NL + jl];
-                p = Q[CS_ST * NL + jl] + beta * p;
+                p = dir_of(Q[CS_ST * NL + jl], hess) + beta * p;
                 Q[CS_P * NL + jl] = p;
             }
             if (!done) prep_col<TIER>(ws, j, v + alpha * p, gamma, G64);

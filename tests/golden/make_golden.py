@@ -5,7 +5,7 @@ from the CUDA library.  Each record holds, for one (cost kind, seed, target gap)
   H_min, the Prop. 2 gamma_f, the oracle's rounded-plan cost and c-transform bound, its
   evaluation counts, and the exact OT value (column generation priced over all n^2 arcs).
 Usage:  python tests/golden/make_golden.py [k] [eps ...]   (defaults: k = 64, eps = 1e-6)
-        python tests/golden/make_golden.py --exact-only [k]   (only the exact OT values)
+        python tests/golden/make_golden.py --exact-only [k [kind]]   (only the exact OT values)
         python tests/golden/make_golden.py --oracle-only k kind eps   (one oracle solve, no exact value)
         python tests/golden/make_golden.py --line n ...   (exact costs of the points-on-a-line
             problems, seed 11: the monotone coupling, into tests/golden/line_exact.json)
@@ -101,7 +101,8 @@ def main():
     ctx = mp.get_context("spawn")
     if len(sys.argv) > 1 and sys.argv[1] == "--exact-only":
         k = int(sys.argv[2]) if len(sys.argv) > 2 else 64
-        cases = [(k, kind, SEED) for kind in ("l2sq", "l1")]
+        kinds = sys.argv[3:] or ["l2sq", "l1"]
+        cases = [(k, kind, SEED) for kind in kinds]
         path = os.path.join(HERE, f"exact{k * k}.json")
         with ctx.Pool(len(cases)) as pool:
             for rec in pool.imap_unordered(exact_case, cases):
