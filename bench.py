@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample-evals", type=int, default=0, help="oracle evaluations in the CPU sample")
     ap.add_argument("--case", default="solve",
-                    choices=["solve", "dual_eval", "stage", "batch", "serve", "sinkhorn", "large_n", "nscale", "hmin"],
+                    choices=["solve", "dual_eval", "dual_eval_regen", "stage", "batch", "serve", "sinkhorn", "large_n",
+                             "nscale", "hmin"],
                     help="dual_eval / stage: run only that kernel (for profiler captures); sinkhorn, large_n, "
                          "nscale, hmin: the comparison studies (one JSON line per solve)")
     ap.add_argument("--grid", type=int, default=64, help="k of the k x k grid for --case runs")
@@ -51,6 +52,19 @@ def parse():
     ap.add_argument("--serve-lanes", type=int, default=None, help="server routing: big lanes")
     ap.add_argument("--serve-lane-ctas", type=int, default=None, help="server routing: CTAs per big lane")
     return ap.parse_args()
+
+
+# fp32 operations per entry of an evaluation with the squared-Euclidean cost regenerated in the
+# exact order of the dense cost: 3 differences, 3 products, 2 sums, the scale (9); the exponent
+# argument from the row and column constants (4: two adds, two fmas); the row and column sums (2)
+ALU_OPS_PER_ENTRY = 15
+
+
+def alu_peak_ops():
+    """fp32 issue bound of the GPU: SMs x 128 fp32 lanes per SM per clock x the maximum SM clock
+    (2070 MHz on GB300)."""
+    import torch
+    return torch.cuda.get_device_properties(0).multi_processor_count * 128 * 2070e6
 
 
 def golden_case(kind="l2sq"):
@@ -437,18 +451,39 @@ def run_ours(args, rank, world):
         lr, _ = h.dual_eval(uq, vq, gam, Cq)
         for _ in range(3):
             h.dual_eval(uq, vq, gam, Cq, ref_log_rP=lr)
-        ts = []
+        ts, tk = [], []
         for _ in range(10):
-            flush.fill_(1.0)
+            flush.fill_(1.0)                      # C (64 MiB / 1 GiB) starts outside L2
             ev0.record(stream)
             h.dual_eval(uq, vq, gam, Cq, ref_log_rP=lr)
             ev1.record(stream)
             torch.cuda.synchronize()
             ts.append(ev0.elapsed_time(ev1) / 1e3)
+            tk.append(h.dual_eval_time() / 1e3)   # the kernel alone: events around its launch
         tmed = sorted(ts)[len(ts) // 2]
-        gbs = 4.0 * q.n * q.n / tmed / 1e9
-        dual[f"n{q.n}"] = {"us": tmed * 1e6, "GBps": gbs, "frac_hbm": gbs / hbm}
+        kmed = sorted(tk)[len(tk) // 2]
+        gbs = 4.0 * q.n * q.n / kmed / 1e9
+        dual[f"n{q.n}"] = {"us": kmed * 1e6, "GBps": gbs, "frac_hbm": gbs / hbm,
+                           "us_call": tmed * 1e6, "bytes": 4 * q.n * q.n}
         del Cq
+    # the same evaluation with C regenerated from the 2-D grid coordinates (n = 16384): no n^2
+    # bytes, bound by the fp32 pipe (ALU_OPS_PER_ENTRY fp32 operations and one ex2 per entry)
+    q = I.grid_problem(128, SEED, dense=False)
+    xy = torch.from_numpy(I.coords3(q.x)).to(dev)
+    uq = torch.from_numpy(np.log(q.r)).to(dev)
+    vq = torch.from_numpy(np.log(q.c)).to(dev)
+    lr, _ = h.dual_eval_points(uq, vq, 2.0 ** 12, xy, xy, M.COST_SQEUCLID, q.scale)
+    tk = []
+    for _ in range(10):
+        h.dual_eval_points(uq, vq, 2.0 ** 12, xy, xy, M.COST_SQEUCLID, q.scale, ref_log_rP=lr)
+        tk.append(h.dual_eval_time() / 1e3)
+    kmed = sorted(tk)[len(tk) // 2]
+    ents = float(q.n) * q.n / kmed
+    alu_peak = alu_peak_ops()
+    dual["n16384_regen"] = {"us": kmed * 1e6, "entries_per_s": ents, "bound": "alu",
+                            "achieved_ops": ents * ALU_OPS_PER_ENTRY, "peak_ops": alu_peak,
+                            "frac_alu": ents * ALU_OPS_PER_ENTRY / alu_peak,
+                            "ops_per_entry": ALU_OPS_PER_ENTRY}
 
     batch = measure_batch(h, dev, stream) if (rank == 0 and not args.no_batch) else None
     serving = measure_serving(dev, args.serve_count) if (rank == 0 and args.serve_count > 0) else None
@@ -629,6 +664,13 @@ def run_case(args):
         lr, _ = h.dual_eval(u, v, 2.0 ** 12, C)
         for _ in range(args.reps):
             h.dual_eval(u, v, 2.0 ** 12, C, ref_log_rP=lr)
+    elif args.case == "dual_eval_regen":
+        u = torch.from_numpy(np.log(p.r)).to(dev)
+        v = torch.from_numpy(np.log(p.c)).to(dev)
+        xy = torch.from_numpy(I.coords3(p.x)).to(dev)
+        lr, _ = h.dual_eval_points(u, v, 2.0 ** 12, xy, xy, M.COST_SQEUCLID, p.scale)
+        for _ in range(args.reps):
+            h.dual_eval_points(u, v, 2.0 ** 12, xy, xy, M.COST_SQEUCLID, p.scale, ref_log_rP=lr)
     else:
         r = torch.from_numpy(p.r).to(dev)
         c = torch.from_numpy(p.c).to(dev)

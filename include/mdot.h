@@ -216,6 +216,15 @@ mdot_status mdot_dual_eval_points(mdot_handle* h, const double* u, const double*
                                   int64_t n, const double* ref_log_rP, int32_t precision,
                                   double* log_rP, double* log_cP);
 
+/*
+ * Device time, in milliseconds, of the evaluation kernel launched by the last successful
+ * mdot_dual_eval / mdot_dual_eval_points call on h (CUDA events recorded on the handle's stream
+ * immediately around that launch; the copies of the results are outside it).  ms_out: host.
+ * MDOT_NOT_READY if no evaluation has completed on h yet (or the last one failed);
+ * INVALID_ARG for NULL arguments.
+ */
+mdot_status mdot_dual_eval_time(const mdot_handle* h, double* ms_out);
+
 /* One problem of a batch.  Device pointers; either C (dense n x n fp32) or x, y (n x 3 fp32,
  * regenerated cost of kind cost_kind with the given scale). */
 typedef struct mdot_problem {

@@ -89,8 +89,10 @@ def lib():
                                     ct.POINTER(ct.c_double), ct.POINTER(Info)]
     L.mdot_dual_eval_points.argtypes = [_P, _P, _P, ct.c_double, _P, _P, ct.c_int32, ct.c_float, ct.c_int64,
                                         _P, ct.c_int32, _P, _P]
+    L.mdot_dual_eval_time.argtypes = [_P, ct.POINTER(ct.c_double)]
     for name in ("mdot_create", "mdot_destroy", "mdot_dual_eval", "mdot_round", "mdot_lower_bound",
-                 "mdot_solve", "mdot_solve_host", "mdot_solve_points", "mdot_dual_eval_points"):
+                 "mdot_solve", "mdot_solve_host", "mdot_solve_points", "mdot_dual_eval_points",
+                 "mdot_dual_eval_time"):
         getattr(L, name).restype = ct.c_int32
     _lib = L
     return L
@@ -182,6 +184,14 @@ class Handle:
         if s != MDOT_OK:
             raise MdotError(s, "mdot_dual_eval")
         return lr, lc
+
+    def dual_eval_time(self) -> float:
+        """mdot_dual_eval_time: device milliseconds of the last dual-evaluation kernel."""
+        ms = ct.c_double(0.0)
+        s = lib().mdot_dual_eval_time(self._h, ct.byref(ms))
+        if s != MDOT_OK:
+            raise MdotError(s, "mdot_dual_eval_time")
+        return ms.value
 
     def round(self, u, v, gamma: float, C, r, c, want_G: bool = False):
         import torch

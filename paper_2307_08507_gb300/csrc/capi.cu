@@ -56,8 +56,13 @@ struct mdot_handle {
     // bound, from the evaluation counts); cleared well before the 32-bit tag could wrap
     unsigned long long tags_used = 0;
     size_t flag_bytes = 0;
+    // device time of the last standalone dual-evaluation kernel (events around its launch)
+    cudaEvent_t de_ev[2] = {nullptr, nullptr};
+    double de_ms = -1.0;
     ~mdot_handle()
     {
+        if (de_ev[0]) cudaEventDestroy(de_ev[0]);
+        if (de_ev[1]) cudaEventDestroy(de_ev[1]);
         cudaFree(d_r); cudaFree(d_c); cudaFree(d_u); cudaFree(d_v); cudaFree(d_C);
         cudaFree(b_slots); cudaFree(b_probs); cudaFree(b_results); cudaFree(b_order); cudaFree(b_next);
     }
@@ -613,11 +618,20 @@ static mdot_status dual_eval_core(mdot_handle* h, const double* u, const double*
     a.ref = ref_log_rP;
     const int tier = (precision == MDOT_PREC_FP64) ? TIER_F64 : (precision == MDOT_PREC_FP32A) ? TIER_F32A : TIER_F32;
     CKR(reset_state(h));
+    if (!h->de_ev[0]) {
+        CKR(cudaEventCreate(&h->de_ev[0]));
+        CKR(cudaEventCreate(&h->de_ev[1]));
+    }
+    h->de_ms = -1.0;
+    CKR(cudaEventRecord(h->de_ev[0], h->stream));
     CKR(launch_dual_eval(tier, ws, a, h->stream));
+    CKR(cudaEventRecord(h->de_ev[1], h->stream));
     CKR(cudaMemcpyAsync(log_rP, ws.lrtr, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     CKR(cudaMemcpyAsync(log_cP, ws.lcout, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     CKR(cudaMemcpyAsync(h->h_state, ws.st, sizeof(State), cudaMemcpyDeviceToHost, h->stream));
     CKR(cudaStreamSynchronize(h->stream));
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, h->de_ev[0], h->de_ev[1]) == cudaSuccess) h->de_ms = ms;
     return h->h_state->status == ST_OK ? MDOT_OK : MDOT_ERR_TIMEOUT;
 }
 
@@ -727,6 +741,13 @@ mdot_status mdot_dual_eval(mdot_handle* h, const double* u, const double* v, dou
     CostSpec cs;
     cs.C = C;
     return dual_eval_core(h, u, v, gamma, cs, n, ref_log_rP, precision, log_rP, log_cP);
+}
+
+mdot_status mdot_dual_eval_time(const mdot_handle* h, double* ms_out)
+{
+    if (!h || !ms_out) return MDOT_ERR_INVALID_ARG;
+    *ms_out = h->de_ms;
+    return h->de_ms >= 0.0 ? MDOT_OK : MDOT_NOT_READY;
 }
 
 mdot_status mdot_dual_eval_points(mdot_handle* h, const double* u, const double* v, double gamma,

@@ -70,6 +70,28 @@ def test_dual_eval_matches_oracle(h, n, gamma, precision):
     np.testing.assert_allclose(lc2.cpu().numpy(), lc_o, rtol=0, atol=tol)
 
 
+def test_dual_eval_time_reports_the_kernel():
+    """mdot_dual_eval_time: NOT_READY before any evaluation on the handle, then the device time of
+    the last evaluation kernel (positive, below the host time of the whole call)."""
+    import time
+    torch.cuda.set_device(0)
+    n = 512
+    rng = np.random.default_rng(3)
+    C = t(rng.uniform(0, 1, (n, n)).astype(np.float32))
+    u = torch.zeros(n, dtype=torch.float64, device=DEV)
+    with M.Handle(n) as hh:
+        with pytest.raises(M.MdotError) as e:
+            hh.dual_eval_time()
+        assert e.value.status == M.MDOT_NOT_READY
+        hh.dual_eval(u, u, 64.0, C)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hh.dual_eval(u, u, 64.0, C)
+        wall = time.perf_counter() - t0
+        ms = hh.dual_eval_time()
+        assert 0.0 < ms < wall * 1e3
+
+
 def test_dual_eval_huge_potentials(h):
     """Potentials of +-2000 (exp overflows without scaling): both log-marginals stay exact."""
     n, gamma = 64, 1e5
