@@ -191,6 +191,94 @@ __device__ __forceinline__ float point_cost(float x0, float x1, float x2, float 
     return __fmul_rn(D, s);
 }
 
+// Packed fp32 pairs: one instruction computes two entries on this GPU; every component is
+// rounded exactly as the scalar operation it stands for (round to nearest), so the packed passes
+// give the same bits as the scalar forms above.
+__device__ __forceinline__ float2 pk(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b with one rounding: b * (-1) is exact inside the fma
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+
+// exp2_acc on a pair.  -k = 1.5 * 2^23 - t is exact (t lies within a factor 2 of 1.5 * 2^23), and
+// the fma with it rounds as the scalar fmaf(G32, d, -k) does.
+__device__ __forceinline__ float2 exp2_acc2(float2 d, float2 G32, float2 Glo, float2 W)
+{
+    const float2 M = pk(12582912.0f);
+    const float2 th = fma2(G32, d, W);
+    const float2 t = add2(th, M);
+    const float2 nk = sub2(M, t);
+    float2 x = fma2(G32, d, nk);
+    x = fma2(Glo, d, add2(x, W));
+    float2 p = pk(1.53458124e-4f);
+    p = fma2(p, x, pk(1.33999309e-3f));
+    p = fma2(p, x, pk(9.61848907e-3f));
+    p = fma2(p, x, pk(5.55032864e-2f));
+    p = fma2(p, x, pk(2.40226462e-1f));
+    p = fma2(p, x, pk(6.93147182e-1f));
+    p = fma2(p, x, pk(1.0f));
+    return mul2(p, make_float2(ex2f(-nk.x), ex2f(-nk.y)));
+}
+
+// Two entries of one row: E = 2^(G ((fh + hh) - C) + wr + wc), as the scalar passes compute it.
+template <bool ACC>
+__device__ __forceinline__ float2 entry2(float2 fh, float2 wr, float2 hh, float2 wc, float2 cv, float2 G32, float2 Glo)
+{
+    const float2 d = sub2(add2(fh, hh), cv);
+    const float2 W = add2(wr, wc);
+    if (ACC) return exp2_acc2(d, G32, Glo, W);
+    const float2 a = fma2(Glo, d, fma2(G32, d, W));
+    return make_float2(ex2f(a.x), ex2f(a.y));
+}
+
+// The four entries of one row in a float4 column group: the row sum takes them in column order,
+// the column partials ca += E s.
+template <bool ACC>
+__device__ __forceinline__ void entry4(float fh, float wr, float s, const float2 (&hh)[2], const float2 (&wc)[2],
+                                       float2 c01, float2 c23, float2 G32, float2 Glo, float& rp, float2 (&ca)[2])
+{
+    const float2 FH = pk(fh), WR = pk(wr), S = pk(s);
+    const float2 E0 = entry2<ACC>(FH, WR, hh[0], wc[0], c01, G32, Glo);
+    const float2 E1 = entry2<ACC>(FH, WR, hh[1], wc[1], c23, G32, Glo);
+    rp += E0.x;
+    rp += E0.y;
+    rp += E1.x;
+    rp += E1.y;
+    ca[0] = fma2(E0, S, ca[0]);
+    ca[1] = fma2(E1, S, ca[1]);
+}
+
+// point_cost on a pair of columns (same row)
+template <int KIND>
+__device__ __forceinline__ float2 point_cost2(float2 x0, float2 x1, float2 x2, float2 y0, float2 y1, float2 y2,
+                                              float2 s)
+{
+    const float2 d0 = sub2(x0, y0), d1 = sub2(x1, y1), d2 = sub2(x2, y2);
+    float2 D;
+    if (KIND == COST_SQEUCLID)
+        D = add2(add2(mul2(d0, d0), mul2(d1, d1)), mul2(d2, d2));
+    else
+        D = add2(add2(make_float2(fabsf(d0.x), fabsf(d0.y)), make_float2(fabsf(d1.x), fabsf(d1.y))),
+                 make_float2(fabsf(d2.x), fabsf(d2.y)));
+    return mul2(D, s);
+}
+
+// column constants of a float4 group as pairs, and the pairs of column partials back to a float4
+template <int KK>
+__device__ __forceinline__ void to_pairs(const float (&a)[KK][4], float2 (&b)[KK][2])
+{
+#pragma unroll
+    for (int k = 0; k < KK; ++k) {
+        b[k][0] = make_float2(a[k][0], a[k][1]);
+        b[k][1] = make_float2(a[k][2], a[k][3]);
+    }
+}
+__device__ __forceinline__ void from_pairs(const float2 (&b)[2], float (&a)[4])
+{
+    a[0] = b[0].x; a[1] = b[0].y; a[2] = b[1].x; a[3] = b[1].y;
+}
+
 __device__ __forceinline__ float4 ldg4(const float* p)
 {
     return __ldg(reinterpret_cast<const float4*>(p));
@@ -567,18 +655,21 @@ __device__ __forceinline__ void pass_f32(const float* __restrict__ C, int n, int
                                          const float* sFh, const float* sWr, const float* sS,
                                          float G32, float Glo, float* sRow, int nloc)
 {
+    const float2 G32p = pk(G32), Glop = pk(Glo);
     const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int BN = 4 * kK * T;
     for (int cb = 0; cb < n; cb += BN) {
-        float hh[kK][4], wc[kK][4], ca[kK][4];
+        float hh[kK][4], wc[kK][4];
+        float2 hh2[kK][2], wc2[kK][2], ca2[kK][2];
         int jk[kK];
 #pragma unroll
         for (int k = 0; k < kK; ++k) {
             jk[k] = cb + 4 * (tid + k * T);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) ca[k][e] = 0.0f;
+            ca2[k][0] = ca2[k][1] = make_float2(0.0f, 0.0f);
         }
         io.load_seg(jk, n, hh, wc);
+        to_pairs(hh, hh2);
+        to_pairs(wc, wc2);
         for (int rg = r0; rg < r1; rg += kRG) {
             float rp[kRG];
 #pragma unroll
@@ -602,18 +693,8 @@ __device__ __forceinline__ void pass_f32(const float* __restrict__ C, int n, int
 #pragma unroll
                             for (int e = 0; e < 4; ++e) cv[e] = (jk[k] + e < n) ? __ldg(Crow + jk[k] + e) : 0.0f;
                         }
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const float d = (fh + hh[k][e]) - cv[e];
-                            float E;
-                            if (ACC) {
-                                E = exp2_acc(d, G32, Glo, wr + wc[k][e]);
-                            } else {
-                                E = ex2f(fmaf(Glo, d, fmaf(G32, d, wr + wc[k][e])));
-                            }
-                            rp[ii] += E;
-                            ca[k][e] = fmaf(E, s, ca[k][e]);
-                        }
+                        entry4<ACC>(fh, wr, s, hh2[k], wc2[k], make_float2(cv[0], cv[1]), make_float2(cv[2], cv[3]),
+                                    G32p, Glop, rp[ii], ca2[k]);
                     }
                 }
             }
@@ -622,7 +703,11 @@ __device__ __forceinline__ void pass_f32(const float* __restrict__ C, int n, int
             if (lane < kRG && il < r1) sRow[warp * nloc + (il - r0)] += rp[0];
         }
 #pragma unroll
-        for (int k = 0; k < kK; ++k) io.store4(jk[k], n, ca[k]);
+        for (int k = 0; k < kK; ++k) {
+            float ca[4];
+            from_pairs(ca2[k], ca);
+            io.store4(jk[k], n, ca);
+        }
     }
 }
 
@@ -755,6 +840,7 @@ __device__ __forceinline__ void pass_f32_tma(const float* __restrict__ C, int n,
                                              float Glo, float* sRow, int nloc, float* ring, int nst,
                                              unsigned long long* bars, int* s_issued, unsigned int* abort)
 {
+    const float2 G32p = pk(G32), Glop = pk(Glo);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nrows = r1 - r0;
     const int ncb = (n + kSegFloats - 1) / kSegFloats;
@@ -795,17 +881,19 @@ __device__ __forceinline__ void pass_f32_tma(const float* __restrict__ C, int n,
         bool ok = true;
         for (int cbi = 0; cbi < ncb; ++cbi) {
             const int cb = cbi * kSegFloats;
-            float hh[kK][4], wc[kK][4], ca[kK][4];
+            float hh[kK][4], wc[kK][4];
+            float2 hh2[kK][2], wc2[kK][2], ca2[kK][2];
             int jk[kK];
 #pragma unroll
             for (int k = 0; k < kK; ++k) {
                 jk[k] = cb + 4 * (tid + k * kConsumerThreads);
-#pragma unroll
-                for (int e = 0; e < 4; ++e) ca[k][e] = 0.0f;
+                ca2[k][0] = ca2[k][1] = make_float2(0.0f, 0.0f);
             }
             // a constant that never arrives (timeout) turns this consumer into a pass-through: it
             // still releases every ring slot so that the producer can finish
             if (!io.load_seg(jk, n, hh, wc)) ok = false;
+            to_pairs(hh, hh2);
+            to_pairs(wc, wc2);
             for (int rg = r0; rg < r1; rg += kRG) {
                 float rp[kRG];
 #pragma unroll
@@ -824,18 +912,8 @@ __device__ __forceinline__ void pass_f32_tma(const float* __restrict__ C, int n,
                                 const float4 t4 = seg[tid + k * kConsumerThreads];
                                 cv[0] = t4.x; cv[1] = t4.y; cv[2] = t4.z; cv[3] = t4.w;
                             }
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const float d = (fh + hh[k][e]) - cv[e];
-                                float E;
-                                if (ACC) {
-                                    E = exp2_acc(d, G32, Glo, wr + wc[k][e]);
-                                } else {
-                                    E = ex2f(fmaf(Glo, d, fmaf(G32, d, wr + wc[k][e])));
-                                }
-                                rp[ii] += E;
-                                ca[k][e] = fmaf(E, sc, ca[k][e]);
-                            }
+                            entry4<ACC>(fh, wr, sc, hh2[k], wc2[k], make_float2(cv[0], cv[1]), make_float2(cv[2], cv[3]),
+                                        G32p, Glop, rp[ii], ca2[k]);
                         }
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&empty[s]);
@@ -848,7 +926,11 @@ __device__ __forceinline__ void pass_f32_tma(const float* __restrict__ C, int n,
                 if (lane < kRG && il < r1) sRow[warp * nloc + (il - r0)] += rp[0];
             }
 #pragma unroll
-            for (int k = 0; k < kK; ++k) io.store4(jk[k], n, ca[k]);
+            for (int k = 0; k < kK; ++k) {
+                float ca[4];
+                from_pairs(ca2[k], ca);
+                io.store4(jk[k], n, ca);
+            }
         }
         if (!ok && lane == 0) atomicExch(abort, 1u);
     }
@@ -928,6 +1010,7 @@ __device__ __forceinline__ void pass_f32_ring(const RingGeom& g, int r1, const I
                                               const float* sS, float G32, float Glo, float* sRow, int nloc,
                                               int& consumed, int& issued, unsigned int* abort)
 {
+    const float2 G32p = pk(G32), Glop = pk(Glo);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = g.n, r0 = g.r0, items = g.items();
     if (warp == kConsumerThreads / 32) {
@@ -940,13 +1023,13 @@ __device__ __forceinline__ void pass_f32_ring(const RingGeom& g, int r1, const I
         bool ok = true;
         for (int cbi = 0; cbi < g.ncb; ++cbi) {
             const int cb = cbi * kSegFloats;
-            float hh[kK][4], wc[kK][4], ca[kK][4];
+            float hh[kK][4], wc[kK][4];
+            float2 hh2[kK][2], wc2[kK][2], ca2[kK][2];
             int jk[kK];
 #pragma unroll
             for (int k = 0; k < kK; ++k) {
                 jk[k] = cb + 4 * (tid + k * kConsumerThreads);
-#pragma unroll
-                for (int e = 0; e < 4; ++e) ca[k][e] = 0.0f;
+                ca2[k][0] = ca2[k][1] = make_float2(0.0f, 0.0f);
             }
             if (pre_hh != nullptr && cbi == 0) {
 #pragma unroll
@@ -956,6 +1039,8 @@ __device__ __forceinline__ void pass_f32_ring(const RingGeom& g, int r1, const I
             } else {
                 io.load_seg(jk, n, hh, wc);
             }
+            to_pairs(hh, hh2);
+            to_pairs(wc, wc2);
             for (int rg = r0; rg < r1; rg += kRG) {
                 float rp[kRG];
 #pragma unroll
@@ -974,18 +1059,8 @@ __device__ __forceinline__ void pass_f32_ring(const RingGeom& g, int r1, const I
                                 const float4 t4 = seg[tid + k * kConsumerThreads];
                                 cv[0] = t4.x; cv[1] = t4.y; cv[2] = t4.z; cv[3] = t4.w;
                             }
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const float d = (fh + hh[k][e]) - cv[e];
-                                float E;
-                                if (ACC) {
-                                    E = exp2_acc(d, G32, Glo, wr + wc[k][e]);
-                                } else {
-                                    E = ex2f(fmaf(Glo, d, fmaf(G32, d, wr + wc[k][e])));
-                                }
-                                rp[ii] += E;
-                                ca[k][e] = fmaf(E, sc, ca[k][e]);
-                            }
+                            entry4<ACC>(fh, wr, sc, hh2[k], wc2[k], make_float2(cv[0], cv[1]), make_float2(cv[2], cv[3]),
+                                        G32p, Glop, rp[ii], ca2[k]);
                         }
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&g.empty[s]);
@@ -997,7 +1072,11 @@ __device__ __forceinline__ void pass_f32_ring(const RingGeom& g, int r1, const I
                 if (lane < kRG && il < r1) sRow[warp * nloc + (il - r0)] += rp[0];
             }
 #pragma unroll
-            for (int k = 0; k < kK; ++k) io.store4(jk[k], n, ca[k]);
+            for (int k = 0; k < kK; ++k) {
+                float ca[4];
+                from_pairs(ca2[k], ca);
+                io.store4(jk[k], n, ca);
+            }
         }
         if (!ok && lane == 0) atomicExch(abort, 1u);
     }
@@ -1017,23 +1096,33 @@ __device__ __forceinline__ void pass_f32_regen(const float* __restrict__ Y, floa
     constexpr int KR = 2;
     const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int BN = 4 * KR * T;
+    const float2 G32p = pk(G32), Glop = pk(Glo), CS = pk(cs);
     for (int cb = 0; cb < n; cb += BN) {
-        float hh[KR][4], wc[KR][4], ca[KR][4], y0[KR][4], y1[KR][4], y2[KR][4];
+        float hh[KR][4], wc[KR][4];
+        float2 hh2[KR][2], wc2[KR][2], ca2[KR][2], y0[KR][2], y1[KR][2], y2[KR][2];
         int jk[KR];
 #pragma unroll
         for (int k = 0; k < KR; ++k) jk[k] = cb + 4 * (tid + k * T);
         io.load_seg(jk, n, hh, wc);
+        to_pairs(hh, hh2);
+        to_pairs(wc, wc2);
 #pragma unroll
         for (int k = 0; k < KR; ++k) {
+            float yv[3][4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int j = jk[k] + e;
                 const bool ok = j < n;
-                y0[k][e] = ok ? __ldg(Y + 3 * (size_t)j) : 0.0f;
-                y1[k][e] = ok ? __ldg(Y + 3 * (size_t)j + 1) : 0.0f;
-                y2[k][e] = ok ? __ldg(Y + 3 * (size_t)j + 2) : 0.0f;
-                ca[k][e] = 0.0f;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) yv[a][e] = ok ? __ldg(Y + 3 * (size_t)j + a) : 0.0f;
             }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                y0[k][q] = make_float2(yv[0][2 * q], yv[0][2 * q + 1]);
+                y1[k][q] = make_float2(yv[1][2 * q], yv[1][2 * q + 1]);
+                y2[k][q] = make_float2(yv[2][2 * q], yv[2][2 * q + 1]);
+            }
+            ca2[k][0] = ca2[k][1] = make_float2(0.0f, 0.0f);
         }
         for (int rg = r0; rg < r1; rg += kRG) {
             float rp[kRG];
@@ -1044,22 +1133,12 @@ __device__ __forceinline__ void pass_f32_regen(const float* __restrict__ Y, floa
                 if (i < r1) {
                     const int il = i - r0;
                     const float fh = sFh[il], wr = sWr[il], sc = sS[il];
-                    const float x0 = sX[3 * il], x1 = sX[3 * il + 1], x2 = sX[3 * il + 2];
+                    const float2 x0 = pk(sX[3 * il]), x1 = pk(sX[3 * il + 1]), x2 = pk(sX[3 * il + 2]);
 #pragma unroll
                     for (int k = 0; k < KR; ++k) {
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const float cv = point_cost<KIND>(x0, x1, x2, y0[k][e], y1[k][e], y2[k][e], cs);
-                            const float d = (fh + hh[k][e]) - cv;
-                            float E;
-                            if (ACC) {
-                                E = exp2_acc(d, G32, Glo, wr + wc[k][e]);
-                            } else {
-                                E = ex2f(fmaf(Glo, d, fmaf(G32, d, wr + wc[k][e])));
-                            }
-                            rp[ii] += E;
-                            ca[k][e] = fmaf(E, sc, ca[k][e]);
-                        }
+                        const float2 c01 = point_cost2<KIND>(x0, x1, x2, y0[k][0], y1[k][0], y2[k][0], CS);
+                        const float2 c23 = point_cost2<KIND>(x0, x1, x2, y0[k][1], y1[k][1], y2[k][1], CS);
+                        entry4<ACC>(fh, wr, sc, hh2[k], wc2[k], c01, c23, G32p, Glop, rp[ii], ca2[k]);
                     }
                 }
             }
@@ -1068,7 +1147,11 @@ __device__ __forceinline__ void pass_f32_regen(const float* __restrict__ Y, floa
             if (lane < kRG && il < r1) sRow[warp * nloc + (il - r0)] += rp[0];
         }
 #pragma unroll
-        for (int k = 0; k < KR; ++k) io.store4(jk[k], n, ca[k]);
+        for (int k = 0; k < KR; ++k) {
+            float ca[4];
+            from_pairs(ca2[k], ca);
+            io.store4(jk[k], n, ca);
+        }
     }
 }
 
