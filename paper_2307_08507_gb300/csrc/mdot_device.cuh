@@ -193,13 +193,42 @@ __device__ __forceinline__ float point_cost(float x0, float x1, float x2, float 
 
 // Packed fp32 pairs: one instruction computes two entries on this GPU; every component is
 // rounded exactly as the scalar operation it stands for (round to nearest), so the packed passes
-// give the same bits as the scalar forms above.
+// give the same bits as the scalar forms above.  Written as PTX with an explicit rounding mode:
+// such adds and multiplies are never contracted into an fma by the compiler (the regenerated
+// cost must round every product and sum on its own).
+__device__ __forceinline__ unsigned long long pk_bits(float2 a)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ float2 unpk_bits(unsigned long long r)
+{
+    float2 a;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+    return a;
+}
 __device__ __forceinline__ float2 pk(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk_bits(a)), "l"(pk_bits(b)));
+    return unpk_bits(r);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b)
+{
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk_bits(a)), "l"(pk_bits(b)));
+    return unpk_bits(r);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(pk_bits(a)), "l"(pk_bits(b)), "l"(pk_bits(c)));
+    return unpk_bits(r);
+}
 // a - b with one rounding: b * (-1) is exact inside the fma
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return fma2(b, make_float2(-1.0f, -1.0f), a); }
 
 // exp2_acc on a pair.  -k = 1.5 * 2^23 - t is exact (t lies within a factor 2 of 1.5 * 2^23), and
 // the fma with it rounds as the scalar fmaf(G32, d, -k) does.
