@@ -278,19 +278,24 @@ __device__ __forceinline__ void entry4(float fh, float wr, float s, const float2
     ca[1] = fma2(E1, S, ca[1]);
 }
 
-// point_cost on a pair of columns (same row)
+// point_cost on a pair of columns (same row).  The code generator fuses a packed multiply into a
+// following packed add even when both carry an explicit rounding mode (and turns an fma with a
+// constant -0 back into a multiply): measured, 18 % of the regenerated costs then differed from
+// the scalar form.  So every product is an fma whose addend z is a -0 the generator cannot see
+// (computed at run time by the caller, e.g. -(s * 0)): exact, since adding -0 changes no product,
+// and an fma is never fused into the next addition.
 template <int KIND>
 __device__ __forceinline__ float2 point_cost2(float2 x0, float2 x1, float2 x2, float2 y0, float2 y1, float2 y2,
-                                              float2 s)
+                                              float2 s, float2 z)
 {
     const float2 d0 = sub2(x0, y0), d1 = sub2(x1, y1), d2 = sub2(x2, y2);
     float2 D;
     if (KIND == COST_SQEUCLID)
-        D = add2(add2(mul2(d0, d0), mul2(d1, d1)), mul2(d2, d2));
+        D = add2(add2(fma2(d0, d0, z), fma2(d1, d1, z)), fma2(d2, d2, z));
     else
         D = add2(add2(make_float2(fabsf(d0.x), fabsf(d0.y)), make_float2(fabsf(d1.x), fabsf(d1.y))),
                  make_float2(fabsf(d2.x), fabsf(d2.y)));
-    return mul2(D, s);
+    return fma2(D, s, z);
 }
 
 // column constants of a float4 group as pairs, and the pairs of column partials back to a float4
@@ -1126,6 +1131,7 @@ __device__ __forceinline__ void pass_f32_regen(const float* __restrict__ Y, floa
     const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int BN = 4 * KR * T;
     const float2 G32p = pk(G32), Glop = pk(Glo), CS = pk(cs);
+    const float2 Z = pk(-(cs * 0.0f));          // -0, opaque to the code generator (see point_cost2)
     for (int cb = 0; cb < n; cb += BN) {
         float hh[KR][4], wc[KR][4];
         float2 hh2[KR][2], wc2[KR][2], ca2[KR][2], y0[KR][2], y1[KR][2], y2[KR][2];
@@ -1165,8 +1171,8 @@ __device__ __forceinline__ void pass_f32_regen(const float* __restrict__ Y, floa
                     const float2 x0 = pk(sX[3 * il]), x1 = pk(sX[3 * il + 1]), x2 = pk(sX[3 * il + 2]);
 #pragma unroll
                     for (int k = 0; k < KR; ++k) {
-                        const float2 c01 = point_cost2<KIND>(x0, x1, x2, y0[k][0], y1[k][0], y2[k][0], CS);
-                        const float2 c23 = point_cost2<KIND>(x0, x1, x2, y0[k][1], y1[k][1], y2[k][1], CS);
+                        const float2 c01 = point_cost2<KIND>(x0, x1, x2, y0[k][0], y1[k][0], y2[k][0], CS, Z);
+                        const float2 c23 = point_cost2<KIND>(x0, x1, x2, y0[k][1], y1[k][1], y2[k][1], CS, Z);
                         entry4<ACC>(fh, wr, sc, hh2[k], wc2[k], c01, c23, G32p, Glop, rp[ii], ca2[k]);
                     }
                 }
