@@ -1034,6 +1034,24 @@ __device__ __forceinline__ void ring_drain(const RingGeom& g, int consumed, int 
     for (int Q = max(consumed, issued - g.nst); Q < issued; ++Q) mbar_wait(&g.full[Q % g.nst], (Q / g.nst) & 1);
 }
 
+// One row of a ring slot for this thread's column groups: the row sum (column order) and the
+// column partials.
+template <bool ACC>
+__device__ __forceinline__ float ring_row(const float4* seg, bool ok, const int (&jk)[kK], int n, int tid, float fh,
+                                          float wr, float sc, const float2 (&hh2)[kK][2], const float2 (&wc2)[kK][2],
+                                          float2 G32p, float2 Glop, float2 (&ca2)[kK][2])
+{
+    float rp = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kK; ++k) {
+        float4 t4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (ok && jk[k] < n) t4 = seg[tid + k * kConsumerThreads];
+        entry4<ACC>(fh, wr, sc, hh2[k], wc2[k], make_float2(t4.x, t4.y), make_float2(t4.z, t4.w), G32p, Glop, rp,
+                    ca2[k]);
+    }
+    return rp;
+}
+
 // One pass over the CTA's rows through the persistent ring (same arithmetic as pass_f32_tma).
 // consumed: items consumed before this pass (identical in every thread); issued: the producer
 // thread's count.  Both advance here.
@@ -1078,27 +1096,34 @@ __device__ __forceinline__ void pass_f32_ring(const RingGeom& g, int r1, const I
             for (int rg = r0; rg < r1; rg += kRG) {
                 float rp[kRG];
 #pragma unroll
-                for (int ii = 0; ii < kRG; ++ii) {
+                for (int ii = 0; ii < kRG; ii += 2) {
                     rp[ii] = 0.0f;
+                    rp[ii + 1] = 0.0f;
                     const int i = rg + ii;
                     if (i < r1) {
-                        const int s = sl;
-                        if (ok) ok = mbar_wait(&g.full[s], ph);
-                        const float fh = sFh[i - r0], wr = sWr[i - r0], sc = sS[i - r0];
-                        const float4* seg = reinterpret_cast<const float4*>(g.ring + (size_t)s * kSegFloats);
-#pragma unroll
-                        for (int k = 0; k < kK; ++k) {
-                            float cv[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-                            if (ok && jk[k] < n) {
-                                const float4 t4 = seg[tid + k * kConsumerThreads];
-                                cv[0] = t4.x; cv[1] = t4.y; cv[2] = t4.z; cv[3] = t4.w;
-                            }
-                            entry4<ACC>(fh, wr, sc, hh2[k], wc2[k], make_float2(cv[0], cv[1]), make_float2(cv[2], cv[3]),
-                                        G32p, Glop, rp[ii], ca2[k]);
+                        // two rows (ring slots) at a time when both exist: their entries are
+                        // independent, so the two instruction streams interleave; each row's sum
+                        // and the column partials keep their order
+                        const bool two = i + 1 < r1;
+                        const int sA = sl, pA = ph;
+                        if (++sl == g.nst) { sl = 0; ph ^= 1; }
+                        const int sB = sl, pB = ph;
+                        if (two && ++sl == g.nst) { sl = 0; ph ^= 1; }
+                        if (ok) ok = mbar_wait(&g.full[sA], pA);
+                        if (two && ok) ok = mbar_wait(&g.full[sB], pB);
+                        const float4* segA = reinterpret_cast<const float4*>(g.ring + (size_t)sA * kSegFloats);
+                        rp[ii] = ring_row<ACC>(segA, ok, jk, n, tid, sFh[i - r0], sWr[i - r0], sS[i - r0], hh2, wc2,
+                                               G32p, Glop, ca2);
+                        if (two) {
+                            const float4* segB = reinterpret_cast<const float4*>(g.ring + (size_t)sB * kSegFloats);
+                            rp[ii + 1] = ring_row<ACC>(segB, ok, jk, n, tid, sFh[i + 1 - r0], sWr[i + 1 - r0],
+                                                       sS[i + 1 - r0], hh2, wc2, G32p, Glop, ca2);
                         }
                         __syncwarp();
-                        if (lane == 0) mbar_arrive(&g.empty[s]);
-                        if (++sl == g.nst) { sl = 0; ph ^= 1; }
+                        if (lane == 0) {
+                            mbar_arrive(&g.empty[sA]);
+                            if (two) mbar_arrive(&g.empty[sB]);
+                        }
                     }
                 }
                 butterfly<kRG>(rp, lane);
