@@ -109,6 +109,34 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def kernel_source_hash() -> str:
+    """sha256 over the CUDA sources of the library (csrc/*.cu, *.cuh, *.h, sorted by name)."""
+    import glob
+    import hashlib
+    hsh = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2307_08507_gb300", "csrc", "*"))):
+        if f.endswith((".cu", ".cuh", ".h")):
+            hsh.update(os.path.basename(f).encode())
+            with open(f, "rb") as fh:
+                hsh.update(fh.read())
+    return hsh.hexdigest()
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes (read + write) per launch of `kernel` from the ncu capture recorded in
+    profiles/ncu_traffic.json, or None when that capture was taken from other sources than the
+    ones built now (the recorded sha256 of the CUDA sources differs)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    rec = d.get("kernels", {}).get(kernel)
+    if rec is None or d.get("source_sha256") != kernel_source_hash():
+        return None
+    return float(rec["dram_bytes_per_launch"])
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -532,7 +560,8 @@ def run_ours(args, rank, world):
                        "stages": info.stages, "grad_l1": info.grad_l1},
             "roofline": {"kernel": "stage_kernel<fp32 entries> (one MDOT stage: PNCG + line search)",
                          "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                         "frac": (achieved / hbm) if achieved else None,
+                         "traffic": ncu_traffic("stage_kernel_flag<2, 0>"),
                          "peak_kind": peak_kind,
                          "bytes_per_launch": bytes_per_launch, "us_per_launch": t_launch * 1e6,
                          "launch_times_ms": {"stage_fp32": ip.t_stage_fp32_ms, "stage_fp64": ip.t_stage_fp64_ms,

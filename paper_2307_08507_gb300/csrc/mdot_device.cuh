@@ -1143,6 +1143,27 @@ __device__ __forceinline__ void pass_f32_ring(const RingGeom& g, int r1, const I
     __syncthreads();
 }
 
+// One row of the regenerated-cost pass for this thread's column groups: the row sum (column order)
+// and the column partials.
+template <bool ACC, int KIND, int KR>
+__device__ __forceinline__ float regen_row(const float* sX, int il, const float* sFh, const float* sWr,
+                                           const float* sS, const float2 (&y0)[KR][2], const float2 (&y1)[KR][2],
+                                           const float2 (&y2)[KR][2], const float2 (&hh2)[KR][2],
+                                           const float2 (&wc2)[KR][2], float2 CS, float2 Z, float2 G32p, float2 Glop,
+                                           float2 (&ca2)[KR][2])
+{
+    const float fh = sFh[il], wr = sWr[il], sc = sS[il];
+    const float2 x0 = pk(sX[3 * il]), x1 = pk(sX[3 * il + 1]), x2 = pk(sX[3 * il + 2]);
+    float rp = 0.0f;
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+        const float2 c01 = point_cost2<KIND>(x0, x1, x2, y0[k][0], y1[k][0], y2[k][0], CS, Z);
+        const float2 c23 = point_cost2<KIND>(x0, x1, x2, y0[k][1], y1[k][1], y2[k][1], CS, Z);
+        entry4<ACC>(fh, wr, sc, hh2[k], wc2[k], c01, c23, G32p, Glop, rp, ca2[k]);
+    }
+    return rp;
+}
+
 // Pass over the CTA's rows with C regenerated from coordinates (no C in memory): same structure
 // as pass_f32 with two float4 column groups per thread; the row coordinates come from shared
 // memory (sX: 3 floats per local row), the column coordinates sit in registers per sweep.
@@ -1187,19 +1208,20 @@ __device__ __forceinline__ void pass_f32_regen(const float* __restrict__ Y, floa
         for (int rg = r0; rg < r1; rg += kRG) {
             float rp[kRG];
 #pragma unroll
-            for (int ii = 0; ii < kRG; ++ii) {
+            for (int ii = 0; ii < kRG; ii += 2) {
                 rp[ii] = 0.0f;
+                rp[ii + 1] = 0.0f;
                 const int i = rg + ii;
-                if (i < r1) {
-                    const int il = i - r0;
-                    const float fh = sFh[il], wr = sWr[il], sc = sS[il];
-                    const float2 x0 = pk(sX[3 * il]), x1 = pk(sX[3 * il + 1]), x2 = pk(sX[3 * il + 2]);
-#pragma unroll
-                    for (int k = 0; k < KR; ++k) {
-                        const float2 c01 = point_cost2<KIND>(x0, x1, x2, y0[k][0], y1[k][0], y2[k][0], CS, Z);
-                        const float2 c23 = point_cost2<KIND>(x0, x1, x2, y0[k][1], y1[k][1], y2[k][1], CS, Z);
-                        entry4<ACC>(fh, wr, sc, hh2[k], wc2[k], c01, c23, G32p, Glop, rp[ii], ca2[k]);
-                    }
+                // two rows in one block when both exist, so that their instruction streams
+                // interleave (row sums and column partials keep their order)
+                if (i + 1 < r1) {
+                    rp[ii] = regen_row<ACC, KIND, KR>(sX, i - r0, sFh, sWr, sS, y0, y1, y2, hh2, wc2, CS, Z, G32p,
+                                                      Glop, ca2);
+                    rp[ii + 1] = regen_row<ACC, KIND, KR>(sX, i + 1 - r0, sFh, sWr, sS, y0, y1, y2, hh2, wc2, CS, Z,
+                                                          G32p, Glop, ca2);
+                } else if (i < r1) {
+                    rp[ii] = regen_row<ACC, KIND, KR>(sX, i - r0, sFh, sWr, sS, y0, y1, y2, hh2, wc2, CS, Z, G32p,
+                                                      Glop, ca2);
                 }
             }
             butterfly<kRG>(rp, lane);
