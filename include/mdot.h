@@ -98,7 +98,10 @@ typedef struct mdot_params {
     int32_t precond;        /* 0: Sinkhorn direction s (Eq. (17)); 1: diagonal-Hessian direction       */
                             /*    (r~ / r(P), c~ / c(P)) - 1 (Eq. (16)) at iterations where every ratio  */
                             /*    lies in [0.01, 100], else s (mdot_solve and mdot_solve_points only)   */
-    int32_t reserved[3];
+    int32_t ls_init;        /* first trial step of each line search (App. B leaves it open):           */
+                            /*    0: 1; 1 (default): the step accepted by the previous line search of  */
+                            /*    the stage, clamped to [1/2, 2] (1 at a stage's first iteration)      */
+    int32_t reserved[2];
 } mdot_params;
 
 /* Diagnostics of one solve. */

@@ -24,7 +24,7 @@ class OrParams(ct.Structure):
                 ("q", ct.c_double), ("ls_c1", ct.c_double), ("ls_c2", ct.c_double),
                 ("ls_max_trials", ct.c_int), ("max_iter", ct.c_int), ("projector", ct.c_int),
                 ("warm_start", ct.c_int), ("precond", ct.c_int), ("smoothing", ct.c_int),
-                ("final_tol", ct.c_double), ("stop_entropy", ct.c_int)]
+                ("final_tol", ct.c_double), ("stop_entropy", ct.c_int), ("ls_init", ct.c_int)]
 
 
 class OrStats(ct.Structure):

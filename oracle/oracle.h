@@ -36,6 +36,8 @@ typedef struct {
     int    smoothing;      /* 0 = variable weight eps_d/4 (Alg. 1), 1 = fixed weight at gamma_f */
     double final_tol;      /* if > 0: tolerance used at the final stage instead of eps_d/2         */
     int    stop_entropy;   /* entropy in eps_d (Alg. 1): 0 = H_min(r, c), 1 = log n (App. C ablation) */
+    int    ls_init;        /* first trial of each line search (App. B leaves it open): 0 = 1;      */
+                           /* 1 = the previous accepted step of the stage clamped to [1/2, 2]      */
 } or_params;
 
 typedef struct {

@@ -32,7 +32,8 @@ class Params(ct.Structure):
                 ("ls_max_trials", ct.c_int32), ("max_iter", ct.c_int32), ("precision", ct.c_int32),
                 ("warm_start", ct.c_int32), ("final_tol", ct.c_double), ("fp32_floor", ct.c_double),
                 ("profile", ct.c_int32), ("smoothing", ct.c_int32), ("projector", ct.c_int32),
-                ("stop_entropy", ct.c_int32), ("precond", ct.c_int32), ("reserved", ct.c_int32 * 3)]
+                ("stop_entropy", ct.c_int32), ("precond", ct.c_int32), ("ls_init", ct.c_int32),
+                ("reserved", ct.c_int32 * 2)]
 
 
 class Info(ct.Structure):

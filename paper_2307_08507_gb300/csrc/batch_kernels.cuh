@@ -52,7 +52,7 @@ struct BatchArgs {
     size_t slot_doubles;
     // parameters of Alg. 1 / App. B
     double gamma_i, p, q, c1, c2, fp32_floor, final_tol;
-    int ls_max_trials, max_iter, warm_start, precision, smoothing;
+    int ls_max_trials, max_iter, warm_start, precision, smoothing, ls_init;
 };
 
 // slot layout (vectors of `stride` elements): 18 fp64 vectors, then 7 fp32 / int32 vectors
@@ -244,6 +244,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a)
             sa.c1 = a.c1;
             sa.c2 = a.c2;
             sa.ls_max_trials = a.ls_max_trials;
+            sa.ls_init = a.ls_init;
             sa.max_iter = a.max_iter;
             sa.tier = acc ? TIER_F32A : TIER_F32;
             const double inv_gamma = 1.0 / gamma, G64 = sa.G64;

@@ -103,6 +103,7 @@ void mdot_default_params(mdot_params* prm)
     prm->final_tol = 0.0;
     prm->fp32_floor = 5e-8;
     prm->profile = 0;
+    prm->ls_init = 1;                    // App. B leaves the first trial step open (see mdot.h)
 }
 
 const char* mdot_status_string(int32_t s)
@@ -240,7 +241,7 @@ mdot_status params_ok(const mdot_params& P)
         !(P.ls_c2 > P.ls_c1) || !(P.ls_c2 < 1.0) || P.ls_max_trials < 1 || P.max_iter < 1 ||
         P.precision < 0 || P.precision > 3 || P.warm_start < 0 || P.warm_start > 2 ||
         P.smoothing < 0 || P.smoothing > 1 || P.projector < 0 || P.projector > 1 || P.stop_entropy < 0 ||
-        P.stop_entropy > 1 || P.precond < 0 || P.precond > 1 ||
+        P.stop_entropy > 1 || P.precond < 0 || P.precond > 1 || P.ls_init < 0 || P.ls_init > 1 ||
         !(P.fp32_floor >= 0.0) || !std::isfinite(P.gamma_f))
         return MDOT_ERR_INVALID_ARG;
     return MDOT_OK;
@@ -427,6 +428,7 @@ mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const C
         a.first = (t == 1);
         a.warm_start = P.warm_start;
         a.ls_max_trials = P.ls_max_trials;
+        a.ls_init = P.ls_init;
         a.max_iter = P.max_iter;
         a.Aglob = 0;
         a.precond = P.precond;
@@ -710,6 +712,7 @@ mdot_status mdot_solve_batch(mdot_handle* h, int32_t nprob, const mdot_problem* 
         a.ls_max_trials = P.ls_max_trials; a.max_iter = P.max_iter; a.warm_start = P.warm_start;
         a.precision = P.precision;
         a.smoothing = P.smoothing;
+        a.ls_init = P.ls_init;
         CKR(launch_batch(kind, h->b_grid, a, h->stream));
         CKR(cudaStreamSynchronize(h->stream));     // the order buffer is reused by the next form
     }

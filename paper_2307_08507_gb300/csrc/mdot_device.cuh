@@ -107,6 +107,7 @@ struct StageArgs {
     double gamma, G64, tol, w, ratio, c1, c2;
     int first, warm_start, tier, ls_max_trials, max_iter, Aglob;
     int precond;           // 1: diagonal-Hessian direction (Eq. (16)) where every ratio allows it
+    int ls_init;           // 1: first trial step = previous accepted step clamped to [1/2, 2]
 };
 
 // Arguments of the standalone dual evaluation (mdot_dual_eval).

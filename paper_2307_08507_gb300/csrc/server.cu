@@ -277,6 +277,7 @@ cudaError_t admit(mdot_server* s)
         a.ls_max_trials = P.ls_max_trials; a.max_iter = P.max_iter; a.warm_start = P.warm_start;
         a.precision = P.precision;
         a.smoothing = P.smoothing;
+        a.ls_init = P.ls_init;
         e = launch_batch(kind, m, a, st);
         if (e == cudaSuccess) e = cudaEventRecord(r->ev, st);
         if (e != cudaSuccess) return e;

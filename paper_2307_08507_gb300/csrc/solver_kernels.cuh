@@ -119,7 +119,8 @@ static __device__ void decide(State* S, const double* tot, const StageArgs& a)
     }
     S->d0 = pg;
     S->lo = 0.0; S->dlo = pg; S->hi = INFINITY; S->dhi = INFINITY;
-    S->alpha = 1.0;
+    // first trial step: 1, or the step just accepted clamped to [1/2, 2] (App. B leaves it open)
+    S->alpha = (a.ls_init && !was_init) ? fmin(fmax(S->alpha_commit, 0.5), 2.0) : 1.0;
     S->trials = 0;
     S->kind = KIND_TRIAL;
 }
