@@ -561,7 +561,7 @@ def run_ours(args, rank, world):
             "roofline": {"kernel": "stage_kernel<fp32 entries> (one MDOT stage: PNCG + line search)",
                          "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": (achieved / hbm) if achieved else None,
-                         "traffic": ncu_traffic("stage_kernel_flag<2, 0>"),
+                         "traffic": ncu_traffic("stage_kernel_flag<2, 0>") or ncu_traffic("stage_kernel_flag<0, 0>"),
                          "peak_kind": peak_kind,
                          "bytes_per_launch": bytes_per_launch, "us_per_launch": t_launch * 1e6,
                          "launch_times_ms": {"stage_fp32": ip.t_stage_fp32_ms, "stage_fp64": ip.t_stage_fp64_ms,
