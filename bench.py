@@ -142,7 +142,8 @@ class Clocks:
 
     def __init__(self, index=0):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), f"mdot_clocks_{os.getpid()}.csv")
         self.index = index
 
     def __enter__(self):

@@ -278,8 +278,7 @@ mdot_status mdot_solve_batch(mdot_handle* h, int32_t nprob, const mdot_problem* 
                              const mdot_params* prm, mdot_result* results);
 
 /*
- * Serving: a request loop with continuous batching (the benchmark spec pattern 5; the paper has no
- * counterpart).  mdot_server_create starts a background worker on the current device with a
+ * Serving: a request loop with continuous batching (the paper has no counterpart).  mdot_server_create starts a background worker on the current device with a
  * workspace pool of workspace_bytes (the HBM budget): a request of size n needs
  * 180 * ceil32(n) bytes of it (ceil32: n rounded up to a multiple of 32).  Requests are admitted in arrival order as soon as their workspace
  * fits; each admission round is one persistent batched launch (the solver of mdot_solve_batch,
