@@ -40,8 +40,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample-evals", type=int, default=0, help="oracle evaluations in the CPU sample")
     ap.add_argument("--case", default="solve",
-                    choices=["solve", "dual_eval", "dual_eval_regen", "stage", "batch", "serve", "sinkhorn", "large_n",
-                             "nscale", "hmin"],
+                    choices=["solve", "dual_eval", "dual_eval_regen", "stage", "batch", "serve", "tune_serve", "sinkhorn",
+                             "large_n", "nscale", "hmin"],
                     help="dual_eval / stage: run only that kernel (for profiler captures); sinkhorn, large_n, "
                          "nscale, hmin: the comparison studies (one JSON line per solve)")
     ap.add_argument("--grid", type=int, default=64, help="k of the k x k grid for --case runs")
@@ -681,6 +681,14 @@ def run_case(args):
     if args.case == "batch":
         stream = torch.cuda.current_stream()
         print(json.dumps(measure_batch(h, dev, stream)))
+        h.close()
+        return
+    if args.case == "tune_serve":
+        # the served form's routing picked by measurement (M.tune_server) on the serving trace
+        reqs = [(ta, prob, keep) for (ta, _, _, prob, keep) in serving_requests(dev, args.serve_count)]
+        best, table = M.tune_server(SERVE_WORKSPACE, reqs)
+        print(json.dumps({"best": best, "candidates": [{k: v for k, v in row.items() if k not in ("statuses", "costs")}
+                                                      for row in table]}))
         h.close()
         return
     if args.case == "serve":

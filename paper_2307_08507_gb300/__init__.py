@@ -462,3 +462,42 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def tune_server(workspace_bytes: int, requests, candidates=None, params: Params | None = None,
+                timeout: float = 600.0):
+    """Pick the served form's routing by measurement on this device: for each candidate
+    (big_n, big_lanes, lane_ctas) a fresh Server replays `requests` -- a list of
+    (arrival offset in seconds, mdot_problem, tensors to keep alive) -- at their arrival times and
+    the wall time to the last result is taken.  Returns (best candidate as a dict, one dict per
+    candidate with problems_per_s, seconds and the per-request statuses and costs in request
+    order).  Candidates default to three routings around the built-in one."""
+    import time
+    import torch
+    if candidates is None:
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        candidates = [dict(big_n=2048, big_lanes=2, lane_ctas=sms // 4),
+                      dict(big_n=1024, big_lanes=4, lane_ctas=sms // 8),
+                      dict(big_n=4096, big_lanes=1, lane_ctas=sms // 4)]
+    table = []
+    for cand in candidates:
+        torch.cuda.synchronize()
+        srv = Server(workspace_bytes, params, **cand)
+        try:
+            tickets = []
+            t0 = time.perf_counter()
+            for (ta, prob, keep) in sorted(requests, key=lambda q: q[0]):
+                delay = t0 + ta - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                tickets.append(srv.submit(prob, keep))
+            results = [srv.wait(t, timeout) for t in tickets]
+            dt = time.perf_counter() - t0
+        finally:
+            srv.close()
+        if any(r is None for r in results):
+            raise MdotError(MDOT_ERR_TIMEOUT, "tune_server")
+        table.append(dict(cand, problems_per_s=len(results) / dt, seconds=dt,
+                          statuses=[r.status for r in results], costs=[r.cost for r in results]))
+    best = max(table, key=lambda row: row["problems_per_s"])
+    return {k: best[k] for k in ("big_n", "big_lanes", "lane_ctas")}, table

@@ -143,3 +143,23 @@ def test_big_request_same_alone_and_in_a_stream(h):
     _, _, s = h.solve_points(d["r"], d["c"], d["x"], d["y"], M.COST_SQEUCLID, p.scale, 1e-6, prm)
     eps_d = alone.H_min / gf ** 1.5
     assert abs(alone.cost - s.cost) <= max(1e-7, eps_d), (alone.cost, s.cost)
+
+
+def test_tune_server_picks_a_measured_routing():
+    """tune_server replays the same short trace under each candidate routing and returns the
+    fastest.  Every request here is below both candidates' big_n, so all take the batched route
+    and give bit-identical results under either routing."""
+    torch.cuda.set_device(0)
+    reqs, hold = [], []
+    for q, k in enumerate((10, 12, 14, 16, 12, 10)):
+        p, d, prob = grid_request(k, 7100 + q, eps=1e-5)
+        reqs.append((0.01 * q, prob, tuple(d.values())))
+        hold.append(d)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cands = [dict(big_n=2048, big_lanes=2, lane_ctas=sms // 4), dict(big_n=1024, big_lanes=4, lane_ctas=sms // 8)]
+    best, table = M.tune_server(1 << 28, reqs, cands)
+    assert best in cands
+    assert len(table) == 2 and all(row["problems_per_s"] > 0 for row in table)
+    for row in table:
+        assert row["statuses"] == [M.MDOT_OK] * len(reqs)
+    assert table[0]["costs"] == table[1]["costs"]
