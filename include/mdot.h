@@ -101,7 +101,11 @@ typedef struct mdot_params {
     int32_t ls_init;        /* first trial step of each line search (App. B leaves it open):           */
                             /*    0: 1; 1 (default): the step accepted by the previous line search of  */
                             /*    the stage, clamped to [1/2, 2] (1 at a stage's first iteration)      */
-    int32_t reserved[2];
+    int32_t wait_limit_us;  /* limit of every bounded device-side wait (a CTA waiting for another CTA's
+                               flag, a grid barrier), in microseconds; <= 0: 2 seconds.  A wait that
+                               runs out ends the call with MDOT_ERR_TIMEOUT (outputs hold the last
+                               iterate) and leaves the handle usable                                */
+    int32_t reserved;
 } mdot_params;
 
 /* Diagnostics of one solve. */
@@ -153,18 +157,24 @@ mdot_status mdot_destroy(mdot_handle* h);
 
 /*
  * One dual evaluation (the two reductions of Alg. 2): one pass over C giving both log-marginals of
- * P(u, v; gamma):
- *   log_rP[i] = u_i + LSE_j(v_j - gamma C_ij),   log_cP[j] = v_j + LSE_i(u_i - gamma C_ij).
+ * P(u, v; gamma) and, optionally, the dual objective of Eq. (4):
+ *   log_rP[i] = u_i + LSE_j(v_j - gamma C_ij),   log_cP[j] = v_j + LSE_i(u_i - gamma C_ij),
+ *   g(u, v; gamma, r, c) = sum_ij P_ij - <u, r> - <v, c> = sum_i r(P)_i - <u, r> - <v, c>.
+ * The gradient of g is (r(P) - r, c(P) - c) (Sec. 2.1).
  * u, v: n doubles each.  C: n x n float32, row-major.  gamma > 0.
  * ref_log_rP (nullable, n doubles): an estimate of log_rP, used only to scale the row sums;
  *   when NULL an extra max pass over C computes the scales (so the call reads C twice).
- * precision: MDOT_PREC_FP32 or MDOT_PREC_FP64 (AUTO means FP32).
- * Outputs log_rP, log_cP (n doubles each).  Entries of P more than 2^120 below the largest row
- * scale are flushed from the column sums.
+ * precision: MDOT_PREC_FP32, MDOT_PREC_FP32A or MDOT_PREC_FP64 (AUTO means FP32).
+ * Outputs log_rP, log_cP (device, n doubles each).  Entries of P more than 2^120 below the largest
+ * row scale are flushed from the column sums.
+ * g_out (HOST pointer, nullable): receives g, summed in fp64 in a fixed order inside the same
+ *   launch (one more grid barrier); r, c (device, n doubles each) are then required, else they may
+ *   be NULL.  INVALID_ARG if g_out is given without r or c.
  */
 mdot_status mdot_dual_eval(mdot_handle* h, const double* u, const double* v, double gamma,
                            const float* C, int64_t n, const double* ref_log_rP,
-                           int32_t precision, double* log_rP, double* log_cP);
+                           int32_t precision, double* log_rP, double* log_cP,
+                           const double* r, const double* c, double* g_out);
 
 /*
  * Alg. 3 applied to P = exp(u 1^T + 1 v^T - gamma C) (the final plan of Alg. 1): the rounded plan
@@ -212,12 +222,31 @@ mdot_status mdot_solve_points(mdot_handle* h, const double* r, const double* c, 
                               double* v_out, double* cost_out, double* gap_out, mdot_info* info);
 
 /*
- * mdot_dual_eval with the cost regenerated from coordinates (see mdot_cost_kind).
+ * mdot_dual_eval with the cost regenerated from coordinates (see mdot_cost_kind); same outputs,
+ * including the optional dual objective.
  */
 mdot_status mdot_dual_eval_points(mdot_handle* h, const double* u, const double* v, double gamma,
                                   const float* x, const float* y, int32_t cost_kind, float scale,
                                   int64_t n, const double* ref_log_rP, int32_t precision,
-                                  double* log_rP, double* log_cP);
+                                  double* log_rP, double* log_cP,
+                                  const double* r, const double* c, double* g_out);
+
+/* One kernel launch of a profiled solve (mdot_params.profile != 0), in launch order. */
+typedef struct mdot_trace_row {
+    int32_t kind;       /* 0: stage with fp32 entries, 1: stage with fp64 entries, 2: rounding, 3: bound */
+    int32_t reserved;
+    double  ms;         /* device time of the launch (CUDA events around it on the handle's stream)    */
+    int64_t evals;      /* dual evaluations the launch made (from the device state's counter)          */
+} mdot_trace_row;
+
+/*
+ * Per-launch rows of the last solve on h that ran with mdot_params.profile != 0 (up to 512
+ * launches): rows (host, max_rows entries) receives the first max_rows rows, *count (host) the
+ * number recorded.  MDOT_NOT_READY if no profiled solve has completed on h; INVALID_ARG for NULL
+ * arguments.  Diagnostic only (the paper has no counterpart): it ties a profiler's per-launch
+ * figures to evaluation counts.
+ */
+mdot_status mdot_solve_trace(const mdot_handle* h, int32_t max_rows, mdot_trace_row* rows, int32_t* count);
 
 /*
  * Device time, in milliseconds, of the evaluation kernel launched by the last successful
@@ -252,7 +281,7 @@ typedef struct mdot_result {
     int64_t evals;            /* dual evaluations                                                */
     int64_t iters;            /* PNCG iterations                                                 */
     double  cost;             /* <G, C> of the rounded plan                                      */
-    double  lower_bound;      /* c-transform bound (fp32 differences in the batched form)        */
+    double  lower_bound;      /* c-transform bound (fp64, as mdot_lower_bound)                    */
     double  gap_cert;         /* cost - lower_bound                                              */
     double  grad_l1;          /* final ||grad g||_1                                              */
     double  gamma_f;
@@ -324,6 +353,17 @@ mdot_status mdot_solve_host(mdot_handle* h, const double* r_host, const double* 
                             const mdot_params* prm, double* u_host, double* v_host,
                             double* cost_out, double* gap_out, mdot_info* info);
 
+
+/*
+ * Read-rate probe (a measurement utility; the paper has no counterpart): reads the n_floats
+ * floats at buf (device, 16-byte aligned, n_floats a multiple of 4) reps times with 128-bit
+ * loads on 4 CTAs per SM and adds a checksum into *out (device, cleared by the call).  The
+ * caller times it with CUDA events on `stream` (a cudaStream_t or NULL); the call does not
+ * synchronise.  A buffer that fits in L2 is read from L2 after the first pass, so
+ * reps x n_floats x 4 bytes / time is the L2 read rate; a buffer far larger than L2 gives the HBM
+ * read rate.  INVALID_ARG for a bad size, alignment or reps < 1; CUDA if the launch fails.
+ */
+mdot_status mdot_read_probe(const float* buf, int64_t n_floats, int32_t reps, float* out, void* stream);
 
 /* ------------------------------------------------------------------------------------------ */
 /* Dual evaluation without any allocation.                                                     */

@@ -17,6 +17,8 @@ _SO = os.path.join(_HERE, "_build", "liboracle.so")
 _lib = None
 
 _D = ct.POINTER(ct.c_double)
+_DPHI = ct.CFUNCTYPE(ct.c_double, ct.c_void_p, ct.c_double)
+_KEEP = ct.CFUNCTYPE(None, ct.c_void_p)
 
 
 class OrParams(ct.Structure):
@@ -33,18 +35,46 @@ class OrStats(ct.Structure):
                 ("grad_l1", ct.c_double), ("gamma_last", ct.c_double), ("grad_l1_init", ct.c_double)]
 
 
-def build(force: bool = False) -> str:
-    """Compile oracle.c into _build/liboracle.so with gcc (plain -O2, IEEE semantics kept)."""
+_SO_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")
+
+
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile oracle.c into _build/liboracle.so with gcc (plain -O2, IEEE semantics kept).
+    openmp=True builds _build/liboracle_omp.so from the same source with -fopenmp (the dual
+    evaluation's rows and column strips on every host core, same arithmetic), used only to time
+    the CPU baseline."""
     src = os.path.join(_HERE, "oracle.c")
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= max(
+    so = _SO_OMP if openmp else _SO
+    if not force and os.path.exists(so) and os.path.getmtime(so) >= max(
             os.path.getmtime(src), os.path.getmtime(os.path.join(_HERE, "oracle.h"))):
-        return _SO
-    os.makedirs(os.path.dirname(_SO), exist_ok=True)
-    tmp = _SO + f".tmp{os.getpid()}"
+        return so
+    os.makedirs(os.path.dirname(so), exist_ok=True)
+    tmp = so + f".tmp{os.getpid()}"
     subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
-                    "-ffp-contract=off", "-o", tmp, src, "-lm"], check=True)
-    os.replace(tmp, _SO)
-    return _SO
+                    "-ffp-contract=off", *(["-fopenmp"] if openmp else []), "-o", tmp, src, "-lm"],
+                   check=True)
+    os.replace(tmp, so)
+    return so
+
+
+def omp_dual_eval_timer():
+    """(seconds per call of or_dual_eval, threads) on the OpenMP build: a callable timing one dual
+    evaluation of (C, u, v, gamma) on every host core.  For the CPU baseline only."""
+    L = ct.CDLL(build(openmp=True))
+    L.or_dual_eval.argtypes = [ct.c_int, _D, _D, _D, ct.c_double, _D, _D]
+    try:
+        nthreads = int(ct.CFUNCTYPE(ct.c_int)(("omp_get_max_threads", L))())
+    except Exception:
+        nthreads = os.cpu_count() or 1
+
+    def run(C, u, v, gamma):
+        C, u, v = _f64(C), _f64(u), _f64(v)
+        n = u.size
+        lr, lc = np.empty(n), np.empty(n)
+        L.or_dual_eval(n, _p(C), _p(u), _p(v), gamma, _p(lr), _p(lc))
+        return lr, lc
+
+    return run, nthreads
 
 
 def lib():
@@ -70,6 +100,9 @@ def lib():
         L.or_ctransform_lb.restype = ct.c_double
         L.or_gamma_f_for_eps.argtypes = [ct.c_double] * 5
         L.or_gamma_f_for_eps.restype = ct.c_double
+        L.or_ls_search.argtypes = [ct.c_double, ct.c_double, ct.POINTER(OrParams), _DPHI, _KEEP,
+                                   ct.c_void_p, _D]
+        L.or_ls_search.restype = ct.c_int
     return _lib
 
 
@@ -156,6 +189,25 @@ def round_plan(C, u, v, gamma, r, c, want_G: bool = False):
 def ctransform_lb(C, u, gamma, r, c) -> float:
     C, u, r, c = map(_f64, (C, u, r, c))
     return lib().or_ctransform_lb(u.size, _p(C), _p(u), gamma, _p(r), _p(c))
+
+
+def ls_search(dphi, d0: float, a0: float = 1.0, **kw):
+    """The App. B line search (or_ls_search) on a Python function dphi(alpha) = phi'(alpha).
+    Returns (rc, alpha, trials, lows): the return code, the step, every trial step in order and the
+    trial steps that became the lower end of the bracket."""
+    trials, lows = [], []
+
+    def _dphi(_ctx, a):
+        trials.append(a)
+        return float(dphi(a))
+
+    def _keep(_ctx):
+        lows.append(trials[-1])
+
+    f, k = _DPHI(_dphi), _KEEP(_keep)
+    alpha = np.zeros(1)
+    rc = lib().or_ls_search(float(d0), float(a0), ct.byref(params(**kw)), f, k, None, _p(alpha))
+    return rc, float(alpha[0]), trials, lows
 
 
 def gamma_f_for_eps(H, eps, gamma_i=16.0, q=2.0 ** (1.0 / 3.0), p=1.5) -> float:

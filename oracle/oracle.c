@@ -47,9 +47,12 @@ double or_entropy(int n, const double* r)
     return h;
 }
 
-/* LSE_r(1 v^T - gamma C)_i = log sum_j exp(v_j - gamma C_ij), stabilised by the row max. */
+/* LSE_r(1 v^T - gamma C)_i = log sum_j exp(v_j - gamma C_ij), stabilised by the row max.
+ * (Rows are independent; a build with OpenMP, used only to time the CPU baseline on every host
+ * core, splits them over threads without changing any row's arithmetic.) */
 static void lse_rows(int n, const double* C, const double* v, double gamma, double* out)
 {
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) {
         double m = -INFINITY;
         for (int j = 0; j < n; ++j) {
@@ -63,21 +66,28 @@ static void lse_rows(int n, const double* C, const double* v, double gamma, doub
 }
 
 /* LSE_c(u 1^T - gamma C)_j = log sum_i exp(u_i - gamma C_ij), stabilised by the column max.
- * The loops run over i outside only so that C is read row by row; the arithmetic per column is
- * the same max-then-sum as above. */
+ * The loops run over i outside only so that C is read row by row (in strips of columns, which a
+ * build with OpenMP hands to different threads); the arithmetic per column is the same
+ * max-then-sum over i = 0 .. n-1 as above. */
 static void lse_cols(int n, const double* C, const double* u, double gamma, double* out)
 {
+    enum { STRIP = 512 };
     double* m = (double*)malloc(sizeof(double) * (size_t)n);
     double* s = (double*)malloc(sizeof(double) * (size_t)n);
-    for (int j = 0; j < n; ++j) { m[j] = -INFINITY; s[j] = 0.0; }
-    for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j) {
-            double z = u[i] - gamma * C[IDX(i, j)];
-            if (z > m[j]) m[j] = z;
-        }
-    for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j) s[j] += exp(u[i] - gamma * C[IDX(i, j)] - m[j]);
-    for (int j = 0; j < n; ++j) out[j] = m[j] + log(s[j]);
+    const int nstrip = (n + STRIP - 1) / STRIP;
+#pragma omp parallel for schedule(static)
+    for (int b = 0; b < nstrip; ++b) {
+        const int j0 = b * STRIP, j1 = (j0 + STRIP < n) ? j0 + STRIP : n;
+        for (int j = j0; j < j1; ++j) { m[j] = -INFINITY; s[j] = 0.0; }
+        for (int i = 0; i < n; ++i)
+            for (int j = j0; j < j1; ++j) {
+                double z = u[i] - gamma * C[IDX(i, j)];
+                if (z > m[j]) m[j] = z;
+            }
+        for (int i = 0; i < n; ++i)
+            for (int j = j0; j < j1; ++j) s[j] += exp(u[i] - gamma * C[IDX(i, j)] - m[j]);
+        for (int j = j0; j < j1; ++j) out[j] = m[j] + log(s[j]);
+    }
     free(m);
     free(s);
 }
@@ -125,40 +135,26 @@ static double phi_prime(int n, const double* pu, const double* pv, const double*
 }
 
 /*
- * App. B line search: find alpha with (2 c1 - 1) phi'(0) >= phi'(alpha) >= c2 phi'(0)
- * (approximate Wolfe, Eq. (24)).  The bracket [lo, hi] keeps phi'(lo) < 0 < phi'(hi); inside a
- * bracket the next trial is alpha_hyb = alpha_sec / 2 + (lo + hi) / 4 (Eq. (25) and the text
- * after it).  Readings: the first trial is alpha = 1; until an upper end is found alpha doubles;
- * a non-finite phi' counts as an upper end and the next trial bisects; after ls_max_trials the
- * lower end is accepted if it is > 0.
- * On entry log_rP / log_cP hold the marginals at alpha = 0; on success they hold the marginals at
- * the accepted alpha (so the next PNCG iteration reuses them, App. B).  Returns 0 on success.
+ * App. B line search on a scalar function: find alpha with (2 c1 - 1) phi'(0) >= phi'(alpha) >=
+ * c2 phi'(0) (approximate Wolfe, Eq. (24)).  The bracket [lo, hi] keeps phi'(lo) < 0 < phi'(hi);
+ * inside a bracket the next trial is alpha_hyb = alpha_sec / 2 + (lo + hi) / 4 (Eq. (25) and the
+ * text after it), alpha_sec the secant root through (lo, phi'(lo)) and (hi, phi'(hi)).
+ * Readings: the first trial is a0; until an upper end is found alpha doubles; a non-finite phi'
+ * counts as an upper end and the next trial bisects; after ls_max_trials the lower end is taken if
+ * it is > 0.  dphi(ctx, alpha) evaluates phi'(alpha); keep_lo(ctx) is called when the trial just
+ * evaluated becomes the lower end (the PNCG caller keeps its marginals).
+ * Returns 0 (accepted: the last trial evaluated, *alpha_out), 1 (cap reached, lower end taken:
+ * *alpha_out = lo) or 2 (no step: d0 >= 0, or the cap with lo = 0).
  */
-static int line_search(int n, const double* C, double gamma, const double* r, const double* c,
-                       const double* u, const double* v, const double* pu, const double* pv,
-                       double* log_rP, double* log_cP, double a0, double* alpha_out,
-                       const or_params* prm, or_stats* st)
+int or_ls_search(double d0, double a0, const or_params* prm, or_dphi_fn dphi, or_keep_fn keep_lo,
+                 void* ctx, double* alpha_out)
 {
     const double c1 = prm->ls_c1, c2 = prm->ls_c2;
-    double* ut = (double*)malloc(sizeof(double) * (size_t)n);
-    double* vt = (double*)malloc(sizeof(double) * (size_t)n);
-    double* lr = (double*)malloc(sizeof(double) * (size_t)n);
-    double* lc = (double*)malloc(sizeof(double) * (size_t)n);
-    double* lr_lo = (double*)malloc(sizeof(double) * (size_t)n);
-    double* lc_lo = (double*)malloc(sizeof(double) * (size_t)n);
-
-    const double d0 = phi_prime(n, pu, pv, log_rP, log_cP, r, c);   /* O(n), App. B */
-    int rc = 2;
     double lo = 0.0, dlo = d0, hi = INFINITY, dhi = INFINITY;
     double a = a0;                              /* first trial step */
-    if (!(d0 < 0.0)) goto done;                 /* not a descent direction */
+    if (!(d0 < 0.0)) return 2;                  /* not a descent direction */
     for (int trial = 0; trial < prm->ls_max_trials; ++trial) {
-        for (int i = 0; i < n; ++i) ut[i] = u[i] + a * pu[i];
-        for (int j = 0; j < n; ++j) vt[j] = v[j] + a * pv[j];
-        or_dual_eval(n, C, ut, vt, gamma, lr, lc);
-        st->evals++;
-        st->ls_trials++;
-        double d = phi_prime(n, pu, pv, lr, lc, r, c);
+        double d = dphi(ctx, a);
         if (!isfinite(d)) {                     /* overshoot into overflow: shrink */
             hi = a;
             dhi = INFINITY;
@@ -166,17 +162,13 @@ static int line_search(int n, const double* C, double gamma, const double* r, co
             continue;
         }
         if (d <= (2.0 * c1 - 1.0) * d0 && d >= c2 * d0) {   /* Eq. (24) holds */
-            memcpy(log_rP, lr, sizeof(double) * (size_t)n);
-            memcpy(log_cP, lc, sizeof(double) * (size_t)n);
             *alpha_out = a;
-            rc = 0;
-            goto done;
+            return 0;
         }
         if (d < c2 * d0) {                      /* still descending steeply: raise lower end */
             lo = a;
             dlo = d;
-            memcpy(lr_lo, lr, sizeof(double) * (size_t)n);
-            memcpy(lc_lo, lc, sizeof(double) * (size_t)n);
+            if (keep_lo) keep_lo(ctx);
         } else {                                /* overshoot: lower the upper end */
             hi = a;
             dhi = d;
@@ -191,13 +183,69 @@ static int line_search(int n, const double* C, double gamma, const double* r, co
         }
     }
     if (lo > 0.0) {                             /* cap reached: take the lower end */
-        memcpy(log_rP, lr_lo, sizeof(double) * (size_t)n);
-        memcpy(log_cP, lc_lo, sizeof(double) * (size_t)n);
         *alpha_out = lo;
-        rc = 1;
+        return 1;
     }
-done:
-    free(ut); free(vt); free(lr); free(lc); free(lr_lo); free(lc_lo);
+    return 2;
+}
+
+/* The PNCG line search: phi'(alpha) from a full dual evaluation at (u, v) + alpha p (App. B). */
+typedef struct {
+    int n;
+    const double *C, *r, *c, *u, *v, *pu, *pv;
+    double gamma;
+    double *ut, *vt, *lr, *lc, *lr_lo, *lc_lo;
+    or_stats* st;
+} pncg_ls_ctx;
+
+static double pncg_dphi(void* vctx, double a)
+{
+    pncg_ls_ctx* x = (pncg_ls_ctx*)vctx;
+    const int n = x->n;
+    for (int i = 0; i < n; ++i) x->ut[i] = x->u[i] + a * x->pu[i];
+    for (int j = 0; j < n; ++j) x->vt[j] = x->v[j] + a * x->pv[j];
+    or_dual_eval(n, x->C, x->ut, x->vt, x->gamma, x->lr, x->lc);
+    x->st->evals++;
+    x->st->ls_trials++;
+    return phi_prime(n, x->pu, x->pv, x->lr, x->lc, x->r, x->c);
+}
+
+static void pncg_keep_lo(void* vctx)
+{
+    pncg_ls_ctx* x = (pncg_ls_ctx*)vctx;
+    memcpy(x->lr_lo, x->lr, sizeof(double) * (size_t)x->n);
+    memcpy(x->lc_lo, x->lc, sizeof(double) * (size_t)x->n);
+}
+
+/*
+ * On entry log_rP / log_cP hold the marginals at alpha = 0; on success they hold the marginals at
+ * the accepted alpha (so the next PNCG iteration reuses them, App. B).  Returns as or_ls_search.
+ */
+static int line_search(int n, const double* C, double gamma, const double* r, const double* c,
+                       const double* u, const double* v, const double* pu, const double* pv,
+                       double* log_rP, double* log_cP, double a0, double* alpha_out,
+                       const or_params* prm, or_stats* st)
+{
+    pncg_ls_ctx x;
+    x.n = n; x.C = C; x.r = r; x.c = c; x.u = u; x.v = v; x.pu = pu; x.pv = pv; x.gamma = gamma;
+    x.st = st;
+    x.ut = (double*)malloc(sizeof(double) * (size_t)n);
+    x.vt = (double*)malloc(sizeof(double) * (size_t)n);
+    x.lr = (double*)malloc(sizeof(double) * (size_t)n);
+    x.lc = (double*)malloc(sizeof(double) * (size_t)n);
+    x.lr_lo = (double*)malloc(sizeof(double) * (size_t)n);
+    x.lc_lo = (double*)malloc(sizeof(double) * (size_t)n);
+
+    const double d0 = phi_prime(n, pu, pv, log_rP, log_cP, r, c);   /* O(n), App. B */
+    int rc = or_ls_search(d0, a0, prm, pncg_dphi, pncg_keep_lo, &x, alpha_out);
+    if (rc == 0) {
+        memcpy(log_rP, x.lr, sizeof(double) * (size_t)n);
+        memcpy(log_cP, x.lc, sizeof(double) * (size_t)n);
+    } else if (rc == 1) {
+        memcpy(log_rP, x.lr_lo, sizeof(double) * (size_t)n);
+        memcpy(log_cP, x.lc_lo, sizeof(double) * (size_t)n);
+    }
+    free(x.ut); free(x.vt); free(x.lr); free(x.lc); free(x.lr_lo); free(x.lc_lo);
     return rc;
 }
 

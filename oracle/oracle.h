@@ -66,6 +66,17 @@ void   or_dual_eval(int n, const double* C, const double* u, const double* v, do
 double or_dual_value(int n, const double* C, const double* u, const double* v, double gamma,
                      const double* r, const double* c);
 
+/* The App. B line search on a scalar function phi (approximate Wolfe test Eq. (24), doubling
+ * until bracketed, hybrid secant/bisection step Eq. (25) inside the bracket).  dphi(ctx, alpha)
+ * returns phi'(alpha) (non-finite: an overshoot); keep_lo(ctx) (nullable) is called whenever the
+ * trial just evaluated becomes the lower end of the bracket.  d0 = phi'(0) < 0, a0 = first trial.
+ * Returns 0 with the accepted step (the last trial) in *alpha_out, 1 when the trial cap took the
+ * lower end (*alpha_out = lo), 2 when no step was found. */
+typedef double (*or_dphi_fn)(void* ctx, double alpha);
+typedef void (*or_keep_fn)(void* ctx);
+int    or_ls_search(double d0, double a0, const or_params* prm, or_dphi_fn dphi, or_keep_fn keep_lo,
+                    void* ctx, double* alpha_out);
+
 /* One PNCG projection (Alg. 2) with the App. B line search; u, v updated in place.
  * tol is the threshold on ||grad g||_1.  log_rP / log_cP (n each) receive the final marginals. */
 int    or_pncg(int n, const double* C, double gamma, const double* r, const double* c, double tol,

@@ -33,7 +33,7 @@ class Params(ct.Structure):
                 ("warm_start", ct.c_int32), ("final_tol", ct.c_double), ("fp32_floor", ct.c_double),
                 ("profile", ct.c_int32), ("smoothing", ct.c_int32), ("projector", ct.c_int32),
                 ("stop_entropy", ct.c_int32), ("precond", ct.c_int32), ("ls_init", ct.c_int32),
-                ("reserved", ct.c_int32 * 2)]
+                ("wait_limit_us", ct.c_int32), ("reserved", ct.c_int32)]
 
 
 class Info(ct.Structure):
@@ -47,6 +47,11 @@ class Info(ct.Structure):
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
+
+
+class TraceRow(ct.Structure):
+    """mdot_trace_row: one kernel launch of a profiled solve."""
+    _fields_ = [("kind", ct.c_int32), ("reserved", ct.c_int32), ("ms", ct.c_double), ("evals", ct.c_int64)]
 
 
 class MdotError(RuntimeError):
@@ -78,7 +83,8 @@ def lib():
     L.mdot_last_error.restype = ct.c_char_p
     L.mdot_create.argtypes = [ct.POINTER(_P), ct.c_int64, _P]
     L.mdot_destroy.argtypes = [_P]
-    L.mdot_dual_eval.argtypes = [_P, _P, _P, ct.c_double, _P, ct.c_int64, _P, ct.c_int32, _P, _P]
+    L.mdot_dual_eval.argtypes = [_P, _P, _P, ct.c_double, _P, ct.c_int64, _P, ct.c_int32, _P, _P, _P, _P,
+                                 ct.POINTER(ct.c_double)]
     L.mdot_round.argtypes = [_P, _P, _P, ct.c_double, _P, _P, _P, ct.c_int64,
                              ct.POINTER(ct.c_double), _P]
     L.mdot_lower_bound.argtypes = [_P, _P, ct.c_double, _P, _P, _P, ct.c_int64, ct.POINTER(ct.c_double)]
@@ -89,7 +95,7 @@ def lib():
                                     ct.POINTER(Params), _P, _P, ct.POINTER(ct.c_double),
                                     ct.POINTER(ct.c_double), ct.POINTER(Info)]
     L.mdot_dual_eval_points.argtypes = [_P, _P, _P, ct.c_double, _P, _P, ct.c_int32, ct.c_float, ct.c_int64,
-                                        _P, ct.c_int32, _P, _P]
+                                        _P, ct.c_int32, _P, _P, _P, _P, ct.POINTER(ct.c_double)]
     L.mdot_dual_eval_time.argtypes = [_P, ct.POINTER(ct.c_double)]
     for name in ("mdot_create", "mdot_destroy", "mdot_dual_eval", "mdot_round", "mdot_lower_bound",
                  "mdot_solve", "mdot_solve_host", "mdot_solve_points", "mdot_dual_eval_points",
@@ -173,18 +179,40 @@ class Handle:
         self.close()
 
     # ---- calls -------------------------------------------------------------------------------
-    def dual_eval(self, u, v, gamma: float, C, ref_log_rP=None, precision: int = PREC_FP32):
+    def dual_eval(self, u, v, gamma: float, C, ref_log_rP=None, precision: int = PREC_FP32, r=None, c=None):
+        """mdot_dual_eval: (log r(P), log c(P)); with the marginals r, c also the dual objective g
+        of Eq. (4): (log r(P), log c(P), g)."""
         import torch
         n = u.numel()
         lr = torch.empty(n, dtype=torch.float64, device=u.device)
         lc = torch.empty(n, dtype=torch.float64, device=u.device)
         ref = _ptr(ref_log_rP, torch.float64, n, "ref_log_rP") if ref_log_rP is not None else None
+        want_g = r is not None or c is not None
+        g = ct.c_double(0.0)
         s = lib().mdot_dual_eval(self._h, _ptr(u, torch.float64, n, "u"), _ptr(v, torch.float64, n, "v"),
                                  float(gamma), _ptr(C, torch.float32, n * n, "C"), n, ref,
-                                 int(precision), _ptr(lr, torch.float64), _ptr(lc, torch.float64))
+                                 int(precision), _ptr(lr, torch.float64), _ptr(lc, torch.float64),
+                                 _ptr(r, torch.float64, n, "r") if r is not None else None,
+                                 _ptr(c, torch.float64, n, "c") if c is not None else None,
+                                 ct.byref(g) if want_g else None)
         if s != MDOT_OK:
             raise MdotError(s, "mdot_dual_eval")
-        return lr, lc
+        return (lr, lc, g.value) if want_g else (lr, lc)
+
+    def solve_trace(self):
+        """mdot_solve_trace: one dict per kernel launch of the last profiled solve (kind: 0 fp32-entry
+        stage, 1 fp64-entry stage, 2 rounding, 3 bound; device ms; evaluations it made)."""
+        L = lib()
+        if not hasattr(L, "_trace_typed"):
+            L.mdot_solve_trace.argtypes = [_P, ct.c_int32, ct.POINTER(TraceRow), ct.POINTER(ct.c_int32)]
+            L.mdot_solve_trace.restype = ct.c_int32
+            L._trace_typed = True
+        rows = (TraceRow * 512)()
+        cnt = ct.c_int32(0)
+        s = L.mdot_solve_trace(self._h, 512, rows, ct.byref(cnt))
+        if s != MDOT_OK:
+            raise MdotError(s, "mdot_solve_trace")
+        return [{"kind": rows[k].kind, "ms": rows[k].ms, "evals": rows[k].evals} for k in range(min(cnt.value, 512))]
 
     def dual_eval_time(self) -> float:
         """mdot_dual_eval_time: device milliseconds of the last dual-evaluation kernel."""
@@ -236,20 +264,26 @@ class Handle:
         return u, v, SolveResult(s, cost.value, gap.value, info)
 
     def dual_eval_points(self, u, v, gamma: float, x, y, kind: int, scale: float, ref_log_rP=None,
-                         precision: int = PREC_FP32):
-        """mdot_dual_eval_points: C regenerated from coordinates x, y (CUDA float32 tensors n x 3)."""
+                         precision: int = PREC_FP32, r=None, c=None):
+        """mdot_dual_eval_points: C regenerated from coordinates x, y (CUDA float32 tensors n x 3);
+        with r, c also the dual objective g of Eq. (4)."""
         import torch
         n = u.numel()
         lr = torch.empty(n, dtype=torch.float64, device=u.device)
         lc = torch.empty(n, dtype=torch.float64, device=u.device)
         ref = _ptr(ref_log_rP, torch.float64, n, "ref_log_rP") if ref_log_rP is not None else None
+        want_g = r is not None or c is not None
+        g = ct.c_double(0.0)
         s = lib().mdot_dual_eval_points(self._h, _ptr(u, torch.float64, n, "u"), _ptr(v, torch.float64, n, "v"),
                                         float(gamma), _ptr(x, torch.float32, 3 * n, "x"),
                                         _ptr(y, torch.float32, 3 * n, "y"), int(kind), float(scale), n, ref,
-                                        int(precision), _ptr(lr, torch.float64), _ptr(lc, torch.float64))
+                                        int(precision), _ptr(lr, torch.float64), _ptr(lc, torch.float64),
+                                        _ptr(r, torch.float64, n, "r") if r is not None else None,
+                                        _ptr(c, torch.float64, n, "c") if c is not None else None,
+                                        ct.byref(g) if want_g else None)
         if s != MDOT_OK:
             raise MdotError(s, "mdot_dual_eval_points")
-        return lr, lc
+        return (lr, lc, g.value) if want_g else (lr, lc)
 
     def solve_points(self, r, c, x, y, kind: int, scale: float, eps_target: float = 1e-6,
                      params: Params | None = None, u_out=None, v_out=None, check: bool = True):
@@ -285,6 +319,25 @@ class Handle:
         if check and s not in (MDOT_OK, MDOT_ERR_NOT_CONVERGED):
             raise MdotError(s, "mdot_solve_host")
         return u, v, SolveResult(s, cost.value, gap.value, info)
+
+
+def read_probe(buf, reps: int, stream=None):
+    """mdot_read_probe: read the float32 CUDA tensor buf `reps` times (128-bit loads); returns the
+    checksum tensor (the caller times the call with CUDA events on `stream`)."""
+    import torch
+    L = lib()
+    if not hasattr(L, "_probe_typed"):
+        L.mdot_read_probe.argtypes = [_P, ct.c_int64, ct.c_int32, _P, _P]
+        L.mdot_read_probe.restype = ct.c_int32
+        L._probe_typed = True
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    out = torch.empty(1, dtype=torch.float32, device=buf.device)
+    s = L.mdot_read_probe(_ptr(buf, torch.float32, None, "buf"), buf.numel(), int(reps), _ptr(out, torch.float32),
+                          ct.c_void_p(stream.cuda_stream))
+    if s != MDOT_OK:
+        raise MdotError(s, "mdot_read_probe")
+    return out
 
 
 NOALLOC_MAX_N = 4096

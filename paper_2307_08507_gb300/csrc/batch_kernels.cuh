@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a)
         // ---- MDOT (Alg. 1): stage after stage ----
         if (tid == 0) memset(&st, 0, sizeof(State));
         __syncthreads();
-        double gamma = fmin(a.gamma_i, gf), dgamma_prev = gamma, ratio = 0.0;
+        double gamma = fmin(a.gamma_i, gf), dgamma_prev = gamma, ratio = 0.0, tol_last = 0.0;
         int stages = 0;
         for (int t = 1;; ++t) {
             const double eps_d = H / pow(gamma, a.p);
@@ -247,6 +247,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a)
             sa.ls_init = a.ls_init;
             sa.max_iter = a.max_iter;
             sa.tier = acc ? TIER_F32A : TIER_F32;
+            sa.stall_below = stall_floor(sa.tier);
             const double inv_gamma = 1.0 / gamma, G64 = sa.G64;
             const float G32 = (float)G64, Glo = (float)(G64 - (double)G32);
             // prologue: smoothing, rank-one start or warm start (Eq. (13)), constants at alpha = 0
@@ -347,6 +348,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a)
                 if (done) break;
             }
             ++stages;
+            tol_last = sa.tol;
             if (last || st.status >= ST_LSFAIL) break;
             double dg = (a.q - 1.0) * gamma;
             const double gnext = fmin(gamma + dg, gf);
@@ -417,31 +419,29 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a)
             if (tid == 0) res.cost = x[0] + ((x[1] > 0.0) ? x[2] / x[1] : 0.0);
         }
 
-        // ---- c-transform lower bound from f = u / gamma_f (fp32 differences, fp64 sums) ----
+        // ---- c-transform lower bound from f = u / gamma_f, fp64 throughout (the gap estimate) ----
         {
             const double inv_gamma = 1.0 / gf;
-            for (int i = tid; i < n; i += T) {
-                const double f = V[SV_U][i] * inv_gamma;
-                sFh[i] = (float)f;
-                sWr[i] = (float)(f - (double)sFh[i]);
-            }
+            double* fv = V[SV_SRT];                      // free once the stages are over
+            double* gv = V[SV_SCT];
+            for (int i = tid; i < n; i += T) fv[i] = V[SV_U][i] * inv_gamma;
             __syncthreads();
             for (int j = tid; j < n; j += T) {           // g'_j = min_i (C_ij - f_i)
-                float m = INFINITY;
-                for (int i = 0; i < n; ++i) m = fminf(m, (batch_cost<COST>(P, i, j) - sFh[i]) - sWr[i]);
-                colsum[j] = m;
+                double m = INFINITY;
+                for (int i = 0; i < n; ++i) m = fmin(m, (double)batch_cost<COST>(P, i, j) - fv[i]);
+                gv[j] = m;
             }
             __syncthreads();
 #pragma unroll
             for (int q = 0; q < kNRed; ++q) x[q] = 0.0;
             for (int i = warp; i < n; i += nw) {         // f'_i = min_j (C_ij - g'_j)
-                float m = INFINITY;
-                for (int j = lane; j < n; j += 32) m = fminf(m, batch_cost<COST>(P, i, j) - colsum[j]);
+                double m = INFINITY;
+                for (int j = lane; j < n; j += 32) m = fmin(m, (double)batch_cost<COST>(P, i, j) - gv[j]);
 #pragma unroll
-                for (int o = 16; o >= 1; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
-                if (lane == 0) x[0] += (double)m * P.r[i];
+                for (int o = 16; o >= 1; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+                if (lane == 0) x[0] += m * P.r[i];
             }
-            for (int j = tid; j < n; j += T) x[1] += (double)colsum[j] * P.c[j];
+            for (int j = tid; j < n; j += T) x[1] += gv[j] * P.c[j];
             block_reduce_nred(x, red_smem);
             if (tid == 0) res.lower_bound = x[0] + x[1];
         }
@@ -451,7 +451,8 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a)
         }
         __syncthreads();           // every output is written before the result (and done flag)
         if (tid == 0) {
-            res.status = st.status;
+            // a last stage that ended above its tolerance (by the stall rule) has not converged
+            res.status = (st.status == ST_OK && !(st.gnorm <= tol_last)) ? (int)ST_CAP : st.status;
             res.stages = stages;
             res.evals = st.evals;
             res.iters = st.iters;

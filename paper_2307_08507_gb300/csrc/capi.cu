@@ -18,6 +18,7 @@ using namespace mdot;
 namespace {
 
 thread_local char g_err[512] = "";
+constexpr int kTraceMax = 512;          // launches recorded by a profiled solve
 
 struct Deleter {
     std::vector<void*> dev, host;
@@ -39,6 +40,7 @@ struct mdot_handle {
     double* d_out = nullptr;       // [16] device results
     double* h_out = nullptr;       // [16] pinned
     State* h_state = nullptr;      // pinned copy of the state
+    unsigned int* h_limit = nullptr;   // pinned: the wait limit copied into the state of a solve
     double *Y = nullptr, *EC = nullptr, *ER = nullptr, *gp = nullptr;
     // device buffers of mdot_solve_host
     double *d_r = nullptr, *d_c = nullptr, *d_u = nullptr, *d_v = nullptr;
@@ -56,6 +58,9 @@ struct mdot_handle {
     // bound, from the evaluation counts); cleared well before the 32-bit tag could wrap
     unsigned long long tags_used = 0;
     size_t flag_bytes = 0;
+    // per-launch rows of the last profiled solve (mdot_solve_trace)
+    long long* h_trace_evals = nullptr;     // pinned [kTraceMax]
+    std::vector<mdot_trace_row> trace;
     // device time of the last standalone dual-evaluation kernel (events around its launch)
     cudaEvent_t de_ev[2] = {nullptr, nullptr};
     double de_ms = -1.0;
@@ -104,6 +109,7 @@ void mdot_default_params(mdot_params* prm)
     prm->fp32_floor = 5e-8;
     prm->profile = 0;
     prm->ls_init = 1;                    // App. B leaves the first trial step open (see mdot.h)
+    prm->wait_limit_us = 0;              // bounded device waits: the 2 s default
 }
 
 const char* mdot_status_string(int32_t s)
@@ -163,14 +169,15 @@ mdot_status mdot_create(mdot_handle** out, int64_t max_n, void* stream)
     double* blockred = (double*)dalloc(G * kNRedP * sizeof(double));
     double* scratch = (double*)dalloc(G * 8 * sizeof(double));
     State* st = (State*)dalloc(sizeof(State));
-    // stage-kernel flags [2][G] and the tag base; published column state (v, p double-floats, s)
+    // stage-kernel flags [2][G] and the tag base; published column state (hb, rb, P, S per column)
     const size_t flag_words = 2 * G + 1;
     unsigned int* flagw = (unsigned int*)dalloc(flag_words * sizeof(unsigned int));
-    float* pubw = (float*)dalloc(5 * n * sizeof(float));
+    float* pubw = (float*)dalloc(4 * n * sizeof(float));
     unsigned long long* tspw = (unsigned long long*)dalloc(G * 2 * kNRed * sizeof(unsigned long long));
     h->d_out = (double*)dalloc(16 * sizeof(double));
     void* hp = nullptr;
-    if (cudaMallocHost(&hp, 16 * sizeof(double) + sizeof(State)) == cudaSuccess) h->mem.host.push_back(hp);
+    if (cudaMallocHost(&hp, 16 * sizeof(double) + sizeof(State) + 16 + kTraceMax * sizeof(long long)) == cudaSuccess)
+        h->mem.host.push_back(hp);
     if (!vec || !f32 || !A || !colpart || !colpartd || !blockred || !scratch || !st || !flagw || !pubw || !tspw || !h->d_out || !hp) {
         snprintf(g_err, sizeof g_err, "workspace allocation failed for max_n = %lld", (long long)max_n);
         delete h;
@@ -178,6 +185,8 @@ mdot_status mdot_create(mdot_handle** out, int64_t max_n, void* stream)
     }
     h->h_out = (double*)hp;
     h->h_state = (State*)((char*)hp + 16 * sizeof(double));
+    h->h_limit = (unsigned int*)((char*)hp + 16 * sizeof(double) + sizeof(State));
+    h->h_trace_evals = (long long*)((char*)hp + 16 * sizeof(double) + sizeof(State) + 16);
     WS& w = h->ws;
     double* p = vec;
     auto take = [&]() { double* q = p; p += n; return q; };
@@ -196,9 +205,7 @@ mdot_status mdot_create(mdot_handle** out, int64_t max_n, void* stream)
     w.flags = flagw;
     w.epoch = flagw + 2 * G;
     w.tsp = tspw;
-    w.pub_v = reinterpret_cast<float2*>(pubw);
-    w.pub_p = reinterpret_cast<float2*>(pubw + 2 * n);
-    w.pub_s = pubw + 4 * n;
+    w.pub = reinterpret_cast<float4*>(pubw);
     h->flag_bytes = flag_words * sizeof(unsigned int);
     w.G = h->G;
     if (cudaMemsetAsync(st, 0, sizeof(State), h->stream) != cudaSuccess ||
@@ -280,10 +287,13 @@ mdot_status handle_set_grid(mdot_handle* h, int G)
 
 namespace {
 
-// Optional per-launch timing with CUDA events on the handle's stream.
+// Optional per-launch timing with CUDA events on the handle's stream; after each launch the
+// cumulative evaluation count of the state is copied into a pinned slot (the solve trace).
 struct Timer {
     bool on = false;
     cudaStream_t s = nullptr;
+    const long long* dev_evals = nullptr;     // State::evals on the device
+    long long* host_evals = nullptr;          // pinned, kTraceMax slots
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
     std::vector<int> kind;
     void begin(int k)
@@ -298,15 +308,25 @@ struct Timer {
     }
     void end()
     {
-        if (on) cudaEventRecord(ev.back().second, s);
+        if (!on) return;
+        cudaEventRecord(ev.back().second, s);
+        if (host_evals && ev.size() <= (size_t)kTraceMax)
+            cudaMemcpyAsync(host_evals + ev.size() - 1, dev_evals, sizeof(long long), cudaMemcpyDeviceToHost, s);
     }
-    // call after the stream is synchronised; sums[k] += ms
-    void collect(double* sums)
+    // call after the stream is synchronised; sums[k] += ms; the per-launch rows go to trace
+    void collect(double* sums, std::vector<mdot_trace_row>* trace = nullptr)
     {
+        if (trace) trace->clear();
+        long long prev = 0;
         for (size_t q = 0; q < ev.size(); ++q) {
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, ev[q].first, ev[q].second);
             sums[kind[q]] += ms;
+            if (trace && host_evals && q < (size_t)kTraceMax) {
+                const long long e = host_evals[q];
+                trace->push_back(mdot_trace_row{kind[q], 0, (double)ms, e - prev});
+                prev = e;
+            }
             cudaEventDestroy(ev[q].first);
             cudaEventDestroy(ev[q].second);
         }
@@ -316,8 +336,16 @@ struct Timer {
     ~Timer() { double d[8] = {0}; collect(d); }
 };
 
-// Reset the barrier and counters before a new call (also clears an aborted barrier).
-cudaError_t reset_state(mdot_handle* h) { return cudaMemsetAsync(h->ws.st, 0, sizeof(State), h->stream); }
+// Reset the barrier and counters before a new call (also clears an aborted barrier); limit_us > 0
+// sets the limit of the call's bounded waits (0: the default of the device code).
+cudaError_t reset_state(mdot_handle* h, int limit_us = 0)
+{
+    cudaError_t e = cudaMemsetAsync(h->ws.st, 0, sizeof(State), h->stream);
+    if (e != cudaSuccess || limit_us <= 0) return e;
+    *h->h_limit = (unsigned int)limit_us;      // pinned; the call synchronises before it returns
+    return cudaMemcpyAsync(&h->ws.st->bar.limit_us, h->h_limit, sizeof(unsigned int), cudaMemcpyHostToDevice,
+                           h->stream);
+}
 
 double gamma_f_for_eps(double H, double eps, double gi, double q, double p)
 {
@@ -394,7 +422,7 @@ mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const C
     constexpr double kAccSwitch = 2e-6;
     const bool all64 = P.precision == MDOT_PREC_FP64 || (P.precision == MDOT_PREC_AUTO && n <= 512);
     const bool polish = P.precision == MDOT_PREC_AUTO && !all64;
-    CKR(reset_state(h));
+    CKR(reset_state(h, P.wait_limit_us));
     if (h->tags_used > (1ull << 31)) {
         // restart the stage kernel's tags from zero long before the 32-bit tag could wrap
         CKR(cudaMemsetAsync(h->ws.flags, 0, h->flag_bytes, h->stream));
@@ -404,7 +432,10 @@ mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const C
     Timer tm;
     tm.on = P.profile != 0;
     tm.s = h->stream;
+    tm.dev_evals = &ws.st->evals;
+    tm.host_evals = h->h_trace_evals;
     int launches = 1, launches32 = 0;
+    double tol_last = 0.0;           // tolerance the last stage launch was asked for
     // Alg. 1: gamma schedule, stage by stage (same arithmetic as the paper's loop)
     double gamma = std::min(P.gamma_i, gf);
     double dgamma_prev = gamma;      // stage 0 is gamma = 0 (Prop. 1): the first step is gamma_1
@@ -435,32 +466,46 @@ mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const C
         if (all64) {
             a.tier = TIER_F64;
             a.tol = tol;
+            a.stall_below = stall_floor(TIER_F64);
             tm.begin(1);
             CKR(launch_projection(P.projector, TIER_F64, ws, a, h->stream));
             tm.end();
             ++launches;
+            tol_last = a.tol;
         } else {
             int tier = TIER_F32;
             if (P.precision == MDOT_PREC_FP32A || (P.precision == MDOT_PREC_AUTO && tol < kAccSwitch)) tier = TIER_F32A;
             a.tier = tier;
             a.tol = std::max(tol, (double)P.fp32_floor);
+            a.stall_below = stall_floor(tier);
             tm.begin(0);
             CKR(launch_projection(P.projector, tier, ws, a, h->stream));
             tm.end();
             ++launches;
             ++launches32;
-            if (last && polish && tol < P.fp32_floor) {
-                // final stage below the fp32 noise floor: continue in fp64 entries from the
-                // fp32 iterate (same gamma, same smoothing, no warm start)
+            tol_last = a.tol;
+            bool polish_now = last && polish && tol < P.fp32_floor;
+            if (last && polish && !polish_now) {
+                // the last fp32 stage may have ended by the stall rule above its tolerance: read
+                // its outcome (one synchronisation per solve) and polish in fp64 if so
+                CKR(cudaMemcpyAsync(h->h_state, ws.st, sizeof(State), cudaMemcpyDeviceToHost, h->stream));
+                CKR(cudaStreamSynchronize(h->stream));
+                polish_now = h->h_state->status == ST_OK && !(h->h_state->gnorm <= a.tol);
+            }
+            if (polish_now) {
+                // final stage below the fp32 noise floor, or stalled above its tolerance: continue
+                // in fp64 entries from the fp32 iterate (same gamma, same smoothing, no warm start)
                 StageArgs b = a;
                 b.tier = TIER_F64;
                 b.tol = tol;
                 b.first = 0;
                 b.warm_start = 2;
+                b.stall_below = stall_floor(TIER_F64);
                 tm.begin(1);
                 CKR(launch_projection(P.projector, TIER_F64, ws, b, h->stream));
                 tm.end();
                 ++launches;
+                tol_last = b.tol;
             }
         }
         ++stages;
@@ -509,12 +554,15 @@ mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const C
     const State& S = *h->h_state;
     h->tags_used += (unsigned long long)S.evals + 4ull * (unsigned long long)(launches + 1);
     double tsum[8] = {0};
-    tm.collect(tsum);
+    tm.collect(tsum, tm.on ? &h->trace : nullptr);
     const double cost = h->h_out[0], lb = h->h_out[8];
     if (cost_out) *cost_out = cost;
     if (gap_out) *gap_out = cost - lb;
     mdot_status out = map_status(S.status);
     if (out == MDOT_OK && !(std::isfinite(cost) && std::isfinite(lb))) out = MDOT_ERR_NUMERIC;
+    // the last stage must have reached the tolerance it was asked for (a stage that stalled above
+    // it and could not be polished leaves the best iterate in the outputs)
+    if (out == MDOT_OK && !(S.gnorm <= tol_last)) out = MDOT_ERR_NOT_CONVERGED;
     if (info) {
         memset(info, 0, sizeof(*info));
         info->status = out;
@@ -604,10 +652,11 @@ mdot_status mdot_solve_host(mdot_handle* h, const double* r_host, const double* 
 
 static mdot_status dual_eval_core(mdot_handle* h, const double* u, const double* v, double gamma,
                                   const CostSpec& cs, int64_t n, const double* ref_log_rP, int32_t precision,
-                                  double* log_rP, double* log_cP)
+                                  double* log_rP, double* log_cP, const double* r, const double* c,
+                                  double* g_out)
 {
     if (!h || !u || !v || !cs.valid() || !log_rP || !log_cP || n < 1 || n > h->max_n || !(gamma > 0.0) ||
-        !std::isfinite(gamma) || precision < 0 || precision > 3)
+        !std::isfinite(gamma) || precision < 0 || precision > 3 || (g_out && (!r || !c)))
         return MDOT_ERR_INVALID_ARG;
     WS ws = h->ws;
     ws.n = (int)n;
@@ -618,6 +667,11 @@ static mdot_status dual_eval_core(mdot_handle* h, const double* u, const double*
     a.u = u;
     a.v = v;
     a.ref = ref_log_rP;
+    if (g_out) {
+        a.r = r;
+        a.c = c;
+        a.g_out = h->d_out + 15;
+    }
     const int tier = (precision == MDOT_PREC_FP64) ? TIER_F64 : (precision == MDOT_PREC_FP32A) ? TIER_F32A : TIER_F32;
     CKR(reset_state(h));
     if (!h->de_ev[0]) {
@@ -631,10 +685,13 @@ static mdot_status dual_eval_core(mdot_handle* h, const double* u, const double*
     CKR(cudaMemcpyAsync(log_rP, ws.lrtr, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     CKR(cudaMemcpyAsync(log_cP, ws.lcout, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     CKR(cudaMemcpyAsync(h->h_state, ws.st, sizeof(State), cudaMemcpyDeviceToHost, h->stream));
+    if (g_out) CKR(cudaMemcpyAsync(h->h_out + 15, h->d_out + 15, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CKR(cudaStreamSynchronize(h->stream));
     float ms = 0.0f;
     if (cudaEventElapsedTime(&ms, h->de_ev[0], h->de_ev[1]) == cudaSuccess) h->de_ms = ms;
-    return h->h_state->status == ST_OK ? MDOT_OK : MDOT_ERR_TIMEOUT;
+    if (h->h_state->status != ST_OK) return map_status(h->h_state->status);
+    if (g_out) *g_out = h->h_out[15];
+    return MDOT_OK;
 }
 
 mdot_status mdot_solve_batch(mdot_handle* h, int32_t nprob, const mdot_problem* probs, const mdot_params* prm,
@@ -739,11 +796,19 @@ mdot_status mdot_solve_batch(mdot_handle* h, int32_t nprob, const mdot_problem* 
 
 mdot_status mdot_dual_eval(mdot_handle* h, const double* u, const double* v, double gamma, const float* C,
                            int64_t n, const double* ref_log_rP, int32_t precision, double* log_rP,
-                           double* log_cP)
+                           double* log_cP, const double* r, const double* c, double* g_out)
 {
     CostSpec cs;
     cs.C = C;
-    return dual_eval_core(h, u, v, gamma, cs, n, ref_log_rP, precision, log_rP, log_cP);
+    return dual_eval_core(h, u, v, gamma, cs, n, ref_log_rP, precision, log_rP, log_cP, r, c, g_out);
+}
+
+mdot_status mdot_solve_trace(const mdot_handle* h, int32_t max_rows, mdot_trace_row* rows, int32_t* count)
+{
+    if (!h || !count || max_rows < 0 || (max_rows > 0 && !rows)) return MDOT_ERR_INVALID_ARG;
+    *count = (int32_t)h->trace.size();
+    for (int32_t k = 0; k < max_rows && k < *count; ++k) rows[k] = h->trace[k];
+    return h->trace.empty() ? MDOT_NOT_READY : MDOT_OK;
 }
 
 mdot_status mdot_dual_eval_time(const mdot_handle* h, double* ms_out)
@@ -755,7 +820,8 @@ mdot_status mdot_dual_eval_time(const mdot_handle* h, double* ms_out)
 
 mdot_status mdot_dual_eval_points(mdot_handle* h, const double* u, const double* v, double gamma,
                                   const float* x, const float* y, int32_t cost_kind, float scale, int64_t n,
-                                  const double* ref_log_rP, int32_t precision, double* log_rP, double* log_cP)
+                                  const double* ref_log_rP, int32_t precision, double* log_rP, double* log_cP,
+                                  const double* r, const double* c, double* g_out)
 {
     CostSpec cs;
     cs.X = x;
@@ -763,7 +829,7 @@ mdot_status mdot_dual_eval_points(mdot_handle* h, const double* u, const double*
     cs.kind = cost_kind;
     cs.scale = scale;
     if (cost_kind == COST_DENSE) return MDOT_ERR_INVALID_ARG;
-    return dual_eval_core(h, u, v, gamma, cs, n, ref_log_rP, precision, log_rP, log_cP);
+    return dual_eval_core(h, u, v, gamma, cs, n, ref_log_rP, precision, log_rP, log_cP, r, c, g_out);
 }
 
 mdot_status mdot_round(mdot_handle* h, const double* u, const double* v, double gamma, const float* C,

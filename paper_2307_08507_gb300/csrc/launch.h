@@ -5,11 +5,17 @@
 
 #include <mutex>
 
+#include "mdot.h"
 #include "mdot_device.cuh"
 
 namespace mdot {
 
 struct BatchArgs;
+
+// The library's per-thread error text (what mdot_last_error returns) and the mapping of a device
+// status (SolveStatus) to mdot_status; both defined in capi.cu.
+void set_last_error(const char* msg);
+mdot_status status_of(int st);
 
 // Raise (never lower) a kernel's dynamic shared-memory limit: handles of different sizes, the
 // serving runtime and the no-allocation entry share the kernels of one process.

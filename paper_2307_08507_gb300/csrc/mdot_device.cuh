@@ -48,7 +48,7 @@ struct GridBar {
     unsigned int count;
     unsigned int gen;
     unsigned int abort;
-    unsigned int pad;
+    unsigned int limit_us;     // limit of every bounded wait in microseconds (0: kBarrierTimeoutNs)
 };
 
 // Scalar state of one projection (one MDOT stage) plus cumulative counters.
@@ -71,6 +71,16 @@ struct State {
     long long evals, evals64, iters, ls_trials;
     GridBar bar;
 };
+
+// Noise floor of ||grad g||_1 per entry tier: twice the largest relative error of one entry of P
+// (ex2.approx 2^-22.7; the accurate fp32 tier 1.1e-7, measured on 4e6 points per gamma; fp64 the
+// 1e-13 resolution floor of the stage tolerance).  The stall rule (a last-resort end of a stage
+// that stops improving) is armed only for stages whose tolerance is below 4x this floor; above it
+// the stage runs to its tolerance or to max_iter.
+__host__ __device__ inline double stall_floor(int tier)
+{
+    return 4.0 * (tier == TIER_F64 ? 1e-13 : tier == TIER_F32A ? 2.2e-7 : 3.0e-7);
+}
 
 struct WS {
     int n, G;
@@ -99,12 +109,12 @@ struct WS {
     unsigned int* flags;
     unsigned int* epoch;
     unsigned long long* tsp;          // [G][2 kNRed] tagged per-CTA scalar partials (fp64 halves)
-    float2 *pub_v, *pub_p;            // [n] committed column potentials / directions (double-float)
-    float* pub_s;                     // [n] Sinkhorn direction of the last evaluation (columns)
+    float4* pub;                      // [n] published column state (see col_publish)
 };
 
 struct StageArgs {
     double gamma, G64, tol, w, ratio, c1, c2;
+    double stall_below;    // the stall rule applies only when tol < stall_below (see stall_floor)
     int first, warm_start, tier, ls_max_trials, max_iter, Aglob;
     int precond;           // 1: diagonal-Hessian direction (Eq. (16)) where every ratio allows it
     int ls_init;           // 1: first trial step = previous accepted step clamped to [1/2, 2]
@@ -116,6 +126,11 @@ struct EvalArgs {
     const double* u;
     const double* v;
     const double* ref;   // nullable
+    // the dual objective g(u, v; gamma, r, c) of Eq. (4) into *g_out (device) when g_out is not
+    // null (r, c then given): sum_i r(P)_i - <u, r> - <v, c>, fp64 sums in a fixed order
+    const double* r;
+    const double* c;
+    double* g_out;
 };
 
 // Arguments of the rounding kernel (Alg. 3).
@@ -410,7 +425,13 @@ __device__ __forceinline__ void block_reduce_nred(double (&x)[NR], double* red_s
 // grid barrier with a bounded wait: a CTA that waits longer than the limit raises `abort`, every
 // waiter leaves, and the kernel returns with ST_TIMEOUT instead of hanging.
 // ---------------------------------------------------------------------------------------------
-constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;   // 2 s
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;   // 2 s: default wait limit
+
+__device__ __forceinline__ unsigned long long wait_limit_ns(const GridBar* gb)
+{
+    const unsigned int us = *reinterpret_cast<const volatile unsigned int*>(&gb->limit_us);
+    return us ? 1000ull * us : kBarrierTimeoutNs;
+}
 
 // s_flag points at two ints in shared memory: [0] "last to arrive", [1] "wait succeeded" (kept
 // apart so that a thread still reading one cannot see the other being rewritten).
@@ -438,14 +459,15 @@ __device__ __forceinline__ bool bar_wait(GridBar* gb, unsigned int target, int* 
 {
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned long long t0 = globaltimer();
+        const unsigned long long t0 = globaltimer(), lim = wait_limit_ns(gb);
         unsigned int spins = 0;
         while (true) {
             unsigned int g = ld_acquire(&gb->gen);
             if ((int)(g - target) >= 0) break;
             if (ld_acquire(&gb->abort)) { ok = 0; break; }
             if (++spins > 64u) __nanosleep(64);
-            if ((spins & 255u) == 0u && globaltimer() - t0 > kBarrierTimeoutNs) {
+            // the clock is read at every poll for the first 64, then every 64th
+            if ((spins <= 64u || (spins & 63u) == 0u) && globaltimer() - t0 > lim) {
                 atomicExch(&gb->abort, 1u);
                 ok = 0;
                 break;
@@ -485,21 +507,25 @@ __device__ __forceinline__ void ld_tag2(const unsigned long long* p, unsigned lo
 }
 
 // One step of a bounded wait on flags written by other CTAs: back off, and give up (raising the
-// shared abort flag) after kBarrierTimeoutNs or when another CTA has raised it.  Returns false to
-// give up.
-__device__ __forceinline__ bool wait_backoff(unsigned int& spins, unsigned long long& t0, unsigned int* abort)
+// shared abort flag gb->abort) once the wait has lasted longer than the limit (gb->limit_us,
+// default kBarrierTimeoutNs) or when another CTA has raised the flag.  deadline = 0 on the first
+// call (it is then set from the clock and the limit).  Returns false to give up.
+__device__ __forceinline__ bool wait_backoff(unsigned int& spins, unsigned long long& deadline, GridBar* gb)
 {
     ++spins;
     // poll without sleeping at first: a flag poll is a handful of loads by one warp, and the
     // sleep's granularity would add to every hand-off
     if (spins > 4096u) __nanosleep(64);
-    if ((spins & 63u) == 0u) {
-        if (ld_acquire(abort)) return false;
+    // the clock is read at every poll for the first 64 (a register read), then with the abort
+    // flag (a load from L2) at every 64th
+    const bool every64 = (spins & 63u) == 0u;
+    if (spins <= 64u || every64) {
+        if (every64 && ld_acquire(&gb->abort)) return false;
         const unsigned long long now = globaltimer();
-        if (t0 == 0ull) {
-            t0 = now;
-        } else if (now - t0 > kBarrierTimeoutNs) {
-            atomicExch(abort, 1u);
+        if (deadline == 0ull) {
+            deadline = now + wait_limit_ns(gb);
+        } else if (now > deadline) {
+            atomicExch(&gb->abort, 1u);
             return false;
         }
     }
@@ -604,52 +630,57 @@ __device__ __forceinline__ void col_commit(const ColStep& d, float2& v, float2& 
     }
 }
 
-// Trial constants of one column: x = (v + alpha p) / gamma in cost units, split into a part
-// quantised to 2^-21 (hh, exact in fp32 while |x| < 8) and the remainder in exponent units
-// (wc = gamma log2 e (x - hh)), as split_cost_unit does in fp64.
-__device__ __forceinline__ void col_trial(const ColStep& d, float2 v, float2 p, float2 inv_gamma, float G32,
-                                          float Glo, float& hh, float& wc)
+// Published state of one column for the next pass, computed by the column's owner from its
+// committed v, p (double-floats) and the new direction s:
+//   x = v / gamma in cost units, split into a part quantised to 2^-21 (hb, exact in fp32 while
+//   |x| < 8) and the remainder in exponent units (rb = gamma log2 e (x - hb));
+//   P = log2 e p and S = log2 e s, the directions in exponent units (gamma log2 e / gamma = log2 e).
+// Any trial point of the next pass, v + k1 p + k2 s, then has the column constants
+//   hh = hb,  wc = rb + k1 P + k2 S,
+// two fmas per column and consumer (see ColDelta).  The step terms carry the fp32 rounding of
+// k1 P + k2 S (relative 2^-24 of a term that is small near convergence); the committed (v, p)
+// stay exact double-floats in the owner.
+__device__ __forceinline__ float4 col_publish(float2 v, float2 p, float s, float2 inv_gamma, float G32, float Glo)
 {
-    const float2 x = df_mul(df_add(v, df_mul_f(p, d.alpha)), inv_gamma);
+    const float2 x = df_mul(v, inv_gamma);
     const float h = __fmul_rn(rintf(__fmul_rn(x.x, 2097152.0f)), 1.0f / 2097152.0f);
     const float lo = __fadd_rn(__fsub_rn(x.x, h), x.y);       // x.x - h is exact
-    hh = h;
-    wc = __fmaf_rn(lo, G32, __fmul_rn(lo, Glo));
+    const float rb = __fmaf_rn(lo, G32, __fmul_rn(lo, Glo));
+    return make_float4(h, rb, (float)(kLog2e * df_to_double(p)), (float)(kLog2e * (double)s));
 }
 
-// Column constants derived in place by each consumer thread from the owners' published state
-// (committed v, p and the new direction s of the last evaluation) and the decision: no hand-off
-// of constants between CTAs.  Partials go to plain arrays.
-struct ColDerived {
-    const float2* pv;
-    const float2* pp;
-    const float* ps;
+// The (k1, k2) of the next trial point v + k1 p + k2 s for a decision: after an accepted step the
+// owner commits v <- v + alpha_c p, p <- s + beta p, and the trial is v + alpha p of those, i.e.
+// k1 = alpha_c + alpha beta, k2 = alpha; otherwise the trial is v + alpha p (k1 = alpha, k2 = 0).
+__device__ __forceinline__ float2 col_step_coeffs(const ColStep& d)
+{
+    return d.accept ? make_float2(__fmaf_rn(d.alpha, d.beta, d.alpha_c), d.alpha) : make_float2(d.alpha, 0.0f);
+}
+
+// Column constants of a pass derived in place by every consumer thread from the owners'
+// published state (col_publish) and the decision: no hand-off of constants between CTAs.
+// Partials go to plain arrays.
+struct ColDelta {
+    const float4* pub;
     float* out;
-    ColStep d;
-    float2 inv_gamma;
-    float G32, Glo;
+    float k1, k2;
     template <int KK>
     __device__ __forceinline__ bool load_seg(const int (&jk)[KK], int n, float (&hh)[KK][4], float (&wc)[KK][4]) const
     {
-        float2 v[KK][4], p[KK][4];
-        float sv[KK][4];
+        float4 q[KK][4];
 #pragma unroll
         for (int k = 0; k < KK; ++k)
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 const int j = jk[k] + e;
-                const bool ok = j < n;
-                v[k][e] = ok ? __ldcg(pv + j) : make_float2(0.0f, 0.0f);
-                p[k][e] = ok ? __ldcg(pp + j) : make_float2(0.0f, 0.0f);
-                sv[k][e] = ok ? __ldcg(ps + j) : 0.0f;
+                q[k][e] = (j < n) ? __ldcg(pub + j) : make_float4(0.0f, kPadW, 0.0f, 0.0f);
             }
 #pragma unroll
         for (int k = 0; k < KK; ++k)
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                col_commit(d, v[k][e], p[k][e], sv[k][e]);
-                col_trial(d, v[k][e], p[k][e], inv_gamma, G32, Glo, hh[k][e], wc[k][e]);
-                if (jk[k] + e >= n) { hh[k][e] = 0.0f; wc[k][e] = kPadW; }
+                hh[k][e] = q[k][e].x;
+                wc[k][e] = (jk[k] + e < n) ? __fmaf_rn(k1, q[k][e].z, __fmaf_rn(k2, q[k][e].w, q[k][e].y)) : kPadW;
             }
         return true;
     }

@@ -44,7 +44,18 @@ struct DeviceSetup {
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 DeviceSetup g_setup[kMaxDevices];
-thread_local char g_noalloc_err[256] = "";
+
+// The message mdot_last_error() returns (the library's per-thread error text).
+mdot_status fail(mdot_status st, const char* what, cudaError_t e = cudaSuccess)
+{
+    char msg[256];
+    if (e != cudaSuccess)
+        snprintf(msg, sizeof msg, "mdot_dual_eval_noalloc: %s: %s", what, cudaGetErrorString(e));
+    else
+        snprintf(msg, sizeof msg, "mdot_dual_eval_noalloc: %s", what);
+    set_last_error(msg);
+    return st;
+}
 
 // Once per device, with that device current: the scratch's device address and the grid size.
 cudaError_t setup_device(int dev, DeviceSetup** out)
@@ -82,16 +93,19 @@ extern "C" mdot_status mdot_dual_eval_noalloc(const double* u, const double* v, 
                                               double* log_rP, double* log_cP, void* stream)
 {
     if (!u || !v || !C || !log_rP || !log_cP || n < 1 || !(gamma > 0.0) || !std::isfinite(gamma))
-        return MDOT_ERR_INVALID_ARG;
+        return fail(MDOT_ERR_INVALID_ARG, "null pointer, n < 1 or gamma not positive and finite");
     if (n > kMaxN) {
-        snprintf(g_noalloc_err, sizeof g_noalloc_err,
-                 "mdot_dual_eval_noalloc: n = %lld exceeds MDOT_NOALLOC_MAX_N = %d", (long long)n, kMaxN);
-        return MDOT_ERR_INVALID_ARG;
+        char what[128];
+        snprintf(what, sizeof what, "n = %lld exceeds MDOT_NOALLOC_MAX_N = %d", (long long)n, kMaxN);
+        return fail(MDOT_ERR_INVALID_ARG, what);
     }
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MDOT_ERR_CUDA;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(MDOT_ERR_CUDA, "cudaGetDevice", e);
+    if (dev < 0 || dev >= kMaxDevices) return fail(MDOT_ERR_CUDA, "device index beyond the set-up table");
     DeviceSetup* s = nullptr;
-    if (setup_device(dev, &s) != cudaSuccess) return MDOT_ERR_CUDA;
+    e = setup_device(dev, &s);
+    if (e != cudaSuccess) return fail(MDOT_ERR_CUDA, "set-up (scratch address, kernel attributes)", e);
     cudaStream_t st = (cudaStream_t)stream;
 
     WS ws{};
@@ -118,17 +132,20 @@ extern "C" mdot_status mdot_dual_eval_noalloc(const double* u, const double* v, 
     a.ref = ref_log_rP;
 
     // the barrier and status must start at zero; everything else is overwritten by the call
-    if (cudaMemsetAsync(ws.st, 0, sizeof(State), st) != cudaSuccess) return MDOT_ERR_CUDA;
+    e = cudaMemsetAsync(ws.st, 0, sizeof(State), st);
+    if (e != cudaSuccess) return fail(MDOT_ERR_CUDA, "clearing the scratch state", e);
     WS wk = ws;
     EvalArgs ak = a;
     void* args[] = {(void*)&wk, (void*)&ak};
     const size_t smem = smem_layout((int)n, s->G, TIER_F32, kStageThreads, true).bytes;
-    if (cudaLaunchCooperativeKernel((const void*)dual_eval_kernel<TIER_F32, COST_DENSE>, dim3(s->G), dim3(kStageThreads),
-                                    args, smem, st) != cudaSuccess)
-        return MDOT_ERR_CUDA;
+    e = cudaLaunchCooperativeKernel((const void*)dual_eval_kernel<TIER_F32, COST_DENSE>, dim3(s->G), dim3(kStageThreads),
+                                    args, smem, st);
+    if (e != cudaSuccess) return fail(MDOT_ERR_CUDA, "kernel launch", e);
     int status = 0;
-    if (cudaMemcpyAsync(&status, &ws.st->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
-        return MDOT_ERR_CUDA;
-    return status == ST_OK ? MDOT_OK : MDOT_ERR_TIMEOUT;
+    e = cudaMemcpyAsync(&status, &ws.st->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(MDOT_ERR_CUDA, "reading the status", e);
+    const mdot_status out = status_of(status);       // the device status, one to one
+    if (out != MDOT_OK) return fail(out, "the evaluation kernel reported a failure");
+    return MDOT_OK;
 }

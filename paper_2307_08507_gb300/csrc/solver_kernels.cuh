@@ -86,12 +86,14 @@ static __device__ void decide(State* S, const double* tot, const StageArgs& a)
     if (!was_init) { S->k += 1; S->iters += 1; }
     S->gnorm = gn;
     if (gn <= a.tol) { S->phase = PH_DONE; S->beta = 0.0; return; }
-    // stall rule: a stage whose tolerance lies below the noise floor of its arithmetic stops after
-    // kStallIters accepted iterations without 1 % progress (the next stage or tier continues)
+    // stall rule: a stage whose tolerance lies within 4x of the noise floor of its arithmetic
+    // (a.stall_below = stall_floor(tier)) stops after kStallIters accepted iterations without 1 %
+    // progress; the host then continues from the iterate (the next stage, the fp64 polish of the
+    // last stage) or reports MDOT_ERR_NOT_CONVERGED
     if (was_init || gn < 0.99 * S->best_gnorm) {
         S->best_gnorm = gn;
         S->since_best = 0;
-    } else if (++S->since_best >= kStallIters) {
+    } else if (++S->since_best >= kStallIters && a.tol < a.stall_below) {
         S->stalls += 1;
         S->phase = PH_DONE;
         S->beta = 0.0;
@@ -583,11 +585,11 @@ __device__ __forceinline__ void post_flag(unsigned int* flag, unsigned int tag)
 }
 
 // One warp waits (bounded) until every flags[0..G) has reached tag; false if it gave up.
-__device__ __forceinline__ bool wait_flags(const unsigned int* flags, int G, unsigned int tag, unsigned int* abort)
+__device__ __forceinline__ bool wait_flags(const unsigned int* flags, int G, unsigned int tag, GridBar* gb)
 {
     const int lane = threadIdx.x & 31;
     unsigned int spins = 0;
-    unsigned long long t0 = 0;
+    unsigned long long deadline = 0;
     for (;;) {
         bool ready = true;
         for (int b = lane; b < G; b += 32) {
@@ -599,17 +601,17 @@ __device__ __forceinline__ bool wait_flags(const unsigned int* flags, int G, uns
             asm volatile("fence.acq_rel.gpu;" ::: "memory");     // acquire for the relaxed polls
             return true;
         }
-        const bool go_on = wait_backoff(spins, t0, abort);
+        const bool go_on = wait_backoff(spins, deadline, gb);
         if (!__all_sync(0xffffffffu, go_on)) return false;
     }
 }
 
 // Warp 0 waits on the flags; the whole CTA learns the outcome (s_ok) after a __syncthreads.
 __device__ __forceinline__ bool cta_wait_flags(const unsigned int* flags, int G, unsigned int tag,
-                                               unsigned int* abort, int* s_ok)
+                                               GridBar* gb, int* s_ok)
 {
     if (threadIdx.x < 32) {
-        const bool ok = wait_flags(flags, G, tag, abort);
+        const bool ok = wait_flags(flags, G, tag, gb);
         if (threadIdx.x == 0 && !ok) *s_ok = 0;
     }
     __syncthreads();
@@ -721,21 +723,20 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
         Q[CS_G * NL + jl] = 0.0;
         Q[CS_T * NL + jl] = ct;
         Q[CS_ST * NL + jl] = 0.0;
-        ws.pub_v[j] = QV[jl];
-        ws.pub_p[j] = QP[jl];
-        ws.pub_s[j] = 0.0f;
+        ws.pub[j] = col_publish(QV[jl], QP[jl], 0.0f, inv_gamma, G32, Glo);
     }
     // tags: base + 1 for this prologue, base + 2 + t for evaluation t (flags start at 0, and every
     // tag of an earlier launch is at most its base + t + 3 <= this base)
     __syncthreads();
     if (tid == 0) post_flag(fpub + b, base + 1u);
-    cta_wait_flags(fpub, G, base + 1u, abort, &s_ok);
+    cta_wait_flags(fpub, G, base + 1u, &ws.st->bar, &s_ok);
 
     for (; s_ok; ++t) {
         const unsigned int tag = base + 2u + t;
         // ---------------- phase A: pass over own rows; column constants derived in place ----------------
         {
-            const ColDerived io{ws.pub_v, ws.pub_p, ws.pub_s, ws.colpart + (size_t)b * n, s_step, inv_gamma, G32, Glo};
+            const float2 kk = col_step_coeffs(s_step);
+            const ColDelta io{ws.pub, ws.colpart + (size_t)b * n, kk.x, kk.y};
             if (use_ring) {
                 float* sRow = reinterpret_cast<float*>(sm + L.off_row);
                 for (int x = tid; x < (T >> 5) * NL; x += T) sRow[x] = 0.0f;
@@ -778,7 +779,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
         }
 
         // ---------------- phase B: column merge and epilogue; publish the column state ----------------
-        if (!cta_wait_flags(fcp, G, tag, abort, &s_ok)) break;
+        if (!cta_wait_flags(fcp, G, tag, &ws.st->bar, &s_ok)) break;
         for (int j0 = c0; j0 < c1; j0 += 32) {
             const double colsum = merge_cols_f32(ws.colpart, n, G, j0, c1, reinterpret_cast<float*>(sm + L.off_merge));
             const int j = j0 + tid;
@@ -802,9 +803,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
                     Q[CS_GT * NL + jl] = g;
                 }
                 Q[CS_ST * NL + jl] = (double)sf;
-                ws.pub_v[j] = QV[jl];
-                ws.pub_p[j] = QP[jl];
-                ws.pub_s[j] = sf;
+                ws.pub[j] = col_publish(QV[jl], QP[jl], sf, inv_gamma, G32, Glo);
             }
         }
         // CTA partial sums: only the warps that hold rows (columns sit in warp 0) take part
@@ -836,7 +835,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
         if (warp < kNRed) {
             double v5[5];
             unsigned int spins = 0;
-            unsigned long long t0 = 0;
+            unsigned long long deadline = 0;
             for (;;) {
                 bool ready = true;
 #pragma unroll
@@ -851,7 +850,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
                     }
                 }
                 if (__all_sync(0xffffffffu, ready)) break;
-                const bool go_on = wait_backoff(spins, t0, abort);
+                const bool go_on = wait_backoff(spins, deadline, &ws.st->bar);
                 if (!__all_sync(0xffffffffu, go_on)) {      // the warp gives up together
                     ok = false;
                     break;
@@ -882,7 +881,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
 
         // the next pass reads every owner's column state: one warp acquires their flags while
         // warp 0 commits (the barrier at the end of the iteration covers it)
-        if (warp == kNRed && !done && !wait_flags(fpub, G, tag, abort)) s_ok = 0;
+        if (warp == kNRed && !done && !wait_flags(fpub, G, tag, &ws.st->bar)) s_ok = 0;
 
         // ---------------- phase C: commit, new direction, next trial constants (rows) ----------------
         for (int i = r0 + tid; i < r1; i += T) {
@@ -1121,6 +1120,7 @@ template <int TIER, int COST>
 __global__ void __launch_bounds__(kStageThreads, 1) dual_eval_kernel(WS ws, EvalArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ double red_g[32];
     __shared__ int s_flag[2];
     __shared__ unsigned int s_gen;
     const int n = ws.n, G = ws.G, b = blockIdx.x, T = blockDim.x, tid = threadIdx.x;
@@ -1204,7 +1204,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) dual_eval_kernel(WS ws, Eval
                 }
             }
         }
-        return;
+        goto dual_value;
     }
     // ---- two-scale path: max pass for row and column scales, then both LSEs exactly ----
     // unscaled row constants (they are also the column-view row constants)
@@ -1328,6 +1328,23 @@ __global__ void __launch_bounds__(kStageThreads, 1) dual_eval_kernel(WS ws, Eval
         const int j = j0 + tid;
         if (tid < 32 && j < c1)
             ws.lcout[j] = log(colsum) + (TIER != TIER_F64 ? (double)__ldcg(ws.A + j) * kLn2 : __ldcg(ws.Fd + j));
+    }
+dual_value:
+    // Eq. (4): g = sum_i r(P)_i - <u, r> - <v, c>.  Each CTA sums its own rows (log r(P)_i was
+    // written by the same thread above) and its own columns, then CTA 0 adds the G partials in
+    // CTA order after one more barrier.
+    if (a.g_out != nullptr) {
+        double x[1] = {0.0};
+        for (int i = r0 + tid; i < r1; i += T) x[0] += exp(ws.lrtr[i]) - a.u[i] * a.r[i];
+        for (int j = c0 + tid; j < c1; j += T) x[0] -= a.v[j] * a.c[j];
+        block_reduce_nred<1>(x, red_g);
+        if (tid == 0) reinterpret_cast<volatile double*>(ws.scratch)[G + b] = x[0];
+        if (!grid_sync(&S->bar, G, gen, s_flag)) goto timeout;
+        if (b == 0 && tid == 0) {
+            double g = 0.0;
+            for (int bb = 0; bb < G; ++bb) g += reinterpret_cast<const volatile double*>(ws.scratch)[G + bb];
+            *a.g_out = g;
+        }
     }
     return;
 timeout:

@@ -70,6 +70,41 @@ def test_dual_eval_matches_oracle(h, n, gamma, precision):
     np.testing.assert_allclose(lc2.cpu().numpy(), lc_o, rtol=0, atol=tol)
 
 
+@pytest.mark.parametrize("n", [1, 33, 1000, 4096])
+@pytest.mark.parametrize("gamma", [64.0, 65536.0])
+@pytest.mark.parametrize("precision", [M.PREC_FP32, M.PREC_FP64, M.PREC_FP32A])
+def test_dual_objective_matches_oracle(h, n, gamma, precision):
+    """Eq. (4): g(u, v) = sum_ij P_ij - <u, r> - <v, c> from the same launch as the marginals,
+    against the oracle's sum over every entry.  The fp64 sums of <u, r> and <v, c> are exact to
+    n ulps of sum |u_i r_i| + sum |v_j c_j| at most; sum_i r(P)_i carries the per-tier relative error
+    of the marginals (the log-marginal tolerances above), on both the one-pass and two-pass paths."""
+    rng = np.random.default_rng(n * 3 + int(math.log2(gamma)))
+    C = rng.uniform(0, 1, (n, n)).astype(np.float32)
+    u, v, r, c = rand_potentials(n, gamma, n + 2, C)
+    g_o = O.dual_value(C.astype(np.float64), u, v, gamma, r, c)
+    scale = np.abs(u * r).sum() + np.abs(v * c).sum()
+    rel = {M.PREC_FP32: TOL_F32, M.PREC_FP32A: TOL_F32A, M.PREC_FP64: TOL_F64}[precision]
+    lr_o, _ = O.dual_eval(C.astype(np.float64), u, v, gamma)
+    mass = np.exp(lr_o).sum()
+    tol = rel * mass + 1e-12 * scale
+    lr, lc, g = h.dual_eval(t(u), t(v), gamma, t(C), precision=precision, r=t(r), c=t(c))
+    assert abs(g - g_o) <= tol, (g, g_o, tol)
+    lr2, lc2, g2 = h.dual_eval(t(u), t(v), gamma, t(C), ref_log_rP=lr, precision=precision, r=t(r), c=t(c))
+    assert abs(g2 - g_o) <= tol, (g2, g_o, tol)
+    # the marginals of the same call are the ones of the call without g
+    lr3, lc3 = h.dual_eval(t(u), t(v), gamma, t(C), ref_log_rP=lr, precision=precision)
+    assert torch.equal(lr2, lr3) and torch.equal(lc2, lc3)
+
+
+def test_dual_objective_needs_both_marginals(h):
+    n = 8
+    z = torch.zeros(n, dtype=torch.float64, device=DEV)
+    C = torch.zeros((n, n), dtype=torch.float32, device=DEV)
+    with pytest.raises(M.MdotError) as e:
+        h.dual_eval(z, z, 1.0, C, r=z)
+    assert e.value.status == M.MDOT_ERR_INVALID_ARG
+
+
 def test_dual_eval_time_reports_the_kernel():
     """mdot_dual_eval_time: NOT_READY before any evaluation on the handle, then the device time of
     the last evaluation kernel (positive, below the host time of the whole call)."""

@@ -172,6 +172,37 @@ def test_line_search_trials_per_iteration_in_paper_range():
         assert abs(r1.cost - r0.cost) <= H / gf ** 1.5, (r1.cost, r0.cost)
 
 
+def test_line_search_hybrid_step_on_a_linear_derivative():
+    """App. B on phi'(alpha) = alpha - 2.6 (a quadratic phi), with a narrow acceptance window
+    (c1 = 0.49, c2 = 0.01: accept iff -0.026 <= phi'(alpha) <= 0.052).  Worked by hand: trials 1 and
+    2 raise the lower end and double; 4 overshoots; inside the bracket every secant root is the
+    exact root 2.6, so each next trial is alpha_hyb = 2.6 / 2 + (lo + hi) / 4 (Eq. (25)):
+      lo = 2,   hi = 4   -> 2.8   (phi' = 0.2:   new upper end)
+      lo = 2,   hi = 2.8 -> 2.5   (phi' = -0.1:  new lower end)
+      lo = 2.5, hi = 2.8 -> 2.625 (phi' = 0.025: accepted).
+    A pure secant step would stop at 2.6 after four trials, a pure bisection would try 3.0 fourth;
+    a sign slip in the secant root sends the fourth trial to 1.6."""
+    rc, alpha, trials, lows = O.ls_search(lambda a: a - 2.6, -2.6, 1.0, ls_c1=0.49, ls_c2=0.01)
+    assert rc == 0
+    assert trials == pytest.approx([1.0, 2.0, 4.0, 2.8, 2.5, 2.625], rel=1e-12, abs=1e-12)
+    assert lows == pytest.approx([1.0, 2.0, 2.5], rel=1e-12)
+    assert alpha == pytest.approx(2.625, rel=1e-12)
+
+
+def test_line_search_cap_bisection_and_no_descent():
+    """The readings around Eq. (24): after ls_max_trials the lower end is taken (rc 1); a
+    non-finite phi' counts as an upper end and the next trial bisects; a non-negative phi'(0) is
+    no descent direction (rc 2, no evaluation)."""
+    rc, alpha, trials, lows = O.ls_search(lambda a: a - 2.6, -2.6, 1.0, ls_c1=0.49, ls_c2=0.01, ls_max_trials=3)
+    assert rc == 1 and alpha == 2.0 and trials == [1.0, 2.0, 4.0] and lows == [1.0, 2.0]
+    # phi' overflows beyond alpha = 5: the first trial 8 is an upper end, then (0 + 8) / 2 = 4 is
+    # accepted (c1 = 0.1, c2 = 0.5, phi'(0) = -2.6: accept iff -1.3 <= phi' <= 2.08; phi'(4) = -0.5)
+    rc, alpha, trials, _ = O.ls_search(lambda a: (a - 4.5) if a <= 5.0 else float("inf"), -2.6, 8.0)
+    assert rc == 0 and trials == [8.0, 4.0] and alpha == 4.0
+    rc, alpha, trials, _ = O.ls_search(lambda a: a, 0.0, 1.0)
+    assert rc == 2 and trials == []
+
+
 def test_diag_hessian_variant_converges_to_same_plan():
     n, gamma = 10, 30.0
     C, r, c = _rand_problem(n, 12)
