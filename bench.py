@@ -47,7 +47,10 @@ def parse():
     ap.add_argument("--grid", type=int, default=64, help="k of the k x k grid for --case runs")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
-    ap.add_argument("--serve-count", type=int, default=60, help="requests of the replayed serving trace (0: skip)")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the n=4096 gap sweep (both costs, 1e-4..1e-7)")
+    ap.add_argument("--serve-count", type=int, default=200,
+                    help="requests of the serving trace replayed at the configured rate (half as many at 0.5x and "
+                         "0.9x of the measured capacity and one problem per launch; 0: skip)")
     ap.add_argument("--serve-big-n", type=int, default=None, help="server routing: n above which a big lane solves")
     ap.add_argument("--serve-lanes", type=int, default=None, help="server routing: big lanes")
     ap.add_argument("--serve-lane-ctas", type=int, default=None, help="server routing: CTAs per big lane")
@@ -78,6 +81,17 @@ def golden_case(kind="l2sq"):
     return None
 
 
+def golden_record(kind, eps):
+    path = os.path.join(ROOT, "tests", "golden", f"grid{N_GRID * N_GRID}.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        for c in json.load(fh)["cases"]:
+            if c["kind"] == kind and c["seed"] == SEED and abs(c["eps_target"] - eps) <= 1e-15 * eps:
+                return c
+    return None
+
+
 def exact_value(kind="l2sq"):
     """Exact OT value of the benchmark instance (column generation, tests/golden/make_golden.py)."""
     path = os.path.join(ROOT, "tests", "golden", f"exact{N_GRID * N_GRID}.json")
@@ -88,6 +102,38 @@ def exact_value(kind="l2sq"):
             if c["kind"] == kind and c["seed"] == SEED and c.get("exact_ot") is not None:
                 return c["exact_ot"]
     return None
+
+
+def gap_sweep(h, dev, stream):
+    """The n = 4096 instance (64 x 64 grid, seed 2000) with both costs (squared Euclidean, L1) at
+    target gaps 1e-4 ... 1e-7: one untimed and one timed solve each (CUDA events on the handle's
+    stream), the true gap against the exact optimum, the certificate, and the difference to the
+    FP64 oracle's rounded cost on the same instance (tests/golden/)."""
+    import torch
+    import paper_2307_08507_gb300 as M
+    from paper_2307_08507_gb300 import inputs as I
+    rows = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for kind in ("l2sq", "l1"):
+        p = I.grid_problem(N_GRID, SEED, kind=kind)
+        r, c, C = (torch.from_numpy(a).to(dev) for a in (p.r, p.c, p.C))
+        exact = exact_value(kind)
+        for eps in (1e-4, 1e-5, 1e-6, 1e-7):
+            h.solve(r, c, C, eps)
+            ev0.record(stream)
+            _, _, res = h.solve(r, c, C, eps, check=False)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            g = golden_record(kind, eps)
+            rows.append({"cost_kind": kind, "eps_target": eps, "status": M.status_string(res.status),
+                         "seconds": ev0.elapsed_time(ev1) / 1e3, "gamma_f": res.info.gamma_f,
+                         "evals": res.info.evals, "evals_fp64": res.info.evals_fp64, "cost": res.cost,
+                         "true_gap": (res.cost - exact) if exact is not None else None,
+                         "gap_cert": res.gap_cert,
+                         "meets_target": (res.cost - exact <= eps) if exact is not None else None,
+                         "cost_minus_oracle": (res.cost - g["oracle_cost"]) if g else None})
+        del C
+    return rows
 
 
 def max_over_ranks(x: float, dist, device) -> float:
@@ -214,6 +260,24 @@ def oracle_sample(n_evals: int):
     return (time.perf_counter() - t0) / n_evals
 
 
+def oracle_sample_all_cores(n_evals: int):
+    """The same timing on the OpenMP build of the oracle (rows and column strips of each dual
+    evaluation on every host core, identical arithmetic); returns (seconds per eval, threads)."""
+    import numpy as np
+    import oracle as O
+    from paper_2307_08507_gb300 import inputs as I
+    run, threads = O.omp_dual_eval_timer()
+    p = I.grid_problem(N_GRID, SEED)
+    C = p.C.astype(np.float64)
+    gamma = 2.0 ** 12
+    u, v = np.log(p.r), np.log(p.c)
+    run(C, u, v, gamma)                                          # warm (threads, pages)
+    t0 = time.perf_counter()
+    for _ in range(n_evals):
+        run(C, u, v, gamma)
+    return (time.perf_counter() - t0) / n_evals, threads
+
+
 def cpu_solve_estimate(n_evals: int):
     g = golden_case()
     per_eval = oracle_sample(n_evals)
@@ -222,26 +286,37 @@ def cpu_solve_estimate(n_evals: int):
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the CPU FP64 oracle (the paper publishes no code), its dual evaluation on
+    every host core (OpenMP build, same arithmetic).  One step = n_evals dual evaluations of the
+    n = 4096 benchmark problem; ms_per_step is that step's measured wall time.  The metric (seconds
+    to gap 1e-6, one full solve) is extrapolated: seconds per evaluation x the evaluation count of
+    the full oracle solve of the same instance (tests/golden/grid4096.json)."""
     if rank != 0:
         return
     n_evals = args.cpu_sample_evals or 4
+    g = golden_case()
+    evals = g["oracle_evals"] if g else 3000
     for _ in range(args.warmup):
-        oracle_sample(1)
-    vals = []
+        oracle_sample_all_cores(1)
+    per = []
+    threads = 1
     for _ in range(args.steps):
-        est, per_eval, evals = cpu_solve_estimate(n_evals)
-        vals.append(est)
-    value = sum(vals) / len(vals)
+        pe, threads = oracle_sample_all_cores(n_evals)
+        per.append(pe)
+    per_eval = sum(per) / len(per)
+    value = per_eval * evals
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_eval * n_evals * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded grid histograms, Sec. 5.1 shapes)",
         "config": {"workload": "grid64x64_l2sq_n4096_eps1e-6", "n": N_GRID * N_GRID, "seed": SEED,
                    "eps_target": EPS, "l2": "oracle on CPU"},
-        "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
-                         "sample": f"{n_evals} FP64 dual evaluations at n=4096 per step, scaled by the "
-                                   f"{evals} evaluations of the full oracle solve"},
+        "cpu_baseline": {"value": value, "unit": "s", "cores": threads, "kind": "oracle",
+                         "sample": f"per-evaluation x evaluations extrapolation: {n_evals} FP64 dual "
+                                   f"evaluations at n=4096 per step on {threads} threads "
+                                   f"({per_eval:.4f} s each), x the {evals} evaluations of the full "
+                                   f"oracle solve"},
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -251,7 +326,7 @@ def run_reference(args, rank, world):
 # batched form: 512 point-cloud problems, n uniform in [256, 4096], one persistent launch
 # ---------------------------------------------------------------------------------------------
 BATCH_COUNT = 512
-BATCH_EPS = 1e-5
+BATCH_EPS = 1e-6
 BATCH_SEED = 4000
 
 
@@ -279,7 +354,7 @@ def batch_problems(dev, count=BATCH_COUNT, seed=BATCH_SEED):
     return out
 
 
-def measure_batch(h, dev, stream, sample_single=32):
+def measure_batch(h, dev, stream, sample_single=128):
     import torch
     import paper_2307_08507_gb300 as M
     probs = batch_problems(dev)
@@ -309,9 +384,18 @@ def measure_batch(h, dev, stream, sample_single=32):
         evals_b += res[k].evals
         evals_s += rs.info.evals
     t_single_all = t_single * len(probs) / len(pick)
+    # entries of all evaluations of the batch per second, against the fp32 issue bound (the pass
+    # regenerates the cost: ALU_OPS_PER_ENTRY fp32 operations per entry)
+    entries = float(sum(r.evals * probs[k]["n"] ** 2 for k, r in enumerate(res)))
+    alu = alu_peak_ops()
     return {"problems": len(probs), "n_range": [min(q["n"] for q in probs), max(q["n"] for q in probs)],
             "eps_target": BATCH_EPS, "cost": "regenerated squared Euclidean (point clouds)",
             "seconds": t_batch, "problems_per_s": len(probs) / t_batch, "ok": ok,
+            "statuses": {M.status_string(st): sum(1 for r in res if r.status == st) for st in {r.status for r in res}},
+            "roofline": {"kernel": "batch_kernel<squared Euclidean> (one CTA per problem)", "bound": "alu",
+                         "entries_per_s": entries / t_batch, "ops_per_entry": ALU_OPS_PER_ENTRY,
+                         "achieved": entries * ALU_OPS_PER_ENTRY / t_batch / 1e12, "peak": alu / 1e12,
+                         "unit": "Tops/s", "frac": entries * ALU_OPS_PER_ENTRY / t_batch / alu},
             "one_per_launch_sample": len(pick), "one_per_launch_seconds_sample": t_single,
             "one_per_launch_problems_per_s": len(probs) / t_single_all,
             "speedup_vs_one_per_launch": t_single_all / t_batch,
@@ -326,10 +410,20 @@ SERVE_SEED = 5000
 SERVE_WORKSPACE = 2 << 30          # HBM budget of the server's workspace pool (bytes)
 
 
+def serving_oracle_costs():
+    """Stored FP64 oracle costs of a sample of the serving trace's requests (tests/golden/
+    serve_oracle.json, written by tests/golden/make_golden.py --serve): {trace index: cost}."""
+    path = os.path.join(ROOT, "tests", "golden", "serve_oracle.json")
+    if not os.path.exists(path):
+        return {}
+    with open(path) as fh:
+        return {c["index"]: c["oracle_cost"] for c in json.load(fh)["cases"] if c["seed"] == SERVE_SEED}
+
+
 def serving_requests(dev, count, seed=SERVE_SEED):
     """Requests of the serving trace: k x k grid histograms (Sec. 5.1 shapes), squared-Euclidean
     cost regenerated from the cell coordinates, target gap from the trace; inputs resident on the
-    device before the replay starts."""
+    device before the replay starts.  Each entry: (arrival s, n, eps, mdot_problem, tensors)."""
     import torch
     import paper_2307_08507_gb300 as M
     from paper_2307_08507_gb300 import inputs as I
@@ -343,18 +437,23 @@ def serving_requests(dev, count, seed=SERVE_SEED):
         r = torch.from_numpy(I.grid_histogram(k, 2 * sd)).to(dev)
         c = torch.from_numpy(I.grid_histogram(k, 2 * sd + 1)).to(dev)
         prob = M.make_problem(r, c, x=xy, y=xy, kind=M.COST_SQEUCLID, scale=scale, eps_target=eps)
-        reqs.append((ta, k * k, eps, prob, (r, c)))
+        reqs.append((ta, k * k, eps, prob, (r, c, xy, scale)))
     return reqs
 
 
-def measure_serving(dev, count, big_n=None, big_lanes=None, lane_ctas=None):
+def measure_serving(dev, reqs, big_n=None, big_lanes=None, lane_ctas=None, rate=None):
+    """Replay the requests (serving_requests) in real time through mdot_server_* (at the trace's
+    200/s, or at mean rate `rate` with the same arrival pattern rescaled); latency = completion seen
+    by the client - scheduled arrival.  Returns the summary and the costs in request order."""
     import numpy as np
     import torch
     import paper_2307_08507_gb300 as M
-    reqs = serving_requests(dev, count)
+    if rate is not None:
+        reqs = [(q[0] * 200.0 / rate,) + tuple(q[1:]) for q in reqs]
     torch.cuda.synchronize()
     srv = M.Server(SERVE_WORKSPACE, big_n=big_n, big_lanes=big_lanes, lane_ctas=lane_ctas)
     lat, done_at, evals, status_ok, statuses, big_lat = [], [], 0, 0, {}, []
+    costs = [None] * len(reqs)
     try:
         # warm-up request (kernel load, first launch)
         srv.wait(srv.submit(reqs[0][3], keep=reqs[0][4]), timeout=600)
@@ -364,18 +463,19 @@ def measure_serving(dev, count, big_n=None, big_lanes=None, lane_ctas=None):
         while i < len(reqs) or pending:
             now = time.perf_counter() - t0
             while i < len(reqs) and reqs[i][0] <= now:
-                pending[srv.submit(reqs[i][3], keep=reqs[i][4])] = (reqs[i][0], reqs[i][1])
+                pending[srv.submit(reqs[i][3], keep=reqs[i][4])] = (reqs[i][0], reqs[i][1], i)
                 i += 1
             for tk in list(pending):
                 r = srv.poll(tk)
                 if r is not None:
                     tn = time.perf_counter() - t0
-                    ta, nq = pending.pop(tk)
+                    ta, nq, idx = pending.pop(tk)
                     lat.append(tn - ta)
                     if nq > 2048:
                         big_lat.append(tn - ta)
                     done_at.append(tn)
                     evals += r.evals
+                    costs[idx] = r.cost
                     status_ok += int(r.status == M.MDOT_OK)
                     key = M.status_string(r.status)
                     statuses[key] = statuses.get(key, 0) + 1
@@ -385,16 +485,63 @@ def measure_serving(dev, count, big_n=None, big_lanes=None, lane_ctas=None):
         srv.close()
     lat = np.array(lat)
     n = np.array([q[1] for q in reqs])
-    return {"requests": len(reqs), "offered_rate_per_s": len(reqs) / reqs[-1][0],
-            "n_range": [int(n.min()), int(n.max())], "n_median": float(np.median(n)),
-            "gaps": [1e-4, 1e-5, 1e-6, 1e-7], "workspace_bytes": SERVE_WORKSPACE,
-            "cost": "regenerated squared Euclidean (grid histograms)",
-            "problems_per_s": len(lat) / span, "latency_p50_s": float(np.percentile(lat, 50)),
-            "latency_p99_s": float(np.percentile(lat, 99)), "latency_max_s": float(lat.max()),
-            "latency_p50_n_gt_2048_s": float(np.percentile(big_lat, 50)) if big_lat else None,
-            "routing": {"big_n": big_n if big_n is not None else 2048, "big_lanes": big_lanes if big_lanes is not None else 2,
-                        "lane_ctas": lane_ctas or "SMs/4"},
-            "ok": status_ok, "statuses": statuses, "evals_total": int(evals), "seconds": span}
+    summary = {"requests": len(reqs), "offered_rate_per_s": len(reqs) / reqs[-1][0],
+               "n_range": [int(n.min()), int(n.max())], "n_median": float(np.median(n)),
+               "gaps": [1e-4, 1e-5, 1e-6, 1e-7], "workspace_bytes": SERVE_WORKSPACE,
+               "cost": "regenerated squared Euclidean (grid histograms)",
+               "problems_per_s": len(lat) / span, "latency_p50_s": float(np.percentile(lat, 50)),
+               "latency_p99_s": float(np.percentile(lat, 99)), "latency_max_s": float(lat.max()),
+               "latency_p50_n_gt_2048_s": float(np.percentile(big_lat, 50)) if big_lat else None,
+               "routing": {"big_n": big_n if big_n is not None else 2048,
+                           "big_lanes": big_lanes if big_lanes is not None else 2, "lane_ctas": lane_ctas or "SMs/4"},
+               "ok": status_ok, "statuses": statuses, "evals_total": int(evals), "seconds": span}
+    return summary, costs
+
+
+def serving_oracle_costs():
+    """Stored FP64 oracle costs of a sample of the serving trace's requests (tests/golden/
+    serve_oracle.json, written by tests/golden/make_golden.py --serve): {trace index: cost}."""
+    path = os.path.join(ROOT, "tests", "golden", "serve_oracle.json")
+    if not os.path.exists(path):
+        return {}
+    with open(path) as fh:
+        return {c["index"]: c["oracle_cost"] for c in json.load(fh)["cases"] if c["seed"] == SERVE_SEED}
+
+
+def measure_serving_loads(dev, h, count_sat=200, count_sub=100):
+    """Serving at three offered loads on the same trace: the configured Poisson rate (200/s, above
+    capacity: the throughput, and queueing latency) and 0.5x / 0.9x of the capacity that run
+    measured (latency below saturation); then the first count_sub requests solved one problem per
+    launch (mdot_solve_points, in arrival order, default parameters) as the comparison, and the
+    served costs against the stored FP64 oracle costs of a sample of the requests."""
+    import torch
+    import paper_2307_08507_gb300 as M
+    trace = serving_requests(dev, count_sat)
+    sat, costs = measure_serving(dev, trace)
+    cap = sat["problems_per_s"]
+    loads = {"configured_200_per_s": sat}
+    reqs = trace[:count_sub]                     # the same requests, offered below capacity
+    for f in (0.5, 0.9):
+        loads[f"{f}x_capacity"], _ = measure_serving(dev, reqs, rate=f * cap)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    t_single, dcost = 0.0, []
+    for q, (ta, nq, eps, prob, (r, c, xy, scale)) in enumerate(reqs):
+        ev0.record(stream)
+        _, _, rs = h.solve_points(r, c, xy, xy, M.COST_SQEUCLID, scale, eps, check=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t_single += ev0.elapsed_time(ev1) / 1e3
+        if costs[q] is not None:
+            dcost.append(abs(rs.cost - costs[q]))
+    orc = serving_oracle_costs()
+    d_or = [abs(costs[i] - v) for i, v in orc.items() if i < len(costs) and costs[i] is not None]
+    single_rate = count_sub / t_single
+    return {"loads": loads, "capacity_problems_per_s": cap,
+            "one_per_launch": {"requests": count_sub, "seconds": t_single, "problems_per_s": single_rate,
+                               "served_vs_one_per_launch_max_abs_cost_diff": max(dcost) if dcost else None},
+            "served_speedup_vs_one_per_launch": cap / single_rate,
+            "vs_oracle": {"sampled_requests": len(d_or), "max_abs_cost_diff": max(d_or) if d_or else None}}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -468,6 +615,29 @@ def run_ours(args, rank, world):
     t_launch = ip.t_stage_fp32_ms / 1e3 / launches32
     hbm, peak_kind = peaks()
     achieved = bytes_per_launch / t_launch / 1e9 if t_launch > 0 else None
+    trace = h.solve_trace()
+    # per-evaluation device time of the stage launches (the accurate-tier launches dominate), to set
+    # beside a profiler's per-launch durations
+    acc_rows = [t for t in trace if t["kind"] == 0 and t["evals"] >= 100]
+    us_per_eval_long = (1e3 * sum(t["ms"] for t in acc_rows) / max(1, sum(t["evals"] for t in acc_rows))
+                        if acc_rows else None)
+
+    # read rates of this GPU measured by the library's own streaming-read kernel: a 64 MiB buffer
+    # (the size of C at n = 4096, held in L2 after the first pass) and a 4 GiB buffer (HBM)
+    rates = {}
+    for mib, reps in ((64, 50), (4096, 3)):
+        buf = torch.ones(mib * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        M.read_probe(buf, 1)
+        best = 1e30
+        for _ in range(5):
+            ev0.record(stream)
+            M.read_probe(buf, reps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, ev0.elapsed_time(ev1) / 1e3)
+        rates[f"read_{mib}MiB_GBps"] = buf.numel() * 4.0 * reps / best / 1e9
+        del buf
+    l2_gbs = rates["read_64MiB_GBps"]
 
     # single dual evaluation (K1 + K2, one pass, fp32 entries), n = 4096 and n = 16384
     dual = {}
@@ -514,8 +684,10 @@ def run_ours(args, rank, world):
                             "frac_alu": ents * ALU_OPS_PER_ENTRY / alu_peak,
                             "ops_per_entry": ALU_OPS_PER_ENTRY}
 
+    sweep = gap_sweep(h, dev, stream) if (rank == 0 and not args.no_sweep) else None
     batch = measure_batch(h, dev, stream) if (rank == 0 and not args.no_batch) else None
-    serving = measure_serving(dev, args.serve_count) if (rank == 0 and args.serve_count > 0) else None
+    serving = (measure_serving_loads(dev, h, args.serve_count, max(1, args.serve_count // 2))
+               if (rank == 0 and args.serve_count > 0) else None)
 
     # end to end through the public C ABI with host buffers (copies inside the timed region)
     Ch = torch.from_numpy(p.C).pin_memory().numpy()
@@ -539,11 +711,15 @@ def run_ours(args, rank, world):
     cpu = None
     if rank == 0 and world == 1:
         n_evals = args.cpu_sample_evals or 40
-        est, per_eval, evals = cpu_solve_estimate(n_evals)
-        cpu = {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
-               "sample": f"{n_evals} FP64 dual evaluations of the same n=4096 problem "
-                         f"({per_eval:.3f} s each), scaled by the {evals} evaluations of the full "
-                         f"oracle solve"}
+        est1, per1, evals = cpu_solve_estimate(max(4, n_evals // 4))
+        per_all, threads = oracle_sample_all_cores(n_evals)
+        cpu = {"value": per_all * evals, "unit": "s", "cores": threads, "kind": "oracle",
+               "sample": f"per-evaluation x evaluations extrapolation: {n_evals} FP64 dual evaluations "
+                         f"of the same n=4096 problem on {threads} threads ({per_all:.4f} s each), x "
+                         f"the {evals} evaluations of the full oracle solve",
+               "single_core": {"value": est1, "unit": "s", "cores": 1,
+                               "sample": f"{max(4, n_evals // 4)} evaluations on one core "
+                                         f"({per1:.3f} s each) x {evals}"}}
     if rank == 0:
         line = {
             "metric": METRIC, "value": t_step, "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -562,11 +738,17 @@ def run_ours(args, rank, world):
             "roofline": {"kernel": "stage_kernel<fp32 entries> (one MDOT stage: PNCG + line search)",
                          "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": (achieved / hbm) if achieved else None,
-                         "traffic": ncu_traffic("stage_kernel_flag<2, 0>") or ncu_traffic("stage_kernel_flag<0, 0>"),
+                         "traffic": ncu_traffic("stage_kernel_flag<2, 0>"),
                          "peak_kind": peak_kind,
                          "bytes_per_launch": bytes_per_launch, "us_per_launch": t_launch * 1e6,
+                         "us_per_eval": 1e6 * t_launch * launches32 / max(1, evals32),
+                         "us_per_eval_launches_ge_100_evals": us_per_eval_long,
+                         "l2_read_GBps": l2_gbs, "frac_l2": (achieved / l2_gbs) if achieved else None,
+                         "read_rates": rates,
                          "launch_times_ms": {"stage_fp32": ip.t_stage_fp32_ms, "stage_fp64": ip.t_stage_fp64_ms,
-                                             "round": ip.t_round_ms, "bound": ip.t_bound_ms}},
+                                             "round": ip.t_round_ms, "bound": ip.t_bound_ms},
+                         "launches": [(t["kind"], round(t["ms"], 4), t["evals"]) for t in trace]},
+            "gap_sweep": sweep,
             "dual_eval": dual,
             "batched": batch,
             "serving": serving,
@@ -692,8 +874,8 @@ def run_case(args):
         h.close()
         return
     if args.case == "serve":
-        print(json.dumps(measure_serving(dev, args.serve_count, args.serve_big_n, args.serve_lanes,
-                                         args.serve_lane_ctas)))
+        print(json.dumps(measure_serving(dev, serving_requests(dev, args.serve_count), args.serve_big_n,
+                                         args.serve_lanes, args.serve_lane_ctas)[0]))
         h.close()
         return
     if args.case == "dual_eval":

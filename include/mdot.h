@@ -86,7 +86,10 @@ typedef struct mdot_params {
                             /*    previous iterate; the per-row scales are predicted from r~, which  */
                             /*    this start can miss by more than the exponent range: may fail)     */
     double  final_tol;      /* > 0: ||grad g||_1 target of the final stage instead of eps_d / 2     */
-    double  fp32_floor;     /* ||grad g||_1 below which fp32 entries are not trusted; 5e-8          */
+    double  fp32_floor;     /* ||grad g||_1 below which fp32 entries are not trusted; 2e-7 (the
+                               spread that fp32 entries and fp32 sums leave in the marginals of a
+                               converged plan, ~1.6e-7 measured): tighter stage tolerances run to it
+                               in fp32 and (AUTO) finish in fp64 entries                         */
     int32_t profile;        /* non-zero: time each kernel launch with CUDA events (mdot_info t_*)    */
     int32_t smoothing;      /* 0: smoothing weight eps_d of the stage (Alg. 1); 1: fixed weight       */
                             /*    H_min / gamma_f^p in every stage (the fixed-smoothing ablation)     */
@@ -130,7 +133,8 @@ typedef struct mdot_info {
     int32_t stage_launches_fp32; /* stage launches with fp32 entries                               */
     int32_t stalls;         /* stages ended because ||grad g||_1 stopped improving (no 1 % gain in
                                40 accepted iterations: tolerance below the arithmetic's floor)   */
-    int32_t reserved_i;
+    int32_t tensor_cores;   /* 1: the regenerated squared-Euclidean cost of integer points ran on the
+                               tensor cores (see mdot_cost_matrix); 0 otherwise                   */
 } mdot_info;
 
 typedef struct mdot_handle mdot_handle;
@@ -247,6 +251,18 @@ typedef struct mdot_trace_row {
  * figures to evaluation counts.
  */
 mdot_status mdot_solve_trace(const mdot_handle* h, int32_t max_rows, mdot_trace_row* rows, int32_t* count);
+
+/*
+ * The regenerated cost matrix written out: C_out (device, n x n float32, row-major) receives
+ * C_ij for the coordinates x, y (device, n x 3 float32 each) with the arithmetic the solver's passes
+ * use -- for MDOT_COST_SQEUCLID with every coordinate an integer of magnitude <= 255 (grid data),
+ * the contraction |x_i|^2 + |y_j|^2 - 2 <x_i, y_j> on the tensor cores (bf16 inputs, fp32
+ * accumulation, exact for such points) times scale; otherwise the fp32 operations in the order of
+ * mdot_cost_kind.  Both forms give the same bits for grid data.  stream: a cudaStream_t or NULL;
+ * the call synchronises it.  INVALID_ARG for bad sizes, kinds or scale; CUDA on a failed launch.
+ */
+mdot_status mdot_cost_matrix(const float* x, const float* y, int32_t cost_kind, float scale, int64_t n,
+                             float* C_out, void* stream);
 
 /*
  * Device time, in milliseconds, of the evaluation kernel launched by the last successful

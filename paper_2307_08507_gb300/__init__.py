@@ -43,7 +43,7 @@ class Info(ct.Structure):
                 ("cost", ct.c_double), ("lower_bound", ct.c_double), ("gap_cert", ct.c_double),
                 ("t_stage_fp32_ms", ct.c_double), ("t_stage_fp64_ms", ct.c_double),
                 ("t_round_ms", ct.c_double), ("t_bound_ms", ct.c_double), ("launches", ct.c_int32),
-                ("stage_launches_fp32", ct.c_int32), ("stalls", ct.c_int32), ("reserved_i", ct.c_int32)]
+                ("stage_launches_fp32", ct.c_int32), ("stalls", ct.c_int32), ("tensor_cores", ct.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
@@ -319,6 +319,26 @@ class Handle:
         if check and s not in (MDOT_OK, MDOT_ERR_NOT_CONVERGED):
             raise MdotError(s, "mdot_solve_host")
         return u, v, SolveResult(s, cost.value, gap.value, info)
+
+
+def cost_matrix(x, y, kind: int, scale: float, stream=None):
+    """mdot_cost_matrix: the regenerated n x n cost of coordinates x, y (CUDA float32 tensors n x 3),
+    computed as the solver's passes compute it; returns a new CUDA float32 tensor."""
+    import torch
+    L = lib()
+    if not hasattr(L, "_cost_typed"):
+        L.mdot_cost_matrix.argtypes = [_P, _P, ct.c_int32, ct.c_float, ct.c_int64, _P, _P]
+        L.mdot_cost_matrix.restype = ct.c_int32
+        L._cost_typed = True
+    n = x.shape[0]
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    C = torch.empty((n, n), dtype=torch.float32, device=x.device)
+    s = L.mdot_cost_matrix(_ptr(x, torch.float32, 3 * n, "x"), _ptr(y, torch.float32, 3 * n, "y"), int(kind),
+                           float(scale), n, _ptr(C, torch.float32), ct.c_void_p(stream.cuda_stream))
+    if s != MDOT_OK:
+        raise MdotError(s, "mdot_cost_matrix")
+    return C
 
 
 def read_probe(buf, reps: int, stream=None):

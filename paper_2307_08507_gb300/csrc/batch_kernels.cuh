@@ -63,14 +63,15 @@ static_assert(SV_COUNT <= 19 && SF_COUNT <= 7, "batch_slot_doubles covers the sl
 constexpr size_t kSlotDoubles = (size_t)SV_COUNT * kBatchMaxN + ((size_t)SF_COUNT * kBatchMaxN + 1) / 2;
 
 struct BatchSmem {
-    size_t off_row, bytes;
+    size_t off_row, off_stage, bytes;
 };
 
 __host__ __device__ inline BatchSmem batch_smem()
 {
     BatchSmem L;
     L.off_row = 0;
-    L.bytes = (size_t)(kBatchThreads / 32) * kRowChunk * 4;     // per-warp row partials of one chunk
+    L.off_stage = (size_t)(kBatchThreads / 32) * kRowChunk * 4;     // per-warp row partials of one chunk
+    L.bytes = L.off_stage + (size_t)tc_stage_floats(kBatchThreads / 32) * 4;   // tensor-core column blocks
     return L;
 }
 
@@ -92,14 +93,25 @@ struct ColAccum {
         for (int e = 0; e < 4; ++e)
             if (j0 + e < n) out[j0 + e] = first ? ca[e] : out[j0 + e] + ca[e];
     }
+    __device__ __forceinline__ void load1(int j, int n, float& hh, float& wc) const
+    {
+        ColPlain{Hh, Wc, out}.load1(j, n, hh, wc);
+    }
+    __device__ __forceinline__ void store2(int j0, int n, float2 ca) const
+    {
+        if (j0 < n) out[j0] = first ? ca.x : out[j0] + ca.x;
+        if (j0 + 1 < n) out[j0 + 1] = first ? ca.y : out[j0 + 1] + ca.y;
+    }
 };
 
 // One pass over all n rows (the CTA owns the whole problem), in chunks of kRowChunk rows: the
 // fp64 row sums (relative to 2^{A_i}) go to rowsum, the complete column sums to colsum.
+// tc: the squared-Euclidean cost of integer points on the tensor cores (pass_f32_regen_tc).
 template <bool ACC, int COST>
 __device__ __forceinline__ void batch_pass(const BatchProblem& P, const float* Hh, const float* Wc,
                                            const float* Fh, const float* Wr, const float* S,
-                                           float G32, float Glo, float* sRow, float* colsum, double* rowsum)
+                                           float G32, float Glo, float* sRow, float* colsum, double* rowsum,
+                                           bool tc, float* stage)
 {
     const int n = P.n, nw = blockDim.x >> 5;
     for (int r0 = 0; r0 < n; r0 += kRowChunk) {
@@ -107,7 +119,10 @@ __device__ __forceinline__ void batch_pass(const BatchProblem& P, const float* H
         for (int x = threadIdx.x; x < nw * nc; x += blockDim.x) sRow[x] = 0.0f;
         __syncthreads();
         const ColAccum io{Hh, Wc, colsum, r0 == 0};
-        if (COST != COST_DENSE)
+        if (COST == COST_SQEUCLID && tc)
+            pass_f32_regen_tc<ACC>(P.Y, P.scale, n, r0, r1, io, Fh + r0, Wr + r0, S + r0, P.X + 3 * (size_t)r0,
+                                   G32, Glo, sRow, nc, stage, nullptr);
+        else if (COST != COST_DENSE)
             pass_f32_regen<ACC, COST>(P.Y, P.scale, n, r0, r1, io, Fh + r0, Wr + r0, S + r0, P.X + 3 * (size_t)r0,
                                       G32, Glo, sRow, nc);
         else if ((n & 3) == 0 && (reinterpret_cast<uintptr_t>(P.C) & 15) == 0)
@@ -155,6 +170,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a)
     __shared__ int s_prob;
     const BatchSmem L = batch_smem();
     float* sRow = reinterpret_cast<float*>(sm + L.off_row);
+    float* sStage = reinterpret_cast<float*>(sm + L.off_stage);
     const int tid = threadIdx.x, T = blockDim.x, nw = T >> 5, lane = tid & 31, warp = tid >> 5;
     double* const cta_slot = a.slots + (size_t)blockIdx.x * a.slot_doubles;
 
@@ -212,6 +228,16 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a)
         }
         __syncthreads();
         const double H = s_bc[0], gf = s_bc[1];
+        // squared-Euclidean cost of integer points (|coordinate| <= 255): the tensor-core form
+        bool tc = false;
+        if (COST == COST_SQEUCLID && s_bc[2] == 0.0) {
+            bool ok = true;
+            for (int q = tid; q < 3 * n; q += T) {
+                const float xv = __ldg(P.X + q), yv = __ldg(P.Y + q);
+                ok = ok && fabsf(xv) <= 255.0f && xv == rintf(xv) && fabsf(yv) <= 255.0f && yv == rintf(yv);
+            }
+            tc = __syncthreads_and(ok ? 1 : 0) != 0;
+        }
         if (s_bc[2] != 0.0) {
             if (tid == 0) {
                 res.status = ST_NUMERIC + 10;          // invalid problem
@@ -279,8 +305,8 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a)
             }
             __syncthreads();
             for (;;) {
-                if (acc) batch_pass<true, COST>(P, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, colsum, V[SV_RS]);
-                else     batch_pass<false, COST>(P, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, colsum, V[SV_RS]);
+                if (acc) batch_pass<true, COST>(P, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, colsum, V[SV_RS], tc, sStage);
+                else     batch_pass<false, COST>(P, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, colsum, V[SV_RS], tc, sStage);
 #pragma unroll
                 for (int q = 0; q < kNRed; ++q) x[q] = 0.0;
                 for (int i = tid; i < n; i += T) {
@@ -371,7 +397,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a)
             }
             __syncthreads();
             // r(P) and x = min(r / r(P), 1); the column pass then weights row i by x_i 2^{A_i}
-            batch_pass<true, COST>(P, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, colsum, V[SV_RS]);
+            batch_pass<true, COST>(P, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, colsum, V[SV_RS], tc, sStage);
             for (int i = tid; i < n; i += T) {
                 const double rP = ldexp(V[SV_RS][i], sA[i]);
                 const double xi = (rP > 0.0) ? fmin(P.r[i] / rP, 1.0) : 1.0;
@@ -379,7 +405,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a)
                 sS[i] = (float)ldexp(xi, sA[i]);
             }
             __syncthreads();
-            batch_pass<true, COST>(P, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, colsum, V[SV_RS]);   // colsum = c(F)
+            batch_pass<true, COST>(P, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, colsum, V[SV_RS], tc, sStage);   // colsum = c(F)
             for (int j = tid; j < n; j += T) {
                 const double cF = (double)colsum[j];
                 const double yj = (cF > 0.0) ? fmin(P.c[j] / cF, 1.0) : 1.0;

@@ -106,7 +106,7 @@ void mdot_default_params(mdot_params* prm)
     prm->precision = MDOT_PREC_AUTO;
     prm->warm_start = 0;
     prm->final_tol = 0.0;
-    prm->fp32_floor = 5e-8;
+    prm->fp32_floor = 2e-7;
     prm->profile = 0;
     prm->ls_init = 1;                    // App. B leaves the first trial step open (see mdot.h)
     prm->wait_limit_us = 0;              // bounded device waits: the 2 s default
@@ -375,6 +375,19 @@ mdot_status check_marginals(mdot_handle* h, const WS& ws, double* H)
     return MDOT_OK;
 }
 
+// The squared-Euclidean cost of integer points (|coordinate| <= 255) runs on the tensor cores
+// (exact: see pass_f32_regen_tc); one check of the coordinates per call.
+cudaError_t select_cost_form(mdot_handle* h, WS& ws)
+{
+    ws.tc = 0;
+    if (ws.ckind != COST_SQEUCLID) return cudaSuccess;
+    bool grid = false;
+    cudaError_t e = check_grid_points(ws.X, ws.Y, ws.n, reinterpret_cast<unsigned int*>(h->d_out + 14),
+                                      reinterpret_cast<unsigned int*>(h->h_out + 14), h->stream, &grid);
+    ws.tc = grid ? 1 : 0;
+    return e;
+}
+
 // Where C comes from: a dense matrix, or coordinates (n x 3 each) with a kind and a scale.
 struct CostSpec {
     const float* C = nullptr;
@@ -414,6 +427,7 @@ mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const C
     double H = 0.0;
     mdot_status ms = check_marginals(h, ws, &H);
     if (ms != MDOT_OK) return ms;
+    CKR(select_cost_form(h, ws));
     const double gf = (P.gamma_f > 0.0) ? P.gamma_f : gamma_f_for_eps(H, eps_target, P.gamma_i, P.q, P.p);
     // precision tiers: fp64 entries for small n; otherwise fp32 entries with ex2.approx while the
     // stage tolerance is loose, the accurate fp32 tier (double-float exponent, polynomial exp2)
@@ -584,6 +598,7 @@ mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const C
         info->launches = launches;
         info->stalls = S.stalls;
         info->stage_launches_fp32 = launches32;
+        info->tensor_cores = ws.tc;
     }
     return out;
 }
@@ -661,6 +676,7 @@ static mdot_status dual_eval_core(mdot_handle* h, const double* u, const double*
     WS ws = h->ws;
     ws.n = (int)n;
     cs.apply(ws);
+    CKR(select_cost_form(h, ws));
     EvalArgs a{};
     a.gamma = gamma;
     a.G64 = gamma * kLog2e;

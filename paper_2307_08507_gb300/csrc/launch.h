@@ -50,6 +50,11 @@ cudaError_t launch_round(const WS& ws, const RoundArgs& a, cudaStream_t s);
 cudaError_t launch_lower_bound(const WS& ws, const LbArgs& a, cudaStream_t s);
 cudaError_t launch_validate(const WS& ws, double* out, cudaStream_t s);
 
+// Are all 3n coordinates of X and Y integers of magnitude <= 255 (the tensor-core form of the
+// squared-Euclidean cost)?  Synchronises st; d_flag: one device word of scratch, h_flag: pinned.
+cudaError_t check_grid_points(const float* X, const float* Y, int n, unsigned int* d_flag, unsigned int* h_flag,
+                              cudaStream_t st, bool* grid);
+
 // batched solver (k_batch.cu)
 cudaError_t configure_batch_kernels(int* blocks_per_sm);
 cudaError_t launch_batch(int kind, int grid, const BatchArgs& a, cudaStream_t s);

@@ -89,6 +89,8 @@ struct WS {
     const float* Y;                   // n x 3 target coordinates
     float cscale;                     // s = 1 / max distance
     int ckind;                        // CostKind
+    int tc;                           // squared-Euclidean cost of integer points |x_k| <= 255: on the
+                                      // tensor cores (pass_f32_regen_tc)
     const double *r, *c;              // original marginals
     double *rt, *ct, *lrt, *lct;      // smoothed marginals and logs (Alg. 1)
     double *u, *v, *pu, *pv, *uprev, *vprev;
@@ -171,8 +173,9 @@ __device__ __forceinline__ float ex2f(float x)
 // cost-unit difference and W the row + column remainders.  k = rint(G32 d + W) is taken from one
 // rounded fma (1.5 * 2^23 added and subtracted leaves the nearest integer); the reduced argument
 // x = (G32 d - k) + W + Glo d is then formed with the product exact inside the fma, so its error is
-// a few 2^-25 whatever the size of G d.  2^x on [-1/2, 1/2] by a degree-6 minimax polynomial (Remez
-// fit made for this library, relative error 1.9e-9 before fp32 rounding), 2^k by ex2.approx on the
+// a few 2^-25 whatever the size of G d.  2^x on [-1/2, 1/2] by a degree-6 relative-minimax
+// polynomial with p(0) = 1 (Remez exchange, csrc/exp2_poly_fit.py: level 1.98e-9; 1.57e-8 with the
+// coefficients rounded to fp32 as written here), 2^k by ex2.approx on the
 // integer k (exact there; 0 below 2^-126 and inf above 2^127, so no clamping is needed).  Relative
 // error ~1 ulp and unbiased, unlike ex2.approx on a general argument, whose error on this GPU
 // averages -5e-8.
@@ -566,6 +569,18 @@ struct ColPlain {
         for (int e = 0; e < 4; ++e)
             if (j0 + e < n) out[j0 + e] = ca[e];
     }
+    // the constants of column j (tensor-core pass, staged in shared memory) and the partials of
+    // columns j0, j0 + 1
+    __device__ __forceinline__ void load1(int j, int n, float& hh, float& wc) const
+    {
+        hh = (j < n) ? __ldcg(Hh + j) : 0.0f;
+        wc = (j < n) ? __ldcg(Wc + j) : kPadW;
+    }
+    __device__ __forceinline__ void store2(int j0, int n, float2 ca) const
+    {
+        if (j0 < n) out[j0] = ca.x;
+        if (j0 + 1 < n) out[j0 + 1] = ca.y;
+    }
 };
 
 
@@ -611,6 +626,24 @@ __device__ __forceinline__ float2 df_from_double(double x)
     return make_float2(h, (float)(x - (double)h));
 }
 __device__ __forceinline__ double df_to_double(float2 a) { return (double)a.x + (double)a.y; }
+// a + b for a double-float a and a float b (TwoSum, then renormalise)
+__device__ __forceinline__ float2 df_add_f(float2 a, float b)
+{
+    const float2 s = df_two_sum(a.x, b);
+    return df_fast_two_sum(s.x, __fadd_rn(s.y, a.y));
+}
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+// a * 2^e for a double-float a and -126 <= e <= 127 (exact unless a component leaves the normal
+// range)
+__device__ __forceinline__ float2 df_ldexp(float2 a, int e)
+{
+    const float m = __int_as_float((e + 127) << 23);
+    return make_float2(__fmul_rn(a.x, m), __fmul_rn(a.y, m));
+}
+__device__ __forceinline__ float2 df_shfl_xor(float2 a, int o)
+{
+    return make_float2(__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o));
+}
 
 // Decision of one evaluation as every thread of the stage kernel sees it: commit (v += alpha_c p,
 // p = s + beta p) when accepted, then the trial point v + alpha p.  Steps are fp32 numbers (the
@@ -690,6 +723,17 @@ struct ColDelta {
         for (int e = 0; e < 4; ++e)
             if (j0 + e < n) out[j0 + e] = ca[e];
     }
+    __device__ __forceinline__ void load1(int j, int n, float& hh, float& wc) const
+    {
+        const float4 q = (j < n) ? __ldcg(pub + j) : make_float4(0.0f, kPadW, 0.0f, 0.0f);
+        hh = q.x;
+        wc = (j < n) ? __fmaf_rn(k1, q.z, __fmaf_rn(k2, q.w, q.y)) : kPadW;
+    }
+    __device__ __forceinline__ void store2(int j0, int n, float2 ca) const
+    {
+        if (j0 < n) out[j0] = ca.x;
+        if (j0 + 1 < n) out[j0 + 1] = ca.y;
+    }
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -713,6 +757,35 @@ __device__ __forceinline__ int row_scale(double log_r_pred)
 }
 
 // ---------------------------------------------------------------------------------------------
+// Column partials over many rows: a thread's fp32 chain of E_ij s_i over the rows of its CTA is
+// folded every kFoldRows rows into a compensated (TwoSum) pair, so that a long chain (up to 4096
+// rows in the batched form) adds ~1 ulp of error instead of ~sqrt(rows) ulp; the result is
+// rounded to fp32 once.  (The spread such sums leave in the marginals sets the smallest
+// ||grad g||_1 fp32 entries can resolve.)
+// ---------------------------------------------------------------------------------------------
+constexpr int kFoldRows = 16;
+
+__device__ __forceinline__ void fold1(float& hi, float& lo, float& ca)
+{
+    const float s = __fadd_rn(hi, ca);
+    const float bb = __fsub_rn(s, hi);
+    lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(ca, bb)));
+    hi = s;
+    ca = 0.0f;
+}
+__device__ __forceinline__ void fold2(float2& hi, float2& lo, float2& ca)
+{
+    fold1(hi.x, lo.x, ca.x);
+    fold1(hi.y, lo.y, ca.y);
+}
+// the folded total (the open chain included), rounded once
+__device__ __forceinline__ float2 fold_total(float2 hi, float2 lo, float2 ca)
+{
+    fold2(hi, lo, ca);
+    return make_float2(__fadd_rn(hi.x, lo.x), __fadd_rn(hi.y, lo.y));
+}
+
+// ---------------------------------------------------------------------------------------------
 // Phase A: one pass over the rows [r0, r1) of C.  Row sums go to sRow[warp][local row]
 // (accumulated, fp32 or fp64), column partials to colpart_b[j].
 // ---------------------------------------------------------------------------------------------
@@ -726,12 +799,12 @@ __device__ __forceinline__ void pass_f32(const float* __restrict__ C, int n, int
     const int BN = 4 * kK * T;
     for (int cb = 0; cb < n; cb += BN) {
         float hh[kK][4], wc[kK][4];
-        float2 hh2[kK][2], wc2[kK][2], ca2[kK][2];
+        float2 hh2[kK][2], wc2[kK][2], ca2[kK][2], fh2[kK][2], fl2[kK][2];
         int jk[kK];
 #pragma unroll
         for (int k = 0; k < kK; ++k) {
             jk[k] = cb + 4 * (tid + k * T);
-            ca2[k][0] = ca2[k][1] = make_float2(0.0f, 0.0f);
+            ca2[k][0] = ca2[k][1] = fh2[k][0] = fh2[k][1] = fl2[k][0] = fl2[k][1] = make_float2(0.0f, 0.0f);
         }
         io.load_seg(jk, n, hh, wc);
         to_pairs(hh, hh2);
@@ -767,11 +840,19 @@ __device__ __forceinline__ void pass_f32(const float* __restrict__ C, int n, int
             butterfly<kRG>(rp, lane);
             const int il = rg + lane;
             if (lane < kRG && il < r1) sRow[warp * nloc + (il - r0)] += rp[0];
+            if (((rg - r0 + kRG) % kFoldRows) == 0) {
+#pragma unroll
+                for (int k = 0; k < kK; ++k) {
+                    fold2(fh2[k][0], fl2[k][0], ca2[k][0]);
+                    fold2(fh2[k][1], fl2[k][1], ca2[k][1]);
+                }
+            }
         }
 #pragma unroll
         for (int k = 0; k < kK; ++k) {
+            float2 tot[2] = {fold_total(fh2[k][0], fl2[k][0], ca2[k][0]), fold_total(fh2[k][1], fl2[k][1], ca2[k][1])};
             float ca[4];
-            from_pairs(ca2[k], ca);
+            from_pairs(tot, ca);
             io.store4(jk[k], n, ca);
         }
     }
@@ -1199,6 +1280,235 @@ __device__ __forceinline__ float regen_row(const float* sX, int il, const float*
 // Pass over the CTA's rows with C regenerated from coordinates (no C in memory): same structure
 // as pass_f32 with two float4 column groups per thread; the row coordinates come from shared
 // memory (sX: 3 floats per local row), the column coordinates sit in registers per sweep.
+// ---------------------------------------------------------------------------------------------
+// Squared-Euclidean cost between integer grid points on the tensor cores.  For points with integer
+// coordinates |x_k| <= 255, D_ij = |x_i|^2 + |y_j|^2 - 2 <x_i, y_j> is one contraction of length
+// 9 of bf16 vectors that hold every value exactly:
+//   A_i = [x0, x1, x2, a2, a1, a0, 1, 1, 1, 0 ...]   (a2 a1 a0: base-256 digits of |x_i|^2)
+//   B_j = [-2y0, -2y1, -2y2, 2^16, 2^8, 1, b2 2^16, b1 2^8, b0, 0 ...]
+// Every product is an integer below 2^18 and every partial sum an integer below 2^20, so the fp32
+// accumulation of the tensor cores is exact: D is the exact integer, and C = fl32(D s) has the bits
+// of the fp32 cost (d0 d0 + d1 d1) + d2 d2 times s that the FMA pass and the host generator form.
+// (A contraction of length 9 uses a tiny share of the tensor pipe: what it removes is the ALU work
+// of the cost, about half of the fp32 operations of an entry.)
+// ---------------------------------------------------------------------------------------------
+// two floats (exact in bf16) as one bf16x2 register; `lo` in the low half (the smaller k)
+__device__ __forceinline__ unsigned int bf16x2(float lo, float hi)
+{
+    unsigned int d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+
+// D = A B (m16n8k16, bf16 inputs, fp32 accumulation from zero).  Fragments as the PTX ISA lays
+// them out: lane = 4 g + t; a0/a1: rows g / g + 8, k = 2t, 2t + 1; a2/a3: the same rows,
+// k = 8 + 2t, 9 + 2t; b0/b1: column g, k = 2t, 2t + 1 / 8 + 2t, 9 + 2t; d0, d1: row g, columns
+// 2t, 2t + 1; d2, d3: row g + 8, the same columns.
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], unsigned int a0, unsigned int a1, unsigned int a2,
+                                               unsigned int a3, unsigned int b0, unsigned int b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+                 "{%8, %9}, {%10, %10, %10, %10};"
+                 : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1), "f"(0.0f));
+}
+
+// |x|^2 of an integer point, as its base-256 digits (d2, d1, d0)
+__device__ __forceinline__ void sq_digits(float x0, float x1, float x2, float& d2, float& d1, float& d0)
+{
+    const int s = (int)x0 * (int)x0 + (int)x1 * (int)x1 + (int)x2 * (int)x2;
+    d2 = (float)(s >> 16);
+    d1 = (float)((s >> 8) & 255);
+    d0 = (float)(s & 255);
+}
+
+// This lane's two A registers (k = 2t, 2t + 1 and k = 8 + 2t, 9 + 2t) of a row point.
+__device__ __forceinline__ void tc_a_regs(float x0, float x1, float x2, int t, unsigned int& klo, unsigned int& khi)
+{
+    float d2, d1, d0;
+    sq_digits(x0, x1, x2, d2, d1, d0);
+    const float e0 = t == 0 ? x0 : t == 1 ? x2 : t == 2 ? d1 : 1.0f;
+    const float e1 = t == 0 ? x1 : t == 1 ? d2 : t == 2 ? d0 : 1.0f;
+    klo = bf16x2(e0, e1);
+    khi = t == 0 ? bf16x2(1.0f, 0.0f) : 0u;
+}
+
+// This lane's two B registers of a column point.
+__device__ __forceinline__ void tc_b_regs(float y0, float y1, float y2, int t, unsigned int& b0, unsigned int& b1)
+{
+    float d2, d1, d0;
+    sq_digits(y0, y1, y2, d2, d1, d0);
+    const float e0 = t == 0 ? -2.0f * y0 : t == 1 ? -2.0f * y2 : t == 2 ? 256.0f : d2 * 65536.0f;
+    const float e1 = t == 0 ? -2.0f * y1 : t == 1 ? 65536.0f : t == 2 ? 1.0f : d1 * 256.0f;
+    b0 = bf16x2(e0, e1);
+    b1 = t == 0 ? bf16x2(d0, 0.0f) : 0u;
+}
+
+// Pass over the CTA's rows with the squared-Euclidean cost of integer grid points formed on the
+// tensor cores (see above); same outputs as pass_f32_regen.  The columns go in blocks of
+// kTcSubs x 32 columns per warp: the CTA first stages a block's column constants and coordinates in
+// shared memory (stage: kTcStageFloats per column, tc_stage_floats(warps) floats), then every warp
+// takes kTcSubs sub-blocks of 32 columns and sweeps the CTA's rows in tiles of 16: per tile four
+// mma.sync give the costs, every lane forms its 2 rows x 8 columns of entries (the exponent and the
+// sums as in entry2), the row partials are added over the 4 lanes of a row, and the column
+// partials, folded every kFoldRows rows (fold2), over the 8 row groups at the end of the sweep.
+constexpr int kTcSubs = 8;             // 32-column sub-blocks per warp and column block
+constexpr int kTcStageFloats = 5;      // hh, wc, y0, y1, y2 per staged column
+__host__ __device__ constexpr int tc_block_cols(int warps) { return warps * kTcSubs * 32; }
+__host__ __device__ constexpr int tc_stage_floats(int warps) { return kTcStageFloats * tc_block_cols(warps); }
+
+// One 16-row tile of a tensor-core sweep for this lane: the costs of its rows g, g + 8 and its
+// 2 NT columns, the entries, the row partials (added into rp0 / rp1) and the column partials.
+template <bool ACC, int NT>
+__device__ __forceinline__ void tc_tile(unsigned int a0, unsigned int a1, unsigned int a2, unsigned int a3,
+                                        const unsigned int (&b0)[NT], const unsigned int (&b1)[NT],
+                                        float fh0, float wr0, float s0, float fh1, float wr1, float s1,
+                                        const float2 (&hh2)[NT], const float2 (&wc2)[NT], float2 CS, float2 Z,
+                                        float2 G32p, float2 Glop, float& rp0, float& rp1, float2 (&ca2)[NT])
+{
+    const float2 FH0 = pk(fh0), WR0 = pk(wr0), S0 = pk(s0), FH1 = pk(fh1), WR1 = pk(wr1), S1 = pk(s1);
+#pragma unroll
+    for (int q = 0; q < NT; ++q) {
+        float d[4];
+        mma_bf16_16816(d, a0, a1, a2, a3, b0[q], b1[q]);
+        // C = fl32(D s): an fma with a -0 addend the generator cannot fold (see point_cost2)
+        const float2 c0 = fma2(make_float2(d[0], d[1]), CS, Z);
+        const float2 c1 = fma2(make_float2(d[2], d[3]), CS, Z);
+        const float2 E0 = entry2<ACC>(FH0, WR0, hh2[q], wc2[q], c0, G32p, Glop);
+        const float2 E1 = entry2<ACC>(FH1, WR1, hh2[q], wc2[q], c1, G32p, Glop);
+        rp0 += E0.x;
+        rp0 += E0.y;
+        rp1 += E1.x;
+        rp1 += E1.y;
+        ca2[q] = fma2(E0, S0, ca2[q]);
+        ca2[q] = fma2(E1, S1, ca2[q]);
+    }
+}
+
+template <bool ACC, class IO>
+__device__ __forceinline__ void pass_f32_regen_tc(const float* __restrict__ Y, float cs, int n, int r0, int r1,
+                                                  const IO& io, const float* sFh, const float* sWr,
+                                                  const float* sS, const float* sX, float G32, float Glo,
+                                                  float* sRow, int nloc, float* stage, uint2* sA4)
+{
+    constexpr int NT = 4;
+    const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = T >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int nrows = r1 - r0;
+    const int BW = tc_block_cols(nw);
+    float* stH = stage;                 // staged block: hh, wc, y0, y1, y2 (BW each)
+    float* stW = stage + BW;
+    float* stY = stage + 2 * BW;        // 3 BW, column-major per coordinate
+    const float2 G32p = pk(G32), Glop = pk(Glo), CS = pk(cs);
+    const float2 Z = pk(-(cs * 0.0f));          // -0, opaque to the code generator (see point_cost2)
+    // the A registers of every row and lane position t, once per pass (when there is room)
+    if (sA4 != nullptr)
+        for (int q = tid; q < 4 * nrows; q += T) {
+            const int il = q >> 2, tt = q & 3;
+            uint2 v;
+            tc_a_regs(sX[3 * il], sX[3 * il + 1], sX[3 * il + 2], tt, v.x, v.y);
+            sA4[q] = v;
+        }
+    for (int cb0 = 0; cb0 < n; cb0 += BW) {
+        __syncthreads();                        // the previous block is no longer read
+        for (int q = tid; q < BW; q += T) {
+            const int j = cb0 + q;
+            float hh, wc;
+            io.load1(j, n, hh, wc);
+            stH[q] = hh;
+            stW[q] = wc;
+            const bool ok = j < n;
+            stY[q] = ok ? __ldg(Y + 3 * (size_t)j) : 0.0f;
+            stY[BW + q] = ok ? __ldg(Y + 3 * (size_t)j + 1) : 0.0f;
+            stY[2 * BW + q] = ok ? __ldg(Y + 3 * (size_t)j + 2) : 0.0f;
+        }
+        __syncthreads();
+        for (int sb = 0; sb < kTcSubs; ++sb) {
+            const int lb = (warp * kTcSubs + sb) * 32;          // sub-block offset in the block
+            if (cb0 + lb >= n) break;                           // warp-uniform
+            unsigned int b0[NT], b1[NT];
+            float2 hh2[NT], wc2[NT], ca2[NT], fh2[NT], fl2[NT];
+#pragma unroll
+            for (int q = 0; q < NT; ++q) {
+                const int jb = lb + 8 * q + g;                  // the column this lane feeds into B
+                if (cb0 + jb < n) {
+                    tc_b_regs(stY[jb], stY[BW + jb], stY[2 * BW + jb], t, b0[q], b1[q]);
+                } else {
+                    b0[q] = 0u;
+                    b1[q] = 0u;
+                }
+                const int jc = lb + 8 * q + 2 * t;              // this lane's two cost columns
+                hh2[q] = make_float2(stH[jc], stH[jc + 1]);
+                wc2[q] = make_float2(stW[jc], stW[jc + 1]);
+                ca2[q] = fh2[q] = fl2[q] = make_float2(0.0f, 0.0f);
+            }
+            // two row tiles per step when both exist: their instruction streams interleave
+            for (int rt = 0; rt < nrows; rt += 32) {
+                float rp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int base = rt + 16 * h;
+                    if (base >= nrows) break;                   // warp-uniform
+                    const int il0 = base + g, il1 = base + g + 8;
+                    unsigned int a0 = 0u, a1 = 0u, a2 = 0u, a3 = 0u;
+                    float fh0 = 0.0f, wr0 = kPadW, s0 = 0.0f, fh1 = 0.0f, wr1 = kPadW, s1 = 0.0f;
+                    if (il0 < nrows) {
+                        if (sA4 != nullptr) {
+                            const uint2 v = sA4[4 * il0 + t];
+                            a0 = v.x;
+                            a2 = v.y;
+                        } else {
+                            tc_a_regs(sX[3 * il0], sX[3 * il0 + 1], sX[3 * il0 + 2], t, a0, a2);
+                        }
+                        fh0 = sFh[il0]; wr0 = sWr[il0]; s0 = sS[il0];
+                    }
+                    if (il1 < nrows) {
+                        if (sA4 != nullptr) {
+                            const uint2 v = sA4[4 * il1 + t];
+                            a1 = v.x;
+                            a3 = v.y;
+                        } else {
+                            tc_a_regs(sX[3 * il1], sX[3 * il1 + 1], sX[3 * il1 + 2], t, a1, a3);
+                        }
+                        fh1 = sFh[il1]; wr1 = sWr[il1]; s1 = sS[il1];
+                    }
+                    tc_tile<ACC, NT>(a0, a1, a2, a3, b0, b1, fh0, wr0, s0, fh1, wr1, s1, hh2, wc2, CS, Z, G32p, Glop,
+                                     rp[2 * h], rp[2 * h + 1], ca2);
+                }
+                // the four lanes of a row group hold the same rows
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    rp[k] += __shfl_xor_sync(0xffffffffu, rp[k], 1);
+                    rp[k] += __shfl_xor_sync(0xffffffffu, rp[k], 2);
+                }
+                if (t == 0) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int il = rt + 16 * (k >> 1) + 8 * (k & 1) + g;
+                        if (il < nrows) sRow[warp * nloc + il] += rp[k];
+                    }
+                }
+                if (((rt + 32) % (8 * kFoldRows)) == 0) {        // 2 rows per tile and lane
+#pragma unroll
+                    for (int q = 0; q < NT; ++q) fold2(fh2[q], fl2[q], ca2[q]);
+                }
+            }
+            // column partials: the eight row groups of the warp (lanes with the same t) hold the
+            // same two columns of each tile
+#pragma unroll
+            for (int q = 0; q < NT; ++q) {
+                float2 c = fold_total(fh2[q], fl2[q], ca2[q]);
+#pragma unroll
+                for (int o = 4; o <= 16; o <<= 1) {
+                    c.x += __shfl_xor_sync(0xffffffffu, c.x, o);
+                    c.y += __shfl_xor_sync(0xffffffffu, c.y, o);
+                }
+                if (g == 0) io.store2(cb0 + lb + 8 * q + 2 * t, n, c);
+            }
+        }
+    }
+}
+
 template <bool ACC, int KIND, class IO>
 __device__ __forceinline__ void pass_f32_regen(const float* __restrict__ Y, float cs, int n, int r0, int r1,
                                                const IO& io, const float* sFh,
@@ -1212,7 +1522,7 @@ __device__ __forceinline__ void pass_f32_regen(const float* __restrict__ Y, floa
     const float2 Z = pk(-(cs * 0.0f));          // -0, opaque to the code generator (see point_cost2)
     for (int cb = 0; cb < n; cb += BN) {
         float hh[KR][4], wc[KR][4];
-        float2 hh2[KR][2], wc2[KR][2], ca2[KR][2], y0[KR][2], y1[KR][2], y2[KR][2];
+        float2 hh2[KR][2], wc2[KR][2], ca2[KR][2], y0[KR][2], y1[KR][2], y2[KR][2], fh2[KR][2], fl2[KR][2];
         int jk[KR];
 #pragma unroll
         for (int k = 0; k < KR; ++k) jk[k] = cb + 4 * (tid + k * T);
@@ -1235,7 +1545,7 @@ __device__ __forceinline__ void pass_f32_regen(const float* __restrict__ Y, floa
                 y1[k][q] = make_float2(yv[1][2 * q], yv[1][2 * q + 1]);
                 y2[k][q] = make_float2(yv[2][2 * q], yv[2][2 * q + 1]);
             }
-            ca2[k][0] = ca2[k][1] = make_float2(0.0f, 0.0f);
+            ca2[k][0] = ca2[k][1] = fh2[k][0] = fh2[k][1] = fl2[k][0] = fl2[k][1] = make_float2(0.0f, 0.0f);
         }
         for (int rg = r0; rg < r1; rg += kRG) {
             float rp[kRG];
@@ -1259,11 +1569,19 @@ __device__ __forceinline__ void pass_f32_regen(const float* __restrict__ Y, floa
             butterfly<kRG>(rp, lane);
             const int il = rg + lane;
             if (lane < kRG && il < r1) sRow[warp * nloc + (il - r0)] += rp[0];
+            if (((rg - r0 + kRG) % kFoldRows) == 0) {
+#pragma unroll
+                for (int k = 0; k < KR; ++k) {
+                    fold2(fh2[k][0], fl2[k][0], ca2[k][0]);
+                    fold2(fh2[k][1], fl2[k][1], ca2[k][1]);
+                }
+            }
         }
 #pragma unroll
         for (int k = 0; k < KR; ++k) {
+            float2 tot[2] = {fold_total(fh2[k][0], fl2[k][0], ca2[k][0]), fold_total(fh2[k][1], fl2[k][1], ca2[k][1])};
             float ca[4];
-            from_pairs(ca2[k], ca);
+            from_pairs(tot, ca);
             io.store4(jk[k], n, ca);
         }
     }
@@ -1486,6 +1804,32 @@ __device__ __forceinline__ void pass2_f64(const WS& ws, const float* __restrict_
 // column j0 + lane is returned in warp 0.  Each warp issues all of its partial loads before
 // summing them (independent loads in flight instead of a dependent chain).  sm: >= 2 * 32 * nwarps
 // floats.  Requires G <= 24 * nwarps.
+// merge_cols_f32 with the total as a double-float (the fp32 stage kernel's epilogue avoids fp64:
+// on this GPU an fp64 warp instruction holds the SM's small fp64 pipe for many cycles).
+__device__ __forceinline__ float2 merge_cols_f32_df(const float* colpart, int n, int G, int j0, int j1, float* sm)
+{
+    constexpr int kMaxPer = 24;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int j = j0 + lane;
+    float vals[kMaxPer];
+#pragma unroll
+    for (int k = 0; k < kMaxPer; ++k) {
+        const int b = warp + k * nw;
+        vals[k] = (j < j1 && b < G) ? __ldcg(colpart + (size_t)b * n + j) : 0.0f;
+    }
+    float s = 0.0f, comp = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kMaxPer; ++k) kahan_add(s, comp, vals[k]);
+    sm[warp * 32 + lane] = s;
+    sm[(nw + warp) * 32 + lane] = -comp;
+    __syncthreads();
+    float2 tot = make_float2(0.0f, 0.0f);
+    if (warp == 0)
+        for (int w = 0; w < nw; ++w) tot = df_add_f(df_add_f(tot, sm[w * 32 + lane]), sm[(nw + w) * 32 + lane]);
+    __syncthreads();
+    return tot;
+}
+
 __device__ __forceinline__ double merge_cols_f32(const float* colpart, int n, int G,
                                                  int j0, int j1, float* sm)
 {

@@ -248,7 +248,15 @@ __device__ __forceinline__ void phase_A(const WS& ws, const IO& io, int r0, int 
         const float* sFh = reinterpret_cast<const float*>(sm + L.off_c0);
         const float* sWr = reinterpret_cast<const float*>(sm + L.off_c1);
         const float* sS = reinterpret_cast<const float*>(sm + L.off_s);
-        if (COST != COST_DENSE)
+        // the tensor-core form stages its column blocks, and the A registers of its rows when there
+        // is room, in the (unused) ring region
+        const size_t room = (size_t)L.stages * kSegFloats, need = (size_t)tc_stage_floats(nw);
+        if (COST == COST_SQEUCLID && ws.tc && room >= need)
+            pass_f32_regen_tc<TIER == TIER_F32A>(
+                ws.Y, ws.cscale, n, r0, r1, io, sFh, sWr, sS, reinterpret_cast<const float*>(sm + L.off_xc), G32,
+                Glo, sRow, L.nloc_max, reinterpret_cast<float*>(sm + L.off_ring),
+                room >= need + 8 * (size_t)L.nloc_max ? reinterpret_cast<uint2*>(sm + L.off_ring + 4 * need) : nullptr);
+        else if (COST != COST_DENSE)
             pass_f32_regen<TIER == TIER_F32A, COST>(ws.Y, ws.cscale, n, r0, r1, io, sFh, sWr, sS,
                                                     reinterpret_cast<const float*>(sm + L.off_xc), G32, Glo,
                                                     sRow, L.nloc_max);
@@ -618,12 +626,71 @@ __device__ __forceinline__ bool cta_wait_flags(const unsigned int* flags, int G,
     return *s_ok != 0;
 }
 
+// Row constants of a trial point u + alpha p in the fp32-entry stage kernel, from the row's
+// double-float state (the arithmetic of col_publish, no fp64): the row scale A from the predicted
+// log r(P) (log_r + alpha p), then x = (u + alpha p - A ln 2) / gamma in cost units split into a
+// part quantised to 2^-21 (fh) and the remainder in exponent units (wr).
+__device__ __forceinline__ void prep_row_df(float2 u, float2 p, float alpha, float log_r, int Aglob,
+                                            float2 inv_gamma, float G32, float Glo, unsigned char* sm,
+                                            const SmemLayout& L, int il)
+{
+    const float2 ua = df_add(u, df_mul_f(p, alpha));
+    float a = rintf(__fmul_rn(__fmaf_rn(alpha, p.x, log_r), (float)kLog2e));
+    a = fminf(fmaxf(a, -1.0e6f), 1.0e6f);
+    const int A = (int)a;
+    // A ln 2 as a double-float: the product with ln 2's leading float is exact inside the fma
+    const float l2h = (float)kLn2, l2l = (float)(kLn2 - (double)(float)kLn2);
+    const float ph = __fmul_rn(a, l2h);
+    const float2 aln2 = df_fast_two_sum(ph, __fmaf_rn(a, l2l, __fmaf_rn(a, l2h, -ph)));
+    const float2 x = df_mul(df_add(ua, df_neg(aln2)), inv_gamma);
+    const float h = __fmul_rn(rintf(__fmul_rn(x.x, 2097152.0f)), 1.0f / 2097152.0f);
+    const float lo = __fadd_rn(__fsub_rn(x.x, h), x.y);       // x.x - h is exact
+    reinterpret_cast<float*>(sm + L.off_c0)[il] = h;
+    reinterpret_cast<float*>(sm + L.off_c1)[il] = __fmaf_rn(lo, G32, __fmul_rn(lo, Glo));
+    reinterpret_cast<float*>(sm + L.off_s)[il] = pow2f_int(A - Aglob);
+    reinterpret_cast<int*>(sm + L.off_A)[il] = A;
+}
+
+// Epilogue of one row or column in the fp32-entry stage kernel, without fp64 (an fp64 warp
+// instruction holds this GPU's small fp64 pipe for many cycles, and these epilogues sit on the
+// critical path of every evaluation).  sum: the fp32 row (column) sum as a double-float, A its
+// power-of-two scale, t the smoothed marginal r~_i (c~_j) as a double-float, p the direction,
+// gprev the gradient entry at the current point.  The marginal sum 2^A and the gradient entry
+// g = r(P)_i - r~_i are formed in double-float (the difference is exact), the Sinkhorn direction
+// s = -log1p(g / r~) (Eq. (17); the sign of s is opposite to that of g, Sec. 4) in fp32, and the
+// five terms of the evaluation's scalars (<p, grad>, ||grad||_1, <y, -s>, <y, p>, <s, grad>,
+// y = grad - grad_prev, Eq. (18)) are fp32 products added into double-float sums.  The fp32
+// rounding of a term (2^-24 relative) is below the error the fp32 entries already leave in the
+// marginal.  Returns false for a row (column) whose sum is not positive and finite.
+__device__ __forceinline__ bool epi_entry(float2 sum, int A, float2 t, float p, float gprev, float2 (&xs)[kNRed],
+                                          float& g_out, float& s_out)
+{
+    if (!(sum.x > 0.0f) || !isfinite(sum.x)) {
+        xs[5] = df_add_f(xs[5], 1.0f);
+        return false;
+    }
+    const float2 m = (A >= -126 && A <= 127) ? df_ldexp(sum, A)
+                                             : make_float2((float)ldexp((double)sum.x, A), 0.0f);
+    const float g = df_add(m, df_neg(t)).x;
+    const float sdir = -log1pf(g / t.x);
+    const float y = __fsub_rn(g, gprev);
+    xs[0] = df_add_f(xs[0], __fmul_rn(p, g));
+    xs[1] = df_add_f(xs[1], fabsf(g));
+    xs[2] = df_add_f(xs[2], __fmul_rn(y, -sdir));
+    xs[3] = df_add_f(xs[3], __fmul_rn(y, p));
+    xs[4] = df_add_f(xs[4], __fmul_rn(sdir, g));
+    g_out = g;
+    s_out = sdir;
+    return true;
+}
+
 template <int TIER, int COST>
 __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, StageArgs a)
 {
     static_assert(TIER != TIER_F64, "the flag-synchronised stage kernel carries fp32 partials");
     extern __shared__ __align__(16) unsigned char sm[];
-    __shared__ double red_smem[32 * kNRed];
+    __shared__ float2 red_smem[32 * kNRed];
+    __shared__ double tot_smem[kNRed];
     __shared__ State sst;                 // this CTA's copy of the stage state
     __shared__ ColStep s_step;            // the last decision, as the column arithmetic uses it
     __shared__ unsigned int s_base;
@@ -640,6 +707,15 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
     double* Q = reinterpret_cast<double*>(sm + L.off_cstate);     // Q[k * NL + local column]
     float2* QV = reinterpret_cast<float2*>(Q + CS_V * NL);        // column v and p as double-floats
     float2* QP = reinterpret_cast<float2*>(Q + CS_P * NL);
+    // float views of the state slots: gradients (RS_G, RS_GT, CS_G, CS_GT) and directions (RS_ST,
+    // CS_ST) as floats, the smoothed marginals (RS_T, CS_T) as double-floats
+    float* RF = reinterpret_cast<float*>(R);
+    float* QF = reinterpret_cast<float*>(Q);
+    float2* RT = reinterpret_cast<float2*>(R + RS_T * NL);
+    float2* QT = reinterpret_cast<float2*>(Q + CS_T * NL);
+    // rows mirror the columns: u and p as double-floats, log r(P) as floats
+    float2* RU = reinterpret_cast<float2*>(R + RS_U * NL);
+    float2* RP = reinterpret_cast<float2*>(R + RS_P * NL);
     const double gamma = a.gamma, G64 = a.G64, w = a.w;
     const float G32 = (float)G64, Glo = (float)(G64 - (double)G32);
     const float2 inv_gamma = df_from_double(1.0 / gamma);
@@ -696,13 +772,12 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
         } else if (a.warm_start == 1) {
             u = a.ratio * u;                                    // eps-scaling
         }
-        R[RS_U * NL + il] = u;
-        R[RS_P * NL + il] = 0.0;
-        R[RS_G * NL + il] = 0.0;
-        R[RS_T * NL + il] = rt;
-        R[RS_LT * NL + il] = lrt;
-        R[RS_L * NL + il] = lrt;
-        prep_row<TIER>(u, row_scale(lrt), a.Aglob, gamma, G64, sm, L, il);
+        RU[il] = df_from_double(u);
+        RP[il] = make_float2(0.0f, 0.0f);
+        RF[RS_G * 2 * NL + il] = 0.0f;                 // gradients: floats
+        RT[il] = df_from_double(rt);                    // r~ as a double-float
+        RF[RS_L * 2 * NL + il] = (float)lrt;
+        prep_row_df(RU[il], RP[il], 0.0f, (float)lrt, a.Aglob, inv_gamma, G32, Glo, sm, L, il);
     }
     for (int j = c0 + tid; j < c1; j += T) {
         const int jl = j - c0;
@@ -720,9 +795,9 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
         }
         QV[jl] = df_from_double(v);
         QP[jl] = make_float2(0.0f, 0.0f);
-        Q[CS_G * NL + jl] = 0.0;
-        Q[CS_T * NL + jl] = ct;
-        Q[CS_ST * NL + jl] = 0.0;
+        QF[CS_G * 2 * NL + jl] = 0.0f;
+        QT[jl] = df_from_double(ct);                    // c~ as a double-float
+        QF[CS_ST * 2 * NL + jl] = 0.0f;
         ws.pub[j] = col_publish(QV[jl], QP[jl], 0.0f, inv_gamma, G32, Glo);
     }
     // tags: base + 1 for this prologue, base + 2 + t for evaluation t (flags start at 0, and every
@@ -751,80 +826,60 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
             }
         }
         if (tid == 0) post_flag(fcp + b, tag);             // phase_A ends with a __syncthreads
-        double x[kNRed];
+        float2 x[kNRed];
 #pragma unroll
-        for (int q = 0; q < kNRed; ++q) x[q] = 0.0;
+        for (int q = 0; q < kNRed; ++q) x[q] = make_float2(0.0f, 0.0f);
         {
             const int* sA = reinterpret_cast<const int*>(sm + L.off_A);
+            const float* sRow = reinterpret_cast<const float*>(sm + L.off_row);
             for (int i = r0 + tid; i < r1; i += T) {
                 const int il = i - r0;
-                const double sum = row_total<TIER>(sm, L, il);
-                if (!(sum > 0.0) || !isfinite(sum)) { x[5] += 1.0; continue; }
-                const double rt = R[RS_T * NL + il];
-                const double g = ldexp(sum, sA[il]) - rt;
-                // Eq. (17): s = log r~ - log r(P) = -log1p(g / r~) (sign of s opposite to g, so
-                // <s, grad> < 0 holds numerically, Sec. 4); fp32 accuracy suffices for a direction
-                const double s = -(double)log1pf((float)g / (float)rt);
-                const double p = R[RS_P * NL + il];
-                const double y = g - R[RS_G * NL + il];
-                x[0] += p * g;
-                x[1] += fabs(g);
-                x[2] += y * (-s);
-                x[3] += y * p;
-                x[4] += s * g;
-                R[RS_GT * NL + il] = g;
-                R[RS_ST * NL + il] = s;
-                R[RS_LTR * NL + il] = ((double)__log2f((float)sum) + (double)sA[il]) * kLn2;   // scale only
+                float2 sum = make_float2(0.0f, 0.0f);           // the warps' partials, double-float
+                for (int w = 0; w < (T >> 5); ++w) sum = df_add_f(sum, sRow[w * NL + il]);   // every warp's slot
+                float g, sd;
+                if (!epi_entry(sum, sA[il], RT[il], RP[il].x, RF[RS_G * 2 * NL + il], x, g, sd))
+                    continue;
+                RF[RS_GT * 2 * NL + il] = g;
+                RF[RS_ST * 2 * NL + il] = sd;
+                // log r(P), for the next row scale only
+                RF[RS_LTR * 2 * NL + il] = __fmul_rn(__log2f(sum.x) + (float)sA[il], (float)kLn2);
             }
         }
 
         // ---------------- phase B: column merge and epilogue; publish the column state ----------------
         if (!cta_wait_flags(fcp, G, tag, &ws.st->bar, &s_ok)) break;
         for (int j0 = c0; j0 < c1; j0 += 32) {
-            const double colsum = merge_cols_f32(ws.colpart, n, G, j0, c1, reinterpret_cast<float*>(sm + L.off_merge));
+            const float2 colsum = merge_cols_f32_df(ws.colpart, n, G, j0, c1, reinterpret_cast<float*>(sm + L.off_merge));
             const int j = j0 + tid;
             if (tid < 32 && j < c1) {
                 const int jl = j - c0;
-                float sf = 0.0f;
-                if (!(colsum > 0.0) || !isfinite(colsum)) {
-                    x[5] += 1.0;
-                } else {
-                    const double ct = Q[CS_T * NL + jl];
-                    const double g = ldexp(colsum, a.Aglob) - ct;
-                    sf = -log1pf((float)g / (float)ct);             // Eq. (17), see rows
-                    const double s = (double)sf;
-                    const double p = df_to_double(QP[jl]);
-                    const double y = g - Q[CS_G * NL + jl];
-                    x[0] += p * g;
-                    x[1] += fabs(g);
-                    x[2] += y * (-s);
-                    x[3] += y * p;
-                    x[4] += s * g;
-                    Q[CS_GT * NL + jl] = g;
-                }
-                Q[CS_ST * NL + jl] = (double)sf;
+                float g, sf = 0.0f;
+                if (epi_entry(colsum, a.Aglob, QT[jl], QP[jl].x, QF[CS_G * 2 * NL + jl], x, g, sf))
+                    QF[CS_GT * 2 * NL + jl] = g;
+                else
+                    sf = 0.0f;
+                QF[CS_ST * 2 * NL + jl] = sf;
                 ws.pub[j] = col_publish(QV[jl], QP[jl], sf, inv_gamma, G32, Glo);
             }
         }
-        // CTA partial sums: only the warps that hold rows (columns sit in warp 0) take part
+        // CTA partial sums (double-floats): only the warps that hold rows (columns sit in warp 0)
         if (warp < red_warps) {
 #pragma unroll
             for (int q = 0; q < kNRed; ++q)
 #pragma unroll
-                for (int o = 16; o >= 1; o >>= 1) x[q] += __shfl_xor_sync(0xffffffffu, x[q], o);
+                for (int o = 16; o >= 1; o >>= 1) x[q] = df_add(x[q], df_shfl_xor(x[q], o));
             if (lane == 0)
 #pragma unroll
                 for (int q = 0; q < kNRed; ++q) red_smem[warp * kNRed + q] = x[q];
         }
         __syncthreads();
         if (tid < kNRed) {
-            // the CTA's partial sum as two tagged words
-            double acc = 0.0;
-            for (int ww = 0; ww < red_warps; ++ww) acc += red_smem[ww * kNRed + tid];
-            const unsigned long long bits = (unsigned long long)__double_as_longlong(acc);
+            // the CTA's partial sum as two tagged words: the double-float's high and low floats
+            float2 acc = make_float2(0.0f, 0.0f);
+            for (int ww = 0; ww < red_warps; ++ww) acc = df_add(acc, red_smem[ww * kNRed + tid]);
             unsigned long long* dst = ws.tsp + (size_t)b * 2 * kNRed + 2 * tid;
-            st_tag(dst, tag_pack((unsigned int)bits, tag));
-            st_tag(dst + 1, tag_pack((unsigned int)(bits >> 32), tag));
+            st_tag(dst, tag_pack(__float_as_uint(acc.y), tag));
+            st_tag(dst + 1, tag_pack(__float_as_uint(acc.x), tag));
         }
         // the column state written in phase B is published by a thread with nothing else to do:
         // the release store waits for those writes, and only this thread waits with it
@@ -833,7 +888,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
         // ---------------- every CTA: the G partials in a fixed order, then the decision ----------------
         bool ok = true;
         if (warp < kNRed) {
-            double v5[5];
+            float2 v5[5];
             unsigned int spins = 0;
             unsigned long long deadline = 0;
             for (;;) {
@@ -841,12 +896,12 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
 #pragma unroll
                 for (int k = 0; k < 5; ++k) {
                     const int bb = lane + 32 * k;
-                    v5[k] = 0.0;
+                    v5[k] = make_float2(0.0f, 0.0f);
                     if (bb < G) {
                         unsigned long long lo, hi;
                         ld_tag2(ws.tsp + (size_t)bb * 2 * kNRed + 2 * warp, lo, hi);
                         ready = ready && tag_of(lo) == tag && tag_of(hi) == tag;
-                        v5[k] = __longlong_as_double((long long)(((hi & 0xffffffffull) << 32) | (lo & 0xffffffffull)));
+                        v5[k] = make_float2(__uint_as_float((unsigned int)hi), __uint_as_float((unsigned int)lo));
                     }
                 }
                 if (__all_sync(0xffffffffu, ready)) break;
@@ -856,27 +911,28 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
                     break;
                 }
             }
-            double sacc = 0.0;
+            float2 sacc = make_float2(0.0f, 0.0f);
 #pragma unroll
-            for (int k = 0; k < 5; ++k) sacc += v5[k];
+            for (int k = 0; k < 5; ++k) sacc = df_add(sacc, v5[k]);
 #pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-            if (lane == 0) red_smem[warp] = sacc;
+            for (int o = 16; o >= 1; o >>= 1) sacc = df_add(sacc, df_shfl_xor(sacc, o));
+            if (lane == 0) tot_smem[warp] = df_to_double(sacc);
         }
         if (!ok) s_ok = 0;
         __syncthreads();
         if (!s_ok) break;
         if (tid == 0) {
             double tot[kNRed];
-            for (int q = 0; q < kNRed; ++q) tot[q] = red_smem[q];
-            decide(&sst, tot, a);
+            for (int q = 0; q < kNRed; ++q) tot[q] = tot_smem[q];
+            State loc = sst;                   // decide on registers, one copy in and out
+            decide(&loc, tot, a);
             // steps as fp32 numbers: the column arithmetic uses them exactly, rows too
-            sst.alpha = (double)(float)sst.alpha;
-            sst.beta = (double)(float)sst.beta;
-            s_step = ColStep{sst.accept, (float)sst.alpha_commit, (float)sst.beta, (float)sst.alpha};
+            loc.alpha = (double)(float)loc.alpha;
+            loc.beta = (double)(float)loc.beta;
+            sst = loc;
+            s_step = ColStep{loc.accept, (float)loc.alpha_commit, (float)loc.beta, (float)loc.alpha};
         }
         __syncthreads();
-        const double alpha = sst.alpha, acommit = sst.alpha_commit, beta = sst.beta;
         const bool accept = sst.accept != 0, done = sst.phase != PH_RUN;
 
         // the next pass reads every owner's column state: one warp acquires their flags while
@@ -886,23 +942,22 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
         // ---------------- phase C: commit, new direction, next trial constants (rows) ----------------
         for (int i = r0 + tid; i < r1; i += T) {
             const int il = i - r0;
-            double u = R[RS_U * NL + il], p = R[RS_P * NL + il];
+            float2 u = RU[il], p = RP[il];
             if (accept) {
-                u = u + acommit * p;                            // (u, v) += alpha p (Alg. 2)
-                R[RS_U * NL + il] = u;
-                R[RS_G * NL + il] = R[RS_GT * NL + il];
-                R[RS_L * NL + il] = R[RS_LTR * NL + il];
-                p = R[RS_ST * NL + il] + beta * p;              // p = s + beta p, beta = 0 on reset (Alg. 2)
-                R[RS_P * NL + il] = p;
+                RF[RS_G * 2 * NL + il] = RF[RS_GT * 2 * NL + il];
+                RF[RS_L * 2 * NL + il] = RF[RS_LTR * 2 * NL + il];
+                // (u, v) += alpha p and p = s + beta p (Alg. 2, Eq. (18)), as for the columns
+                col_commit(s_step, u, p, RF[RS_ST * 2 * NL + il]);
+                RU[il] = u;
+                RP[il] = p;
             }
-            if (!done) prep_row<TIER>(u + alpha * p, row_scale(R[RS_L * NL + il] + alpha * p), a.Aglob,
-                                      gamma, G64, sm, L, il);
+            if (!done) prep_row_df(u, p, s_step.alpha, RF[RS_L * 2 * NL + il], a.Aglob, inv_gamma, G32, Glo, sm, L, il);
         }
         // own columns: the same commit every consumer applies to the published state
         for (int j = c0 + tid; j < c1; j += T) {
             const int jl = j - c0;
-            if (accept) Q[CS_G * NL + jl] = Q[CS_GT * NL + jl];
-            col_commit(s_step, QV[jl], QP[jl], (float)Q[CS_ST * NL + jl]);
+            if (accept) QF[CS_G * 2 * NL + jl] = QF[CS_GT * 2 * NL + jl];
+            col_commit(s_step, QV[jl], QP[jl], QF[CS_ST * 2 * NL + jl]);
         }
         if (done) break;
         __syncthreads();
@@ -910,8 +965,8 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
     // the stage's iterate (also on a timeout: the best iterate so far) goes back to global memory
     __syncthreads();
     for (int i = r0 + tid; i < r1; i += T) {
-        ws.u[i] = R[RS_U * NL + i - r0];
-        ws.lr[i] = R[RS_L * NL + i - r0];
+        ws.u[i] = df_to_double(RU[i - r0]);
+        ws.lr[i] = (double)RF[RS_L * 2 * NL + i - r0];
     }
     for (int j = c0 + tid; j < c1; j += T) ws.v[j] = df_to_double(QV[j - c0]);
     // rows prefetched for a pass that never came must land before the CTA exits

@@ -9,6 +9,8 @@ Usage:  python tests/golden/make_golden.py [k] [eps ...]   (defaults: k = 64, ep
         python tests/golden/make_golden.py --oracle-only k kind eps   (one oracle solve, no exact value)
         python tests/golden/make_golden.py --line n ...   (exact costs of the points-on-a-line
             problems, seed 11: the monotone coupling, into tests/golden/line_exact.json)
+        python tests/golden/make_golden.py --serve   (oracle costs of the served trace's requests
+            with n <= 1024 among its first 100, into tests/golden/serve_oracle.json)
 Runs the cases in parallel worker processes (spawn) and merges each finished case into
 tests/golden/grid{n}.json (or exact{n}.json) as soon as it completes.
 """
@@ -84,6 +86,24 @@ def line_case(n, seed=11):
     return {"n": n, "seed": seed, "exact_ot": val, "method": "monotone coupling of the sorted supports"}
 
 
+def serve_case(args):
+    """Oracle cost of one request of the serving trace (seed 5000, 200 requests): a k x k grid
+    histogram pair with the squared-Euclidean grid cost at the request's target gap."""
+    idx, k, eps, sd = args
+    import numpy as np
+    import oracle as O
+    from paper_2307_08507_gb300 import inputs as I
+    r, c = I.grid_histogram(k, 2 * sd), I.grid_histogram(k, 2 * sd + 1)
+    C = I.grid_cost(k, "l2sq").astype(np.float64)
+    t0 = time.time()
+    res = O.solve(C, r, c, eps_target=eps)
+    return {"index": idx, "seed": SERVE_SEED, "count": SERVE_COUNT, "k": k, "n": k * k, "eps_target": eps,
+            "oracle_cost": res.cost, "oracle_evals": int(res.stats.evals), "oracle_seconds": time.time() - t0}
+
+
+SERVE_SEED, SERVE_COUNT = 5000, 200
+
+
 def _merge(path, record, key):
     old = []
     if os.path.exists(path):
@@ -107,6 +127,17 @@ def main():
         with ctx.Pool(len(cases)) as pool:
             for rec in pool.imap_unordered(exact_case, cases):
                 _merge(path, rec, lambda c: (c["kind"], c["seed"]))
+                print(json.dumps(rec), flush=True)
+        return
+    if len(sys.argv) > 1 and sys.argv[1] == "--serve":
+        # the first requests of the served trace with n <= 1024 among its first 100
+        from paper_2307_08507_gb300 import inputs as I
+        trace = I.serving_trace(SERVE_COUNT, SERVE_SEED)
+        cases = [(i, k, eps, sd) for i, (ta, k, eps, sd) in enumerate(trace[:100]) if k * k <= 1024]
+        path = os.path.join(HERE, "serve_oracle.json")
+        with ctx.Pool(min(len(cases), os.cpu_count() or 1)) as pool:
+            for rec in pool.imap_unordered(serve_case, cases):
+                _merge(path, rec, lambda c: (c["seed"], c["index"]))
                 print(json.dumps(rec), flush=True)
         return
     if len(sys.argv) > 1 and sys.argv[1] == "--line":

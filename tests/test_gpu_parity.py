@@ -256,66 +256,89 @@ def test_invalid_arguments_are_rejected(h):
     assert res.status == M.MDOT_OK
 
 
-@pytest.mark.parametrize("warm_start,smoothing,prec", [(1, 0, 0), (0, 1, 0), (1, 1, 0), (1, 0, 3), (0, 1, 3)])
-def test_solve_ablation_variants_match_oracle(h, warm_start, smoothing, prec):
+# Last-stage tolerances shared by the GPU and the oracle in the variant tests below, so that both
+# stop at the same entropic optimum and the rounded costs must agree to the 1e-7 target:
+# TIGHT where the GPU can finish in fp64 entries (AUTO: n <= 512, or the last fp32 stage polished
+# in fp64), FLOOR (the fp32 floor, mdot_params.fp32_floor) where the tier is forced to fp32.
+TIGHT, FLOOR = 1e-10, 2e-7
+
+
+def _tol_for(prec):
+    return TIGHT if prec in (M.PREC_AUTO, M.PREC_FP64) else FLOOR
+
+
+@pytest.mark.parametrize("warm_start,smoothing,side,prec", [(1, 0, 16, 0), (0, 1, 16, 0), (1, 1, 16, 0),
+                                                            (1, 0, 30, 3), (0, 1, 30, 3), (1, 1, 30, 0)])
+def test_solve_ablation_variants_match_oracle(h, warm_start, smoothing, side, prec):
     """The ablation switches of Sec. 5 (eps-scaling instead of the Eq. (13) warm start; the
-    smoothing weight fixed at its gamma_f value instead of eps_d), on the fp64 tier (n <= 512)
-    and on the accurate fp32 tier (a 30 x 30 grid), against the oracle run with the same switch."""
-    p = I.grid_problem(16 if prec == 0 else 30, 40 + warm_start + 3 * smoothing, kind="l2sq")
+    smoothing weight fixed at its gamma_f value instead of eps_d), on the fp64 tier (n <= 512),
+    on the accurate fp32 tier (a 30 x 30 grid) and on the automatic fp32 tiers with an fp64 last
+    stage, against the oracle run with the same switch and the same last-stage tolerance."""
+    p = I.grid_problem(side, 40 + warm_start + 3 * smoothing, kind="l2sq")
     gamma_f = 2.0 ** 12
-    prm = M.default_params(gamma_f=gamma_f, warm_start=warm_start, smoothing=smoothing, precision=prec)
+    ft = _tol_for(prec)
+    prm = M.default_params(gamma_f=gamma_f, warm_start=warm_start, smoothing=smoothing, precision=prec,
+                           final_tol=ft)
     u, v, res = h.solve(t(p.r), t(p.c), t(p.C), 1e-6, prm)
-    ref = O.solve(p.C.astype(np.float64), p.r, p.c, gamma_f=gamma_f, warm_start=warm_start, smoothing=smoothing)
+    ref = O.solve(p.C.astype(np.float64), p.r, p.c, gamma_f=gamma_f, warm_start=warm_start, smoothing=smoothing,
+                  final_tol=ft)
     assert res.status == M.MDOT_OK, M.status_string(res.status)
-    eps_d = res.info.H_min / gamma_f ** 1.5
-    assert abs(res.cost - ref.cost) <= max(1e-7, eps_d), (res.cost, ref.cost)
+    assert res.info.grad_l1 <= ft
+    assert abs(res.cost - ref.cost) <= 1e-7, (res.cost, ref.cost)
     assert res.info.stages == ref.stats.stages
 
 
-@pytest.mark.parametrize("prec", [0, 3])
-def test_solve_log_n_stopping_matches_oracle(h, prec):
+@pytest.mark.parametrize("side,prec", [(16, 0), (30, 3)])
+def test_solve_log_n_stopping_matches_oracle(h, side, prec):
     """App. C's comparison: log n in place of H_min in the stage tolerance eps_d, against the
-    oracle run with the same switch (fp64 tier on a 16 x 16 grid, accurate fp32 tier on 30 x 30)."""
-    p = I.grid_problem(16 if prec == 0 else 30, 47, kind="l2sq")
+    oracle run with the same switch (fp64 tier on a 16 x 16 grid, accurate fp32 tier on 30 x 30),
+    the last stage at the shared tolerance; the stages before it stop at eps_d / 2 with log n."""
+    p = I.grid_problem(side, 47, kind="l2sq")
     gamma_f = 2.0 ** 12
-    prm = M.default_params(gamma_f=gamma_f, stop_entropy=1, precision=prec)
+    ft = _tol_for(prec)
+    prm = M.default_params(gamma_f=gamma_f, stop_entropy=1, precision=prec, final_tol=ft)
     u, v, res = h.solve(t(p.r), t(p.c), t(p.C), 1e-6, prm)
-    ref = O.solve(p.C.astype(np.float64), p.r, p.c, gamma_f=gamma_f, stop_entropy=1)
+    ref = O.solve(p.C.astype(np.float64), p.r, p.c, gamma_f=gamma_f, stop_entropy=1, final_tol=ft)
     assert res.status == M.MDOT_OK, M.status_string(res.status)
-    eps_d = np.log(p.n) / gamma_f ** 1.5
-    assert abs(res.cost - ref.cost) <= max(1e-7, eps_d), (res.cost, ref.cost)
+    assert abs(res.cost - ref.cost) <= 1e-7, (res.cost, ref.cost)
     assert res.info.stages == ref.stats.stages
-    assert res.info.grad_l1 <= eps_d / 2
+    assert res.info.grad_l1 <= ft
+    # the switch is live: log n loosens every stage tolerance (App. C), fewer evaluations
+    u1, v1, res1 = h.solve(t(p.r), t(p.c), t(p.C), 1e-6, M.default_params(gamma_f=gamma_f, precision=prec,
+                                                                             final_tol=ft))
+    assert res1.info.evals > res.info.evals
 
 
-@pytest.mark.parametrize("side,prec", [(16, 0), (30, 3), (30, 1)])
+@pytest.mark.parametrize("side,prec", [(16, 0), (30, 3), (30, 0)])
 def test_solve_diag_hessian_direction_matches_oracle(h, side, prec):
     """The diagonal-Hessian direction (Eq. (16), taken where every ratio r~/r(P), c~/c(P) lies in
     [0.01, 100], else the Sinkhorn direction) against the oracle run with the same variant: fp64
-    tier, accurate and fast fp32 tiers (barrier-synchronised stage kernel)."""
+    tier (16 x 16), accurate fp32 tier (30 x 30), and the automatic tiers on 30 x 30 (the fast fp32
+    tier for every stage tolerance above 2e-6, then the accurate tier and an fp64 last stage) --
+    the barrier-synchronised stage kernel on each."""
     p = I.grid_problem(side, 48 + prec, kind="l2sq")
     gamma_f = 2.0 ** 12
-    prm = M.default_params(gamma_f=gamma_f, precond=1, precision=prec)
+    ft = _tol_for(prec)
+    prm = M.default_params(gamma_f=gamma_f, precond=1, precision=prec, final_tol=ft)
     u, v, res = h.solve(t(p.r), t(p.c), t(p.C), 1e-6, prm)
-    ref = O.solve(p.C.astype(np.float64), p.r, p.c, gamma_f=gamma_f, precond=1)
+    ref = O.solve(p.C.astype(np.float64), p.r, p.c, gamma_f=gamma_f, precond=1, final_tol=ft)
     assert res.status == M.MDOT_OK, M.status_string(res.status)
-    eps_d = res.info.H_min / gamma_f ** 1.5
-    assert abs(res.cost - ref.cost) <= max(1e-7, eps_d), (res.cost, ref.cost)
+    assert abs(res.cost - ref.cost) <= 1e-7, (res.cost, ref.cost)
     assert res.info.stages == ref.stats.stages
-    if prec == 0:
+    if side == 16:
         # same decisions as the oracle up to rounding: iteration counts agree closely
         assert abs(res.info.iters - ref.stats.iters) <= 0.02 * ref.stats.iters + ref.stats.stages
     # the plain direction on the same problem takes a different path (the switch is live)
-    u0, v0, res0 = h.solve(t(p.r), t(p.c), t(p.C), 1e-6, M.default_params(gamma_f=gamma_f, precision=prec))
+    u0, v0, res0 = h.solve(t(p.r), t(p.c), t(p.C), 1e-6, M.default_params(gamma_f=gamma_f, precision=prec,
+                                                                             final_tol=ft))
     assert res0.info.evals != res.info.evals
 
 
 def test_diag_hessian_direction_regenerated_cost(h):
     p = I.point_cloud_problem(600, 4601)
     gf = 2.0 ** 11
-    prm = M.default_params(gamma_f=gf, precond=1)
+    prm = M.default_params(gamma_f=gf, precond=1, final_tol=TIGHT)
     u, v, res = h.solve_points(t(p.r), t(p.c), t(p.x), t(p.y), M.COST_SQEUCLID, p.scale, 1e-6, prm)
-    ref = O.solve(p.C.astype(np.float64), p.r, p.c, gamma_f=gf, precond=1)
+    ref = O.solve(p.C.astype(np.float64), p.r, p.c, gamma_f=gf, precond=1, final_tol=TIGHT)
     assert res.status == M.MDOT_OK, M.status_string(res.status)
-    eps_d = res.info.H_min / gf ** 1.5
-    assert abs(res.cost - ref.cost) <= max(1e-7, eps_d), (res.cost, ref.cost)
+    assert abs(res.cost - ref.cost) <= 1e-7, (res.cost, ref.cost)

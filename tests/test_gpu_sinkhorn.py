@@ -23,16 +23,21 @@ def h():
         yield handle
 
 
+# The last stage of both sides runs to the same residual (1e-9 where the GPU can finish in fp64
+# entries, the fp32 floor 2e-7 where the tier is forced to fp32), so both stop at the same
+# entropic optimum and the rounded costs must agree to the 1e-7 target.
+TIGHT, FLOOR = 1e-9, 2e-7
+
+
 def _check(res, ref, gf, iter_slack):
     assert res.status == M.MDOT_OK, M.status_string(res.status)
     assert ref.status == 0
-    # both stop anywhere inside ||r(P) - r~||_1 <= eps_d / 2 with c(P) = c~: the rounded costs may
-    # differ by about eps_d (the same argument as for the PNCG projector)
-    eps_d = res.info.H_min / gf ** 1.5
-    assert abs(res.cost - ref.cost) <= max(1e-7, eps_d), (res.cost, ref.cost, eps_d)
+    assert abs(res.cost - ref.cost) <= 1e-7, (res.cost, ref.cost)
     assert res.info.stages == ref.stats.stages
-    # one pass over C per half step, plus the residual pass at the start of each stage
-    assert res.info.evals == ref.stats.stages + 2 * res.info.iters
+    # one pass over C per half step, plus the residual pass at the start of each projection launch
+    # (the stages and, when the last fp32 stage is finished in fp64 entries, that polish)
+    projections = res.info.launches - 3          # less the validation, rounding and bound launches
+    assert res.info.evals == projections + 2 * res.info.iters
     assert res.info.ls_trials == 0
     assert abs(res.info.iters - ref.stats.iters) <= iter_slack * ref.stats.iters + ref.stats.stages, \
         (res.info.iters, ref.stats.iters)
@@ -41,14 +46,16 @@ def _check(res, ref, gf, iter_slack):
 
 # grid 16 on the fp64 tier (n <= 512), grid 24 on the fast fp32 tier (automatic choice, every
 # stage tolerance above the accurate tier's switch), grid 20 forced onto the accurate fp32 tier
+# (whose last stage stops where the fp32 sums' noise lets the residual through: ~10 % slack)
 @pytest.mark.parametrize("side,seed,prec,slack", [(16, 50, M.PREC_AUTO, 0.0), (24, 52, M.PREC_AUTO, 0.05),
-                                                  (20, 53, M.PREC_FP32A, 0.02)])
+                                                  (20, 53, M.PREC_FP32A, 0.1)])
 def test_sinkhorn_projector_matches_oracle(h, side, seed, prec, slack):
     p = I.grid_problem(side, seed, kind="l2sq")
     gf = 2.0 ** 12
-    prm = M.default_params(gamma_f=gf, projector=1, precision=prec)
+    ft = FLOOR if prec == M.PREC_FP32A else TIGHT
+    prm = M.default_params(gamma_f=gf, projector=1, precision=prec, final_tol=ft)
     u, v, res = h.solve(t(p.r), t(p.c), t(p.C), 1e-6, prm)
-    ref = O.solve(p.C.astype(np.float64), p.r, p.c, gamma_f=gf, projector=1)
+    ref = O.solve(p.C.astype(np.float64), p.r, p.c, gamma_f=gf, projector=1, final_tol=ft)
     _check(res, ref, gf, slack)
     if side == 16:
         # the fp64 tier takes the oracle's decisions: the same iterations, dual values to rounding
@@ -61,9 +68,12 @@ def test_sinkhorn_projector_regenerated_cost(h):
     """The same projector with C regenerated from point coordinates (fp64 and accurate fp32)."""
     p = I.point_cloud_problem(300, 4501)
     gf = 2.0 ** 11
-    ref = O.solve(p.C.astype(np.float64), p.r, p.c, gamma_f=gf, projector=1)
-    for prec, slack in ((M.PREC_AUTO, 0.0), (M.PREC_FP32A, 0.02)):
-        prm = M.default_params(gamma_f=gf, projector=1, precision=prec)
+    # fp32 entries: the last stage's residual falls through the floor at a point set by the noise
+    # of the fp32 sums, so its iteration count can differ from the oracle's by ~10 %
+    for prec, slack in ((M.PREC_AUTO, 0.0), (M.PREC_FP32A, 0.1)):
+        ft = FLOOR if prec == M.PREC_FP32A else TIGHT
+        ref = O.solve(p.C.astype(np.float64), p.r, p.c, gamma_f=gf, projector=1, final_tol=ft)
+        prm = M.default_params(gamma_f=gf, projector=1, precision=prec, final_tol=ft)
         u, v, res = h.solve_points(t(p.r), t(p.c), t(p.x), t(p.y), M.COST_SQEUCLID, p.scale, 1e-6, prm)
         _check(res, ref, gf, slack)
 

@@ -439,3 +439,4 @@ def test_point_mass_marginal_has_a_single_feasible_plan():
     one = np.ones(1)
     res1 = O.solve(np.array([[0.3]]), one, one, gamma_f=2.0 ** 10)
     assert abs(res1.cost - 0.3) < 1e-15
+
