@@ -61,6 +61,9 @@ def parse():
 # exact order of the dense cost: 3 differences, 3 products, 2 sums, the scale (9); the exponent
 # argument from the row and column constants (4: two adds, two fmas); the row and column sums (2)
 ALU_OPS_PER_ENTRY = 15
+# with the cost on the tensor cores: the scale of the exact integer distance (1), the exponent
+# argument (4) and the row and column sums (2)
+ALU_OPS_PER_ENTRY_TC = 7
 
 
 def alu_peak_ops():
@@ -363,6 +366,17 @@ def measure_batch(h, dev, stream, sample_single=128):
     h.solve_batch(plist[:8])                                       # warm-up (small subset)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # the fixed tiles (the default variant for every size) ...
+    h.set_batch_tuning(M.BatchTuning())
+    ev0.record(stream)
+    res_fixed = h.solve_batch(plist)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_fixed = ev0.elapsed_time(ev1) / 1e3
+    # ... and the tiles the autotuner picks per size bucket (timed on 8 problems of each bucket)
+    t0 = time.perf_counter()
+    tuned = h.tune_batch(plist, sample=8)
+    t_tune = time.perf_counter() - t0
     ev0.record(stream)
     res = h.solve_batch(plist)
     ev1.record(stream)
@@ -391,6 +405,12 @@ def measure_batch(h, dev, stream, sample_single=128):
     return {"problems": len(probs), "n_range": [min(q["n"] for q in probs), max(q["n"] for q in probs)],
             "eps_target": BATCH_EPS, "cost": "regenerated squared Euclidean (point clouds)",
             "seconds": t_batch, "problems_per_s": len(probs) / t_batch, "ok": ok,
+            "fixed_tiles": {"seconds": t_fixed, "problems_per_s": len(probs) / t_fixed,
+                            "ok": sum(1 for r in res_fixed if r.status == M.MDOT_OK)},
+            "tuning": {**tuned.as_dict(), "seconds": t_tune,
+                       "buckets": ["n<512", "n<1024", "n<2048", "n<4096", "n<=8192"],
+                       "variants": ["256 threads, 1 problem per SM", "128 threads, 2 problems per SM"]},
+            "max_abs_cost_diff_tuned_vs_fixed": max(abs(a.cost - b.cost) for a, b in zip(res, res_fixed)),
             "statuses": {M.status_string(st): sum(1 for r in res if r.status == st) for st in {r.status for r in res}},
             "roofline": {"kernel": "batch_kernel<squared Euclidean> (one CTA per problem)", "bound": "alu",
                          "entries_per_s": entries / t_batch, "ops_per_entry": ALU_OPS_PER_ENTRY,
@@ -671,18 +691,19 @@ def run_ours(args, rank, world):
     xy = torch.from_numpy(I.coords3(q.x)).to(dev)
     uq = torch.from_numpy(np.log(q.r)).to(dev)
     vq = torch.from_numpy(np.log(q.c)).to(dev)
-    lr, _ = h.dual_eval_points(uq, vq, 2.0 ** 12, xy, xy, M.COST_SQEUCLID, q.scale)
-    tk = []
-    for _ in range(10):
-        h.dual_eval_points(uq, vq, 2.0 ** 12, xy, xy, M.COST_SQEUCLID, q.scale, ref_log_rP=lr)
-        tk.append(h.dual_eval_time() / 1e3)
-    kmed = sorted(tk)[len(tk) // 2]
-    ents = float(q.n) * q.n / kmed
     alu_peak = alu_peak_ops()
-    dual["n16384_regen"] = {"us": kmed * 1e6, "entries_per_s": ents, "bound": "alu",
-                            "achieved_ops": ents * ALU_OPS_PER_ENTRY, "peak_ops": alu_peak,
-                            "frac_alu": ents * ALU_OPS_PER_ENTRY / alu_peak,
-                            "ops_per_entry": ALU_OPS_PER_ENTRY}
+    for name, prec, ops in (("n16384_regen", M.PREC_FP32, ALU_OPS_PER_ENTRY),
+                            ("n16384_regen_tensor_cores", M.PREC_FP32 | M.PREC_TENSOR_CORES, ALU_OPS_PER_ENTRY_TC)):
+        lr, _ = h.dual_eval_points(uq, vq, 2.0 ** 12, xy, xy, M.COST_SQEUCLID, q.scale, precision=prec)
+        tk = []
+        for _ in range(10):
+            h.dual_eval_points(uq, vq, 2.0 ** 12, xy, xy, M.COST_SQEUCLID, q.scale, ref_log_rP=lr, precision=prec)
+            tk.append(h.dual_eval_time() / 1e3)
+        kmed = sorted(tk)[len(tk) // 2]
+        ents = float(q.n) * q.n / kmed
+        dual[name] = {"us": kmed * 1e6, "entries_per_s": ents, "bound": "alu",
+                      "achieved_ops": ents * ops, "peak_ops": alu_peak, "frac_alu": ents * ops / alu_peak,
+                      "ops_per_entry": ops}
 
     sweep = gap_sweep(h, dev, stream) if (rank == 0 and not args.no_sweep) else None
     batch = measure_batch(h, dev, stream) if (rank == 0 and not args.no_batch) else None
@@ -708,6 +729,11 @@ def run_ours(args, rank, world):
     g = golden_case()
     exact = exact_value()
     true_gap = (res.cost - exact) if exact is not None else None
+    # a certificate of the target without the exact LP: the c-transform bound of a solve at
+    # gamma_f = 2^21 is a feasible OT dual (weak duality), so OT >= lb_hi and the benchmark solve's
+    # true gap is at most cost - lb_hi
+    _, _, res_hi = h.solve(r, c, C, EPS, M.default_params(gamma_f=2.0 ** 21), check=False)
+    lb_hi = res_hi.cost - res_hi.gap_cert
     cpu = None
     if rank == 0 and world == 1:
         n_evals = args.cpu_sample_evals or 40
@@ -731,6 +757,8 @@ def run_ours(args, rank, world):
                        "l2": "flushed (256 MiB write) between timed steps", "replicas": world},
             "result": {"status": M.status_string(res.status), "cost": res.cost,
                        "true_gap": true_gap, "gap_cert": res.gap_cert,
+                       "true_gap_bound": res.cost - lb_hi,
+                       "true_gap_bound_how": "cost - c-transform lower bound of a gamma_f = 2^21 solve (weak duality)",
                        "oracle_cost": g["oracle_cost"] if g else None,
                        "cost_minus_oracle": (res.cost - g["oracle_cost"]) if g else None,
                        "evals": info.evals, "evals_fp64": info.evals_fp64, "iters": info.iters,
@@ -895,7 +923,12 @@ def run_case(args):
         r = torch.from_numpy(p.r).to(dev)
         c = torch.from_numpy(p.c).to(dev)
         for _ in range(args.reps):
-            h.solve(r, c, C, EPS)
+            h.solve(r, c, C, EPS, M.default_params(profile=1))
+        # the evaluations of every stage launch, counted by the kernel itself (State.evals): a
+        # profiler's per-launch time divided by these gives its time per evaluation
+        torch.cuda.synchronize()
+        print(json.dumps({"stage_launches": [{"launch": q, "kind": t["kind"], "evals": t["evals"]}
+                                             for q, t in enumerate(h.solve_trace())]}))
     torch.cuda.synchronize()
     h.close()
     print(f"case {args.case} n={p.n} reps={args.reps} done")

@@ -50,7 +50,9 @@ typedef enum mdot_status {
 } mdot_status;
 
 /* Arithmetic used for the per-entry work of a dual evaluation (the O(n) work, the line-search test,
- * rounding sums and the bound are fp64 in every mode). */
+ * rounding sums and the bound are fp64 in every mode).  The `precision` argument of the
+ * *_dual_eval* calls may be OR'ed with MDOT_PREC_TENSOR_CORES (see mdot_params.tensor_cores). */
+#define MDOT_PREC_TENSOR_CORES 256
 typedef enum mdot_precision {
     MDOT_PREC_AUTO = 0,   /* fp32 entries while its noise floor is below the stage tolerance,
                              fp64 entries for the final stage when it is not (and for n <= 512) */
@@ -108,7 +110,10 @@ typedef struct mdot_params {
                                flag, a grid barrier), in microseconds; <= 0: 2 seconds.  A wait that
                                runs out ends the call with MDOT_ERR_TIMEOUT (outputs hold the last
                                iterate) and leaves the handle usable                                */
-    int32_t reserved;
+    int32_t tensor_cores;   /* 1: the regenerated squared-Euclidean cost of integer points
+                               (|coordinate| <= 255, e.g. grid data) on the tensor cores, exact (see
+                               mdot_cost_matrix); 0 (default): fp32 operations, measured faster on
+                               GB300 because the pass is bound by the exponentials and sums      */
 } mdot_params;
 
 /* Diagnostics of one solve. */
@@ -309,7 +314,8 @@ typedef struct mdot_result {
 
 /*
  * Solve nprob independent problems (host array probs, each with device data) in one persistent
- * launch per cost form: every CTA takes the next problem from a work queue (largest n first) and
+ * launch per cost form and tile variant (see mdot_batch_tuning; by default one variant): every CTA
+ * takes the next problem from a work queue (largest n first) and
  * runs the whole of Alg. 1 + Alg. 3 on it (PNCG projections, line search, rounding, bound) with
  * block-level synchronisation.  Each problem gets its own gamma schedule (from its eps_target or
  * gamma_f), potentials and line-search state; a problem's result does not depend on the rest of
@@ -321,6 +327,29 @@ typedef struct mdot_result {
  */
 mdot_status mdot_solve_batch(mdot_handle* h, int32_t nprob, const mdot_problem* probs,
                              const mdot_params* prm, mdot_result* results);
+
+/* Tile variants of the batched form, one per problem-size bucket (n < 512, < 1024, < 2048, < 4096,
+ * <= MDOT_BATCH_MAX_N): 0 ("wide") 256 threads per problem, one problem per SM; 1 ("narrow") 128
+ * threads per problem, two problems per SM.  A new handle uses 0 for every bucket. */
+typedef struct mdot_batch_tuning {
+    int32_t variant[5];
+    int32_t reserved;
+    double  problems_per_s[5][2];   /* measured by mdot_tune_batch, per bucket and variant (0: not timed) */
+} mdot_batch_tuning;
+
+/*
+ * The tile autotuner of the batched form: for every size bucket that probs (host array, device data)
+ * populates, times each variant on up to `sample` of the bucket's problems, repeated to fill every
+ * CTA of the wider grid twice, solved to gamma_f = min(their gamma_f, 2^12) without writing
+ * potentials (CUDA events around the launches), and keeps the faster variant in the handle's table
+ * for later mdot_solve_batch calls.  *out (host) receives the table and the measured rates.
+ * Errors as mdot_solve_batch.
+ */
+mdot_status mdot_tune_batch(mdot_handle* h, int32_t nprob, const mdot_problem* probs, const mdot_params* prm,
+                            int32_t sample, mdot_batch_tuning* out);
+
+/* Install a stored tuning table (e.g. from an earlier mdot_tune_batch) in the handle. */
+mdot_status mdot_set_batch_tuning(mdot_handle* h, const mdot_batch_tuning* t);
 
 /*
  * Serving: a request loop with continuous batching (the paper has no counterpart).  mdot_server_create starts a background worker on the current device with a

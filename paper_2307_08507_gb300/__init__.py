@@ -23,6 +23,7 @@ MDOT_ERR_TIMEOUT = 4
 MDOT_ERR_OOM = 5
 MDOT_ERR_CUDA = 6
 PREC_AUTO, PREC_FP32, PREC_FP64, PREC_FP32A = 0, 1, 2, 3
+PREC_TENSOR_CORES = 256      # OR'ed into a dual evaluation's precision: grid costs on the tensor cores
 COST_SQEUCLID, COST_L1 = 1, 2
 
 
@@ -33,7 +34,7 @@ class Params(ct.Structure):
                 ("warm_start", ct.c_int32), ("final_tol", ct.c_double), ("fp32_floor", ct.c_double),
                 ("profile", ct.c_int32), ("smoothing", ct.c_int32), ("projector", ct.c_int32),
                 ("stop_entropy", ct.c_int32), ("precond", ct.c_int32), ("ls_init", ct.c_int32),
-                ("wait_limit_us", ct.c_int32), ("reserved", ct.c_int32)]
+                ("wait_limit_us", ct.c_int32), ("tensor_cores", ct.c_int32)]
 
 
 class Info(ct.Structure):
@@ -450,6 +451,48 @@ def _solve_batch(self, problems, params: Params | None = None):
 
 
 Handle.solve_batch = _solve_batch
+
+
+class BatchTuning(ct.Structure):
+    """mdot_batch_tuning: the batched form's tile variant per size bucket and the measured rates."""
+    _fields_ = [("variant", ct.c_int32 * 5), ("reserved", ct.c_int32), ("problems_per_s", (ct.c_double * 2) * 5)]
+
+    def as_dict(self) -> dict:
+        return {"variant": list(self.variant), "problems_per_s": [list(r) for r in self.problems_per_s]}
+
+
+def _tune_batch(self, problems, params: Params | None = None, sample: int = 16) -> BatchTuning:
+    """mdot_tune_batch: time each tile variant per size bucket and keep the faster (in the handle)."""
+    L = _batch_lib()
+    if not hasattr(L, "_tune_typed"):
+        L.mdot_tune_batch.argtypes = [_P, ct.c_int32, ct.POINTER(Problem), ct.POINTER(Params), ct.c_int32,
+                                      ct.POINTER(BatchTuning)]
+        L.mdot_tune_batch.restype = ct.c_int32
+        L.mdot_set_batch_tuning.argtypes = [_P, ct.POINTER(BatchTuning)]
+        L.mdot_set_batch_tuning.restype = ct.c_int32
+        L._tune_typed = True
+    k = len(problems)
+    arr = (Problem * k)(*problems)
+    out = BatchTuning()
+    s = L.mdot_tune_batch(self._h, k, arr, ct.byref(params) if params is not None else None, int(sample),
+                          ct.byref(out))
+    if s != MDOT_OK:
+        raise MdotError(s, "mdot_tune_batch")
+    return out
+
+
+def _set_batch_tuning(self, table: BatchTuning):
+    """mdot_set_batch_tuning: install a stored table of tile variants in the handle."""
+    L = _batch_lib()
+    L.mdot_set_batch_tuning.argtypes = [_P, ct.POINTER(BatchTuning)]
+    L.mdot_set_batch_tuning.restype = ct.c_int32
+    s = L.mdot_set_batch_tuning(self._h, ct.byref(table))
+    if s != MDOT_OK:
+        raise MdotError(s, "mdot_set_batch_tuning")
+
+
+Handle.tune_batch = _tune_batch
+Handle.set_batch_tuning = _set_batch_tuning
 
 
 MDOT_NOT_READY = 7

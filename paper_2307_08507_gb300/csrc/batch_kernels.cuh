@@ -12,8 +12,17 @@
 namespace mdot {
 
 constexpr int kBatchMaxN = 8192;
-constexpr int kBatchThreads = 256;
+constexpr int kBatchThreads = 256;     // threads of the default ("wide") variant
 constexpr int kRowChunk = 4096;        // rows whose per-warp partial sums sit in shared memory at once
+
+// Tile variants of the batched kernel, chosen per problem-size bucket by mdot_tune_batch:
+// 0 ("wide"): 256 threads, one CTA (problem) per SM; 1 ("narrow"): 128 threads, two CTAs
+// (problems) per SM -- half the warps per problem, twice the problems in flight.
+constexpr int kBatchVariants = 2;
+__host__ __device__ constexpr int batch_threads(int variant) { return variant == 1 ? 128 : 256; }
+// problem-size buckets of the tuning table: n < 512, < 1024, < 2048, < 4096, <= kBatchMaxN
+constexpr int kBatchBuckets = 5;
+__host__ __device__ inline int batch_bucket(int n) { return n < 512 ? 0 : n < 1024 ? 1 : n < 2048 ? 2 : n < 4096 ? 3 : 4; }
 
 struct BatchProblem {
     int n, kind;               // size, CostKind
@@ -53,6 +62,7 @@ struct BatchArgs {
     // parameters of Alg. 1 / App. B
     double gamma_i, p, q, c1, c2, fp32_floor, final_tol;
     int ls_max_trials, max_iter, warm_start, precision, smoothing, ls_init;
+    int tensor_cores;          // 1: integer-point squared-Euclidean costs on the tensor cores
 };
 
 // slot layout (vectors of `stride` elements): 18 fp64 vectors, then 7 fp32 / int32 vectors
@@ -66,12 +76,12 @@ struct BatchSmem {
     size_t off_row, off_stage, bytes;
 };
 
-__host__ __device__ inline BatchSmem batch_smem()
+__host__ __device__ inline BatchSmem batch_smem(int threads)
 {
     BatchSmem L;
     L.off_row = 0;
-    L.off_stage = (size_t)(kBatchThreads / 32) * kRowChunk * 4;     // per-warp row partials of one chunk
-    L.bytes = L.off_stage + (size_t)tc_stage_floats(kBatchThreads / 32) * 4;   // tensor-core column blocks
+    L.off_stage = (size_t)(threads / 32) * kRowChunk * 4;            // per-warp row partials of one chunk
+    L.bytes = L.off_stage + (size_t)tc_stage_floats(threads / 32) * 4;    // tensor-core column blocks
     return L;
 }
 
@@ -160,15 +170,15 @@ __device__ __forceinline__ void batch_prep_row(double ua, int A, double inv_gamm
     sA[i] = A;
 }
 
-template <int COST>
-__global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a)
+template <int COST, int THREADS>
+__global__ void __launch_bounds__(THREADS, THREADS == 128 ? 2 : 1) batch_kernel(BatchArgs a)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ double red_smem[32 * kNRed];
     __shared__ double s_bc[8];
     __shared__ State st;
     __shared__ int s_prob;
-    const BatchSmem L = batch_smem();
+    const BatchSmem L = batch_smem(THREADS);
     float* sRow = reinterpret_cast<float*>(sm + L.off_row);
     float* sStage = reinterpret_cast<float*>(sm + L.off_stage);
     const int tid = threadIdx.x, T = blockDim.x, nw = T >> 5, lane = tid & 31, warp = tid >> 5;
@@ -230,7 +240,7 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchArgs a)
         const double H = s_bc[0], gf = s_bc[1];
         // squared-Euclidean cost of integer points (|coordinate| <= 255): the tensor-core form
         bool tc = false;
-        if (COST == COST_SQEUCLID && s_bc[2] == 0.0) {
+        if (COST == COST_SQEUCLID && a.tensor_cores && s_bc[2] == 0.0) {
             bool ok = true;
             for (int q = tid; q < 3 * n; q += T) {
                 const float xv = __ldg(P.X + q), yv = __ldg(P.Y + q);

@@ -46,9 +46,10 @@ struct mdot_handle {
     double *d_r = nullptr, *d_c = nullptr, *d_u = nullptr, *d_v = nullptr;
     float* d_C = nullptr;
     int64_t host_n = 0;
-    // batched solver workspace (allocated on first use)
+    // batched solver workspace (allocated on first use) and its tile-variant table per size bucket
     double* b_slots = nullptr;
-    int b_grid = 0;
+    int b_grid[kBatchVariants] = {0, 0};
+    int b_variant[kBatchBuckets] = {0, 0, 0, 0, 0};
     BatchProblem* b_probs = nullptr;
     BatchResult* b_results = nullptr;
     int* b_order = nullptr;
@@ -74,9 +75,7 @@ struct mdot_handle {
 };
 
 namespace mdot {
-size_t batch_smem_bytes();
-cudaError_t configure_batch_kernels(int* blocks_per_sm);
-cudaError_t launch_batch(int kind, int grid, const BatchArgs& a, cudaStream_t s);
+
 }
 
 #define CKR(call)                                                                                  \
@@ -110,6 +109,7 @@ void mdot_default_params(mdot_params* prm)
     prm->profile = 0;
     prm->ls_init = 1;                    // App. B leaves the first trial step open (see mdot.h)
     prm->wait_limit_us = 0;              // bounded device waits: the 2 s default
+    prm->tensor_cores = 0;               // grid costs in fp32 operations (measured faster)
 }
 
 const char* mdot_status_string(int32_t s)
@@ -249,7 +249,7 @@ mdot_status params_ok(const mdot_params& P)
         P.precision < 0 || P.precision > 3 || P.warm_start < 0 || P.warm_start > 2 ||
         P.smoothing < 0 || P.smoothing > 1 || P.projector < 0 || P.projector > 1 || P.stop_entropy < 0 ||
         P.stop_entropy > 1 || P.precond < 0 || P.precond > 1 || P.ls_init < 0 || P.ls_init > 1 ||
-        !(P.fp32_floor >= 0.0) || !std::isfinite(P.gamma_f))
+        !(P.fp32_floor >= 0.0) || !std::isfinite(P.gamma_f) || P.tensor_cores < 0 || P.tensor_cores > 1)
         return MDOT_ERR_INVALID_ARG;
     return MDOT_OK;
 }
@@ -376,11 +376,11 @@ mdot_status check_marginals(mdot_handle* h, const WS& ws, double* H)
 }
 
 // The squared-Euclidean cost of integer points (|coordinate| <= 255) runs on the tensor cores
-// (exact: see pass_f32_regen_tc); one check of the coordinates per call.
-cudaError_t select_cost_form(mdot_handle* h, WS& ws)
+// when the caller allows it (exact: see pass_f32_regen_tc); one check of the coordinates per call.
+cudaError_t select_cost_form(mdot_handle* h, WS& ws, bool allow)
 {
     ws.tc = 0;
-    if (ws.ckind != COST_SQEUCLID) return cudaSuccess;
+    if (ws.ckind != COST_SQEUCLID || !allow) return cudaSuccess;
     bool grid = false;
     cudaError_t e = check_grid_points(ws.X, ws.Y, ws.n, reinterpret_cast<unsigned int*>(h->d_out + 14),
                                       reinterpret_cast<unsigned int*>(h->h_out + 14), h->stream, &grid);
@@ -427,7 +427,7 @@ mdot_status solve_core(mdot_handle* h, const double* r, const double* c, const C
     double H = 0.0;
     mdot_status ms = check_marginals(h, ws, &H);
     if (ms != MDOT_OK) return ms;
-    CKR(select_cost_form(h, ws));
+    CKR(select_cost_form(h, ws, P.tensor_cores != 0));
     const double gf = (P.gamma_f > 0.0) ? P.gamma_f : gamma_f_for_eps(H, eps_target, P.gamma_i, P.q, P.p);
     // precision tiers: fp64 entries for small n; otherwise fp32 entries with ex2.approx while the
     // stage tolerance is loose, the accurate fp32 tier (double-float exponent, polynomial exp2)
@@ -670,13 +670,15 @@ static mdot_status dual_eval_core(mdot_handle* h, const double* u, const double*
                                   double* log_rP, double* log_cP, const double* r, const double* c,
                                   double* g_out)
 {
+    const int32_t tier_bits = precision & ~MDOT_PREC_TENSOR_CORES;
     if (!h || !u || !v || !cs.valid() || !log_rP || !log_cP || n < 1 || n > h->max_n || !(gamma > 0.0) ||
-        !std::isfinite(gamma) || precision < 0 || precision > 3 || (g_out && (!r || !c)))
+        !std::isfinite(gamma) || tier_bits < 0 || tier_bits > 3 || (g_out && (!r || !c)))
         return MDOT_ERR_INVALID_ARG;
     WS ws = h->ws;
     ws.n = (int)n;
     cs.apply(ws);
-    CKR(select_cost_form(h, ws));
+    CKR(select_cost_form(h, ws, (precision & MDOT_PREC_TENSOR_CORES) != 0));
+    precision &= ~MDOT_PREC_TENSOR_CORES;
     EvalArgs a{};
     a.gamma = gamma;
     a.G64 = gamma * kLog2e;
@@ -710,17 +712,14 @@ static mdot_status dual_eval_core(mdot_handle* h, const double* u, const double*
     return MDOT_OK;
 }
 
-mdot_status mdot_solve_batch(mdot_handle* h, int32_t nprob, const mdot_problem* probs, const mdot_params* prm,
-                             mdot_result* results)
+}  // extern "C"
+
+namespace {
+
+// mdot_problem -> BatchProblem; INVALID_ARG if malformed
+mdot_status batch_problems(int32_t nprob, const mdot_problem* probs, std::vector<BatchProblem>& bp)
 {
-    if (!h || nprob < 0 || (nprob > 0 && (!probs || !results))) return MDOT_ERR_INVALID_ARG;
-    if (nprob == 0) return MDOT_OK;
-    mdot_params P;
-    if (prm) P = *prm; else mdot_default_params(&P);
-    if (params_ok(P) != MDOT_OK || P.precision == MDOT_PREC_FP64 || P.projector != 0 || P.stop_entropy != 0 ||
-        P.precond != 0)
-        return MDOT_ERR_INVALID_ARG;
-    std::vector<BatchProblem> bp(nprob);
+    bp.assign(nprob, BatchProblem{});
     for (int k = 0; k < nprob; ++k) {
         const mdot_problem& q = probs[k];
         BatchProblem& b = bp[k];
@@ -739,12 +738,35 @@ mdot_status mdot_solve_batch(mdot_handle* h, int32_t nprob, const mdot_problem* 
         b.r = q.r; b.c = q.c; b.C = q.C; b.X = q.x; b.Y = q.y;
         b.u_out = q.u_out; b.v_out = q.v_out;
     }
+    return MDOT_OK;
+}
+
+mdot_status batch_params(const mdot_params* prm, mdot_params& P)
+{
+    if (prm) P = *prm; else mdot_default_params(&P);
+    if (params_ok(P) != MDOT_OK || P.precision == MDOT_PREC_FP64 || P.projector != 0 || P.stop_entropy != 0 ||
+        P.precond != 0)
+        return MDOT_ERR_INVALID_ARG;
+    return MDOT_OK;
+}
+
+// The batched solve of bp: one persistent launch per (cost form, tile variant) -- the variant of a
+// problem is the handle's table entry for its size bucket, or `forced` (>= 0) for every problem;
+// inside a launch, problems by decreasing n.  *ms (nullable): device time of all launches.
+mdot_status batch_core(mdot_handle* h, const std::vector<BatchProblem>& bp, const mdot_params& P,
+                       std::vector<BatchResult>& br, int forced, double* ms)
+{
+    const int nprob = (int)bp.size();
     if (!h->b_slots) {
-        int bps = 0;
-        CKR(configure_batch_kernels(&bps));
-        if (bps < 1) return MDOT_ERR_INVALID_ARG;
-        h->b_grid = h->sms * bps;
-        if (cudaMalloc(&h->b_slots, (size_t)h->b_grid * kSlotDoubles * sizeof(double)) != cudaSuccess ||
+        int bps[kBatchVariants] = {0, 0};
+        CKR(configure_batch_kernels(bps));
+        int grid_max = 0;
+        for (int v = 0; v < kBatchVariants; ++v) {
+            if (bps[v] < 1) return MDOT_ERR_INVALID_ARG;
+            h->b_grid[v] = h->sms * bps[v];
+            grid_max = std::max(grid_max, h->b_grid[v]);
+        }
+        if (cudaMalloc(&h->b_slots, (size_t)grid_max * kSlotDoubles * sizeof(double)) != cudaSuccess ||
             cudaMalloc(&h->b_next, 4 * sizeof(unsigned int)) != cudaSuccess) {
             snprintf(g_err, sizeof g_err, "batch workspace allocation failed");
             return MDOT_ERR_OOM;
@@ -761,36 +783,71 @@ mdot_status mdot_solve_batch(mdot_handle* h, int32_t nprob, const mdot_problem* 
         }
         h->b_cap = nprob;
     }
-    // one launch per cost form; inside it, problems by decreasing n (longest first)
-    std::vector<BatchResult> br(nprob);
+    br.assign(nprob, BatchResult{});
     CKR(cudaMemcpyAsync(h->b_probs, bp.data(), nprob * sizeof(BatchProblem), cudaMemcpyHostToDevice, h->stream));
+    if (!h->de_ev[0]) {
+        CKR(cudaEventCreate(&h->de_ev[0]));
+        CKR(cudaEventCreate(&h->de_ev[1]));
+    }
+    double total_ms = 0.0;
     for (int kind = 0; kind < 3; ++kind) {
-        std::vector<int> order;
-        for (int k = 0; k < nprob; ++k)
-            if (bp[k].kind == kind) order.push_back(k);
-        if (order.empty()) continue;
-        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return bp[x].n > bp[y].n; });
-        CKR(cudaMemcpyAsync(h->b_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
-        CKR(cudaMemsetAsync(h->b_next, 0, sizeof(unsigned int), h->stream));
-        BatchArgs a{};
-        a.nprob = (int)order.size();
-        a.probs = h->b_probs;
-        a.results = h->b_results;
-        a.order = h->b_order;
-        a.next = h->b_next;
-        a.slots = h->b_slots;
-        a.slot_doubles = kSlotDoubles;
-        a.gamma_i = P.gamma_i; a.p = P.p; a.q = P.q; a.c1 = P.ls_c1; a.c2 = P.ls_c2;
-        a.fp32_floor = P.fp32_floor; a.final_tol = P.final_tol;
-        a.ls_max_trials = P.ls_max_trials; a.max_iter = P.max_iter; a.warm_start = P.warm_start;
-        a.precision = P.precision;
-        a.smoothing = P.smoothing;
-        a.ls_init = P.ls_init;
-        CKR(launch_batch(kind, h->b_grid, a, h->stream));
-        CKR(cudaStreamSynchronize(h->stream));     // the order buffer is reused by the next form
+        for (int v = 0; v < kBatchVariants; ++v) {
+            std::vector<int> order;
+            for (int k = 0; k < nprob; ++k) {
+                const int vk = forced >= 0 ? forced : h->b_variant[batch_bucket(bp[k].n)];
+                if (bp[k].kind == kind && vk == v) order.push_back(k);
+            }
+            if (order.empty()) continue;
+            std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return bp[x].n > bp[y].n; });
+            CKR(cudaMemcpyAsync(h->b_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                h->stream));
+            CKR(cudaMemsetAsync(h->b_next, 0, sizeof(unsigned int), h->stream));
+            BatchArgs a{};
+            a.nprob = (int)order.size();
+            a.probs = h->b_probs;
+            a.results = h->b_results;
+            a.order = h->b_order;
+            a.next = h->b_next;
+            a.slots = h->b_slots;
+            a.slot_doubles = kSlotDoubles;
+            a.gamma_i = P.gamma_i; a.p = P.p; a.q = P.q; a.c1 = P.ls_c1; a.c2 = P.ls_c2;
+            a.fp32_floor = P.fp32_floor; a.final_tol = P.final_tol;
+            a.ls_max_trials = P.ls_max_trials; a.max_iter = P.max_iter; a.warm_start = P.warm_start;
+            a.precision = P.precision;
+            a.smoothing = P.smoothing;
+            a.ls_init = P.ls_init;
+            a.tensor_cores = P.tensor_cores;
+            CKR(cudaEventRecord(h->de_ev[0], h->stream));
+            CKR(launch_batch(kind, v, std::min(h->b_grid[v], a.nprob), a, h->stream));
+            CKR(cudaEventRecord(h->de_ev[1], h->stream));
+            CKR(cudaStreamSynchronize(h->stream));     // the order buffer is reused by the next launch
+            float t = 0.0f;
+            CKR(cudaEventElapsedTime(&t, h->de_ev[0], h->de_ev[1]));
+            total_ms += t;
+        }
     }
     CKR(cudaMemcpyAsync(br.data(), h->b_results, nprob * sizeof(BatchResult), cudaMemcpyDeviceToHost, h->stream));
     CKR(cudaStreamSynchronize(h->stream));
+    if (ms) *ms = total_ms;
+    return MDOT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mdot_status mdot_solve_batch(mdot_handle* h, int32_t nprob, const mdot_problem* probs, const mdot_params* prm,
+                             mdot_result* results)
+{
+    if (!h || nprob < 0 || (nprob > 0 && (!probs || !results))) return MDOT_ERR_INVALID_ARG;
+    if (nprob == 0) return MDOT_OK;
+    mdot_params P;
+    if (batch_params(prm, P) != MDOT_OK) return MDOT_ERR_INVALID_ARG;
+    std::vector<BatchProblem> bp;
+    if (batch_problems(nprob, probs, bp) != MDOT_OK) return MDOT_ERR_INVALID_ARG;
+    std::vector<BatchResult> br;
+    const mdot_status st = batch_core(h, bp, P, br, -1, nullptr);
+    if (st != MDOT_OK) return st;
     for (int k = 0; k < nprob; ++k) {
         const BatchResult& b = br[k];
         mdot_result& r = results[k];
@@ -807,6 +864,66 @@ mdot_status mdot_solve_batch(mdot_handle* h, int32_t nprob, const mdot_problem* 
         r.gamma_f = b.gamma_f;
         r.H_min = b.H_min;
     }
+    return MDOT_OK;
+}
+
+mdot_status mdot_tune_batch(mdot_handle* h, int32_t nprob, const mdot_problem* probs, const mdot_params* prm,
+                            int32_t sample, mdot_batch_tuning* out)
+{
+    if (!h || nprob < 1 || !probs || !out || sample < 1) return MDOT_ERR_INVALID_ARG;
+    mdot_params P;
+    if (batch_params(prm, P) != MDOT_OK) return MDOT_ERR_INVALID_ARG;
+    std::vector<BatchProblem> bp;
+    if (batch_problems(nprob, probs, bp) != MDOT_OK) return MDOT_ERR_INVALID_ARG;
+    memset(out, 0, sizeof(*out));
+    for (int b = 0; b < kBatchBuckets; ++b) out->variant[b] = h->b_variant[b];
+    // the tuning launches write no potentials and stop at gamma_f <= 2^12 (the variants' relative
+    // speed is that of the per-evaluation work, not of the schedule's length)
+    for (BatchProblem& q : bp) {
+        q.u_out = nullptr;
+        q.v_out = nullptr;
+        if (!(q.gamma_f > 0.0) || q.gamma_f > 4096.0) q.gamma_f = 4096.0;
+    }
+    for (int b = 0; b < kBatchBuckets; ++b) {
+        std::vector<BatchProblem> pick;
+        for (const BatchProblem& q : bp)
+            if (batch_bucket(q.n) == b && (int)pick.size() < sample) pick.push_back(q);
+        if (pick.empty()) continue;
+        double best = -1.0;
+        for (int v = 0; v < kBatchVariants; ++v) {
+            // enough copies of the sample to fill every CTA slot of the wider grid, twice
+            std::vector<BatchProblem> fill;
+            int want = 0;
+            if (h->b_slots == nullptr) {
+                int bps[kBatchVariants] = {0, 0};
+                CKR(configure_batch_kernels(bps));
+                for (int w = 0; w < kBatchVariants; ++w) want = std::max(want, 2 * h->sms * bps[w]);
+            } else {
+                for (int w = 0; w < kBatchVariants; ++w) want = std::max(want, 2 * h->b_grid[w]);
+            }
+            for (int k = 0; k < want; ++k) fill.push_back(pick[k % pick.size()]);
+            std::vector<BatchResult> br;
+            double ms = 0.0;
+            const mdot_status st = batch_core(h, fill, P, br, v, &ms);
+            if (st != MDOT_OK) return st;
+            const double rate = ms > 0.0 ? 1e3 * (double)fill.size() / ms : 0.0;
+            out->problems_per_s[b][v] = rate;
+            if (rate > best) {
+                best = rate;
+                out->variant[b] = v;
+            }
+        }
+        h->b_variant[b] = out->variant[b];
+    }
+    return MDOT_OK;
+}
+
+mdot_status mdot_set_batch_tuning(mdot_handle* h, const mdot_batch_tuning* t)
+{
+    if (!h || !t) return MDOT_ERR_INVALID_ARG;
+    for (int b = 0; b < kBatchBuckets; ++b)
+        if (t->variant[b] < 0 || t->variant[b] >= kBatchVariants) return MDOT_ERR_INVALID_ARG;
+    for (int b = 0; b < kBatchBuckets; ++b) h->b_variant[b] = t->variant[b];
     return MDOT_OK;
 }
 

@@ -55,8 +55,8 @@ cudaError_t launch_validate(const WS& ws, double* out, cudaStream_t s);
 cudaError_t check_grid_points(const float* X, const float* Y, int n, unsigned int* d_flag, unsigned int* h_flag,
                               cudaStream_t st, bool* grid);
 
-// batched solver (k_batch.cu)
+// batched solver (k_batch.cu): blocks_per_sm has one entry per tile variant (kBatchVariants)
 cudaError_t configure_batch_kernels(int* blocks_per_sm);
-cudaError_t launch_batch(int kind, int grid, const BatchArgs& a, cudaStream_t s);
+cudaError_t launch_batch(int kind, int variant, int grid, const BatchArgs& a, cudaStream_t s);
 
 }  // namespace mdot

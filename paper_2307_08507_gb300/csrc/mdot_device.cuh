@@ -228,24 +228,9 @@ __device__ __forceinline__ float2 unpk_bits(unsigned long long r)
     return a;
 }
 __device__ __forceinline__ float2 pk(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b)
-{
-    unsigned long long r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk_bits(a)), "l"(pk_bits(b)));
-    return unpk_bits(r);
-}
-__device__ __forceinline__ float2 mul2(float2 a, float2 b)
-{
-    unsigned long long r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk_bits(a)), "l"(pk_bits(b)));
-    return unpk_bits(r);
-}
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
-{
-    unsigned long long r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(pk_bits(a)), "l"(pk_bits(b)), "l"(pk_bits(c)));
-    return unpk_bits(r);
-}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 // a - b with one rounding: b * (-1) is exact inside the fma
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return fma2(b, make_float2(-1.0f, -1.0f), a); }
 
@@ -1352,7 +1337,7 @@ __device__ __forceinline__ void tc_b_regs(float y0, float y1, float y2, int t, u
 // mma.sync give the costs, every lane forms its 2 rows x 8 columns of entries (the exponent and the
 // sums as in entry2), the row partials are added over the 4 lanes of a row, and the column
 // partials, folded every kFoldRows rows (fold2), over the 8 row groups at the end of the sweep.
-constexpr int kTcSubs = 8;             // 32-column sub-blocks per warp and column block
+constexpr int kTcSubs = 16;            // 32-column sub-blocks per warp and column block
 constexpr int kTcStageFloats = 5;      // hh, wc, y0, y1, y2 per staged column
 __host__ __device__ constexpr int tc_block_cols(int warps) { return warps * kTcSubs * 32; }
 __host__ __device__ constexpr int tc_stage_floats(int warps) { return kTcStageFloats * tc_block_cols(warps); }
@@ -1442,36 +1427,29 @@ __device__ __forceinline__ void pass_f32_regen_tc(const float* __restrict__ Y, f
                 wc2[q] = make_float2(stW[jc], stW[jc + 1]);
                 ca2[q] = fh2[q] = fl2[q] = make_float2(0.0f, 0.0f);
             }
-            // two row tiles per step when both exist: their instruction streams interleave
+            // two row tiles per step, in one basic block so that their instruction streams
+            // interleave (a tile past the last row is all padding: its entries are 0)
             for (int rt = 0; rt < nrows; rt += 32) {
                 float rp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int base = rt + 16 * h;
-                    if (base >= nrows) break;                   // warp-uniform
                     const int il0 = base + g, il1 = base + g + 8;
-                    unsigned int a0 = 0u, a1 = 0u, a2 = 0u, a3 = 0u;
-                    float fh0 = 0.0f, wr0 = kPadW, s0 = 0.0f, fh1 = 0.0f, wr1 = kPadW, s1 = 0.0f;
-                    if (il0 < nrows) {
-                        if (sA4 != nullptr) {
-                            const uint2 v = sA4[4 * il0 + t];
-                            a0 = v.x;
-                            a2 = v.y;
-                        } else {
-                            tc_a_regs(sX[3 * il0], sX[3 * il0 + 1], sX[3 * il0 + 2], t, a0, a2);
-                        }
-                        fh0 = sFh[il0]; wr0 = sWr[il0]; s0 = sS[il0];
+                    // rows past the last are padding: read the last row and select zero A registers
+                    // and constants whose entries are 0 (selects, no divergent branches)
+                    const bool ok0 = il0 < nrows, ok1 = il1 < nrows;
+                    const int ic0 = ok0 ? il0 : nrows - 1, ic1 = ok1 ? il1 : nrows - 1;
+                    unsigned int a0, a1, a2, a3;
+                    if (sA4 != nullptr) {
+                        const uint2 v0 = sA4[4 * ic0 + t], v1 = sA4[4 * ic1 + t];
+                        a0 = v0.x; a2 = v0.y; a1 = v1.x; a3 = v1.y;
+                    } else {
+                        tc_a_regs(sX[3 * ic0], sX[3 * ic0 + 1], sX[3 * ic0 + 2], t, a0, a2);
+                        tc_a_regs(sX[3 * ic1], sX[3 * ic1 + 1], sX[3 * ic1 + 2], t, a1, a3);
                     }
-                    if (il1 < nrows) {
-                        if (sA4 != nullptr) {
-                            const uint2 v = sA4[4 * il1 + t];
-                            a1 = v.x;
-                            a3 = v.y;
-                        } else {
-                            tc_a_regs(sX[3 * il1], sX[3 * il1 + 1], sX[3 * il1 + 2], t, a1, a3);
-                        }
-                        fh1 = sFh[il1]; wr1 = sWr[il1]; s1 = sS[il1];
-                    }
+                    a0 = ok0 ? a0 : 0u; a2 = ok0 ? a2 : 0u; a1 = ok1 ? a1 : 0u; a3 = ok1 ? a3 : 0u;
+                    const float fh0 = ok0 ? sFh[ic0] : 0.0f, wr0 = ok0 ? sWr[ic0] : kPadW, s0 = ok0 ? sS[ic0] : 0.0f;
+                    const float fh1 = ok1 ? sFh[ic1] : 0.0f, wr1 = ok1 ? sWr[ic1] : kPadW, s1 = ok1 ? sS[ic1] : 0.0f;
                     tc_tile<ACC, NT>(a0, a1, a2, a3, b0, b1, fh0, wr0, s0, fh1, wr1, s1, hh2, wc2, CS, Z, G32p, Glop,
                                      rp[2 * h], rp[2 * h + 1], ca2);
                 }

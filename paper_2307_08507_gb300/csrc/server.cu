@@ -278,7 +278,8 @@ cudaError_t admit(mdot_server* s)
         a.precision = P.precision;
         a.smoothing = P.smoothing;
         a.ls_init = P.ls_init;
-        e = launch_batch(kind, m, a, st);
+        a.tensor_cores = P.tensor_cores;
+        e = launch_batch(kind, 0, m, a, st);       // the wide variant: one problem per SM
         if (e == cudaSuccess) e = cudaEventRecord(r->ev, st);
         if (e != cudaSuccess) return e;
     }
@@ -416,10 +417,10 @@ mdot_status mdot_server_create(mdot_server** out, uint64_t workspace_bytes, cons
     if (pool_doubles < batch_slot_doubles(kStrideAlign)) return MDOT_ERR_INVALID_ARG;
     mdot_server* s = new mdot_server();
     s->prm = P;
-    int bps = 0;
+    int bps[kBatchVariants] = {0, 0};
     cudaError_t e = cudaGetDevice(&s->dev);
-    if (e == cudaSuccess) e = configure_batch_kernels(&bps);
-    if (e == cudaSuccess && bps < 1) e = cudaErrorInvalidConfiguration;
+    if (e == cudaSuccess) e = configure_batch_kernels(bps);
+    if (e == cudaSuccess && bps[0] < 1) e = cudaErrorInvalidConfiguration;
     for (int i = 0; i < kLanes && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&s->lanes[i], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&s->pool_mem, pool_doubles * sizeof(double));
     for (Record& r : s->rec) {

@@ -54,7 +54,8 @@ def test_struct_layouts_match_the_binding(tmp_path):
         pytest.skip("gcc not available")
     lines = []
     for struct, cls in (("mdot_params", M.Params), ("mdot_info", M.Info), ("mdot_problem", M.Problem),
-                        ("mdot_result", M.Result), ("mdot_trace_row", M.TraceRow)):
+                        ("mdot_result", M.Result), ("mdot_trace_row", M.TraceRow),
+                        ("mdot_batch_tuning", M.BatchTuning)):
         lines.append(f'printf("{struct} size %zu\\n", sizeof({struct}));')
         for name, _ in cls._fields_:
             lines.append(f'printf("{struct} {name} %zu\\n", offsetof({struct}, {name}));')
@@ -66,7 +67,8 @@ def test_struct_layouts_match_the_binding(tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
     got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
     for struct, cls in (("mdot_params", M.Params), ("mdot_info", M.Info), ("mdot_problem", M.Problem),
-                        ("mdot_result", M.Result), ("mdot_trace_row", M.TraceRow)):
+                        ("mdot_result", M.Result), ("mdot_trace_row", M.TraceRow),
+                        ("mdot_batch_tuning", M.BatchTuning)):
         assert got[(struct, "size")] == ctypes.sizeof(cls), struct
         for name, _ in cls._fields_:
             assert got[(struct, name)] == getattr(cls, name).offset, (struct, name)

@@ -115,9 +115,9 @@ def test_batch_rejects_malformed_problems(h):
 
 
 def test_batch_grid_problems_on_the_tensor_cores_match_oracle(h):
-    """Grid histograms with the squared-Euclidean cost regenerated from integer cell coordinates:
-    the batched kernel forms the cost on the tensor cores (exact for such points), every result
-    against the CPU oracle on the dense matrix."""
+    """Grid histograms with the squared-Euclidean cost regenerated from integer cell coordinates,
+    mdot_params.tensor_cores = 1: the batched kernel forms the cost on the tensor cores (exact for
+    such points), every result against the CPU oracle on the dense matrix."""
     gf = 2.0 ** 10
     probs, tens = [], []
     for q, k in enumerate((12, 20, 9)):
@@ -128,8 +128,39 @@ def test_batch_grid_problems_on_the_tensor_cores_match_oracle(h):
         tens.append(d)
     plist = [M.make_problem(d["r"], d["c"], x=d["x"], y=d["y"], kind=M.COST_SQEUCLID, scale=p.scale, gamma_f=gf)
              for p, d in zip(probs, tens)]
-    res = h.solve_batch(plist, M.default_params(final_tol=FLOOR))
+    res = h.solve_batch(plist, M.default_params(final_tol=FLOOR, tensor_cores=1))
     for p, r in zip(probs, res):
         assert r.status == M.MDOT_OK, M.status_string(r.status)
         ref = O.solve(p.C.astype(np.float64), p.r, p.c, gamma_f=gf, final_tol=FLOOR)
         assert abs(r.cost - ref.cost) <= 1e-7, (p.n, r.cost, ref.cost)
+
+
+def test_batch_tile_variants_and_tuner(h):
+    """Both tile variants of the batched kernel (256 threads and one problem per SM; 128 threads
+    and two per SM) give results equal to the oracle's; the tuner times the populated size buckets
+    and installs a table that later solves use."""
+    gf = 2.0 ** 10
+    sizes = [300, 700, 64, 1500]
+    probs = _point_problems(sizes, 4700)
+    tens = [_tensors(p) for p in probs]
+    plist = [_problem(p, d, gf) for p, d in zip(probs, tens)]
+    prm = M.default_params(final_tol=FLOOR)
+    refs = [O.solve(p.C.astype(np.float64), p.r, p.c, gamma_f=gf, final_tol=FLOOR) for p in probs]
+    for variant in (0, 1):
+        table = M.BatchTuning()
+        for b in range(5):
+            table.variant[b] = variant
+        h.set_batch_tuning(table)
+        res = h.solve_batch(plist, prm)
+        for p, r, ref in zip(probs, res, refs):
+            assert r.status == M.MDOT_OK, M.status_string(r.status)
+            assert abs(r.cost - ref.cost) <= 1e-7, (variant, p.n, r.cost, ref.cost)
+    tuned = h.tune_batch(plist, prm, sample=2)
+    rates = tuned.as_dict()["problems_per_s"]
+    for b in (0, 1, 2):                       # buckets of 64/300, 700 and 1500
+        assert rates[b][0] > 0 and rates[b][1] > 0
+        assert tuned.variant[b] == (0 if rates[b][0] >= rates[b][1] else 1)
+    assert rates[3] == [0.0, 0.0] and rates[4] == [0.0, 0.0]
+    res = h.solve_batch(plist, prm)
+    assert all(r.status == M.MDOT_OK for r in res)
+    h.set_batch_tuning(M.BatchTuning())      # back to the default (wide) variant for other tests

@@ -77,6 +77,25 @@ def test_n256_fp64_reaches_gap_1e6(kind):
 
 
 @pytest.mark.parametrize("kind", ["l2sq", "l1"])
+def test_n4096_gap_1e6_certified_by_a_dual_bound(kind):
+    """The benchmark's target without an exact LP: the c-transform bound of a second solve at a far
+    higher gamma_f (2^21) is a feasible OT dual, so OT >= that bound and the benchmark solve's
+    true gap is at most its cost minus the bound -- which must be <= 1e-6 (Remark 1, Prop. 2)."""
+    torch.cuda.set_device(0)
+    p = I.grid_problem(64, 2000, kind=kind)
+    r, c, C = (torch.from_numpy(a).to(DEV) for a in (p.r, p.c, p.C))
+    with M.Handle(p.n) as h:
+        _, _, res = h.solve(r, c, C, 1e-6)
+        _, _, hi = h.solve(r, c, C, 1e-6, M.default_params(gamma_f=2.0 ** 21))
+    assert res.status == M.MDOT_OK and hi.status == M.MDOT_OK
+    lb = hi.cost - hi.gap_cert
+    assert res.cost - lb <= 1e-6, (res.cost, lb)
+    exact = exact_value(4096, kind)
+    if exact is not None:
+        assert lb <= exact + 1e-9 <= res.cost + 2e-9
+
+
+@pytest.mark.parametrize("kind", ["l2sq", "l1"])
 @pytest.mark.parametrize("eps", [1e-4, 1e-5, 1e-6, 1e-7])
 def test_n4096_true_gap(kind, eps):
     torch.cuda.set_device(0)

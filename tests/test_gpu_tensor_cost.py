@@ -1,8 +1,9 @@
 """The squared-Euclidean cost of integer grid points on the tensor cores (mma.sync, bf16 inputs,
-fp32 accumulation): |x|^2 + |y|^2 - 2 <x, y> is exact for integer coordinates of magnitude <= 255,
-so the regenerated C has the bits of the dense matrix the generator builds (inputs.grid_cost), and
-the solver on the regenerated cost matches the CPU oracle on that matrix.  Points that are not
-such integers take the fp32 form (its bits equal inputs.point_cost's)."""
+fp32 accumulation; mdot_params.tensor_cores / MDOT_PREC_TENSOR_CORES): |x|^2 + |y|^2 - 2 <x, y>
+is exact for integer coordinates of magnitude <= 255, so the regenerated C has the bits of the
+dense matrix the generator builds (inputs.grid_cost), and the solver on the regenerated cost
+matches the CPU oracle on that matrix.  Points that are not such integers take the fp32 form (its
+bits equal inputs.point_cost's)."""
 import numpy as np
 import pytest
 import torch
@@ -53,15 +54,19 @@ def test_regenerated_grid_solve_uses_the_tensor_cores_and_matches_the_oracle():
     tight = 1e-10
     with M.Handle(p.n) as h:
         u, v, res = h.solve_points(t(p.r), t(p.c), xy, xy, M.COST_SQEUCLID, p.scale, 1e-6,
-                                   M.default_params(gamma_f=gf, final_tol=tight))
+                                   M.default_params(gamma_f=gf, final_tol=tight, tensor_cores=1))
         assert res.status == M.MDOT_OK and res.info.tensor_cores == 1
         ref = O.solve(p.C.astype(np.float64), p.r, p.c, gamma_f=gf, final_tol=tight)
         assert abs(res.cost - ref.cost) <= 1e-7, (res.cost, ref.cost)
         # the same problem from non-integer coordinates (the fp32 form): no tensor cores
         xs = t(I.coords3(p.x) * np.float32(0.5))
         _, _, r2 = h.solve_points(t(p.r), t(p.c), xs, xs, M.COST_SQEUCLID, p.scale * 4.0, 1e-6,
-                                  M.default_params(gamma_f=gf))
+                                  M.default_params(gamma_f=gf, tensor_cores=1))
         assert r2.info.tensor_cores == 0
+        # and the default: fp32 operations
+        _, _, r3 = h.solve_points(t(p.r), t(p.c), xy, xy, M.COST_SQEUCLID, p.scale, 1e-6,
+                                  M.default_params(gamma_f=gf, final_tol=tight))
+        assert r3.info.tensor_cores == 0 and abs(r3.cost - ref.cost) <= 1e-7
 
 
 @pytest.mark.parametrize("k,gamma", [(20, 2.0 ** 8), (64, 2.0 ** 14), (100, 2.0 ** 12)])
@@ -79,10 +84,11 @@ def test_tensor_core_dual_eval_matches_the_oracle(k, gamma):
     lr_o, lc_o = O.dual_eval(p.C.astype(np.float64), u, v, gamma)
     with M.Handle(p.n) as h:
         for prec, tol in ((M.PREC_FP32, 4e-6), (M.PREC_FP32A, 1e-6)):
-            lr, lc = h.dual_eval_points(t(u), t(v), gamma, xy, xy, M.COST_SQEUCLID, p.scale, precision=prec)
+            tc = prec | M.PREC_TENSOR_CORES
+            lr, lc = h.dual_eval_points(t(u), t(v), gamma, xy, xy, M.COST_SQEUCLID, p.scale, precision=tc)
             np.testing.assert_allclose(lr.cpu().numpy(), lr_o, rtol=0, atol=tol)
             np.testing.assert_allclose(lc.cpu().numpy(), lc_o, rtol=0, atol=tol)
             lr2, lc2 = h.dual_eval_points(t(u), t(v), gamma, xy, xy, M.COST_SQEUCLID, p.scale, ref_log_rP=lr,
-                                          precision=prec)
+                                          precision=tc)
             np.testing.assert_allclose(lr2.cpu().numpy(), lr_o, rtol=0, atol=tol)
             np.testing.assert_allclose(lc2.cpu().numpy(), lc_o, rtol=0, atol=tol)
