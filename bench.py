@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--cpu-sample-evals", type=int, default=0, help="oracle evaluations in the CPU sample")
     ap.add_argument("--case", default="solve",
                     choices=["solve", "dual_eval", "dual_eval_regen", "stage", "batch", "serve", "tune_serve", "sinkhorn",
-                             "large_n", "nscale", "hmin"],
+                             "large_n", "nscale", "hmin", "phases"],
                     help="dual_eval / stage: run only that kernel (for profiler captures); sinkhorn, large_n, "
                          "nscale, hmin: the comparison studies (one JSON line per solve)")
     ap.add_argument("--grid", type=int, default=64, help="k of the k x k grid for --case runs")
@@ -357,6 +357,20 @@ def batch_problems(dev, count=BATCH_COUNT, seed=BATCH_SEED):
     return out
 
 
+def _not_converged_summary(probs, res, M):
+    """The problems whose last stage ended above its tolerance: how many, their sizes and their
+    final ||grad g||_1 (quartiles), to set against the tolerance floor fp32_floor."""
+    bad = [(probs[k]["n"], r.grad_l1) for k, r in enumerate(res) if r.status == M.MDOT_ERR_NOT_CONVERGED]
+    if not bad:
+        return {"count": 0}
+    ns = sorted(b[0] for b in bad)
+    gs = sorted(b[1] for b in bad)
+    q = lambda v, f: v[min(len(v) - 1, int(f * len(v)))]
+    return {"count": len(bad), "n_min": ns[0], "n_median": q(ns, 0.5), "n_max": ns[-1],
+            "grad_l1_quartiles": [gs[0], q(gs, 0.25), q(gs, 0.5), q(gs, 0.75), gs[-1]],
+            "fp32_floor": M.default_params().fp32_floor}
+
+
 def measure_batch(h, dev, stream, sample_single=128):
     import torch
     import paper_2307_08507_gb300 as M
@@ -373,9 +387,10 @@ def measure_batch(h, dev, stream, sample_single=128):
     ev1.record(stream)
     torch.cuda.synchronize()
     t_fixed = ev0.elapsed_time(ev1) / 1e3
-    # ... and the tiles the autotuner picks per size bucket (timed on 8 problems of each bucket)
+    # ... and the table the autotuner picks (each candidate timed on 128 problems of the batch,
+    # evenly spaced in size, at gamma_f <= 2^12)
     t0 = time.perf_counter()
-    tuned = h.tune_batch(plist, sample=8)
+    tuned = h.tune_batch(plist, sample=128)
     t_tune = time.perf_counter() - t0
     ev0.record(stream)
     res = h.solve_batch(plist)
@@ -407,11 +422,13 @@ def measure_batch(h, dev, stream, sample_single=128):
             "seconds": t_batch, "problems_per_s": len(probs) / t_batch, "ok": ok,
             "fixed_tiles": {"seconds": t_fixed, "problems_per_s": len(probs) / t_fixed,
                             "ok": sum(1 for r in res_fixed if r.status == M.MDOT_OK)},
-            "tuning": {**tuned.as_dict(), "seconds": t_tune,
+            "tuning": {**tuned.as_dict(), "tuning_seconds": t_tune, "sample": 128,
+                       "candidates": "table k: size buckets below k on variant 1, the rest on variant 0",
                        "buckets": ["n<512", "n<1024", "n<2048", "n<4096", "n<=8192"],
                        "variants": ["256 threads, 1 problem per SM", "128 threads, 2 problems per SM"]},
             "max_abs_cost_diff_tuned_vs_fixed": max(abs(a.cost - b.cost) for a, b in zip(res, res_fixed)),
             "statuses": {M.status_string(st): sum(1 for r in res if r.status == st) for st in {r.status for r in res}},
+            "not_converged": _not_converged_summary(probs, res, M),
             "roofline": {"kernel": "batch_kernel<squared Euclidean> (one CTA per problem)", "bound": "alu",
                          "entries_per_s": entries / t_batch, "ops_per_entry": ALU_OPS_PER_ENTRY,
                          "achieved": entries * ALU_OPS_PER_ENTRY / t_batch / 1e12, "peak": alu / 1e12,
@@ -934,8 +951,52 @@ def run_case(args):
     print(f"case {args.case} n={p.n} reps={args.reps} done")
 
 
+def run_phases(args):
+    """Per-phase device time of an evaluation of the fp32-entry stage kernel on the benchmark solve
+    (n = 4096 grid, target gap 1e-6), from the diagnostic build with phase timers
+    (build.py --phases): per CTA, SM cycles per phase summed over the solve's launches, divided by
+    its evaluations and by the median SM clock sampled during the solve."""
+    import numpy as np
+    import torch
+    import paper_2307_08507_gb300 as M
+    from paper_2307_08507_gb300 import inputs as I
+    M.use_phase_timer_build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    names = ["loop_top", "pass", "row_epilogue", "wait_column_partials", "merge_column_epilogue",
+             "cta_reduce_publish", "wait_scalar_partials", "decision", "commit_next_rows"]
+    for kind in ("l2sq", "l1"):
+        p = I.grid_problem(N_GRID, SEED, kind=kind)
+        r, c, C = (torch.from_numpy(a).to(dev) for a in (p.r, p.c, p.C))
+        with M.Handle(p.n) as h:
+            h.solve(r, c, C, EPS)
+            torch.cuda.synchronize()
+            M.phase_timers(clear=True)
+            with Clocks() as clk:
+                _, _, res = h.solve(r, c, C, EPS, M.default_params(profile=1))
+                torch.cuda.synchronize()
+            ph = M.phase_timers(clear=True)
+            trace = h.solve_trace()
+        mhz = clk.summary()["sm_mhz"] or 2070.0
+        G = int(np.count_nonzero(ph[:, 9]))
+        cyc = ph[:G, :9].astype(np.float64) / ph[:G, 9:10].astype(np.float64)
+        us = cyc / mhz
+        st32 = [t for t in trace if t["kind"] == 0]
+        print(json.dumps({
+            "cost_kind": kind, "status": M.status_string(res.status), "evals": res.info.evals,
+            "evals_per_cta": [int(ph[:G, 9].min()), int(ph[:G, 9].max())], "sm_mhz": mhz,
+            "us_per_eval_fp32_launches": 1e3 * sum(t["ms"] for t in st32) / max(1, sum(t["evals"] for t in st32)),
+            "phases_us_mean": dict(zip(names, us.mean(0).round(3).tolist())),
+            "phases_us_min": dict(zip(names, us.min(0).round(3).tolist())),
+            "phases_us_max": dict(zip(names, us.max(0).round(3).tolist())),
+            "sum_us_mean": float(us.mean(0).sum())}), flush=True)
+
+
 def main():
     args = parse()
+    if args.case == "phases":
+        run_phases(args)
+        return
     if args.case in ("sinkhorn", "large_n", "nscale", "hmin"):
         run_study(args)
         return

@@ -114,6 +114,11 @@ typedef struct mdot_params {
                                (|coordinate| <= 255, e.g. grid data) on the tensor cores, exact (see
                                mdot_cost_matrix); 0 (default): fp32 operations, measured faster on
                                GB300 because the pass is bound by the exponentials and sums      */
+    int32_t polish_iters;   /* batched form and server only: fp64-entry PNCG iterations at most that
+                               finish a problem's last stage when its fp32 part stalled above the
+                               stage's tolerance (one CTA per problem, where an fp64 evaluation costs
+                               ~5 ns per entry); 64; 0: no polish                                 */
+    int32_t reserved;
 } mdot_params;
 
 /* Diagnostics of one solve. */
@@ -258,6 +263,18 @@ typedef struct mdot_trace_row {
 mdot_status mdot_solve_trace(const mdot_handle* h, int32_t max_rows, mdot_trace_row* rows, int32_t* count);
 
 /*
+ * Phase timers of the fp32-entry stage kernel with dense C (diagnostic; the paper has no
+ * counterpart): per CTA, the SM cycles spent in each phase of an evaluation, summed over every
+ * launch since the last clear -- 0 loop top, 1 pass over C, 2 row epilogue, 3 wait for the column
+ * partials, 4 merge and column epilogue, 5 CTA reduction and publication, 6 wait for the scalar
+ * partials, 7 decision, 8 commit and next row constants -- then the evaluation count (10 counts per
+ * CTA).  out (host): max_ctas x 10 counts; clear != 0 zeroes the counters after reading.  Only a
+ * library built with -DMDOT_PHASE_TIMERS (paper_2307_08507_gb300/build.py --phases) keeps the
+ * counters; any other build returns MDOT_NOT_READY.  INVALID_ARG for a null out or max_ctas < 1.
+ */
+mdot_status mdot_phase_timers(uint64_t* out, int32_t max_ctas, int32_t clear);
+
+/*
  * The regenerated cost matrix written out: C_out (device, n x n float32, row-major) receives
  * C_ij for the coordinates x, y (device, n x 3 float32 each) with the arithmetic the solver's passes
  * use -- for MDOT_COST_SQEUCLID with every coordinate an integer of magnitude <= 255 (grid data),
@@ -319,8 +336,13 @@ typedef struct mdot_result {
  * runs the whole of Alg. 1 + Alg. 3 on it (PNCG projections, line search, rounding, bound) with
  * block-level synchronisation.  Each problem gets its own gamma schedule (from its eps_target or
  * gamma_f), potentials and line-search state; a problem's result does not depend on the rest of
- * the batch (fixed-order reductions).  Entries use the fp32 tiers (the fp64 tier is not offered
- * here).  results: host array of nprob.  prm: NULL for defaults.  Workspace (about 1.4 MiB per
+ * the batch (fixed-order reductions).  Entries use the fp32 tiers, and every stage's tolerance,
+ * the last one's included, is floored at fp32_floor: unlike mdot_solve, which polishes the last
+ * stage below fp32_floor in fp64 entries on every SM, one CTA per problem cannot afford that on
+ * ill-conditioned problems (thousands of fp64 iterations); a caller who needs a tighter last
+ * stage lowers fp32_floor.  With precision AUTO a last stage whose fp32 part ended by the stall
+ * rule above its tolerance continues in fp64 entries for at most polish_iters iterations;
+ * a problem still above it reports MDOT_ERR_NOT_CONVERGED.  results: host array of nprob.  prm: NULL for defaults.  Workspace (about 1.4 MiB per
  * SM) is allocated on the first call and kept by the handle.
  * Returns INVALID_ARG if any problem is malformed (nothing is solved), else MDOT_OK; per-problem
  * outcomes are in results[k].status.
@@ -330,20 +352,24 @@ mdot_status mdot_solve_batch(mdot_handle* h, int32_t nprob, const mdot_problem* 
 
 /* Tile variants of the batched form, one per problem-size bucket (n < 512, < 1024, < 2048, < 4096,
  * <= MDOT_BATCH_MAX_N): 0 ("wide") 256 threads per problem, one problem per SM; 1 ("narrow") 128
- * threads per problem, two problems per SM.  A new handle uses 0 for every bucket. */
+ * threads per problem, two problems per SM.  The problems of each variant form one persistent
+ * launch (wide first).  A new handle uses 0 for every bucket. */
 typedef struct mdot_batch_tuning {
     int32_t variant[5];
-    int32_t reserved;
-    double  problems_per_s[5][2];   /* measured by mdot_tune_batch, per bucket and variant (0: not timed) */
+    int32_t narrow_below;   /* mdot_tune_batch's pick: buckets below this index narrow, the rest wide */
+    double  seconds[6];     /* mdot_tune_batch: device time of the timing batch under table k = 0..5
+                               (buckets below k narrow); 0 where not timed */
 } mdot_batch_tuning;
 
 /*
- * The tile autotuner of the batched form: for every size bucket that probs (host array, device data)
- * populates, times each variant on up to `sample` of the bucket's problems, repeated to fill every
- * CTA of the wider grid twice, solved to gamma_f = min(their gamma_f, 2^12) without writing
- * potentials (CUDA events around the launches), and keeps the faster variant in the handle's table
- * for later mdot_solve_batch calls.  *out (host) receives the table and the measured rates.
- * Errors as mdot_solve_batch.
+ * The tile autotuner of the batched form.  It times the batch itself -- up to `sample` problems of
+ * probs (host array, device data), evenly spaced in size order, solved to gamma_f = min(their
+ * gamma_f, 2^12) without writing potentials, CUDA events around the launches -- under each table
+ * of the form "buckets below k narrow, the others wide" (k = 0 ... 5; k = 0 is the default table),
+ * and keeps the fastest in the handle for later mdot_solve_batch calls (on a tie the smaller k).
+ * The measure is the batch's total device time, so it weighs what decides it: how the problems
+ * pack onto the SMs, and the longest problems at the end of each launch.  *out (host) receives
+ * the table and the time of every candidate.  Errors as mdot_solve_batch.
  */
 mdot_status mdot_tune_batch(mdot_handle* h, int32_t nprob, const mdot_problem* probs, const mdot_params* prm,
                             int32_t sample, mdot_batch_tuning* out);
@@ -361,7 +387,7 @@ mdot_status mdot_set_batch_tuning(mdot_handle* h, const mdot_batch_tuning* t);
  * problem finishes.  Requests above cfg->big_n instead go to "big lanes": cooperative solves (the
  * single-problem solver) on cfg->lane_ctas SMs each; the remaining SMs serve the batched route.  Results do not depend on what else runs (fixed-order reductions): a problem
  * gives the same result alone and in any mix.
- *   prm: NULL for defaults (the fp64 tier is not offered here).  cfg: NULL for the default routing;
+ *   prm: NULL for defaults (entry tiers as mdot_solve_batch).  cfg: NULL for the default routing;
  *   lanes x lane_ctas must leave SMs for the batched route.
  *   submit: non-blocking; validates the problem (same rules as mdot_solve_batch, n up to
  *     MDOT_BATCH_MAX_N) and returns a ticket.  The problem's arrays (r, c, C or x/y, u_out,

@@ -34,7 +34,8 @@ class Params(ct.Structure):
                 ("warm_start", ct.c_int32), ("final_tol", ct.c_double), ("fp32_floor", ct.c_double),
                 ("profile", ct.c_int32), ("smoothing", ct.c_int32), ("projector", ct.c_int32),
                 ("stop_entropy", ct.c_int32), ("precond", ct.c_int32), ("ls_init", ct.c_int32),
-                ("wait_limit_us", ct.c_int32), ("tensor_cores", ct.c_int32)]
+                ("wait_limit_us", ct.c_int32), ("tensor_cores", ct.c_int32), ("polish_iters", ct.c_int32),
+                ("reserved", ct.c_int32)]
 
 
 class Info(ct.Structure):
@@ -66,12 +67,40 @@ _lib = None
 _P = ct.c_void_p
 
 
+_lib_path = None
+
+
+def use_phase_timer_build():
+    """Load the diagnostic build with stage-kernel phase timers (build.py --phases; built here if
+    needed) instead of the default library.  Must be called before anything else loads it."""
+    global _lib_path
+    if _lib is not None:
+        raise RuntimeError("libmdot is already loaded")
+    _lib_path = _build.build(phases=True)
+
+
+def phase_timers(clear: bool = True, max_ctas: int = 160):
+    """mdot_phase_timers: per CTA, cycles per phase (9) and the evaluation count, as a numpy array
+    (max_ctas x 10); None when the loaded library has no phase timers."""
+    import numpy as np
+    L = lib()
+    L.mdot_phase_timers.argtypes = [_P, ct.c_int32, ct.c_int32]
+    L.mdot_phase_timers.restype = ct.c_int32
+    buf = (ct.c_uint64 * (max_ctas * 10))()
+    s = L.mdot_phase_timers(ct.cast(buf, _P), max_ctas, 1 if clear else 0)
+    if s == MDOT_NOT_READY:
+        return None
+    if s != MDOT_OK:
+        raise MdotError(s, "mdot_phase_timers")
+    return np.frombuffer(buf, dtype=np.uint64).reshape(max_ctas, 10).copy()
+
+
 def lib():
     """Load libmdot.so (built in-tree).  Raises if it has not been built."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    path = _lib_path or _build.LIB
     if not os.path.exists(path):
         raise RuntimeError(f"libmdot is not built ({path} missing): run "
                            "`python -c 'import __graft_entry__ as g; g.build()'` first")
@@ -454,15 +483,17 @@ Handle.solve_batch = _solve_batch
 
 
 class BatchTuning(ct.Structure):
-    """mdot_batch_tuning: the batched form's tile variant per size bucket and the measured rates."""
-    _fields_ = [("variant", ct.c_int32 * 5), ("reserved", ct.c_int32), ("problems_per_s", (ct.c_double * 2) * 5)]
+    """mdot_batch_tuning: the batched form's tile variant per size bucket, the tuner's pick (buckets
+    below narrow_below narrow) and the timing batch's seconds under each candidate table."""
+    _fields_ = [("variant", ct.c_int32 * 5), ("narrow_below", ct.c_int32), ("seconds", ct.c_double * 6)]
 
     def as_dict(self) -> dict:
-        return {"variant": list(self.variant), "problems_per_s": [list(r) for r in self.problems_per_s]}
+        return {"variant": list(self.variant), "narrow_below": self.narrow_below, "seconds": list(self.seconds)}
 
 
-def _tune_batch(self, problems, params: Params | None = None, sample: int = 16) -> BatchTuning:
-    """mdot_tune_batch: time each tile variant per size bucket and keep the faster (in the handle)."""
+def _tune_batch(self, problems, params: Params | None = None, sample: int = 64) -> BatchTuning:
+    """mdot_tune_batch: time the batch (up to `sample` problems, gamma_f <= 2^12) under each table
+    "buckets below k narrow" and keep the fastest (in the handle)."""
     L = _batch_lib()
     if not hasattr(L, "_tune_typed"):
         L.mdot_tune_batch.argtypes = [_P, ct.c_int32, ct.POINTER(Problem), ct.POINTER(Params), ct.c_int32,

@@ -63,6 +63,7 @@ struct BatchArgs {
     double gamma_i, p, q, c1, c2, fp32_floor, final_tol;
     int ls_max_trials, max_iter, warm_start, precision, smoothing, ls_init;
     int tensor_cores;          // 1: integer-point squared-Euclidean costs on the tensor cores
+    int polish_iters;          // fp64 iterations at most that finish a stalled last stage
 };
 
 // slot layout (vectors of `stride` elements): 18 fp64 vectors, then 7 fp32 / int32 vectors
@@ -170,6 +171,48 @@ __device__ __forceinline__ void batch_prep_row(double ua, int A, double inv_gamm
     sA[i] = A;
 }
 
+// Per-row constants of an fp64-entry evaluation at ua with row scale A: E_ij = exp(fd_i + v_j -
+// gamma C_ij) relative to 2^{A_i}, weighted by 2^{A_i} into the column sums.
+__device__ __forceinline__ void batch_prep_row64(double ua, int A, double* fd, double* s64, int* sA, int i)
+{
+    fd[i] = ua - (double)A * kLn2;
+    s64[i] = ldexp(1.0, A);
+    sA[i] = A;
+}
+
+// One fp64-entry pass over all n rows (the polish of the last stage) in chunks of kRowChunk / 2 rows,
+// whose per-warp fp64 row partials fill the shared memory of the fp32 passes' chunks: row sums
+// (relative to 2^{A_i}) to rowsum, the complete column sums to colsum (a later chunk's partials go
+// through tmp and are added in a fixed order).
+template <int COST>
+__device__ __forceinline__ void batch_pass64(const BatchProblem& P, const double* hd, const double* fd,
+                                             const double* s64, double gamma, double* sRow, double* colsum,
+                                             double* tmp, double* rowsum)
+{
+    constexpr int kChunk = kRowChunk / 2;
+    const int n = P.n, nw = blockDim.x >> 5;
+    for (int r0 = 0; r0 < n; r0 += kChunk) {
+        const int r1 = min(n, r0 + kChunk), nc = r1 - r0;
+        double* part = (r0 == 0) ? colsum : tmp;
+        for (int x = threadIdx.x; x < nw * nc; x += blockDim.x) sRow[x] = 0.0;
+        __syncthreads();
+        if (COST == COST_DENSE)
+            pass_f64(P.C, n, r0, r1, hd, fd + r0, s64 + r0, gamma, sRow, nc, part);
+        else
+            pass_f64_regen<COST>(P.Y, P.scale, n, r0, r1, hd, fd + r0, s64 + r0, P.X + 3 * (size_t)r0, gamma,
+                                 sRow, nc, part);
+        __syncthreads();
+        if (r0 > 0)
+            for (int j = threadIdx.x; j < n; j += blockDim.x) colsum[j] += tmp[j];
+        for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += sRow[w * nc + (i - r0)];
+            rowsum[i] = t;
+        }
+        __syncthreads();
+    }
+}
+
 template <int COST, int THREADS>
 __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 2 : 1) batch_kernel(BatchArgs a)
 {
@@ -206,6 +249,16 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 2 : 1) batch_kernel(
         float* sWr = F32 + (size_t)SF_WR * sd;
         float* sS = F32 + (size_t)SF_S * sd;
         int* sA = reinterpret_cast<int*>(F32 + (size_t)SF_A * sd);
+        // the fp64 polish of the last stage reuses vectors that are idle by then: the warm-start
+        // history (row and column constants), the rounding's error vector (column sums), the fp32
+        // column constants (row scales 2^A) and the fp32 column sums with the row constants (a row
+        // chunk's column partials); the per-warp row partials take the fp32 passes' shared memory
+        double* fd64 = V[SV_UP];
+        double* hd64 = V[SV_VP];
+        double* col64 = V[SV_EC];
+        double* s64 = reinterpret_cast<double*>(Hh);        // Hh, Wc: 2 sd floats
+        double* tmp64 = reinterpret_cast<double*>(colsum);  // colsum, sFh: 2 sd floats
+        double* sRow64 = reinterpret_cast<double*>(sm + L.off_row);
         BatchResult res;
         memset(&res, 0, sizeof(res));
 
@@ -314,77 +367,117 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 2 : 1) batch_kernel(
                 st.phase = PH_RUN; st.beta = 0.0; st.alpha_commit = 0.0;
             }
             __syncthreads();
-            for (;;) {
-                if (acc) batch_pass<true, COST>(P, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, colsum, V[SV_RS], tc, sStage);
-                else     batch_pass<false, COST>(P, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, colsum, V[SV_RS], tc, sStage);
+            // one PNCG projection (Alg. 2 with the App. B line search) at this gamma, from the
+            // constants already prepared: fp32 entries, or fp64 entries for the polish below
+            auto project = [&](const StageArgs& sx, bool f64) {
+                for (;;) {
+                    if (f64)      batch_pass64<COST>(P, hd64, fd64, s64, gamma, sRow64, col64, tmp64, V[SV_RS]);
+                    else if (acc) batch_pass<true, COST>(P, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, colsum, V[SV_RS], tc, sStage);
+                    else          batch_pass<false, COST>(P, Hh, Wc, sFh, sWr, sS, G32, Glo, sRow, colsum, V[SV_RS], tc, sStage);
 #pragma unroll
-                for (int q = 0; q < kNRed; ++q) x[q] = 0.0;
-                for (int i = tid; i < n; i += T) {
-                    const double sum = V[SV_RS][i];
-                    if (!(sum > 0.0) || !isfinite(sum)) { x[5] += 1.0; continue; }
-                    const double rt = V[SV_RT][i];
-                    const double g = ldexp(sum, sA[i]) - rt;
-                    const double s = -(double)log1pf((float)g / (float)rt);     // Eq. (17)
-                    const double p = V[SV_PU][i], y = g - V[SV_GR][i];
-                    x[0] += p * g; x[1] += fabs(g); x[2] += y * (-s); x[3] += y * p; x[4] += s * g;
-                    V[SV_GRT][i] = g;
-                    V[SV_SRT][i] = s;
-                    V[SV_Y][i] = ((double)__log2f((float)sum) + (double)sA[i]) * kLn2;   // log r(P), scale only
-                }
-                for (int j = tid; j < n; j += T) {
-                    const double cs = (double)colsum[j];
-                    if (!(cs > 0.0) || !isfinite(cs)) { x[5] += 1.0; continue; }
-                    const double ct = V[SV_CT][j];
-                    const double g = cs - ct;
-                    const double s = -(double)log1pf((float)g / (float)ct);
-                    const double p = V[SV_PV][j], y = g - V[SV_GC][j];
-                    x[0] += p * g; x[1] += fabs(g); x[2] += y * (-s); x[3] += y * p; x[4] += s * g;
-                    V[SV_GCT][j] = g;
-                    V[SV_SCT][j] = s;
-                }
-                block_reduce_nred(x, red_smem);
-                if (tid == 0) {
-                    decide(&st, x, sa);
-                    s_bc[0] = st.alpha; s_bc[1] = st.alpha_commit; s_bc[2] = st.beta;
-                    s_bc[3] = (double)st.accept; s_bc[4] = (double)st.phase;
-                }
-                __syncthreads();
-                const double alpha = s_bc[0], acommit = s_bc[1], beta = s_bc[2];
-                const bool accept = s_bc[3] != 0.0, done = s_bc[4] != 0.0;
-                for (int i = tid; i < n; i += T) {
-                    double u = V[SV_U][i], p = V[SV_PU][i];
-                    if (accept) {
-                        u += acommit * p;
-                        V[SV_U][i] = u;
-                        V[SV_GR][i] = V[SV_GRT][i];
-                        V[SV_LR][i] = V[SV_Y][i];
-                        p = V[SV_SRT][i] + beta * p;
-                        V[SV_PU][i] = p;
+                    for (int q = 0; q < kNRed; ++q) x[q] = 0.0;
+                    for (int i = tid; i < n; i += T) {
+                        const double sum = V[SV_RS][i];
+                        if (!(sum > 0.0) || !isfinite(sum)) { x[5] += 1.0; continue; }
+                        const double rt = V[SV_RT][i];
+                        const double g = ldexp(sum, sA[i]) - rt;
+                        const double s = -(double)log1pf((float)g / (float)rt);     // Eq. (17)
+                        const double p = V[SV_PU][i], y = g - V[SV_GR][i];
+                        x[0] += p * g; x[1] += fabs(g); x[2] += y * (-s); x[3] += y * p; x[4] += s * g;
+                        V[SV_GRT][i] = g;
+                        V[SV_SRT][i] = s;
+                        V[SV_Y][i] = ((double)__log2f((float)sum) + (double)sA[i]) * kLn2;   // log r(P), scale only
                     }
-                    if (!done) batch_prep_row(u + alpha * p, row_scale(V[SV_LR][i] + alpha * p), inv_gamma, G64,
-                                              sFh, sWr, sS, sA, i);
-                }
-                for (int j = tid; j < n; j += T) {
-                    double v = V[SV_V][j], p = V[SV_PV][j];
-                    if (accept) {
-                        v += acommit * p;
-                        V[SV_V][j] = v;
-                        V[SV_GC][j] = V[SV_GCT][j];
-                        p = V[SV_SCT][j] + beta * p;
-                        V[SV_PV][j] = p;
+                    for (int j = tid; j < n; j += T) {
+                        const double cs = f64 ? col64[j] : (double)colsum[j];
+                        if (!(cs > 0.0) || !isfinite(cs)) { x[5] += 1.0; continue; }
+                        const double ct = V[SV_CT][j];
+                        const double g = cs - ct;
+                        const double s = -(double)log1pf((float)g / (float)ct);
+                        const double p = V[SV_PV][j], y = g - V[SV_GC][j];
+                        x[0] += p * g; x[1] += fabs(g); x[2] += y * (-s); x[3] += y * p; x[4] += s * g;
+                        V[SV_GCT][j] = g;
+                        V[SV_SCT][j] = s;
                     }
-                    if (!done) {
-                        float gh, wl;
-                        split_cost_unit((v + alpha * p) * inv_gamma, gh, wl, G64);
-                        Hh[j] = gh;
-                        Wc[j] = wl;
+                    block_reduce_nred(x, red_smem);
+                    if (tid == 0) {
+                        decide(&st, x, sx);
+                        s_bc[0] = st.alpha; s_bc[1] = st.alpha_commit; s_bc[2] = st.beta;
+                        s_bc[3] = (double)st.accept; s_bc[4] = (double)st.phase;
                     }
+                    __syncthreads();
+                    const double alpha = s_bc[0], acommit = s_bc[1], beta = s_bc[2];
+                    const bool accept = s_bc[3] != 0.0, done = s_bc[4] != 0.0;
+                    for (int i = tid; i < n; i += T) {
+                        double u = V[SV_U][i], p = V[SV_PU][i];
+                        if (accept) {
+                            u += acommit * p;
+                            V[SV_U][i] = u;
+                            V[SV_GR][i] = V[SV_GRT][i];
+                            V[SV_LR][i] = V[SV_Y][i];
+                            p = V[SV_SRT][i] + beta * p;
+                            V[SV_PU][i] = p;
+                        }
+                        if (done) continue;
+                        const int A = row_scale(V[SV_LR][i] + alpha * p);
+                        if (f64) batch_prep_row64(u + alpha * p, A, fd64, s64, sA, i);
+                        else     batch_prep_row(u + alpha * p, A, inv_gamma, G64, sFh, sWr, sS, sA, i);
+                    }
+                    for (int j = tid; j < n; j += T) {
+                        double v = V[SV_V][j], p = V[SV_PV][j];
+                        if (accept) {
+                            v += acommit * p;
+                            V[SV_V][j] = v;
+                            V[SV_GC][j] = V[SV_GCT][j];
+                            p = V[SV_SCT][j] + beta * p;
+                            V[SV_PV][j] = p;
+                        }
+                        if (done) continue;
+                        if (f64) {
+                            hd64[j] = v + alpha * p;
+                        } else {
+                            float gh, wl;
+                            split_cost_unit((v + alpha * p) * inv_gamma, gh, wl, G64);
+                            Hh[j] = gh;
+                            Wc[j] = wl;
+                        }
+                    }
+                    __syncthreads();
+                    if (done) break;
                 }
-                __syncthreads();
-                if (done) break;
-            }
+            };
+            project(sa, false);
             ++stages;
             tol_last = sa.tol;
+            // a last stage whose fp32 part ended by the stall rule above its tolerance (which is
+            // floored at fp32_floor here, see mdot_solve_batch) continues in fp64 entries from the
+            // fp32 iterate, same gamma and smoothing, for at most polish_iters iterations: an fp64
+            // evaluation on one SM costs ~5 ns per entry (fp64 runs at 1/64 of the fp32 rate on
+            // this GPU), so a problem that needs more reports MDOT_ERR_NOT_CONVERGED with its best
+            // iterate instead of holding its SM
+            if (last && a.precision == 0 && a.polish_iters > 0 && st.status == ST_OK && !(st.gnorm <= sa.tol)) {
+                StageArgs sb = sa;
+                sb.tier = TIER_F64;
+                sb.stall_below = stall_floor(TIER_F64);
+                sb.max_iter = min(a.max_iter, a.polish_iters);
+                for (int i = tid; i < n; i += T) {
+                    V[SV_PU][i] = 0.0;
+                    V[SV_GR][i] = 0.0;
+                    batch_prep_row64(V[SV_U][i], row_scale(V[SV_LR][i]), fd64, s64, sA, i);
+                }
+                for (int j = tid; j < n; j += T) {
+                    V[SV_PV][j] = 0.0;
+                    V[SV_GC][j] = 0.0;
+                    hd64[j] = V[SV_V][j];
+                }
+                if (tid == 0) {
+                    st.alpha = 0.0; st.kind = KIND_INIT; st.accept = 0; st.trials = 0; st.k = 0;
+                    st.phase = PH_RUN; st.beta = 0.0; st.alpha_commit = 0.0;
+                }
+                __syncthreads();
+                project(sb, true);
+                tol_last = sb.tol;
+            }
             if (last || st.status >= ST_LSFAIL) break;
             double dg = (a.q - 1.0) * gamma;
             const double gnext = fmin(gamma + dg, gf);

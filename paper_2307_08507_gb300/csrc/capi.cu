@@ -110,6 +110,8 @@ void mdot_default_params(mdot_params* prm)
     prm->ls_init = 1;                    // App. B leaves the first trial step open (see mdot.h)
     prm->wait_limit_us = 0;              // bounded device waits: the 2 s default
     prm->tensor_cores = 0;               // grid costs in fp32 operations (measured faster)
+    prm->polish_iters = 64;              // batched form: fp64 iterations repairing a stalled last stage
+    prm->reserved = 0;
 }
 
 const char* mdot_status_string(int32_t s)
@@ -249,7 +251,8 @@ mdot_status params_ok(const mdot_params& P)
         P.precision < 0 || P.precision > 3 || P.warm_start < 0 || P.warm_start > 2 ||
         P.smoothing < 0 || P.smoothing > 1 || P.projector < 0 || P.projector > 1 || P.stop_entropy < 0 ||
         P.stop_entropy > 1 || P.precond < 0 || P.precond > 1 || P.ls_init < 0 || P.ls_init > 1 ||
-        !(P.fp32_floor >= 0.0) || !std::isfinite(P.gamma_f) || P.tensor_cores < 0 || P.tensor_cores > 1)
+        !(P.fp32_floor >= 0.0) || !std::isfinite(P.gamma_f) || P.tensor_cores < 0 || P.tensor_cores > 1 ||
+        P.polish_iters < 0)
         return MDOT_ERR_INVALID_ARG;
     return MDOT_OK;
 }
@@ -817,6 +820,7 @@ mdot_status batch_core(mdot_handle* h, const std::vector<BatchProblem>& bp, cons
             a.smoothing = P.smoothing;
             a.ls_init = P.ls_init;
             a.tensor_cores = P.tensor_cores;
+            a.polish_iters = P.polish_iters;
             CKR(cudaEventRecord(h->de_ev[0], h->stream));
             CKR(launch_batch(kind, v, std::min(h->b_grid[v], a.nprob), a, h->stream));
             CKR(cudaEventRecord(h->de_ev[1], h->stream));
@@ -876,45 +880,42 @@ mdot_status mdot_tune_batch(mdot_handle* h, int32_t nprob, const mdot_problem* p
     std::vector<BatchProblem> bp;
     if (batch_problems(nprob, probs, bp) != MDOT_OK) return MDOT_ERR_INVALID_ARG;
     memset(out, 0, sizeof(*out));
-    for (int b = 0; b < kBatchBuckets; ++b) out->variant[b] = h->b_variant[b];
-    // the tuning launches write no potentials and stop at gamma_f <= 2^12 (the variants' relative
-    // speed is that of the per-evaluation work, not of the schedule's length)
-    for (BatchProblem& q : bp) {
+    // the timing batch: up to `sample` problems evenly spaced in size order, no potentials written,
+    // stopped at gamma_f <= 2^12 (the tables' relative speed is that of the per-evaluation work and
+    // of the packing, not of the schedule's length)
+    std::vector<int> order(nprob);
+    for (int k = 0; k < nprob; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return bp[x].n < bp[y].n; });
+    const int m = std::min(sample, nprob);
+    std::vector<BatchProblem> pick;
+    for (int k = 0; k < m; ++k) {
+        BatchProblem q = bp[order[(size_t)k * nprob / m]];
         q.u_out = nullptr;
         q.v_out = nullptr;
         if (!(q.gamma_f > 0.0) || q.gamma_f > 4096.0) q.gamma_f = 4096.0;
+        pick.push_back(q);
     }
-    for (int b = 0; b < kBatchBuckets; ++b) {
-        std::vector<BatchProblem> pick;
-        for (const BatchProblem& q : bp)
-            if (batch_bucket(q.n) == b && (int)pick.size() < sample) pick.push_back(q);
-        if (pick.empty()) continue;
-        double best = -1.0;
-        for (int v = 0; v < kBatchVariants; ++v) {
-            // enough copies of the sample to fill every CTA slot of the wider grid, twice
-            std::vector<BatchProblem> fill;
-            int want = 0;
-            if (h->b_slots == nullptr) {
-                int bps[kBatchVariants] = {0, 0};
-                CKR(configure_batch_kernels(bps));
-                for (int w = 0; w < kBatchVariants; ++w) want = std::max(want, 2 * h->sms * bps[w]);
-            } else {
-                for (int w = 0; w < kBatchVariants; ++w) want = std::max(want, 2 * h->b_grid[w]);
-            }
-            for (int k = 0; k < want; ++k) fill.push_back(pick[k % pick.size()]);
-            std::vector<BatchResult> br;
-            double ms = 0.0;
-            const mdot_status st = batch_core(h, fill, P, br, v, &ms);
-            if (st != MDOT_OK) return st;
-            const double rate = ms > 0.0 ? 1e3 * (double)fill.size() / ms : 0.0;
-            out->problems_per_s[b][v] = rate;
-            if (rate > best) {
-                best = rate;
-                out->variant[b] = v;
-            }
+    int saved[kBatchBuckets];
+    for (int b = 0; b < kBatchBuckets; ++b) saved[b] = h->b_variant[b];
+    int best_k = 0;
+    double best = -1.0;
+    for (int k = 0; k <= kBatchBuckets; ++k) {
+        for (int b = 0; b < kBatchBuckets; ++b) h->b_variant[b] = (b < k) ? 1 : 0;
+        std::vector<BatchResult> br;
+        double ms = 0.0;
+        const mdot_status st = batch_core(h, pick, P, br, -1, &ms);
+        if (st != MDOT_OK) {
+            for (int b = 0; b < kBatchBuckets; ++b) h->b_variant[b] = saved[b];
+            return st;
         }
-        h->b_variant[b] = out->variant[b];
+        out->seconds[k] = ms / 1e3;
+        if (best < 0.0 || ms < best) {
+            best = ms;
+            best_k = k;
+        }
     }
+    for (int b = 0; b < kBatchBuckets; ++b) h->b_variant[b] = out->variant[b] = (b < best_k) ? 1 : 0;
+    out->narrow_below = best_k;
     return MDOT_OK;
 }
 

@@ -1,5 +1,6 @@
 // Instantiation and cooperative launch of the stage and dual-evaluation kernels.
 #include <algorithm>
+#include <cstring>
 #include "launch.h"
 #include "solver_kernels.cuh"
 
@@ -8,11 +9,16 @@ namespace mdot {
 size_t stage_smem_bytes(int n, int G, int tier) { return smem_layout(n, G, tier, kStageThreads).bytes; }
 // the standalone dual evaluation (wide column merge)
 size_t eval_smem_bytes(int n, int G, int tier) { return smem_layout(n, G, tier, kStageThreads, true).bytes; }
+// the flag-synchronised stage kernel with dense C (its own block size, the published-state copy)
+static size_t flag_smem_bytes(int n, int G, int tier)
+{
+    return smem_layout(n, G, tier, kFlagDenseThreads, false, true).bytes;
+}
 
 template <typename K>
-static cudaError_t coop(K kernel, int G, size_t smem, cudaStream_t s, void** args)
+static cudaError_t coop(K kernel, int G, size_t smem, cudaStream_t s, void** args, int threads = kStageThreads)
 {
-    return cudaLaunchCooperativeKernel((const void*)kernel, dim3(G), dim3(kStageThreads), args, smem, s);
+    return cudaLaunchCooperativeKernel((const void*)kernel, dim3(G), dim3(threads), args, smem, s);
 }
 
 cudaError_t launch_stage_regen(int tier, const WS& ws, const StageArgs& a, cudaStream_t s);
@@ -30,10 +36,17 @@ cudaError_t launch_stage(int tier, const WS& ws, const StageArgs& a, cudaStream_
     WS w = ws;
     StageArgs aa = a;
     void* args[] = {(void*)&w, (void*)&aa};
-    const size_t smem = stage_smem_bytes(ws.n, ws.G, tier);
-    if (tier == TIER_F64) return coop(stage_kernel<TIER_F64, COST_DENSE>, ws.G, smem, s, args);
-    if (tier == TIER_F32A) return coop(stage_kernel_flag<TIER_F32A, COST_DENSE>, ws.G, smem, s, args);
-    return coop(stage_kernel_flag<TIER_F32, COST_DENSE>, ws.G, smem, s, args);
+    if (tier == TIER_F64) return coop(stage_kernel<TIER_F64, COST_DENSE>, ws.G, stage_smem_bytes(ws.n, ws.G, tier), s, args);
+    // the flag-synchronised kernel streams dense C through its TMA ring only: other C (n not a
+    // multiple of 4, C not 16-byte aligned, no room for two ring slots) takes the
+    // barrier-synchronised kernel, same arithmetic
+    if ((ws.n & 3) != 0 || (reinterpret_cast<uintptr_t>(ws.C) & 15) != 0 ||
+        smem_layout(ws.n, ws.G, tier, kFlagDenseThreads, false, true).stages < 2)
+        return launch_stage_precond(tier, ws, a, s);
+    const size_t smem = flag_smem_bytes(ws.n, ws.G, tier);
+    if (tier == TIER_F32A)
+        return coop(stage_kernel_flag<TIER_F32A, COST_DENSE>, ws.G, smem, s, args, kFlagDenseThreads);
+    return coop(stage_kernel_flag<TIER_F32, COST_DENSE>, ws.G, smem, s, args, kFlagDenseThreads);
 }
 
 cudaError_t launch_sinkhorn_regen(int tier, const WS& ws, const StageArgs& a, cudaStream_t s);
@@ -64,25 +77,24 @@ cudaError_t launch_dual_eval(int tier, const WS& ws, const EvalArgs& a, cudaStre
 
 cudaError_t configure_stage_kernels(int max_n, int G, int* min_blocks)
 {
-    struct K { const void* f; int tier; } ks[] = {
-        {(const void*)stage_kernel_flag<TIER_F32, COST_DENSE>, TIER_F32},
-        {(const void*)stage_kernel<TIER_F64, COST_DENSE>, TIER_F64},
-        {(const void*)stage_kernel_flag<TIER_F32A, COST_DENSE>, TIER_F32A},
-        {(const void*)dual_eval_kernel<TIER_F32, COST_DENSE>, TIER_F32},
-        {(const void*)dual_eval_kernel<TIER_F64, COST_DENSE>, TIER_F64},
-        {(const void*)dual_eval_kernel<TIER_F32A, COST_DENSE>, TIER_F32A},
-        {(const void*)sinkhorn_kernel<TIER_F32, COST_DENSE>, TIER_F32},
-        {(const void*)sinkhorn_kernel<TIER_F64, COST_DENSE>, TIER_F64},
-        {(const void*)sinkhorn_kernel<TIER_F32A, COST_DENSE>, TIER_F32A}};
+    struct K { const void* f; int tier; int threads; } ks[] = {
+        {(const void*)stage_kernel_flag<TIER_F32, COST_DENSE>, TIER_F32, kFlagDenseThreads},
+        {(const void*)stage_kernel<TIER_F64, COST_DENSE>, TIER_F64, kStageThreads},
+        {(const void*)stage_kernel_flag<TIER_F32A, COST_DENSE>, TIER_F32A, kFlagDenseThreads},
+        {(const void*)dual_eval_kernel<TIER_F32, COST_DENSE>, TIER_F32, kStageThreads},
+        {(const void*)dual_eval_kernel<TIER_F64, COST_DENSE>, TIER_F64, kStageThreads},
+        {(const void*)dual_eval_kernel<TIER_F32A, COST_DENSE>, TIER_F32A, kStageThreads},
+        {(const void*)sinkhorn_kernel<TIER_F32, COST_DENSE>, TIER_F32, kStageThreads},
+        {(const void*)sinkhorn_kernel<TIER_F64, COST_DENSE>, TIER_F64, kStageThreads},
+        {(const void*)sinkhorn_kernel<TIER_F32A, COST_DENSE>, TIER_F32A, kStageThreads}};
     for (auto& k : ks) {
-        const size_t smem = stage_smem_bytes(max_n, G, k.tier);
         // the limit goes to the largest layout any n may take (fewer rows per CTA leave room for
         // more ring slots), not just to the layout of max_n
-        (void)smem;
+        (void)max_n;
         cudaError_t e = raise_smem_limit(k.f, kSmemLimit);
         if (e != cudaSuccess) return e;
         int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k.f, kStageThreads, kSmemLimit);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k.f, k.threads, kSmemLimit);
         if (e != cudaSuccess) return e;
         *min_blocks = std::min(*min_blocks, nb);
     }
@@ -92,3 +104,24 @@ cudaError_t configure_stage_kernels(int max_n, int G, int* min_blocks)
 }
 
 }  // namespace mdot
+
+extern "C" mdot_status mdot_phase_timers(uint64_t* out, int32_t max_ctas, int32_t clear)
+{
+    using namespace mdot;
+    if (!out || max_ctas < 1) return MDOT_ERR_INVALID_ARG;
+#ifdef MDOT_PHASE_TIMERS
+    static unsigned long long h[kPhaseCtas][kPhases + 1];
+    if (cudaMemcpyFromSymbol(h, g_phase, sizeof(h)) != cudaSuccess) return MDOT_ERR_CUDA;
+    const int m = std::min(max_ctas, kPhaseCtas);
+    for (int b = 0; b < m; ++b)
+        for (int k = 0; k <= kPhases; ++k) out[(size_t)b * (kPhases + 1) + k] = h[b][k];
+    if (clear) {
+        memset(h, 0, sizeof(h));
+        if (cudaMemcpyToSymbol(g_phase, h, sizeof(h)) != cudaSuccess) return MDOT_ERR_CUDA;
+    }
+    return MDOT_OK;
+#else
+    (void)clear;
+    return MDOT_NOT_READY;
+#endif
+}

@@ -417,7 +417,9 @@ constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;   // 2 s: defaul
 
 __device__ __forceinline__ unsigned long long wait_limit_ns(const GridBar* gb)
 {
-    const unsigned int us = *reinterpret_cast<const volatile unsigned int*>(&gb->limit_us);
+    // set by the host before the launch and never written by a kernel: a read-only (L1-cached)
+    // load, so that starting a wait does not cost a round trip to L2
+    const unsigned int us = __ldg(&gb->limit_us);
     return us ? 1000ull * us : kBarrierTimeoutNs;
 }
 
@@ -682,10 +684,11 @@ struct ColDelta {
     const float4* pub;
     float* out;
     float k1, k2;
+    // the published state of a thread's column groups: it does not depend on the decision, so the
+    // stage kernel loads it while the decision is being taken (load_pub), then derives (derive)
     template <int KK>
-    __device__ __forceinline__ bool load_seg(const int (&jk)[KK], int n, float (&hh)[KK][4], float (&wc)[KK][4]) const
+    __device__ __forceinline__ void load_pub(const int (&jk)[KK], int n, float4 (&q)[KK][4]) const
     {
-        float4 q[KK][4];
 #pragma unroll
         for (int k = 0; k < KK; ++k)
 #pragma unroll
@@ -693,6 +696,11 @@ struct ColDelta {
                 const int j = jk[k] + e;
                 q[k][e] = (j < n) ? __ldcg(pub + j) : make_float4(0.0f, kPadW, 0.0f, 0.0f);
             }
+    }
+    template <int KK>
+    __device__ __forceinline__ void derive(const float4 (&q)[KK][4], const int (&jk)[KK], int n, float (&hh)[KK][4],
+                                           float (&wc)[KK][4]) const
+    {
 #pragma unroll
         for (int k = 0; k < KK; ++k)
 #pragma unroll
@@ -700,6 +708,13 @@ struct ColDelta {
                 hh[k][e] = q[k][e].x;
                 wc[k][e] = (jk[k] + e < n) ? __fmaf_rn(k1, q[k][e].z, __fmaf_rn(k2, q[k][e].w, q[k][e].y)) : kPadW;
             }
+    }
+    template <int KK>
+    __device__ __forceinline__ bool load_seg(const int (&jk)[KK], int n, float (&hh)[KK][4], float (&wc)[KK][4]) const
+    {
+        float4 q[KK][4];
+        load_pub(jk, n, q);
+        derive(q, jk, n, hh, wc);
         return true;
     }
     __device__ __forceinline__ void store4(int j0, int n, const float ca[4]) const
@@ -1091,12 +1106,14 @@ struct RingGeom {
     __device__ __forceinline__ int items() const { return nrows * ncb; }
 };
 
+// CONS: consumer threads (the producer is the next warp)
+template <int CONS>
 __device__ __forceinline__ void ring_init(const RingGeom& g)
 {
     if (threadIdx.x == 0) {
         for (int s = 0; s < g.nst; ++s) {
             mbar_init(&g.full[s], 1);
-            mbar_init(&g.empty[s], kConsumerThreads / 32);
+            mbar_init(&g.empty[s], CONS / 32);
         }
         mbar_fence_init();
     }
@@ -1134,16 +1151,16 @@ __device__ __forceinline__ void ring_drain(const RingGeom& g, int consumed, int 
 
 // One row of a ring slot for this thread's column groups: the row sum (column order) and the
 // column partials.
-template <bool ACC>
-__device__ __forceinline__ float ring_row(const float4* seg, bool ok, const int (&jk)[kK], int n, int tid, float fh,
-                                          float wr, float sc, const float2 (&hh2)[kK][2], const float2 (&wc2)[kK][2],
-                                          float2 G32p, float2 Glop, float2 (&ca2)[kK][2])
+template <bool ACC, int KK, int CONS>
+__device__ __forceinline__ float ring_row(const float4* seg, bool ok, const int (&jk)[KK], int n, int tid, float fh,
+                                          float wr, float sc, const float2 (&hh2)[KK][2], const float2 (&wc2)[KK][2],
+                                          float2 G32p, float2 Glop, float2 (&ca2)[KK][2])
 {
     float rp = 0.0f;
 #pragma unroll
-    for (int k = 0; k < kK; ++k) {
+    for (int k = 0; k < KK; ++k) {
         float4 t4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (ok && jk[k] < n) t4 = seg[tid + k * kConsumerThreads];
+        if (ok && jk[k] < n) t4 = seg[tid + k * CONS];
         entry4<ACC>(fh, wr, sc, hh2[k], wc2[k], make_float2(t4.x, t4.y), make_float2(t4.z, t4.w), G32p, Glop, rp,
                     ca2[k]);
     }
@@ -1153,17 +1170,23 @@ __device__ __forceinline__ float ring_row(const float4* seg, bool ok, const int 
 // One pass over the CTA's rows through the persistent ring (same arithmetic as pass_f32_tma).
 // consumed: items consumed before this pass (identical in every thread); issued: the producer
 // thread's count.  Both advance here.
-// pre_hh / pre_wc (nullable): this thread's column constants of segment 0, already computed.
-template <bool ACC, class IO>
-__device__ __forceinline__ void pass_f32_ring(const RingGeom& g, int r1, const IO& io, const float (*pre_hh)[4],
-                                              const float (*pre_wc)[4], const float* sFh, const float* sWr,
+// sPub (nullable): the published column state of segment 0 being copied into shared memory (float4
+// per column, in column order) by a bulk copy that completes on pub_bar with parity pub_parity.
+// CONS consumer threads (kSegFloats / (4 CONS) float4 column groups each per segment), the producer
+// warp after them.
+template <bool ACC, int CONS, class IO>
+__device__ __forceinline__ void pass_f32_ring(const RingGeom& g, int r1, const IO& io, const float4* sPub,
+                                              unsigned long long* pub_bar, unsigned int pub_parity,
+                                              const float* sFh, const float* sWr,
                                               const float* sS, float G32, float Glo, float* sRow, int nloc,
                                               int& consumed, int& issued, unsigned int* abort)
 {
+    constexpr int KK = kSegFloats / (4 * CONS);
+    static_assert(KK * 4 * CONS == kSegFloats, "a segment splits evenly over the consumer threads");
     const float2 G32p = pk(G32), Glop = pk(Glo);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = g.n, r0 = g.r0, items = g.items();
-    if (warp == kConsumerThreads / 32) {
+    if (warp == CONS / 32) {
         // ------------------------------ producer warp ------------------------------
         if (lane == 0 && !ring_issue(g, issued, consumed + items + g.nst)) atomicExch(abort, 1u);
         __syncwarp();
@@ -1173,19 +1196,23 @@ __device__ __forceinline__ void pass_f32_ring(const RingGeom& g, int r1, const I
         bool ok = true;
         for (int cbi = 0; cbi < g.ncb; ++cbi) {
             const int cb = cbi * kSegFloats;
-            float hh[kK][4], wc[kK][4];
-            float2 hh2[kK][2], wc2[kK][2], ca2[kK][2];
-            int jk[kK];
+            float hh[KK][4], wc[KK][4];
+            float2 hh2[KK][2], wc2[KK][2], ca2[KK][2];
+            int jk[KK];
 #pragma unroll
-            for (int k = 0; k < kK; ++k) {
-                jk[k] = cb + 4 * (tid + k * kConsumerThreads);
+            for (int k = 0; k < KK; ++k) {
+                jk[k] = cb + 4 * (tid + k * CONS);
                 ca2[k][0] = ca2[k][1] = make_float2(0.0f, 0.0f);
             }
-            if (pre_hh != nullptr && cbi == 0) {
+            if (sPub != nullptr && cbi == 0) {
+                if (ok) ok = mbar_wait(pub_bar, pub_parity);
+                float4 q[KK][4];
 #pragma unroll
-                for (int k = 0; k < kK; ++k)
+                for (int k = 0; k < KK; ++k)
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) { hh[k][e] = pre_hh[k][e]; wc[k][e] = pre_wc[k][e]; }
+                    for (int e = 0; e < 4; ++e)
+                        q[k][e] = (jk[k] + e < n) ? sPub[jk[k] + e] : make_float4(0.0f, kPadW, 0.0f, 0.0f);
+                io.derive(q, jk, n, hh, wc);
             } else {
                 io.load_seg(jk, n, hh, wc);
             }
@@ -1210,11 +1237,11 @@ __device__ __forceinline__ void pass_f32_ring(const RingGeom& g, int r1, const I
                         if (ok) ok = mbar_wait(&g.full[sA], pA);
                         if (two && ok) ok = mbar_wait(&g.full[sB], pB);
                         const float4* segA = reinterpret_cast<const float4*>(g.ring + (size_t)sA * kSegFloats);
-                        rp[ii] = ring_row<ACC>(segA, ok, jk, n, tid, sFh[i - r0], sWr[i - r0], sS[i - r0], hh2, wc2,
+                        rp[ii] = ring_row<ACC, KK, CONS>(segA, ok, jk, n, tid, sFh[i - r0], sWr[i - r0], sS[i - r0], hh2, wc2,
                                                G32p, Glop, ca2);
                         if (two) {
                             const float4* segB = reinterpret_cast<const float4*>(g.ring + (size_t)sB * kSegFloats);
-                            rp[ii + 1] = ring_row<ACC>(segB, ok, jk, n, tid, sFh[i + 1 - r0], sWr[i + 1 - r0],
+                            rp[ii + 1] = ring_row<ACC, KK, CONS>(segB, ok, jk, n, tid, sFh[i + 1 - r0], sWr[i + 1 - r0],
                                                        sS[i + 1 - r0], hh2, wc2, G32p, Glop, ca2);
                         }
                         __syncwarp();
@@ -1229,7 +1256,7 @@ __device__ __forceinline__ void pass_f32_ring(const RingGeom& g, int r1, const I
                 if (lane < kRG && il < r1) sRow[warp * nloc + (il - r0)] += rp[0];
             }
 #pragma unroll
-            for (int k = 0; k < kK; ++k) {
+            for (int k = 0; k < KK; ++k) {
                 float ca[4];
                 from_pairs(ca2[k], ca);
                 io.store4(jk[k], n, ca);

@@ -279,6 +279,7 @@ cudaError_t admit(mdot_server* s)
         a.smoothing = P.smoothing;
         a.ls_init = P.ls_init;
         a.tensor_cores = P.tensor_cores;
+        a.polish_iters = P.polish_iters;
         e = launch_batch(kind, 0, m, a, st);       // the wide variant: one problem per SM
         if (e == cudaSuccess) e = cudaEventRecord(r->ev, st);
         if (e != cudaSuccess) return e;

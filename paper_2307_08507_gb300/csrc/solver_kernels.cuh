@@ -133,8 +133,9 @@ static __device__ void decide(State* S, const double* tot, const StageArgs& a)
 struct SmemLayout {
     int nloc_max;
     size_t off_row, off_c0, off_c1, off_s, off_A, off_x, off_merge, off_ring, off_bars, off_misc,
-        off_rstate, off_cstate, off_xc, bytes;
+        off_rstate, off_cstate, off_xc, off_pub, bytes;
     int stages;        // TMA ring slots (fp32 entries)
+    bool pub;          // room for a copy of the published column state at off_pub
 };
 
 // per-row / per-column state of the CTA's own rows and columns, kept in shared memory for a stage
@@ -143,8 +144,16 @@ enum ColState { CS_V = 0, CS_P, CS_G, CS_T, CS_GT, CS_ST, CS_COUNT };
 
 constexpr int kMergeGroups = 4;        // 32-column groups merged in one round trip by dual_eval_kernel
 
-// wide: the merge scratch of merge_cols_f32_wide (standalone dual evaluation)
-__host__ __device__ inline SmemLayout smem_layout(int n, int G, int tier, int nthreads, bool wide = false)
+// Threads of the flag-synchronised stage kernel: 8 consumer warps (16 columns of a 4096-column
+// ring segment each with dense C) and the producer warp.  (16 consumer warps with 8 columns each,
+// at most 96 registers a thread, measured slower: 30.6 against 29.0 us per evaluation at n = 4096.)
+constexpr int kFlagDenseThreads = kStageThreads;
+__host__ __device__ constexpr int flag_threads(int cost) { return cost == COST_DENSE ? kFlagDenseThreads : kStageThreads; }
+
+// wide: the merge scratch of merge_cols_f32_wide (standalone dual evaluation); pub_copy: room for
+// the flag-synchronised stage kernel's copy of the published column state (dense C)
+__host__ __device__ inline SmemLayout smem_layout(int n, int G, int tier, int nthreads, bool wide = false,
+                                                  bool pub_copy = false)
 {
     SmemLayout L;
     const int nw = nthreads / 32;
@@ -167,6 +176,10 @@ __host__ __device__ inline SmemLayout smem_layout(int n, int G, int tier, int nt
     L.off_xc = o;    o += (size_t)3 * L.nloc_max * 4;           o = (o + 15) & ~(size_t)15;
     L.off_misc = o;  o += 16;
     L.off_bars = o;  o += (tier != TIER_F64) ? (size_t)2 * kStages * 8 : 0;   o = (o + 127) & ~(size_t)127;
+    // stage kernels, fp32 entries, one ring segment: a copy of the published column state (float4
+    // per column) that the flag-synchronised stage kernel fills while the decision is taken
+    L.pub = pub_copy && !wide && tier != TIER_F64 && n <= kSegFloats;
+    L.off_pub = o;   o += L.pub ? (size_t)kSegFloats * 16 : 0;
     L.off_ring = o;
     L.stages = 0;
     if (tier != TIER_F64) {
@@ -684,10 +697,33 @@ __device__ __forceinline__ bool epi_entry(float2 sum, int A, float2 t, float p, 
     return true;
 }
 
+// Phase timers of stage_kernel_flag (diagnostic; only in a library built with
+// -DMDOT_PHASE_TIMERS, read by mdot_phase_timers): thread 0 of every CTA adds the SM cycles
+// since its previous mark to the phase's counter.  Phases: 0 loop top, 1 pass, 2 row epilogue,
+// 3 wait for the column partials, 4 merge and column epilogue, 5 CTA reduction and publication,
+// 6 wait for the scalar partials, 7 decision, 8 commit and next row constants; counter 9 counts
+// the evaluations.
+constexpr int kPhases = 9;
+constexpr int kPhaseCtas = 160;
+#ifdef MDOT_PHASE_TIMERS
+static __device__ unsigned long long g_phase[kPhaseCtas][kPhases + 1];
+#define MDOT_PHASE(k)                                                                        \
+    do {                                                                                     \
+        if (threadIdx.x == 0 && blockIdx.x < kPhaseCtas) {                                   \
+            const unsigned long long t_ = clock64();                                         \
+            g_phase[blockIdx.x][k] += t_ - ph_last;                                          \
+            ph_last = t_;                                                                    \
+        }                                                                                    \
+    } while (0)
+#else
+#define MDOT_PHASE(k) do { } while (0)
+#endif
+
 template <int TIER, int COST>
-__global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, StageArgs a)
+__global__ void __launch_bounds__(flag_threads(COST), 1) stage_kernel_flag(WS ws, StageArgs a)
 {
     static_assert(TIER != TIER_F64, "the flag-synchronised stage kernel carries fp32 partials");
+    constexpr int kCons = flag_threads(COST) - 32;      // consumer threads; the producer warp follows
     extern __shared__ __align__(16) unsigned char sm[];
     __shared__ float2 red_smem[32 * kNRed];
     __shared__ double tot_smem[kNRed];
@@ -698,7 +734,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
 
     const int n = ws.n, G = ws.G, b = blockIdx.x, T = blockDim.x, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    const SmemLayout L = smem_layout(n, G, TIER, T);
+    const SmemLayout L = smem_layout(n, G, TIER, T, false, COST == COST_DENSE);
     int r0, r1, c0, c1;
     row_range(n, G, b, r0, r1);
     row_range(n, G, b, c0, c1);
@@ -727,11 +763,19 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
     unsigned int t = 0;                   // evaluations of this launch so far
     // dense C streamed through a TMA ring that stays alive over the launch (see pass_f32_ring)
     const bool use_ring = COST == COST_DENSE && (n & 3) == 0 && (reinterpret_cast<uintptr_t>(ws.C) & 15) == 0 &&
-                          T == kStageThreads && L.stages >= 2;
+                          T == flag_threads(COST) && L.stages >= 2;
     RingGeom ring{ws.C, n, r0, nrl, (n + kSegFloats - 1) / kSegFloats, L.stages,
                   reinterpret_cast<float*>(sm + L.off_ring), reinterpret_cast<unsigned long long*>(sm + L.off_bars),
                   reinterpret_cast<unsigned long long*>(sm + L.off_bars) + kStages};
     int consumed = 0, issued = 0;
+    // the owners' published column state (one segment: n <= kSegFloats) is bulk-copied into shared
+    // memory as soon as its flags are seen, while the scalar partials are awaited and the decision
+    // is taken; the next pass derives its column constants from that copy
+    float4* sPub = reinterpret_cast<float4*>(sm + L.off_pub);
+    __shared__ __align__(8) unsigned long long s_pub_bar;
+    __shared__ unsigned int s_pub_issued;            // copies issued (written by the issuing lane only)
+    const bool prefetch = use_ring && L.pub;
+    unsigned int pub_used = 0;                       // copies consumed by passes (uniform in the CTA)
 
     if (tid == 0) {
         s_base = *reinterpret_cast<volatile unsigned int*>(ws.epoch);
@@ -749,12 +793,17 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
         s_step = ColStep{0, 0.0f, 0.0f, 0.0f};
         s_ok = 1;
     }
-    if (use_ring) ring_init(ring);
+    if (use_ring) ring_init<kCons>(ring);
+    if (prefetch && tid == 0) {
+        mbar_init(&s_pub_bar, 1);
+        mbar_fence_init();
+    }
+    if (tid == 0) s_pub_issued = 0;
     load_row_coords<COST>(ws, r0, r1, sm, L.off_xc);
     __syncthreads();
     const unsigned int base = s_base;
     // the first rows of the first pass load while the prologue runs
-    if (use_ring && tid == kConsumerThreads && !ring_issue(ring, issued, ring.nst)) atomicExch(abort, 1u);
+    if (use_ring && tid == kCons && !ring_issue(ring, issued, ring.nst)) atomicExch(abort, 1u);
 
     // ---- prologue (Alg. 1): smoothing, rank-one start or warm start, constants at alpha = 0 ----
     for (int i = r0 + tid; i < r1; i += T) {
@@ -806,8 +855,15 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
     if (tid == 0) post_flag(fpub + b, base + 1u);
     cta_wait_flags(fpub, G, base + 1u, &ws.st->bar, &s_ok);
 
+#ifdef MDOT_PHASE_TIMERS
+    unsigned long long ph_last = clock64();
+#endif
     for (; s_ok; ++t) {
         const unsigned int tag = base + 2u + t;
+#ifdef MDOT_PHASE_TIMERS
+        if (tid == 0 && b < kPhaseCtas) g_phase[b][kPhases] += 1;
+#endif
+        MDOT_PHASE(0);
         // ---------------- phase A: pass over own rows; column constants derived in place ----------------
         {
             const float2 kk = col_step_coeffs(s_step);
@@ -816,15 +872,22 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
                 float* sRow = reinterpret_cast<float*>(sm + L.off_row);
                 for (int x = tid; x < (T >> 5) * NL; x += T) sRow[x] = 0.0f;
                 __syncthreads();
-                pass_f32_ring<TIER == TIER_F32A>(ring, r1, io, nullptr, nullptr,
+                const bool from_copy = pub_used < s_pub_issued;   // read after a barrier
+                pass_f32_ring<TIER == TIER_F32A, kCons>(ring, r1, io, from_copy ? sPub : nullptr, &s_pub_bar,
+                                                 pub_used & 1u,
                                                  reinterpret_cast<const float*>(sm + L.off_c0),
                                                  reinterpret_cast<const float*>(sm + L.off_c1),
                                                  reinterpret_cast<const float*>(sm + L.off_s), G32, Glo, sRow, NL,
                                                  consumed, issued, abort);
-            } else {
+                if (from_copy) ++pub_used;
+            } else if (COST != COST_DENSE) {
                 phase_A<TIER, COST>(ws, io, r0, r1, gamma, G64, sm, L);
             }
+            // (dense C that the ring cannot stream -- n not a multiple of 4, C not 16-byte aligned,
+            // no room for two slots -- is solved by the barrier-synchronised stage kernel instead:
+            // flag_stage_ok below)
         }
+        MDOT_PHASE(1);
         if (tid == 0) post_flag(fcp + b, tag);             // phase_A ends with a __syncthreads
         float2 x[kNRed];
 #pragma unroll
@@ -846,8 +909,10 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
             }
         }
 
+        MDOT_PHASE(2);
         // ---------------- phase B: column merge and epilogue; publish the column state ----------------
         if (!cta_wait_flags(fcp, G, tag, &ws.st->bar, &s_ok)) break;
+        MDOT_PHASE(3);
         for (int j0 = c0; j0 < c1; j0 += 32) {
             const float2 colsum = merge_cols_f32_df(ws.colpart, n, G, j0, c1, reinterpret_cast<float*>(sm + L.off_merge));
             const int j = j0 + tid;
@@ -862,29 +927,54 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
                 ws.pub[j] = col_publish(QV[jl], QP[jl], sf, inv_gamma, G32, Glo);
             }
         }
+        MDOT_PHASE(4);
         // CTA partial sums (double-floats): only the warps that hold rows (columns sit in warp 0)
-        if (warp < red_warps) {
+        if (red_warps == 1) {
+            // every partial sits in warp 0 (at most 32 own rows): it reduces them, writes the tagged
+            // words and publishes its column state itself, with no barrier of the whole CTA
+            if (warp == 0) {
 #pragma unroll
-            for (int q = 0; q < kNRed; ++q)
+                for (int q = 0; q < kNRed; ++q)
 #pragma unroll
-                for (int o = 16; o >= 1; o >>= 1) x[q] = df_add(x[q], df_shfl_xor(x[q], o));
-            if (lane == 0)
+                    for (int o = 16; o >= 1; o >>= 1) x[q] = df_add(x[q], df_shfl_xor(x[q], o));
+                float2 acc = x[0];
 #pragma unroll
-                for (int q = 0; q < kNRed; ++q) red_smem[warp * kNRed + q] = x[q];
+                for (int q = 1; q < kNRed; ++q)
+                    if (lane == q) acc = x[q];
+                if (lane < kNRed) {
+                    unsigned long long* dst = ws.tsp + (size_t)b * 2 * kNRed + 2 * lane;
+                    st_tag(dst, tag_pack(__float_as_uint(acc.y), tag));
+                    st_tag(dst + 1, tag_pack(__float_as_uint(acc.x), tag));
+                }
+                // the lanes' column-state writes are ordered before the release by the warp barrier
+                __syncwarp();
+                if (lane == 0) post_flag(fpub + b, tag);
+            }
+        } else {
+            if (warp < red_warps) {
+#pragma unroll
+                for (int q = 0; q < kNRed; ++q)
+#pragma unroll
+                    for (int o = 16; o >= 1; o >>= 1) x[q] = df_add(x[q], df_shfl_xor(x[q], o));
+                if (lane == 0)
+#pragma unroll
+                    for (int q = 0; q < kNRed; ++q) red_smem[warp * kNRed + q] = x[q];
+            }
+            __syncthreads();
+            if (tid < kNRed) {
+                // the CTA's partial sum as two tagged words: the double-float's high and low floats
+                float2 acc = make_float2(0.0f, 0.0f);
+                for (int ww = 0; ww < red_warps; ++ww) acc = df_add(acc, red_smem[ww * kNRed + tid]);
+                unsigned long long* dst = ws.tsp + (size_t)b * 2 * kNRed + 2 * tid;
+                st_tag(dst, tag_pack(__float_as_uint(acc.y), tag));
+                st_tag(dst + 1, tag_pack(__float_as_uint(acc.x), tag));
+            }
+            // the column state written in phase B is published by a thread with nothing else to do:
+            // the release store waits for those writes, and only this thread waits with it
+            if (tid == kCons) post_flag(fpub + b, tag);
         }
-        __syncthreads();
-        if (tid < kNRed) {
-            // the CTA's partial sum as two tagged words: the double-float's high and low floats
-            float2 acc = make_float2(0.0f, 0.0f);
-            for (int ww = 0; ww < red_warps; ++ww) acc = df_add(acc, red_smem[ww * kNRed + tid]);
-            unsigned long long* dst = ws.tsp + (size_t)b * 2 * kNRed + 2 * tid;
-            st_tag(dst, tag_pack(__float_as_uint(acc.y), tag));
-            st_tag(dst + 1, tag_pack(__float_as_uint(acc.x), tag));
-        }
-        // the column state written in phase B is published by a thread with nothing else to do:
-        // the release store waits for those writes, and only this thread waits with it
-        if (tid == kConsumerThreads) post_flag(fpub + b, tag);
 
+        MDOT_PHASE(5);
         // ---------------- every CTA: the G partials in a fixed order, then the decision ----------------
         bool ok = true;
         if (warp < kNRed) {
@@ -917,10 +1007,27 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
 #pragma unroll
             for (int o = 16; o >= 1; o >>= 1) sacc = df_add(sacc, df_shfl_xor(sacc, o));
             if (lane == 0) tot_smem[warp] = df_to_double(sacc);
+        } else if (warp == kNRed) {
+            // the next pass reads every owner's column state (published before its scalar words):
+            // once all of it is visible, one lane starts its bulk copy into shared memory
+            ok = wait_flags(fpub, G, tag, &ws.st->bar);
+            if (ok && prefetch && lane == 0) {
+                // the state was acquired through the generic proxy; the copy reads it through the
+                // async proxy, and overwrites a copy the last pass read through the generic proxy
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                const unsigned int bytes = (unsigned int)n * 16u;
+                mbar_arrive_expect_tx(&s_pub_bar, bytes);
+                for (unsigned int o = 0; o < bytes; o += 16384u)
+                    tma_load_1d(reinterpret_cast<unsigned char*>(sPub) + o,
+                                reinterpret_cast<const unsigned char*>(ws.pub) + o, min(16384u, bytes - o), &s_pub_bar);
+                s_pub_issued += 1u;
+            }
         }
         if (!ok) s_ok = 0;
         __syncthreads();
         if (!s_ok) break;
+        MDOT_PHASE(6);
         if (tid == 0) {
             double tot[kNRed];
             for (int q = 0; q < kNRed; ++q) tot[q] = tot_smem[q];
@@ -933,11 +1040,8 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
             s_step = ColStep{loc.accept, (float)loc.alpha_commit, (float)loc.beta, (float)loc.alpha};
         }
         __syncthreads();
+        MDOT_PHASE(7);
         const bool accept = sst.accept != 0, done = sst.phase != PH_RUN;
-
-        // the next pass reads every owner's column state: one warp acquires their flags while
-        // warp 0 commits (the barrier at the end of the iteration covers it)
-        if (warp == kNRed && !done && !wait_flags(fpub, G, tag, &ws.st->bar)) s_ok = 0;
 
         // ---------------- phase C: commit, new direction, next trial constants (rows) ----------------
         for (int i = r0 + tid; i < r1; i += T) {
@@ -961,6 +1065,7 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
         }
         if (done) break;
         __syncthreads();
+        MDOT_PHASE(8);
     }
     // the stage's iterate (also on a timeout: the best iterate so far) goes back to global memory
     __syncthreads();
@@ -969,8 +1074,10 @@ __global__ void __launch_bounds__(kStageThreads, 1) stage_kernel_flag(WS ws, Sta
         ws.lr[i] = (double)RF[RS_L * 2 * NL + i - r0];
     }
     for (int j = c0 + tid; j < c1; j += T) ws.v[j] = df_to_double(QV[j - c0]);
-    // rows prefetched for a pass that never came must land before the CTA exits
-    if (use_ring && tid == kConsumerThreads) ring_drain(ring, consumed, issued);
+    // rows prefetched for a pass that never came, and a copy of the column state that no pass
+    // consumed, must land before the CTA exits
+    if (use_ring && tid == kCons) ring_drain(ring, consumed, issued);
+    if (prefetch && tid == 0 && pub_used < s_pub_issued) mbar_wait(&s_pub_bar, pub_used & 1u);
     if (tid == 0) {
         // the next launch's tags start above every tag this one may have posted
         atomicMax(ws.epoch, base + t + 3u);

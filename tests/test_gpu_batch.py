@@ -49,12 +49,74 @@ def _problem(p, d, gamma_f):
                           gamma_f=gamma_f, u_out=d["u"], v_out=d["v"])
 
 
-# The batched form has fp32 entries only, so its last stage can be driven down to about the fp32
-# floor (mdot_params.fp32_floor, 2e-7) and no further; on problems of a few dozen points the fp32
-# noise of a row's few significant entries does not average out, so these tests ask for 5e-7.  The
-# oracle is run with the same last-stage tolerance, so both stop within 5e-7 (in L1) of the same
-# entropic optimum and the rounded costs must agree to the 1e-7 target.
+# The fp32 tiers of the batched form drive a stage down to about their noise floor
+# (mdot_params.fp32_floor, 2e-7); on problems of a few dozen points the fp32 noise of a row's few
+# significant entries does not average out, so the tests of the fp32 path ask for 5e-7 (reached
+# without the fp64 polish).  The oracle is run with the same last-stage tolerance, so both stop
+# within 5e-7 (in L1) of the same entropic optimum and the rounded costs must agree to the 1e-7
+# target.  A tighter last-stage tolerance is reached by the fp64 polish (test below).
 FLOOR = 5e-7
+
+
+def _grid_problem(k, seed, gf, dense=False):
+    p = I.grid_problem(k, seed)
+    d = {"r": t(p.r), "c": t(p.c), "u": torch.empty(p.n, dtype=torch.float64, device=DEV),
+         "v": torch.empty(p.n, dtype=torch.float64, device=DEV)}
+    if dense:
+        d["C"] = t(p.C)
+        prob = M.make_problem(d["r"], d["c"], C=d["C"], gamma_f=gf, u_out=d["u"], v_out=d["v"])
+    else:
+        d["xy"] = t(I.coords3(p.x))
+        prob = M.make_problem(d["r"], d["c"], x=d["xy"], y=d["xy"], kind=M.COST_SQEUCLID, scale=p.scale,
+                              gamma_f=gf, u_out=d["u"], v_out=d["v"])
+    return p, d, prob
+
+
+# the batched form floors every stage tolerance at fp32_floor; a caller who needs a tighter last
+# stage lowers it, and the fp64 polish (at most polish_iters iterations) finishes the stage
+TIGHT = 1e-10
+TIGHT_PARAMS = dict(final_tol=TIGHT, fp32_floor=TIGHT, polish_iters=2000)
+
+
+def test_batch_fp64_polish_reaches_a_tight_tolerance(h):
+    """A last-stage tolerance below the accurate fp32 tier's noise: the fp32 part of the stage
+    stalls above it and the batched solver continues in fp64 entries (as mdot_solve does) until it
+    is reached, for the regenerated and the dense cost; the rounded costs match the oracle run to
+    the same tolerance (grid histograms, whose last stage converges in some 100 fp64 iterations)."""
+    tight = TIGHT
+    gf = 2.0 ** 12
+    cases = [_grid_problem(24, 4900, gf), _grid_problem(10, 4901, gf), _grid_problem(24, 4900, gf, dense=True)]
+    res = h.solve_batch([prob for _, _, prob in cases], M.default_params(**TIGHT_PARAMS))
+    refs = {}
+    for (p, d, _), r in zip(cases, res):
+        assert r.status == M.MDOT_OK, M.status_string(r.status)
+        assert r.grad_l1 <= tight, (p.n, r.grad_l1)
+        if p.n not in refs:
+            refs[p.n] = O.solve(p.C.astype(np.float64), p.r, p.c, gamma_f=gf, final_tol=tight)
+        assert abs(r.cost - refs[p.n].cost) <= 1e-7, (p.n, r.cost, refs[p.n].cost)
+
+
+def test_batch_fp64_polish_over_two_row_chunks(h):
+    """n = 2116 > 2048 rows: the fp64 pass adds the column sums of its two row chunks.  Against the
+    single-problem solver (whose fp64 polish the parity tests check against the oracle) at the same
+    tolerance, and the returned potentials' marginals recomputed by the oracle's dual evaluation."""
+    tight = TIGHT
+    gf = 2.0 ** 10
+    p, d, prob = _grid_problem(46, 4902, gf)
+    r = h.solve_batch([prob], M.default_params(**TIGHT_PARAMS))[0]
+    assert r.status == M.MDOT_OK and r.grad_l1 <= tight, (M.status_string(r.status), r.grad_l1)
+    _, _, one = h.solve_points(d["r"], d["c"], d["xy"], d["xy"], M.COST_SQEUCLID, p.scale, 1e-6,
+                               M.default_params(gamma_f=gf, final_tol=tight))
+    assert one.status == M.MDOT_OK
+    assert abs(r.cost - one.cost) <= 1e-8, (r.cost, one.cost)
+    # the gradient norm the batched solver reports, recomputed from its potentials by the oracle's
+    # dual evaluation against the last stage's smoothed marginals (Alg. 1: weight w = eps_d)
+    lr, lc = O.dual_eval(p.C.astype(np.float64), d["u"].cpu().numpy(), d["v"].cpu().numpy(), gf)
+    w = r.H_min / gf ** M.default_params().p
+    rt = (1.0 - w / 4.0) * p.r + w / (4.0 * p.n)
+    ct = (1.0 - w / 4.0) * p.c + w / (4.0 * p.n)
+    gnorm = np.abs(np.exp(lr) - rt).sum() + np.abs(np.exp(lc) - ct).sum()
+    assert gnorm <= 2.0 * tight, gnorm
 
 
 def test_batch_matches_oracle_and_single_solves(h):
@@ -137,8 +199,8 @@ def test_batch_grid_problems_on_the_tensor_cores_match_oracle(h):
 
 def test_batch_tile_variants_and_tuner(h):
     """Both tile variants of the batched kernel (256 threads and one problem per SM; 128 threads
-    and two per SM) give results equal to the oracle's; the tuner times the populated size buckets
-    and installs a table that later solves use."""
+    and two per SM) give results equal to the oracle's; the tuner times every candidate table on
+    the batch and installs the fastest, which later solves use."""
     gf = 2.0 ** 10
     sizes = [300, 700, 64, 1500]
     probs = _point_problems(sizes, 4700)
@@ -155,12 +217,13 @@ def test_batch_tile_variants_and_tuner(h):
         for p, r, ref in zip(probs, res, refs):
             assert r.status == M.MDOT_OK, M.status_string(r.status)
             assert abs(r.cost - ref.cost) <= 1e-7, (variant, p.n, r.cost, ref.cost)
-    tuned = h.tune_batch(plist, prm, sample=2)
-    rates = tuned.as_dict()["problems_per_s"]
-    for b in (0, 1, 2):                       # buckets of 64/300, 700 and 1500
-        assert rates[b][0] > 0 and rates[b][1] > 0
-        assert tuned.variant[b] == (0 if rates[b][0] >= rates[b][1] else 1)
-    assert rates[3] == [0.0, 0.0] and rates[4] == [0.0, 0.0]
-    res = h.solve_batch(plist, prm)
-    assert all(r.status == M.MDOT_OK for r in res)
+    tuned = h.tune_batch(plist, prm, sample=3)
+    secs = tuned.as_dict()["seconds"]
+    k = tuned.narrow_below
+    assert all(t > 0.0 for t in secs)                       # every candidate table was timed
+    assert secs[k] == min(secs) and all(secs[q] > secs[k] for q in range(k))
+    assert list(tuned.variant) == [1 if b < k else 0 for b in range(5)]
+    res = h.solve_batch(plist, prm)                         # the installed table
+    for p, r, ref in zip(probs, res, refs):
+        assert r.status == M.MDOT_OK and abs(r.cost - ref.cost) <= 1e-7, (k, p.n, r.cost, ref.cost)
     h.set_batch_tuning(M.BatchTuning())      # back to the default (wide) variant for other tests
