@@ -40,8 +40,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample-evals", type=int, default=0, help="oracle evaluations in the CPU sample")
     ap.add_argument("--case", default="solve",
-                    choices=["solve", "dual_eval", "dual_eval_regen", "stage", "batch", "serve", "tune_serve", "sinkhorn",
-                             "large_n", "nscale", "hmin", "phases"],
+                    choices=["solve", "dual_eval", "dual_eval_regen", "dual_eval_regen_tc", "stage", "batch", "serve",
+                             "tune_serve", "sinkhorn", "large_n", "nscale", "hmin", "phases"],
                     help="dual_eval / stage: run only that kernel (for profiler captures); sinkhorn, large_n, "
                          "nscale, hmin: the comparison studies (one JSON line per solve)")
     ap.add_argument("--grid", type=int, default=64, help="k of the k x k grid for --case runs")
@@ -110,8 +110,9 @@ def exact_value(kind="l2sq"):
 def gap_sweep(h, dev, stream):
     """The n = 4096 instance (64 x 64 grid, seed 2000) with both costs (squared Euclidean, L1) at
     target gaps 1e-4 ... 1e-7: one untimed and one timed solve each (CUDA events on the handle's
-    stream), the true gap against the exact optimum, the certificate, and the difference to the
-    FP64 oracle's rounded cost on the same instance (tests/golden/)."""
+    stream), the true gap against the exact optimum where it is stored, an upper bound on the true
+    gap (cost minus the c-transform bound of a gamma_f = 2^21 solve), the certificate, and the
+    difference to the FP64 oracle's rounded cost on the same instance (tests/golden/)."""
     import torch
     import paper_2307_08507_gb300 as M
     from paper_2307_08507_gb300 import inputs as I
@@ -135,6 +136,13 @@ def gap_sweep(h, dev, stream):
                          "gap_cert": res.gap_cert,
                          "meets_target": (res.cost - exact <= eps) if exact is not None else None,
                          "cost_minus_oracle": (res.cost - g["oracle_cost"]) if g else None})
+        # an upper bound on every row's true gap without the exact optimum: the c-transform bound of
+        # a solve at gamma_f = 2^21 is a feasible OT dual value, so OT >= it (weak duality)
+        _, _, hi = h.solve(r, c, C, 1e-6, M.default_params(gamma_f=2.0 ** 21), check=False)
+        lb_hi = hi.cost - hi.gap_cert
+        for row in rows:
+            if row["cost_kind"] == kind:
+                row["true_gap_bound"] = row["cost"] - lb_hi
         del C
     return rows
 
@@ -402,16 +410,20 @@ def measure_batch(h, dev, stream, sample_single=128):
     order = sorted(range(len(probs)), key=lambda k: probs[k]["n"])
     pick = order[:: max(1, len(order) // sample_single)][:sample_single]
     t_single, dcost, evals_b, evals_s = 0.0, [], 0, 0
+    st_single, st_batch_pick = {}, {}
     for k in pick:
         q = probs[k]
         ev0.record(stream)
-        _, _, rs = h.solve_points(q["r"], q["c"], q["x"], q["y"], M.COST_SQEUCLID, q["scale"], BATCH_EPS)
+        _, _, rs = h.solve_points(q["r"], q["c"], q["x"], q["y"], M.COST_SQEUCLID, q["scale"], BATCH_EPS,
+                                  check=False)
         ev1.record(stream)
         torch.cuda.synchronize()
         t_single += ev0.elapsed_time(ev1) / 1e3
         dcost.append(abs(rs.cost - res[k].cost))
         evals_b += res[k].evals
         evals_s += rs.info.evals
+        st_single[M.status_string(rs.status)] = st_single.get(M.status_string(rs.status), 0) + 1
+        st_batch_pick[M.status_string(res[k].status)] = st_batch_pick.get(M.status_string(res[k].status), 0) + 1
     t_single_all = t_single * len(probs) / len(pick)
     # entries of all evaluations of the batch per second, against the fp32 issue bound (the pass
     # regenerates the cost: ALU_OPS_PER_ENTRY fp32 operations per entry)
@@ -434,6 +446,7 @@ def measure_batch(h, dev, stream, sample_single=128):
                          "achieved": entries * ALU_OPS_PER_ENTRY / t_batch / 1e12, "peak": alu / 1e12,
                          "unit": "Tops/s", "frac": entries * ALU_OPS_PER_ENTRY / t_batch / alu},
             "one_per_launch_sample": len(pick), "one_per_launch_seconds_sample": t_single,
+            "one_per_launch_statuses": st_single, "batched_statuses_on_that_sample": st_batch_pick,
             "one_per_launch_problems_per_s": len(probs) / t_single_all,
             "speedup_vs_one_per_launch": t_single_all / t_batch,
             "max_abs_cost_diff_vs_one_per_launch": max(dcost), "evals_batch_sample": evals_b,
@@ -929,13 +942,16 @@ def run_case(args):
         lr, _ = h.dual_eval(u, v, 2.0 ** 12, C)
         for _ in range(args.reps):
             h.dual_eval(u, v, 2.0 ** 12, C, ref_log_rP=lr)
-    elif args.case == "dual_eval_regen":
+    elif args.case in ("dual_eval_regen", "dual_eval_regen_tc"):
+        # the regenerated squared-Euclidean cost of the grid points: fp32 operations, or (_tc) the
+        # contraction on the tensor cores
+        prec = M.PREC_FP32 | (M.PREC_TENSOR_CORES if args.case == "dual_eval_regen_tc" else 0)
         u = torch.from_numpy(np.log(p.r)).to(dev)
         v = torch.from_numpy(np.log(p.c)).to(dev)
         xy = torch.from_numpy(I.coords3(p.x)).to(dev)
-        lr, _ = h.dual_eval_points(u, v, 2.0 ** 12, xy, xy, M.COST_SQEUCLID, p.scale)
+        lr, _ = h.dual_eval_points(u, v, 2.0 ** 12, xy, xy, M.COST_SQEUCLID, p.scale, precision=prec)
         for _ in range(args.reps):
-            h.dual_eval_points(u, v, 2.0 ** 12, xy, xy, M.COST_SQEUCLID, p.scale, ref_log_rP=lr)
+            h.dual_eval_points(u, v, 2.0 ** 12, xy, xy, M.COST_SQEUCLID, p.scale, ref_log_rP=lr, precision=prec)
     else:
         r = torch.from_numpy(p.r).to(dev)
         c = torch.from_numpy(p.c).to(dev)

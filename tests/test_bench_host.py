@@ -30,3 +30,27 @@ def test_source_hash_covers_the_cuda_sources():
 
 def test_max_over_ranks_single_process():
     assert bench.max_over_ranks(1.25, None, None) == 1.25
+
+
+def test_not_converged_summary_counts_and_quartiles():
+    """The batched measurement's summary of the problems whose last stage ended above its
+    tolerance: count, sizes, gradient-norm quartiles (no GPU: fake results)."""
+    class R:
+        def __init__(self, status, g):
+            self.status, self.grad_l1 = status, g
+
+    class FakeM:
+        MDOT_ERR_NOT_CONVERGED = 2
+
+        @staticmethod
+        def default_params():
+            class P:
+                fp32_floor = 2e-7
+            return P()
+
+    probs = [{"n": n} for n in (300, 500, 700, 900)]
+    res = [R(0, 1e-7), R(2, 4e-7), R(2, 1e-6), R(0, 5e-8)]
+    s = bench._not_converged_summary(probs, res, FakeM)
+    assert s["count"] == 2 and s["n_min"] == 500 and s["n_max"] == 700
+    assert s["grad_l1_quartiles"][0] == 4e-7 and s["grad_l1_quartiles"][-1] == 1e-6
+    assert bench._not_converged_summary(probs, [R(0, 1e-7)] * 4, FakeM) == {"count": 0}
