@@ -72,3 +72,17 @@ def test_struct_layouts_match_the_binding(tmp_path):
         assert got[(struct, "size")] == ctypes.sizeof(cls), struct
         for name, _ in cls._fields_:
             assert got[(struct, name)] == getattr(cls, name).offset, (struct, name)
+
+
+def test_phase_timers_report_not_ready_in_the_default_build():
+    """mdot_phase_timers keeps counters only in the diagnostic build (-DMDOT_PHASE_TIMERS); the
+    default library answers MDOT_NOT_READY without touching the device, and rejects bad
+    arguments."""
+    lib = ctypes.CDLL(B.build())
+    lib.mdot_phase_timers.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]
+    lib.mdot_phase_timers.restype = ctypes.c_int32
+    buf = (ctypes.c_uint64 * 20)()
+    import paper_2307_08507_gb300 as M
+    assert lib.mdot_phase_timers(ctypes.cast(buf, ctypes.c_void_p), 2, 0) == M.MDOT_NOT_READY
+    assert lib.mdot_phase_timers(None, 2, 0) == M.MDOT_ERR_INVALID_ARG
+    assert lib.mdot_phase_timers(ctypes.cast(buf, ctypes.c_void_p), 0, 0) == M.MDOT_ERR_INVALID_ARG
