@@ -403,8 +403,8 @@ typedef struct mdot_server mdot_server;
 /* Routing of the server (NULL in mdot_server_create: the defaults below). */
 typedef struct mdot_server_config {
     int64_t big_n;            /* requests with n > big_n go to a big lane (default 2048)           */
-    int32_t big_lanes;        /* concurrent cooperative solves (default 2; 0: every request batched) */
-    int32_t lane_ctas;        /* CTAs (SMs) of each big lane (default: SMs / 4)                     */
+    int32_t big_lanes;        /* concurrent cooperative solves (default 3; 0: every request batched) */
+    int32_t lane_ctas;        /* CTAs (SMs) of each big lane (default: 29 % of the SMs, 44 of 152)  */
 } mdot_server_config;
 
 mdot_status mdot_server_create(mdot_server** s, uint64_t workspace_bytes, const mdot_params* prm,

@@ -561,7 +561,7 @@ class Server:
         self._s = _P()
         cfg = None
         if big_n is not None or big_lanes is not None or lane_ctas is not None:
-            cfg = ServerConfig(big_n if big_n is not None else 2048, big_lanes if big_lanes is not None else 2,
+            cfg = ServerConfig(big_n if big_n is not None else 2048, big_lanes if big_lanes is not None else 3,
                                lane_ctas or 0)
         s = L.mdot_server_create(ct.byref(self._s), int(workspace_bytes), ct.byref(params) if params is not None else None,
                                  ct.byref(cfg) if cfg is not None else None)
@@ -618,14 +618,14 @@ def tune_server(workspace_bytes: int, requests, candidates=None, params: Params 
     (arrival offset in seconds, mdot_problem, tensors to keep alive) -- at their arrival times and
     the wall time to the last result is taken.  Returns (best candidate as a dict, one dict per
     candidate with problems_per_s, seconds and the per-request statuses and costs in request
-    order).  Candidates default to three routings around the built-in one."""
+    order).  Candidates default to the built-in routing and two around it."""
     import time
     import torch
     if candidates is None:
         sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-        candidates = [dict(big_n=2048, big_lanes=2, lane_ctas=sms // 4),
-                      dict(big_n=1024, big_lanes=4, lane_ctas=sms // 8),
-                      dict(big_n=4096, big_lanes=1, lane_ctas=sms // 4)]
+        candidates = [dict(big_n=2048, big_lanes=3, lane_ctas=sms * 29 // 100),
+                      dict(big_n=2048, big_lanes=2, lane_ctas=sms * 42 // 100),
+                      dict(big_n=1024, big_lanes=4, lane_ctas=sms * 21 // 100)]
     table = []
     for cand in candidates:
         torch.cuda.synchronize()

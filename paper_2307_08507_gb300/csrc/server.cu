@@ -440,12 +440,13 @@ mdot_status mdot_server_create(mdot_server** out, uint64_t workspace_bytes, cons
     int sms = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->dev);
     const int gmax = std::min(sms, 160);
-    // defaults measured on the serving trace (60 requests, n log-uniform on [128, 8192], gaps
-    // 1e-4 .. 1e-7): two lanes of a quarter of the SMs for n > 2048 gave the best problems/s and
-    // p99 (2.35/s, 25 s) against four lanes of an eighth for n > 1024 (1.39/s, 35 s)
+    // defaults measured on the serving trace (200 requests, n log-uniform on [128, 8192], gaps
+    // 1e-4 .. 1e-7, requests above n = 2048 holding ~90 % of the work): three lanes of 29 % of the
+    // SMs each for n > 2048 served 5.50 problems/s, against 5.19 with two lanes of 64 SMs, 4.74 with
+    // four of 32, 4.58 with four of 32 from n > 1024 and 3.25 with two lanes of a quarter of the SMs
     s->big_n = (cfg && cfg->big_n > 0) ? cfg->big_n : 2048;
-    s->big_lanes = cfg ? cfg->big_lanes : 2;
-    const int share = (cfg && cfg->lane_ctas > 0) ? cfg->lane_ctas : std::max(1, gmax / 4);
+    s->big_lanes = cfg ? cfg->big_lanes : 3;
+    const int share = (cfg && cfg->lane_ctas > 0) ? cfg->lane_ctas : std::max(1, gmax * 29 / 100);
     if (s->big_lanes < 0 || s->big_lanes > kMaxBigLanes || share > gmax || s->big_lanes * share > gmax - 8) {
         destroy_records(s);
         cudaFree(s->pool_mem);
