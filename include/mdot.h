@@ -115,9 +115,10 @@ typedef struct mdot_params {
                                mdot_cost_matrix); 0 (default): fp32 operations, measured faster on
                                GB300 because the pass is bound by the exponentials and sums      */
     int32_t polish_iters;   /* batched form and server only: fp64-entry PNCG iterations at most that
-                               finish a problem's last stage when its fp32 part stalled above the
-                               stage's tolerance (one CTA per problem, where an fp64 evaluation costs
-                               ~5 ns per entry); 64; 0: no polish                                 */
+                               finish a problem's last stage on its own SM when its fp32 part
+                               stalled above the stage's tolerance (an fp64 evaluation on one SM
+                               costs ~5 ns per entry); mdot_solve_batch then finishes what is
+                               left on every SM; 64; 0: neither                                   */
     int32_t reserved;
 } mdot_params;
 
@@ -341,8 +342,13 @@ typedef struct mdot_result {
  * stage below fp32_floor in fp64 entries on every SM, one CTA per problem cannot afford that on
  * ill-conditioned problems (thousands of fp64 iterations); a caller who needs a tighter last
  * stage lowers fp32_floor.  With precision AUTO a last stage whose fp32 part ended by the stall
- * rule above its tolerance continues in fp64 entries for at most polish_iters iterations;
- * a problem still above it reports MDOT_ERR_NOT_CONVERGED.  results: host array of nprob.  prm: NULL for defaults.  Workspace (about 1.4 MiB per
+ * rule above its tolerance continues in fp64 entries on its SM for at most polish_iters
+ * iterations; a problem still above it after the launch is finished by the single-problem
+ * solver's fp64 stage on every SM (from its potentials; for problems that asked for none the
+ * handle keeps them in scratch it allocates, 16 bytes per column; problems larger than the
+ * handle's max_n are not finished) and reports MDOT_ERR_NOT_CONVERGED only if that stage
+ * cannot reach the tolerance either.  polish_iters = 0 turns both off.  results: host array of
+ * nprob.  prm: NULL for defaults.  Workspace (about 1.4 MiB per
  * SM) is allocated on the first call and kept by the handle.
  * Returns INVALID_ARG if any problem is malformed (nothing is solved), else MDOT_OK; per-problem
  * outcomes are in results[k].status.

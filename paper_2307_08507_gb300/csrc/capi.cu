@@ -55,6 +55,8 @@ struct mdot_handle {
     int* b_order = nullptr;
     unsigned int* b_next = nullptr;
     int b_cap = 0;
+    double* b_uv = nullptr;        // potentials of batched problems that asked for none (finish)
+    size_t b_uv_cap = 0;           // doubles
     // evaluation tags consumed by the stage kernel's flags since they were last cleared (an upper
     // bound, from the evaluation counts); cleared well before the 32-bit tag could wrap
     unsigned long long tags_used = 0;
@@ -71,6 +73,7 @@ struct mdot_handle {
         if (de_ev[1]) cudaEventDestroy(de_ev[1]);
         cudaFree(d_r); cudaFree(d_c); cudaFree(d_u); cudaFree(d_v); cudaFree(d_C);
         cudaFree(b_slots); cudaFree(b_probs); cudaFree(b_results); cudaFree(b_order); cudaFree(b_next);
+        cudaFree(b_uv);
     }
 };
 
@@ -836,6 +839,89 @@ mdot_status batch_core(mdot_handle* h, const std::vector<BatchProblem>& bp, cons
     return MDOT_OK;
 }
 
+// Finish one batched problem whose last stage the batch kernel left above its tolerance (its fp32
+// part stalled and the fp64 polish on its one SM did not get there): the single-problem solver's
+// fp64 stage on every SM of the handle, from the batch's potentials (q.u_out, q.v_out), at the
+// same gamma_f, smoothing and floored tolerance, then rounding (Alg. 3) and the bound as in
+// solve_core.  The result record is updated in place (evaluation counts added).
+mdot_status batch_finish(mdot_handle* h, const BatchProblem& q, const mdot_params& P, BatchResult& br)
+{
+    const int n = q.n;
+    WS ws = h->ws;
+    ws.n = n;
+    ws.r = q.r;
+    ws.c = q.c;
+    CostSpec cs;
+    cs.kind = q.kind;
+    cs.C = q.C;
+    cs.X = q.X;
+    cs.Y = q.Y;
+    cs.scale = q.scale;
+    cs.apply(ws);
+    CKR(select_cost_form(h, ws, P.tensor_cores != 0));
+    CKR(reset_state(h, P.wait_limit_us));
+    CKR(cudaMemcpyAsync(ws.u, q.u_out, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    CKR(cudaMemcpyAsync(ws.v, q.v_out, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    const double gf = br.gamma_f;
+    const double eps_d = br.H_min / std::pow(gf, P.p);      // the batch's last stage: gamma = gamma_f
+    double tol = std::max(eps_d / 2.0, 1e-13 + 1e-15 * gf);
+    if (P.final_tol > 0.0) tol = P.final_tol;
+    tol = std::max(tol, (double)P.fp32_floor);             // the batched form's floor
+    StageArgs a{};
+    a.gamma = gf;
+    a.G64 = gf * kLog2e;
+    a.w = eps_d;                                           // smoothing 0 or 1: the same at gamma_f
+    a.ratio = 0.0;
+    a.c1 = P.ls_c1;
+    a.c2 = P.ls_c2;
+    a.first = 0;
+    a.warm_start = 2;                                      // continue from the given potentials
+    a.ls_max_trials = P.ls_max_trials;
+    a.ls_init = P.ls_init;
+    a.max_iter = P.max_iter;
+    a.Aglob = 0;
+    a.precond = 0;
+    a.tier = TIER_F64;
+    a.tol = tol;
+    a.stall_below = stall_floor(TIER_F64);
+    CKR(launch_projection(0, TIER_F64, ws, a, h->stream));
+    RoundArgs ra{};
+    ra.gamma = gf;
+    ra.G64 = gf * kLog2e;
+    ra.u = ws.u;
+    ra.v = ws.v;
+    ra.r = q.r;
+    ra.c = q.c;
+    ra.ref = ws.lr;
+    ra.Y = h->Y;
+    ra.EC = h->EC;
+    ra.ER = h->ER;
+    ra.G_out = nullptr;
+    ra.out = h->d_out;
+    CKR(launch_round(ws, ra, h->stream));
+    LbArgs la{};
+    la.gamma = gf;
+    la.u = ws.u;
+    la.r = q.r;
+    la.c = q.c;
+    la.gp = h->gp;
+    la.out = h->d_out + 8;
+    CKR(launch_lower_bound(ws, la, h->stream));
+    CKR(cudaMemcpyAsync(q.u_out, ws.u, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    CKR(cudaMemcpyAsync(q.v_out, ws.v, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    CKR(cudaMemcpyAsync(h->h_out, h->d_out, 16 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CKR(cudaMemcpyAsync(h->h_state, ws.st, sizeof(State), cudaMemcpyDeviceToHost, h->stream));
+    CKR(cudaStreamSynchronize(h->stream));
+    const State& S = *h->h_state;
+    br.cost = h->h_out[0];
+    br.lower_bound = h->h_out[8];
+    br.grad_l1 = S.gnorm;
+    br.evals += S.evals;
+    br.iters += S.iters;
+    br.status = (S.status != ST_OK) ? S.status : (S.gnorm <= tol ? (int)ST_OK : (int)ST_CAP);
+    return MDOT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -849,9 +935,41 @@ mdot_status mdot_solve_batch(mdot_handle* h, int32_t nprob, const mdot_problem* 
     if (batch_params(prm, P) != MDOT_OK) return MDOT_ERR_INVALID_ARG;
     std::vector<BatchProblem> bp;
     if (batch_problems(nprob, probs, bp) != MDOT_OK) return MDOT_ERR_INVALID_ARG;
+    // with precision AUTO a problem the batch leaves above its tolerance is finished on every SM
+    // (batch_finish), which starts from its potentials: problems that asked for none get some in
+    // the handle's scratch (problems larger than the handle's max_n cannot be finished)
+    const bool finish = P.precision == MDOT_PREC_AUTO && P.polish_iters > 0;
+    if (finish) {
+        size_t need = 0;
+        for (const BatchProblem& q : bp)
+            if ((!q.u_out || !q.v_out) && q.n <= h->max_n) need += 2 * (size_t)q.n;
+        if (need > h->b_uv_cap) {
+            cudaFree(h->b_uv);
+            h->b_uv = nullptr;
+            h->b_uv_cap = 0;
+            if (cudaMalloc(&h->b_uv, need * sizeof(double)) != cudaSuccess) {
+                snprintf(g_err, sizeof g_err, "batch potential scratch allocation failed");
+                return MDOT_ERR_OOM;
+            }
+            h->b_uv_cap = need;
+        }
+        size_t o = 0;
+        for (BatchProblem& q : bp)
+            if ((!q.u_out || !q.v_out) && q.n <= h->max_n) {
+                q.u_out = h->b_uv + o;
+                q.v_out = h->b_uv + o + q.n;
+                o += 2 * (size_t)q.n;
+            }
+    }
     std::vector<BatchResult> br;
-    const mdot_status st = batch_core(h, bp, P, br, -1, nullptr);
+    mdot_status st = batch_core(h, bp, P, br, -1, nullptr);
     if (st != MDOT_OK) return st;
+    if (finish)
+        for (int k = 0; k < nprob; ++k)
+            if (br[k].status == ST_CAP && bp[k].n <= h->max_n) {
+                st = batch_finish(h, bp[k], P, br[k]);
+                if (st != MDOT_OK) return st;
+            }
     for (int k = 0; k < nprob; ++k) {
         const BatchResult& b = br[k];
         mdot_result& r = results[k];

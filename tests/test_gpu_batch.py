@@ -96,6 +96,25 @@ def test_batch_fp64_polish_reaches_a_tight_tolerance(h):
         assert abs(r.cost - refs[p.n].cost) <= 1e-7, (p.n, r.cost, refs[p.n].cost)
 
 
+def test_batch_finishes_stalled_problems_on_every_sm(h):
+    """A problem the batch kernel leaves above its last-stage tolerance (here: a one-iteration fp64
+    polish on its SM cannot reach 1e-10) is finished by the single-problem solver's fp64 stage on
+    every SM, from the batch's potentials; potentials the caller did not ask for are kept in the
+    handle's scratch for that.  Results against the oracle at the same tolerance."""
+    tight = TIGHT
+    gf = 2.0 ** 12
+    cases = [_grid_problem(24, 4910, gf), _grid_problem(10, 4911, gf, dense=True)]
+    plist = [prob for _, _, prob in cases]
+    plist[1].u_out = None                       # no potentials asked for: the handle's scratch
+    plist[1].v_out = None
+    res = h.solve_batch(plist, M.default_params(**{**TIGHT_PARAMS, "polish_iters": 1}))
+    for (p, d, _), r in zip(cases, res):
+        assert r.status == M.MDOT_OK, M.status_string(r.status)
+        assert r.grad_l1 <= tight, (p.n, r.grad_l1)
+        ref = O.solve(p.C.astype(np.float64), p.r, p.c, gamma_f=gf, final_tol=tight)
+        assert abs(r.cost - ref.cost) <= 1e-7, (p.n, r.cost, ref.cost)
+
+
 def test_batch_fp64_polish_over_two_row_chunks(h):
     """n = 2116 > 2048 rows: the fp64 pass adds the column sums of its two row chunks.  Against the
     single-problem solver (whose fp64 polish the parity tests check against the oracle) at the same
