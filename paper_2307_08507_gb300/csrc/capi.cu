@@ -956,8 +956,9 @@ mdot_status mdot_solve_batch(mdot_handle* h, int32_t nprob, const mdot_problem* 
         size_t o = 0;
         for (BatchProblem& q : bp)
             if ((!q.u_out || !q.v_out) && q.n <= h->max_n) {
-                q.u_out = h->b_uv + o;
-                q.v_out = h->b_uv + o + q.n;
+                // only the missing output is replaced: the caller still receives the one it asked for
+                if (!q.u_out) q.u_out = h->b_uv + o;
+                if (!q.v_out) q.v_out = h->b_uv + o + q.n;
                 o += 2 * (size_t)q.n;
             }
     }
