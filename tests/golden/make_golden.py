@@ -11,6 +11,8 @@ Usage:  python tests/golden/make_golden.py [k] [eps ...]   (defaults: k = 64, ep
             problems, seed 11: the monotone coupling, into tests/golden/line_exact.json)
         python tests/golden/make_golden.py --serve   (oracle costs of the served trace's requests
             with n <= 1024 among its first 100, into tests/golden/serve_oracle.json)
+        python tests/golden/make_golden.py --cloud n seed gamma_f final_tol   (the oracle solve of
+            one App. C point cloud, into tests/golden/cloud_oracle.json)
 Runs the cases in parallel worker processes (spawn) and merges each finished case into
 tests/golden/grid{n}.json (or exact{n}.json) as soon as it completes.
 """
@@ -104,6 +106,20 @@ def serve_case(args):
 SERVE_SEED, SERVE_COUNT = 5000, 200
 
 
+def cloud_case(n, seed, gamma_f, final_tol):
+    """Oracle solve of the point cloud inputs.point_cloud_problem(n, seed) (x ~ N(0, I3),
+    y ~ U[-1, 1]^3, uniform weights) at the given gamma_f and last-stage tolerance."""
+    import numpy as np
+    import oracle as O
+    from paper_2307_08507_gb300 import inputs as I
+    p = I.point_cloud_problem(n, seed)
+    t0 = time.time()
+    res = O.solve(p.C.astype(np.float64), p.r, p.c, gamma_f=gamma_f, final_tol=final_tol)
+    return {"n": n, "seed": seed, "gamma_f": gamma_f, "final_tol": final_tol, "oracle_cost": res.cost,
+            "oracle_status": int(res.status), "oracle_evals": int(res.stats.evals),
+            "oracle_grad_l1": res.stats.grad_l1, "oracle_seconds": time.time() - t0}
+
+
 def _merge(path, record, key):
     old = []
     if os.path.exists(path):
@@ -139,6 +155,12 @@ def main():
             for rec in pool.imap_unordered(serve_case, cases):
                 _merge(path, rec, lambda c: (c["seed"], c["index"]))
                 print(json.dumps(rec), flush=True)
+        return
+    if len(sys.argv) > 1 and sys.argv[1] == "--cloud":
+        rec = cloud_case(int(sys.argv[2]), int(sys.argv[3]), float(sys.argv[4]), float(sys.argv[5]))
+        _merge(os.path.join(HERE, "cloud_oracle.json"), rec,
+               lambda c: (c["n"], c["seed"], c["gamma_f"], c["final_tol"]))
+        print(json.dumps(rec), flush=True)
         return
     if len(sys.argv) > 1 and sys.argv[1] == "--line":
         for n in [int(a) for a in sys.argv[2:]]:
