@@ -744,10 +744,13 @@ def run_ours(args, rank, world):
                       "achieved_ops": ents * ops, "peak_ops": alu_peak, "frac_alu": ents * ops / alu_peak,
                       "ops_per_entry": ops}
 
-    sweep = gap_sweep(h, dev, stream) if (rank == 0 and not args.no_sweep) else None
-    batch = measure_batch(h, dev, stream) if (rank == 0 and not args.no_batch) else None
+    # the single-GPU studies (gap sweep, batched and served forms) run once, at N = 1: with N > 1
+    # ranks the other replicas would wait minutes for rank 0 at the next collective
+    solo = rank == 0 and world == 1
+    sweep = gap_sweep(h, dev, stream) if (solo and not args.no_sweep) else None
+    batch = measure_batch(h, dev, stream) if (solo and not args.no_batch) else None
     serving = (measure_serving_loads(dev, h, args.serve_count, max(1, args.serve_count // 2))
-               if (rank == 0 and args.serve_count > 0) else None)
+               if (solo and args.serve_count > 0) else None)
 
     # end to end through the public C ABI with host buffers (copies inside the timed region)
     Ch = torch.from_numpy(p.C).pin_memory().numpy()
