@@ -380,7 +380,9 @@ typedef struct mdot_batch_tuning {
 mdot_status mdot_tune_batch(mdot_handle* h, int32_t nprob, const mdot_problem* probs, const mdot_params* prm,
                             int32_t sample, mdot_batch_tuning* out);
 
-/* Install a stored tuning table (e.g. from an earlier mdot_tune_batch) in the handle. */
+/* Install a stored tuning table (e.g. from an earlier mdot_tune_batch) in the handle: t (host) is
+ * copied; only t->variant is used.  INVALID_ARG for NULL arguments or a variant outside 0 .. 1 (the
+ * handle's table is then unchanged). */
 mdot_status mdot_set_batch_tuning(mdot_handle* h, const mdot_batch_tuning* t);
 
 /*
