@@ -6,6 +6,8 @@ from the CUDA library.  Each record holds, for one (cost kind, seed, target gap)
   evaluation counts, and the exact OT value (column generation priced over all n^2 arcs).
 Usage:  python tests/golden/make_golden.py [k] [eps ...]   (defaults: k = 64, eps = 1e-6)
         python tests/golden/make_golden.py --exact-only [k [kind]]   (only the exact OT values)
+        python tests/golden/make_golden.py --exact-wide k kind k_init add_per_row   (the same with a
+            wider initial arc set and more arcs added per round)
         python tests/golden/make_golden.py --oracle-only k kind eps   (one oracle solve, no exact value)
         python tests/golden/make_golden.py --line n ...   (exact costs of the points-on-a-line
             problems, seed 11: the monotone coupling, into tests/golden/line_exact.json)
@@ -65,13 +67,14 @@ def one_case(args):
 
 
 def exact_case(args):
-    k, kind, seed = args
+    k, kind, seed = args[:3]
+    k_init, add = (args[3], args[4]) if len(args) > 4 else (4, 8)
     import numpy as np
     from oracle import exact as E
     from paper_2307_08507_gb300 import inputs as I
     p = I.grid_problem(k, seed, kind=kind)
     t0 = time.time()
-    val, f, g, rounds = E.exact_ot_colgen(p.C.astype(np.float64), p.r, p.c, k_init=4)
+    val, f, g, rounds = E.exact_ot_colgen(p.C.astype(np.float64), p.r, p.c, k_init=k_init, add_per_row=add)
     return {"k": k, "n": p.n, "kind": kind, "seed": seed, "exact_ot": val, "exact_rounds": rounds,
             "exact_seconds": time.time() - t0}
 
@@ -144,6 +147,12 @@ def main():
             for rec in pool.imap_unordered(exact_case, cases):
                 _merge(path, rec, lambda c: (c["kind"], c["seed"]))
                 print(json.dumps(rec), flush=True)
+        return
+    if len(sys.argv) > 1 and sys.argv[1] == "--exact-wide":
+        k, kind, k_init, add = int(sys.argv[2]), sys.argv[3], int(sys.argv[4]), int(sys.argv[5])
+        rec = exact_case((k, kind, SEED, k_init, add))
+        _merge(os.path.join(HERE, f"exact{k * k}.json"), rec, lambda c: (c["kind"], c["seed"]))
+        print(json.dumps(rec), flush=True)
         return
     if len(sys.argv) > 1 and sys.argv[1] == "--serve":
         # the first requests of the served trace with n <= 1024 among its first 100
