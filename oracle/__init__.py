@@ -77,10 +77,22 @@ def omp_dual_eval_timer():
     return run, nthreads
 
 
+_use_omp = False
+
+
+def use_openmp(flag: bool = True) -> None:
+    """Make later calls load the OpenMP build (same arithmetic and summation order, so the same
+    results; the dual evaluation runs on every host core).  Call before the first oracle call;
+    used by the golden-value script for long solves."""
+    global _use_omp, _lib
+    if flag != _use_omp:
+        _use_omp, _lib = flag, None
+
+
 def lib():
     global _lib
     if _lib is None:
-        _lib = ct.CDLL(build())
+        _lib = ct.CDLL(build(openmp=_use_omp))
         L = _lib
         L.or_default_params.argtypes = [ct.POINTER(OrParams)]
         L.or_entropy.argtypes = [ct.c_int, _D]

@@ -92,11 +92,17 @@ def _northwest(r, c):
 
 
 def exact_ot_colgen(C: np.ndarray, r: np.ndarray, c: np.ndarray, k_init: int = 8,
-                    tol: float = 1e-11, max_rounds: int = 200, add_per_row: int = 8):
+                    tol: float = 1e-11, max_rounds: int = 200, add_per_row: int = 8,
+                    seed_f: np.ndarray | None = None, seed_g: np.ndarray | None = None,
+                    seed_width: float = 0.0):
     """Exact OT by column generation.  Returns (value, f, g, rounds).
     Candidate arcs start as the k_init cheapest arcs of every row and column plus a north-west
     corner basis (so the restricted LP is feasible); each round adds, per row, the add_per_row
-    most negative reduced-cost arcs until none is below -tol."""
+    most negative reduced-cost arcs until none is below -tol.
+    With approximate dual potentials (seed_f, seed_g) -- e.g. f = u/gamma, g = v/gamma of an
+    entropic solve -- every arc whose reduced cost C_ij - f_i - g_j is at most seed_width joins
+    the first candidate set as well.  The seed only shortens the search: the returned value is
+    still certified by pricing all n^2 arcs against the LP's own duals."""
     C = np.asarray(C, np.float64)
     r = np.asarray(r, np.float64)
     c = np.asarray(c, np.float64)
@@ -109,6 +115,11 @@ def exact_ot_colgen(C: np.ndarray, r: np.ndarray, c: np.ndarray, k_init: int = 8
     for j in range(n):
         cand.update((int(i), j) for i in part_c[:, j])
     cand.update(_northwest(r, c))
+    if seed_f is not None and seed_g is not None:
+        red0 = C - np.asarray(seed_f, np.float64)[:, None] - np.asarray(seed_g, np.float64)[None, :]
+        ii, jj = np.nonzero(red0 <= seed_width)
+        cand.update(zip(ii.tolist(), jj.tolist()))
+        del red0
     for rnd in range(max_rounds):
         arr = np.array(sorted(cand), dtype=np.int64)
         val, f, g, _ = _lp(C[arr[:, 0], arr[:, 1]], arr[:, 0], arr[:, 1], n, r, c)

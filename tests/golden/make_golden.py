@@ -8,6 +8,10 @@ Usage:  python tests/golden/make_golden.py [k] [eps ...]   (defaults: k = 64, ep
         python tests/golden/make_golden.py --exact-only [k [kind]]   (only the exact OT values)
         python tests/golden/make_golden.py --exact-wide k kind k_init add_per_row   (the same with a
             wider initial arc set and more arcs added per round)
+        python tests/golden/make_golden.py --exact-seeded k kind eps width   (the same, its first
+            arc set seeded by an oracle solve at target eps: every arc whose reduced cost against
+            the solve's potentials f = u/gamma_f, g = v/gamma_f is at most width; the oracle's
+            OpenMP build, same arithmetic, on every host core)
         python tests/golden/make_golden.py --oracle-only k kind eps   (one oracle solve, no exact value)
         python tests/golden/make_golden.py --line n ...   (exact costs of the points-on-a-line
             problems, seed 11: the monotone coupling, into tests/golden/line_exact.json)
@@ -77,6 +81,28 @@ def exact_case(args):
     val, f, g, rounds = E.exact_ot_colgen(p.C.astype(np.float64), p.r, p.c, k_init=k_init, add_per_row=add)
     return {"k": k, "n": p.n, "kind": kind, "seed": seed, "exact_ot": val, "exact_rounds": rounds,
             "exact_seconds": time.time() - t0}
+
+
+def exact_seeded_case(k, kind, seed, eps, width):
+    """Exact OT by column generation whose first arc set holds every arc that is within `width`
+    of tight for the potentials of an oracle solve at target gap eps."""
+    import numpy as np
+    import oracle as O
+    from oracle import exact as E
+    from paper_2307_08507_gb300 import inputs as I
+    O.use_openmp(True)
+    p = I.grid_problem(k, seed, kind=kind)
+    C = p.C.astype(np.float64)
+    t0 = time.time()
+    res = O.solve(C, p.r, p.c, eps_target=eps)
+    t_seed = time.time() - t0
+    f, g = res.u / res.gamma_f, res.v / res.gamma_f
+    t0 = time.time()
+    val, fd, gd, rounds = E.exact_ot_colgen(C, p.r, p.c, k_init=4, seed_f=f, seed_g=g,
+                                            seed_width=width)
+    return {"k": k, "n": p.n, "kind": kind, "seed": seed, "exact_ot": val, "exact_rounds": rounds,
+            "exact_seconds": time.time() - t0, "seed_eps": eps, "seed_width": width,
+            "seed_seconds": t_seed}
 
 
 def line_case(n, seed=11):
@@ -151,6 +177,12 @@ def main():
     if len(sys.argv) > 1 and sys.argv[1] == "--exact-wide":
         k, kind, k_init, add = int(sys.argv[2]), sys.argv[3], int(sys.argv[4]), int(sys.argv[5])
         rec = exact_case((k, kind, SEED, k_init, add))
+        _merge(os.path.join(HERE, f"exact{k * k}.json"), rec, lambda c: (c["kind"], c["seed"]))
+        print(json.dumps(rec), flush=True)
+        return
+    if len(sys.argv) > 1 and sys.argv[1] == "--exact-seeded":
+        k, kind, eps, width = int(sys.argv[2]), sys.argv[3], float(sys.argv[4]), float(sys.argv[5])
+        rec = exact_seeded_case(k, kind, SEED, eps, width)
         _merge(os.path.join(HERE, f"exact{k * k}.json"), rec, lambda c: (c["kind"], c["seed"]))
         print(json.dumps(rec), flush=True)
         return

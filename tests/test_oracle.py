@@ -413,6 +413,48 @@ def test_ctransform_bound_is_tight_at_lp_duals():
     assert lb2 <= val + 1e-12
 
 
+@pytest.mark.parametrize("kind", ["l2sq", "l1"])
+def test_seeded_column_generation_matches_full_lp(kind):
+    """Column generation seeded with the nearly tight arcs of an entropic solve's potentials
+    returns the full LP's value: the seed only changes the first arc set, and every round still
+    prices all n^2 arcs.  A seed too narrow to contain any arc changes nothing either."""
+    p = I.grid_problem(10, 33, kind=kind)
+    C = p.C.astype(np.float64)
+    ot = E.exact_ot_lp(C, p.r, p.c)
+    res = O.solve(C, p.r, p.c, eps_target=1e-4)
+    f, g = res.u / res.gamma_f, res.v / res.gamma_f
+    red = C - f[:, None] - g[None, :]
+    width = float(np.quantile(red, 0.05))           # about 5 arcs per row
+    for w in (width, -1.0):
+        val, fd, gd, _ = E.exact_ot_colgen(C, p.r, p.c, k_init=2, seed_f=f, seed_g=g, seed_width=w)
+        assert abs(val - ot) <= 1e-10
+        assert (C - fd[:, None] - gd[None, :]).min() >= -1e-9      # the returned duals are feasible
+
+
+def _golden(name):
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)) as fh:
+        return json.load(fh)["cases"]
+
+
+def test_stored_exact_optima_are_bracketed_by_the_oracle_records():
+    """Weak duality on the stored values: every rounded oracle plan is feasible, so its cost is
+    >= OT, and every c-transform bound is a feasible dual, so it is <= OT.  The exact optima stored
+    for the n = 4096 benchmark instance (column generation) and the n = 256 instances (full LP)
+    must lie inside every such bracket of the same instance."""
+    checked = 0
+    exact = {(c["kind"], c["seed"]): c["exact_ot"] for c in _golden("exact4096.json")
+             if c.get("exact_ot") is not None}
+    for rec in _golden("grid4096.json") + _golden("grid256.json"):
+        ot = rec.get("exact_ot") if rec["n"] == 256 else exact.get((rec["kind"], rec["seed"]))
+        if ot is None:
+            continue
+        assert rec["oracle_lb"] - 1e-12 <= ot <= rec["oracle_cost"] + 1e-12, rec
+        checked += 1
+    assert checked >= 6
+
+
 def test_entropy_and_gamma_f_mapping():
     n = 64
     assert abs(O.entropy(np.full(n, 1.0 / n)) - math.log(n)) < 1e-13
