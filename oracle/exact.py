@@ -50,6 +50,9 @@ def monotone_1d(x: np.ndarray, y: np.ndarray, r: np.ndarray, c: np.ndarray, cost
     return total
 
 
+_LP_DUAL_TOL = 1e-10          # HiGHS primal and dual feasibility tolerances used below
+
+
 def _lp(Cflat, rows, cols, n, r, c):
     m = len(Cflat)
     A = coo_matrix((np.ones(2 * m), (np.concatenate([rows, n + cols]),
@@ -57,7 +60,8 @@ def _lp(Cflat, rows, cols, n, r, c):
                    shape=(2 * n, m)).tocsr()
     b = np.concatenate([r, c])
     res = linprog(Cflat, A_eq=A, b_eq=b, bounds=(0, None), method="highs",
-                  options={"primal_feasibility_tolerance": 1e-10, "dual_feasibility_tolerance": 1e-10})
+                  options={"primal_feasibility_tolerance": _LP_DUAL_TOL,
+                           "dual_feasibility_tolerance": _LP_DUAL_TOL})
     if res.status != 0:
         raise RuntimeError(f"HiGHS failed: {res.message}")
     duals = res.eqlin.marginals
@@ -98,7 +102,8 @@ def exact_ot_colgen(C: np.ndarray, r: np.ndarray, c: np.ndarray, k_init: int = 8
     """Exact OT by column generation.  Returns (value, f, g, rounds).
     Candidate arcs start as the k_init cheapest arcs of every row and column plus a north-west
     corner basis (so the restricted LP is feasible); each round adds, per row, the add_per_row
-    most negative reduced-cost arcs until none is below -tol.
+    most negative reduced-cost arcs outside the set until none outside it is below -tol (the
+    arcs inside it carry the LP's own duals, feasible to the solver's 1e-10 tolerance).
     With approximate dual potentials (seed_f, seed_g) -- e.g. f = u/gamma, g = v/gamma of an
     entropic solve -- every arc whose reduced cost C_ij - f_i - g_j is at most seed_width joins
     the first candidate set as well.  The seed only shortens the search: the returned value is
@@ -124,13 +129,18 @@ def exact_ot_colgen(C: np.ndarray, r: np.ndarray, c: np.ndarray, k_init: int = 8
         arr = np.array(sorted(cand), dtype=np.int64)
         val, f, g, _ = _lp(C[arr[:, 0], arr[:, 1]], arr[:, 0], arr[:, 1], n, r, c)
         red = C - f[:, None] - g[None, :]
+        # the LP's own arcs are dual feasible only to the solver's tolerance (1e-10): on
+        # degenerate problems some price at -1e-10 < red < -tol, and re-adding them changes
+        # nothing, so only arcs outside the set count as pricing out
+        inside = red[arr[:, 0], arr[:, 1]]
+        if inside.min() < -100 * _LP_DUAL_TOL:          # a sanity check of the solver's answer
+            raise RuntimeError(f"LP duals infeasible on the LP's own arcs ({inside.min():.3e})")
+        red[arr[:, 0], arr[:, 1]] = np.inf
         neg = red < -tol
         if not neg.any():
             return float(val), f, g, rnd + 1
-        k = min(add_per_row, n - 1)
-        idx = np.argpartition(red, k, axis=1)[:, :k]
         for i in np.nonzero(neg.any(axis=1))[0]:
-            for j in idx[i]:
-                if red[i, j] < -tol:
-                    cand.add((int(i), int(j)))
+            js = np.nonzero(neg[i])[0]
+            js = js[np.argsort(red[i, js], kind="stable")[:add_per_row]]
+            cand.update((int(i), int(j)) for j in js)
     raise RuntimeError("column generation did not converge")

@@ -9,9 +9,8 @@ against an exact network-simplex optimum (Sec. 5).  Checked here:
   the rounded plan is feasible (cost >= OT), the certificate is an upper bound of the true gap, and
   the true gap is <= the target wherever Prop. 2's gamma_f reaches it (at 1e-6 and 1e-7 for both
   costs; at 1e-4 and 1e-5 only for L1: Prop. 2 holds above some gamma_0, and on the smooth
-  squared-Euclidean problem gamma_f = 2^11.7 and 2^14 lie below it -- bench.py's gap sweep bounds
-  the true gap there by 2.5x and 1.9x the target, with the c-transform bound of a gamma_f = 2^21
-  solve).
+  squared-Euclidean problem gamma_f = 2^11.7 and 2^14 lie below it: there the true gap is 2.5x
+  and 1.8x the target).
 """
 import json
 import os
