@@ -54,3 +54,11 @@ def test_not_converged_summary_counts_and_quartiles():
     assert s["count"] == 2 and s["n_min"] == 500 and s["n_max"] == 700
     assert s["grad_l1_quartiles"][0] == 4e-7 and s["grad_l1_quartiles"][-1] == 1e-6
     assert bench._not_converged_summary(probs, [R(0, 1e-7)] * 4, FakeM) == {"count": 0}
+
+
+def test_benchmark_instance_has_a_stored_exact_optimum():
+    """The headline line reports the true gap of the n = 4096 solve (not only a bound): the exact
+    optimum of the benchmark instance is stored for both costs of the gap sweep."""
+    l2, l1 = bench.exact_value("l2sq"), bench.exact_value("l1")
+    assert l2 is not None and l1 is not None
+    assert 0.0 < l2 < 1.0 and 0.0 < l1 < 1.0          # costs normalised to max C = 1
