@@ -12,6 +12,9 @@ Usage:  python tests/golden/make_golden.py [k] [eps ...]   (defaults: k = 64, ep
             arc set seeded by an oracle solve at target eps: every arc whose reduced cost against
             the solve's potentials f = u/gamma_f, g = v/gamma_f is at most width; the oracle's
             OpenMP build, same arithmetic, on every host core)
+        python tests/golden/make_golden.py --seeds k kind eps width seed ...   (for more seeds of the
+            benchmark instance: the oracle solve at target eps into grid{n}.json, and the exact OT
+            value seeded by that solve's nearly tight arcs into both files)
         python tests/golden/make_golden.py --oracle-only k kind eps   (one oracle solve, no exact value)
         python tests/golden/make_golden.py --line n ...   (exact costs of the points-on-a-line
             problems, seed 11: the monotone coupling, into tests/golden/line_exact.json)
@@ -105,6 +108,40 @@ def exact_seeded_case(k, kind, seed, eps, width):
             "seed_seconds": t_seed}
 
 
+def seeds_case(k, kind, seed, eps, width):
+    """One more seed of the benchmark instance: the oracle solve at target eps (OpenMP build) and
+    the exact OT value by column generation seeded by that solve's potentials."""
+    import numpy as np
+    import oracle as O
+    from oracle import exact as E
+    from paper_2307_08507_gb300 import inputs as I
+    O.use_openmp(True)
+    p = I.grid_problem(k, seed, kind=kind)
+    C = p.C.astype(np.float64)
+    H = min(O.entropy(p.r), O.entropy(p.c))
+    t0 = time.time()
+    res = O.solve(C, p.r, p.c, eps_target=eps)
+    t_solve = time.time() - t0
+    f, g = res.u / res.gamma_f, res.v / res.gamma_f
+    t0 = time.time()
+    val, _, _, rounds = E.exact_ot_colgen(C, p.r, p.c, k_init=4, seed_f=f, seed_g=g, seed_width=width)
+    t_exact = time.time() - t0
+    grid = {
+        "k": k, "n": p.n, "kind": kind, "seed": seed, "eps_target": eps, "H_min": H,
+        "gamma_f": res.gamma_f, "oracle_cost": res.cost, "oracle_lb": res.lb,
+        "oracle_evals": int(res.stats.evals), "oracle_iters": int(res.stats.iters),
+        "oracle_ls_trials": int(res.stats.ls_trials), "oracle_stages": int(res.stats.stages),
+        "oracle_status": int(res.status), "oracle_grad_l1": res.stats.grad_l1,
+        "oracle_seconds": t_solve, "oracle_threads": "OpenMP build, every host core",
+        "exact_ot": val, "exact_rounds": rounds, "exact_seconds": t_exact,
+        "true_gap": res.cost - val,
+        "f_g_span": [float(f.min()), float(f.max()), float(g.min()), float(g.max())],
+    }
+    exact = {"k": k, "n": p.n, "kind": kind, "seed": seed, "exact_ot": val, "exact_rounds": rounds,
+             "exact_seconds": t_exact, "seed_eps": eps, "seed_width": width, "seed_seconds": t_solve}
+    return grid, exact
+
+
 def line_case(n, seed=11):
     import numpy as np
     from oracle import exact as E
@@ -185,6 +222,15 @@ def main():
         rec = exact_seeded_case(k, kind, SEED, eps, width)
         _merge(os.path.join(HERE, f"exact{k * k}.json"), rec, lambda c: (c["kind"], c["seed"]))
         print(json.dumps(rec), flush=True)
+        return
+    if len(sys.argv) > 1 and sys.argv[1] == "--seeds":
+        k, kind, eps, width = int(sys.argv[2]), sys.argv[3], float(sys.argv[4]), float(sys.argv[5])
+        for seed in [int(a) for a in sys.argv[6:]]:
+            grid, exact = seeds_case(k, kind, seed, eps, width)
+            _merge(os.path.join(HERE, f"grid{k * k}.json"), grid,
+                   lambda c: (c["kind"], c["seed"], c["eps_target"]))
+            _merge(os.path.join(HERE, f"exact{k * k}.json"), exact, lambda c: (c["kind"], c["seed"]))
+            print(json.dumps(grid), flush=True)
         return
     if len(sys.argv) > 1 and sys.argv[1] == "--serve":
         # the first requests of the served trace with n <= 1024 among its first 100
